@@ -1,0 +1,252 @@
+"""FP64 CPU oracle of the high-order lattice Boltzmann model for the Cahn-Hilliard equation.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline leg use this
+package to check and time the CUDA library; the product path never imports it.  The arithmetic lives
+in ``lbch_oracle.c`` (plain C, double precision, no fast-math, no FMA contraction); this module only
+compiles it with gcc and marshals numpy arrays through ctypes.
+
+Parity status of each oracle function (what pins it is in ``tests/test_oracle_pins.py``):
+  geq, source, dfdphi, grad, lap, div, mu, force, init, step, observe -- pinned
+  (moment identities, exact stencil symbols, polynomial exactness, a linear-stability amplification
+  matrix built independently, conservation, stationarity, special values of K).
+  The long-time benchmark behaviour (paper Sec. III) is pinned only softly (printed max/min of phi);
+  the paper's error curves are figures that are not available, so those are "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbch_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liblbch_oracle.so")
+
+VEL_UNIFORM, VEL_ROTATION, VEL_VORTEX, VEL_SHEAR, VEL_REV_SHEAR, VEL_DEFORM = range(6)
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("walls", ctypes.c_int), ("model", ctypes.c_int),
+        ("vel", ctypes.c_int), ("nvort", ctypes.c_int),
+        ("phiA", ctypes.c_double), ("phiB", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("W", ctypes.c_double),
+        ("M", ctypes.c_double), ("Pe", ctypes.c_double), ("Ustar", ctypes.c_double),
+        ("tau", ctypes.c_double), ("rhoA", ctypes.c_double), ("rhoB", ctypes.c_double),
+        ("U0", ctypes.c_double), ("ux0", ctypes.c_double), ("uy0", ctypes.c_double),
+        ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("half", ctypes.c_double),
+        ("Tper", ctypes.c_double), ("shear", ctypes.c_double),
+    ]
+
+
+class _Consts(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("beta", "kappa", "M", "eta", "a", "b", "K")]
+
+
+@dataclass
+class Consts:
+    beta: float
+    kappa: float
+    M: float
+    eta: float
+    a: float
+    b: float
+    K: float
+
+
+def build(force: bool = False, openmp: bool = True) -> str:
+    """Compile the oracle into a shared library (gcc, -O2, strict IEEE double)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99"]
+    if openmp:
+        cmd.append("-fopenmp")
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd += [_SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        dp = P(ctypes.c_double)
+        _lib.ora_derive.argtypes = [P(_Params), P(_Consts)]
+        _lib.ora_velocity.argtypes = [P(_Params), ctypes.c_double, ctypes.c_double, ctypes.c_long, dp, dp]
+        _lib.ora_geq.argtypes = [ctypes.c_double] * 5 + [dp]
+        _lib.ora_source.argtypes = [ctypes.c_double, ctypes.c_double, dp]
+        _lib.ora_dfdphi.argtypes = [ctypes.c_double] * 4
+        _lib.ora_dfdphi.restype = ctypes.c_double
+        _lib.ora_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        _lib.ora_lap.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        _lib.ora_div.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        _lib.ora_phi.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        _lib.ora_mu.argtypes = [P(_Params), P(_Consts), dp, dp]
+        _lib.ora_velocity_field.argtypes = [P(_Params), ctypes.c_long, dp, dp]
+        _lib.ora_force.argtypes = [P(_Params), P(_Consts), dp, dp, dp, dp, dp, dp]
+        _lib.ora_init.argtypes = [P(_Params), dp, dp]
+        _lib.ora_step.argtypes = [P(_Params), dp, dp, ctypes.c_long]
+        _lib.ora_run.argtypes = [P(_Params), dp, ctypes.c_long, ctypes.c_long]
+        _lib.ora_run.restype = ctypes.c_int
+        _lib.ora_observe.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def params(cfg) -> _Params:
+    """Marshal a configuration (any object or dict with the parameter names) into the C struct."""
+    p = _Params()
+    get = cfg.get if isinstance(cfg, dict) else (lambda k, d=None: getattr(cfg, k, d))
+    for name, ctype in _Params._fields_:
+        v = get(name, None)
+        if v is None:
+            v = {"nvort": 4, "model": 2, "phiA": 1.0, "phiB": 0.0, "rhoA": 1.0, "rhoB": 0.5,
+                 "tau": 1.0}.get(name, 0)
+        setattr(p, name, int(v) if ctype is ctypes.c_int else float(v))
+    return p
+
+
+def derive(cfg) -> Consts:
+    p, c = params(cfg), _Consts()
+    lib().ora_derive(ctypes.byref(p), ctypes.byref(c))
+    return Consts(*[getattr(c, f.name) for f in fields(Consts)])
+
+
+def _consts(cfg):
+    p, c = params(cfg), _Consts()
+    lib().ora_derive(ctypes.byref(p), ctypes.byref(c))
+    return p, c
+
+
+def velocity(cfg, x: float, y: float, n: int):
+    p = params(cfg)
+    ux, uy = ctypes.c_double(), ctypes.c_double()
+    lib().ora_velocity(ctypes.byref(p), x, y, n, ctypes.byref(ux), ctypes.byref(uy))
+    return ux.value, uy.value
+
+
+def velocity_field(cfg, n: int):
+    p = params(cfg)
+    ux = np.zeros((p.ny, p.nx)); uy = np.zeros((p.ny, p.nx))
+    lib().ora_velocity_field(ctypes.byref(p), n, _ptr(ux), _ptr(uy))
+    return ux, uy
+
+
+def geq(phi, mu, ux, uy, eta) -> np.ndarray:
+    out = np.zeros(9)
+    lib().ora_geq(phi, mu, ux, uy, eta, _ptr(out))
+    return out
+
+
+def source(Fx, Fy) -> np.ndarray:
+    out = np.zeros(9)
+    lib().ora_source(Fx, Fy, _ptr(out))
+    return out
+
+
+def dfdphi(phi, beta, phiA, phiB) -> float:
+    return lib().ora_dfdphi(phi, beta, phiA, phiB)
+
+
+def grad(psi, walls: int = 0):
+    psi = _f64(psi); ny, nx = psi.shape
+    gx = np.zeros_like(psi); gy = np.zeros_like(psi)
+    lib().ora_grad(nx, ny, walls, _ptr(psi), _ptr(gx), _ptr(gy))
+    return gx, gy
+
+
+def lap(psi, walls: int = 0):
+    psi = _f64(psi); ny, nx = psi.shape
+    out = np.zeros_like(psi)
+    lib().ora_lap(nx, ny, walls, _ptr(psi), _ptr(out))
+    return out
+
+
+def div(vx, vy, walls: int = 0):
+    vx, vy = _f64(vx), _f64(vy); ny, nx = vx.shape
+    out = np.zeros_like(vx)
+    lib().ora_div(nx, ny, walls, _ptr(vx), _ptr(vy), _ptr(out))
+    return out
+
+
+def phi_of(g) -> np.ndarray:
+    g = _f64(g); _, ny, nx = g.shape
+    out = np.zeros((ny, nx))
+    lib().ora_phi(nx, ny, _ptr(g), _ptr(out))
+    return out
+
+
+def mu(cfg, phi):
+    p, c = _consts(cfg)
+    phi = _f64(phi); out = np.zeros_like(phi)
+    lib().ora_mu(ctypes.byref(p), ctypes.byref(c), _ptr(phi), _ptr(out))
+    return out
+
+
+def force(cfg, phi, mu_, ux, uy):
+    p, c = _consts(cfg)
+    phi, mu_, ux, uy = map(_f64, (phi, mu_, ux, uy))
+    Fx = np.zeros_like(phi); Fy = np.zeros_like(phi)
+    lib().ora_force(ctypes.byref(p), ctypes.byref(c), _ptr(phi), _ptr(mu_), _ptr(ux), _ptr(uy),
+                    _ptr(Fx), _ptr(Fy))
+    return Fx, Fy
+
+
+def init(cfg, phi0) -> np.ndarray:
+    p = params(cfg)
+    phi0 = _f64(phi0)
+    assert phi0.shape == (p.ny, p.nx)
+    g = np.zeros((9, p.ny, p.nx))
+    lib().ora_init(ctypes.byref(p), _ptr(phi0), _ptr(g))
+    return g
+
+
+def step(cfg, g, n: int) -> np.ndarray:
+    p = params(cfg)
+    g = _f64(g); out = np.zeros_like(g)
+    lib().ora_step(ctypes.byref(p), _ptr(g), _ptr(out), n)
+    return out
+
+
+def run(cfg, g, nsteps: int, n0: int = 0) -> np.ndarray:
+    """Advance a copy of g by nsteps steps starting at step index n0."""
+    p = params(cfg)
+    g = _f64(g).copy()
+    rc = lib().ora_run(ctypes.byref(p), _ptr(g), n0, nsteps)
+    if rc != 0:
+        raise MemoryError("oracle run failed to allocate")
+    return g
+
+
+def observe(phi, phi0) -> dict:
+    phi, phi0 = _f64(phi), _f64(phi0)
+    ny, nx = phi.shape
+    out = np.zeros(6)
+    lib().ora_observe(nx, ny, _ptr(phi), _ptr(phi0), _ptr(out))
+    return {"mass": out[0], "err_l2": out[1], "max": out[2], "min": out[3],
+            "err_num": out[4], "err_den": out[5]}
+
+
+def simulate(cfg, phi0, nsteps: int, n0: int = 0):
+    """phi after nsteps steps from the initial field phi0 (initial g from the equilibria)."""
+    g = run(cfg, init(cfg, phi0), nsteps, n0)
+    return phi_of(g), g

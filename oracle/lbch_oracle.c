@@ -1,0 +1,412 @@
+/*
+ * lbch_oracle.c -- plain, slow FP64 CPU oracle of the D2Q9 single-relaxation-time lattice Boltzmann
+ * model for the Cahn-Hilliard equation with the high-order source term of Zhang, Guo & Liang,
+ * "A high-order lattice Boltzmann model for the Cahn-Hilliard equation" (arXiv:1805.00007).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker the CUDA path is compared against.  It shares no
+ * code, header, table or helper with the product library; only tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It is written for a reader who checks it against the
+ * paper by eye: one loop per field, in the order the paper introduces the quantities, double precision
+ * throughout, no blocking, no fusion.  Build with -O2 -fno-fast-math -ffp-contract=off.  The optional
+ * OpenMP pragmas parallelise loops whose iterations are independent, so results do not depend on the
+ * thread count.
+ *
+ * Lattice units: dx = dt = c = 1, so c_s^2 = 1/3 and 3 c_s^2 = 1.  Node (i, j) sits at x = i, y = j and is
+ * stored at index j*nx + i.  Distributions are stored structure-of-arrays: g[q*N + node], N = nx*ny.
+ *
+ * Where the paper is silent the oracle takes these readings (each is restated where it is used):
+ *   R1  no pressure field for prescribed velocities: grad p = 0, so F1 = -(phi^2/rho) grad mu   (Eq. t0-phiu)
+ *   R2  initial distributions are the equilibria of phi0, mu0 = mu(phi0), u(t=0)                 (Eq. geq)
+ *   R3  Model II uses the diffusive-scale force of Eq. mark3 with the general K(tau), for any tau
+ *   R4  the isotropic central stencils are the D2Q9-weighted forms (Sec. III cites them only)
+ *   R5  grad(div(phi u)) is the gradient stencil applied to the divergence stencil (5x5 footprint)
+ *   R6  the step n -> n+1 uses u(x, t = n)
+ *   R7  walls (when enabled) sit half-way below row 0 and above row ny-1: halfway bounce-back of the
+ *       distributions with the moving-wall term 2 w_i phi (c_i . u_w)/c_s^2, and every stencil operand
+ *       (phi, mu, phi*u, div(phi u)) takes at a ghost row the value of that operand at the mirror row
+ *   R8  the order of a step is phi -> mu -> grad mu -> u -> F -> g_eq, S -> collide -> stream
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 9
+
+/* D2Q9 velocity set (Sec. II.B): c0=(0,0), c1=-c3=(1,0), c2=-c4=(0,1), c5=-c7=(1,1), c6=-c8=(-1,1). */
+static const int CX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* Weights w0 = 4/9, w1..4 = 1/9, w5..8 = 1/36 (Sec. II.B, after Eq. geq). */
+static const double WQ[Q] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+/* Index of the opposite direction -c_i. */
+static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const double CS2 = 1.0 / 3.0;
+
+enum { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_SHEAR = 3, VEL_REV_SHEAR = 4, VEL_DEFORM = 5 };
+
+/* Problem parameters, in the paper's notation.  Plain numbers; the derived constants are computed here. */
+typedef struct {
+    int nx, ny;
+    int walls;          /* 0: periodic in x and y; 1: periodic in x, walls at y = -1/2 and y = ny - 1/2 */
+    int model;          /* 1: Model I (F = F1); 2: Model II (F = F1 + F2 of Eq. mark3) */
+    int vel;            /* velocity field, VEL_* */
+    int nvort;          /* vortex count n of the deformation field (Eq. deformation) */
+    double phiA, phiB;  /* bulk values of the order parameter */
+    double sigma, W;    /* surface tension and interface width (Eq. betakappa) */
+    double M;           /* mobility; when <= 0 it is derived from Pe (Sec. III.A) */
+    double Pe, Ustar;   /* Peclet number and characteristic velocity, used when M <= 0 */
+    double tau;         /* tau_g */
+    double rhoA, rhoB;  /* bulk densities (Eq. rho) */
+    double U0, ux0, uy0;/* velocity amplitude; uniform velocity components */
+    double xc, yc, half;/* rotation centre and half-length of the rotation field */
+    double Tper;        /* period / reversal time of the time-dependent fields, in steps */
+    double shear;       /* shear rate of the wall-driven shear flow */
+} ora_params;
+
+/* Constants the model derives from the parameters. */
+typedef struct {
+    double beta, kappa;  /* Eq. betakappa */
+    double M, eta;       /* mobility M = c_s^2 eta (tau - 1/2), after Eq. phit3 */
+    double a, b;         /* rho = a phi + b, Eq. rho */
+    double K;            /* K = (tau - 1/6 - tau^2)/(tau - 1/2), after Eq. F2-1 */
+} ora_consts;
+
+/* ---------------------------------------------------------------- parameters */
+
+void ora_derive(const ora_params* p, ora_consts* c)
+{
+    double dphi = fabs(p->phiA - p->phiB);
+    /* Eq. betakappa */
+    c->beta = 12.0 * p->sigma / (p->W * dphi * dphi * dphi * dphi);
+    c->kappa = 3.0 * p->sigma * p->W / (2.0 * dphi * dphi);
+    /* Pe = U* W / (M beta (phiA - phiB)^2), Sec. III.A, solved for M when M is not given */
+    if (p->M > 0.0)
+        c->M = p->M;
+    else
+        c->M = p->Ustar * p->W / (p->Pe * c->beta * (p->phiA - p->phiB) * (p->phiA - p->phiB));
+    /* M = c_s^2 eta (tau_g - 0.5), stated after Eq. phit3 */
+    c->eta = c->M / (CS2 * (p->tau - 0.5));
+    /* Eq. rho */
+    c->a = (p->rhoA - p->rhoB) / (p->phiA - p->phiB);
+    c->b = (p->rhoB * p->phiA - p->phiB * p->rhoA) / (p->phiA - p->phiB);
+    /* K of Eq. F2-1 */
+    c->K = (p->tau - 1.0 / 6.0 - p->tau * p->tau) / (p->tau - 0.5);
+}
+
+/* ---------------------------------------------------------------- prescribed velocity */
+
+/* u(x, y, t) of the benchmark flows, evaluated at a point (x, y) and time step n (reading R6). */
+void ora_velocity(const ora_params* p, double x, double y, long n, double* ux, double* uy)
+{
+    const double pi = 3.14159265358979323846;
+    double L = (double)p->nx;
+    switch (p->vel) {
+    case VEL_UNIFORM: /* diagonal translation, u = (U0, U0) in Sec. III.A; here any constant vector */
+        *ux = p->ux0;
+        *uy = p->uy0;
+        break;
+    case VEL_ROTATION: /* solid-body rotation of Zalesak's disk (Sec. III.B) about (xc, yc) */
+        *ux = -p->U0 * pi * (y - p->yc) / p->half;
+        *uy = p->U0 * pi * (x - p->xc) / p->half;
+        break;
+    case VEL_VORTEX: { /* single vortex, reversed by cos(pi t / T) */
+        double Ly = (double)p->ny;
+        double sx = sin(pi * x / L), sy = sin(pi * y / Ly);
+        double ct = cos(pi * (double)n / p->Tper);
+        *ux = -p->U0 * sx * sx * sin(2.0 * pi * y / Ly) * ct;
+        *uy = p->U0 * sin(2.0 * pi * x / L) * sy * sy * ct;
+        break;
+    }
+    case VEL_SHEAR: /* wall-driven shear, zero at mid-channel; walls at y = -1/2 and ny - 1/2 */
+        *ux = p->shear * (y - 0.5 * (double)(p->ny - 1));
+        *uy = 0.0;
+        break;
+    case VEL_REV_SHEAR: { /* Eq. shear; the field changes sign at t = T (Sec. III.C) */
+        double s = ((double)n < p->Tper) ? 1.0 : -1.0;
+        *ux = -s * p->U0 * pi * cos(pi * (x / L - 0.5)) * sin(pi * (y / L - 0.5));
+        *uy = s * p->U0 * pi * sin(pi * (x / L - 0.5)) * cos(pi * (y / L - 0.5));
+        break;
+    }
+    case VEL_DEFORM: { /* Eq. deformation with n vortices and period T0 = Tper */
+        double k = (double)p->nvort * pi;
+        double ct = cos(pi * (double)n / p->Tper);
+        *ux = -p->U0 * sin(k * (x / L + 0.5)) * sin(k * (y / L + 0.5)) * ct;
+        *uy = -p->U0 * cos(k * (x / L + 0.5)) * cos(k * (y / L + 0.5)) * ct;
+        break;
+    }
+    default:
+        *ux = 0.0;
+        *uy = 0.0;
+    }
+}
+
+/* ---------------------------------------------------------------- single-node pieces */
+
+/* Equilibrium distribution, Eq. geq. */
+void ora_geq(double phi, double mu, double ux, double uy, double eta, double* geq)
+{
+    double uu = ux * ux + uy * uy;
+    geq[0] = phi + (WQ[0] - 1.0) * eta * mu - WQ[0] * phi * uu / (2.0 * CS2);
+    for (int i = 1; i < Q; i++) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        geq[i] = WQ[i] * eta * mu
+               + WQ[i] * phi * (cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+    }
+}
+
+/* Source distribution S_i = w_i c_i . F / c_s^2, Eq. liangFi. */
+void ora_source(double Fx, double Fy, double* S)
+{
+    for (int i = 0; i < Q; i++)
+        S[i] = WQ[i] * (CX[i] * Fx + CY[i] * Fy) / CS2;
+}
+
+/* Bulk part of the chemical potential, d f / d phi for f = beta (phi - phiA)^2 (phi - phiB)^2 (Eq. bulk). */
+double ora_dfdphi(double phi, double beta, double phiA, double phiB)
+{
+    return 2.0 * beta * (phi - phiA) * (phi - phiB) * (phi - phiB)
+         + 2.0 * beta * (phi - phiA) * (phi - phiA) * (phi - phiB);
+}
+
+/* ---------------------------------------------------------------- stencils */
+
+/* Neighbour index of node (i, j) in direction (dx, dy): periodic in x; periodic or mirrored in y (R7). */
+static long nbr(int nx, int ny, int walls, int i, int j, int dx, int dy)
+{
+    int ii = i + dx, jj = j + dy;
+    ii = ((ii % nx) + nx) % nx;
+    if (walls) {
+        if (jj < 0) jj = -1 - jj;
+        if (jj >= ny) jj = 2 * ny - 1 - jj;
+    } else {
+        jj = ((jj % ny) + ny) % ny;
+    }
+    return (long)jj * nx + ii;
+}
+
+/* Isotropic central gradient (R4): grad psi(x) = sum_k w_k c_k psi(x + c_k) / c_s^2. */
+void ora_grad(int nx, int ny, int walls, const double* psi, double* gx, double* gy)
+{
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            double sx = 0.0, sy = 0.0;
+            for (int k = 1; k < Q; k++) {
+                double v = psi[nbr(nx, ny, walls, i, j, CX[k], CY[k])];
+                sx += WQ[k] * CX[k] * v;
+                sy += WQ[k] * CY[k] * v;
+            }
+            gx[(long)j * nx + i] = sx / CS2;
+            gy[(long)j * nx + i] = sy / CS2;
+        }
+}
+
+/* Isotropic central Laplacian (R4): lap psi(x) = sum_k 2 w_k (psi(x + c_k) - psi(x)) / c_s^2. */
+void ora_lap(int nx, int ny, int walls, const double* psi, double* lap)
+{
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            double c = psi[(long)j * nx + i];
+            double s = 0.0;
+            for (int k = 1; k < Q; k++)
+                s += 2.0 * WQ[k] * (psi[nbr(nx, ny, walls, i, j, CX[k], CY[k])] - c);
+            lap[(long)j * nx + i] = s / CS2;
+        }
+}
+
+/* Divergence of a vector field with the isotropic gradient stencil. */
+void ora_div(int nx, int ny, int walls, const double* vx, const double* vy, double* div)
+{
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            double s = 0.0;
+            for (int k = 1; k < Q; k++) {
+                long m = nbr(nx, ny, walls, i, j, CX[k], CY[k]);
+                s += WQ[k] * (CX[k] * vx[m] + CY[k] * vy[m]);
+            }
+            div[(long)j * nx + i] = s / CS2;
+        }
+}
+
+/* ---------------------------------------------------------------- macroscopic fields */
+
+/* phi = sum_i g_i, Eq. macroscopicg. */
+void ora_phi(int nx, int ny, const double* g, double* phi)
+{
+    long N = (long)nx * ny;
+    for (long n = 0; n < N; n++) {
+        double s = 0.0;
+        for (int i = 0; i < Q; i++) s += g[i * N + n];
+        phi[n] = s;
+    }
+}
+
+/* Chemical potential mu = df/dphi - kappa lap phi, Eq. mu. */
+void ora_mu(const ora_params* p, const ora_consts* c, const double* phi, double* mu)
+{
+    long N = (long)p->nx * p->ny;
+    double* lap = (double*)malloc(sizeof(double) * N);
+    ora_lap(p->nx, p->ny, p->walls, phi, lap);
+    for (long n = 0; n < N; n++)
+        mu[n] = ora_dfdphi(phi[n], c->beta, p->phiA, p->phiB) - c->kappa * lap[n];
+    free(lap);
+}
+
+/* Velocity field at every node at step n. */
+void ora_velocity_field(const ora_params* p, long n, double* ux, double* uy)
+{
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++)
+            ora_velocity(p, (double)i, (double)j, n, &ux[(long)j * p->nx + i], &uy[(long)j * p->nx + i]);
+}
+
+/* The force F of Eq. reFi at every node, as the paper runs it (Remark III):
+ *   F1 = (phi/rho)(Fs - grad p), Fs = -phi grad mu, grad p = 0 for prescribed flows (R1)  -- Eq. t0-phiu
+ *   F2 = 3 c_s^2 K grad(div(phi u))                                                   -- Eq. mark3 (R3, R5)
+ * Model I keeps F1 only; Model II adds F2. */
+void ora_force(const ora_params* p, const ora_consts* c, const double* phi, const double* mu,
+               const double* ux, const double* uy, double* Fx, double* Fy)
+{
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double* gmx = (double*)malloc(sizeof(double) * N);
+    double* gmy = (double*)malloc(sizeof(double) * N);
+    ora_grad(nx, ny, p->walls, mu, gmx, gmy);
+    for (long n = 0; n < N; n++) {
+        double rho = c->a * phi[n] + c->b;           /* Eq. rho */
+        double Fsx = -phi[n] * gmx[n], Fsy = -phi[n] * gmy[n];  /* surface tension force after Eq. NS */
+        Fx[n] = phi[n] / rho * Fsx;
+        Fy[n] = phi[n] / rho * Fsy;
+    }
+    if (p->model == 2) {
+        double* jx = (double*)malloc(sizeof(double) * N);
+        double* jy = (double*)malloc(sizeof(double) * N);
+        double* D = (double*)malloc(sizeof(double) * N);
+        double* gDx = (double*)malloc(sizeof(double) * N);
+        double* gDy = (double*)malloc(sizeof(double) * N);
+        for (long n = 0; n < N; n++) {
+            jx[n] = phi[n] * ux[n];
+            jy[n] = phi[n] * uy[n];
+        }
+        ora_div(nx, ny, p->walls, jx, jy, D);
+        ora_grad(nx, ny, p->walls, D, gDx, gDy);
+        for (long n = 0; n < N; n++) {
+            Fx[n] += 3.0 * CS2 * c->K * gDx[n];
+            Fy[n] += 3.0 * CS2 * c->K * gDy[n];
+        }
+        free(jx); free(jy); free(D); free(gDx); free(gDy);
+    }
+    free(gmx);
+    free(gmy);
+}
+
+/* ---------------------------------------------------------------- initial state and one step */
+
+/* Initial distributions g_i(x, 0) = g_i^eq(phi0, mu0, u(x, 0)) (reading R2). */
+void ora_init(const ora_params* p, const double* phi0, double* g)
+{
+    ora_consts c;
+    ora_derive(p, &c);
+    long N = (long)p->nx * p->ny;
+    double* mu = (double*)malloc(sizeof(double) * N);
+    ora_mu(p, &c, phi0, mu);
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) {
+            long n = (long)j * p->nx + i;
+            double ux, uy, geq[Q];
+            ora_velocity(p, (double)i, (double)j, 0, &ux, &uy);
+            ora_geq(phi0[n], mu[n], ux, uy, c.eta, geq);
+            for (int q = 0; q < Q; q++) g[q * N + n] = geq[q];
+        }
+    free(mu);
+}
+
+/* One step n -> n+1 of Eq. LB: g_i(x + c_i, t + 1) = g_i - (g_i - g_i^eq)/tau + (1 - 1/(2 tau)) S_i.
+ * gin and gout are distinct arrays of 9*N values. */
+void ora_step(const ora_params* p, const double* gin, double* gout, long n)
+{
+    ora_consts c;
+    ora_derive(p, &c);
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double* phi = (double*)malloc(sizeof(double) * N);
+    double* mu = (double*)malloc(sizeof(double) * N);
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* Fx = (double*)malloc(sizeof(double) * N);
+    double* Fy = (double*)malloc(sizeof(double) * N);
+
+    ora_phi(nx, ny, gin, phi);                 /* Eq. macroscopicg */
+    ora_mu(p, &c, phi, mu);                    /* Eq. mu */
+    ora_velocity_field(p, n, ux, uy);          /* prescribed u at t = n (R6) */
+    ora_force(p, &c, phi, mu, ux, uy, Fx, Fy); /* Eqs. t0-phiu, mark3 */
+
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long x = (long)j * nx + i;
+            double geq[Q], S[Q];
+            ora_geq(phi[x], mu[x], ux[x], uy[x], c.eta, geq);  /* Eq. geq */
+            ora_source(Fx[x], Fy[x], S);                       /* Eq. liangFi */
+            for (int q = 0; q < Q; q++) {
+                /* collision, Eq. LB right-hand side */
+                double post = gin[q * N + x] - (gin[q * N + x] - geq[q]) / p->tau
+                            + (1.0 - 1.0 / (2.0 * p->tau)) * S[q];
+                /* streaming to x + c_q */
+                int ii = ((i + CX[q]) % nx + nx) % nx;
+                int jj = j + CY[q];
+                if (!p->walls) {
+                    jj = ((jj % ny) + ny) % ny;
+                } else if (jj < 0 || jj >= ny) {
+                    /* halfway bounce-back from the wall with its velocity u_w (R7): the population that
+                     * leaves along c_q returns along c_opp with 2 w_opp phi (c_opp . u_w)/c_s^2 added */
+                    double uwx, uwy;
+                    ora_velocity(p, (double)i, jj < 0 ? -0.5 : (double)ny - 0.5, n, &uwx, &uwy);
+                    int o = OPP[q];
+                    gout[o * N + x] = post + 2.0 * WQ[o] * phi[x] * (CX[o] * uwx + CY[o] * uwy) / CS2;
+                    continue;
+                }
+                gout[q * N + (long)jj * nx + ii] = post;
+            }
+        }
+    free(phi); free(mu); free(ux); free(uy); free(Fx); free(Fy);
+}
+
+/* nsteps steps starting at step index n0; g holds the state on entry and on return. */
+int ora_run(const ora_params* p, double* g, long n0, long nsteps)
+{
+    long N = (long)p->nx * p->ny;
+    double* tmp = (double*)malloc(sizeof(double) * Q * N);
+    if (!tmp) return -1;
+    for (long s = 0; s < nsteps; s++) {
+        ora_step(p, g, tmp, n0 + s);
+        memcpy(g, tmp, sizeof(double) * Q * N);
+    }
+    free(tmp);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- observables */
+
+/* out[0] = sum phi (mass), out[1] = ||E_phi||_2 against phi0 (Eq. err), out[2] = max phi, out[3] = min phi,
+ * out[4] = sum (phi - phi0)^2, out[5] = sum phi0^2. */
+void ora_observe(int nx, int ny, const double* phi, const double* phi0, double* out)
+{
+    long N = (long)nx * ny;
+    double m = 0.0, e = 0.0, r = 0.0, mx = phi[0], mn = phi[0];
+    for (long n = 0; n < N; n++) {
+        m += phi[n];
+        e += (phi[n] - phi0[n]) * (phi[n] - phi0[n]);
+        r += phi0[n] * phi0[n];
+        if (phi[n] > mx) mx = phi[n];
+        if (phi[n] < mn) mn = phi[n];
+    }
+    out[0] = m;
+    out[1] = sqrt(e / r);
+    out[2] = mx;
+    out[3] = mn;
+    out[4] = e;
+    out[5] = r;
+}

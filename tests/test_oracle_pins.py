@@ -1,0 +1,343 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: moment identities of Eq. feqmoment and
+Eq. conservation, the Fourier symbols of the isotropic stencils worked out by hand, exactness on
+polynomials, the special values of K named in Remarks I and II, a linear-stability amplification matrix
+assembled here in Fourier space, exact conservation of sum(phi), and lattice symmetries.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_00007_gb300 import workloads as wl
+
+# The D2Q9 lattice as the paper lists it (Sec. II.B), written independently of the oracle.
+C = np.array([(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)], float)
+WT = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+CS2 = 1.0 / 3.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------- constants
+
+def test_K_special_values():
+    """Remark I: K = 0 at tau = 0.5 + sqrt(3)/6.  Remark II: 2 tau - 1 + 3K = 0 at tau = 1."""
+    c = oracle.derive(wl.make_params(nx=4, ny=4, tau=0.5 + math.sqrt(3) / 6, M=0.01))
+    assert abs(c.K) < 1e-15
+    c = oracle.derive(wl.make_params(nx=4, ny=4, tau=1.0, M=0.01))
+    assert abs(2 * 1.0 - 1 + 3 * c.K) < 1e-15
+    assert abs(c.K + 1.0 / 3.0) < 1e-15
+
+
+def test_derived_constants():
+    """Eq. betakappa, the mobility relation M = c_s^2 eta (tau - 1/2), Eq. rho and the Peclet number of
+    Sec. III.A: the interface of width W carries surface tension sigma = sqrt(2 kappa beta)/6 * |dphi|^3
+    (double-well identity), rho(phiA) = rhoA, rho(phiB) = rhoB, and Pe is recovered from the derived M."""
+    for phiA, phiB in [(1.0, 0.0), (1.0, -1.0)]:
+        p = wl.make_params(nx=4, ny=4, phiA=phiA, phiB=phiB, sigma=0.01, W=4.0, M=0.0, Pe=200.0,
+                           Ustar=0.02, tau=0.8, rhoA=1.0, rhoB=0.5)
+        c = oracle.derive(p)
+        d = abs(phiA - phiB)
+        # for f = beta (phi-phiA)^2 (phi-phiB)^2 the planar interface has sigma = d^3 sqrt(2 kappa beta)/6
+        assert abs(d ** 3 * math.sqrt(2 * c.kappa * c.beta) / 6 - 0.01) < 1e-15
+        # and width W = 4 sqrt(kappa / (2 beta)) / d  (tanh(2z/W) profile of Eq. analytical)
+        assert abs(4 * math.sqrt(c.kappa / (2 * c.beta)) / d - 4.0) < 1e-13
+        assert abs(c.a * phiA + c.b - 1.0) < 1e-15 and abs(c.a * phiB + c.b - 0.5) < 1e-15
+        assert abs(c.M - CS2 * c.eta * (0.8 - 0.5)) < 1e-17
+        assert abs(0.02 * 4.0 / (c.M * c.beta * d * d) - 200.0) < 1e-10
+
+
+# ----------------------------------------------------------------------------- equilibrium and source
+
+@pytest.mark.parametrize("seed", range(5))
+def test_geq_moments(seed):
+    """Eq. feqmoment: sum g_eq = phi, sum c g_eq = phi u, sum c c g_eq = c_s^2 eta mu I + phi u u."""
+    r = np.random.default_rng(seed)
+    phi, mu, ux, uy, eta = r.uniform(-1, 1), r.uniform(-1, 1), r.uniform(-.1, .1), r.uniform(-.1, .1), r.uniform(0, 1)
+    g = oracle.geq(phi, mu, ux, uy, eta)
+    u = np.array([ux, uy])
+    assert abs(g.sum() - phi) < 1e-15
+    np.testing.assert_allclose(C.T @ g, phi * u, atol=1e-16)
+    P = np.einsum("i,ia,ib->ab", g, C, C)
+    np.testing.assert_allclose(P, CS2 * eta * mu * np.eye(2) + phi * np.outer(u, u), atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_source_moments(seed):
+    """Eq. conservation: sum S = 0 and sum c S = F; also sum c c S = 0 (used after Eq. F2-F)."""
+    r = np.random.default_rng(100 + seed)
+    F = r.uniform(-1, 1, 2)
+    S = oracle.source(*F)
+    assert abs(S.sum()) < 1e-16
+    np.testing.assert_allclose(C.T @ S, F, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", S, C, C), 0, atol=1e-16)
+
+
+def test_dfdphi_is_derivative_of_double_well():
+    """Eq. mu's bulk part is d/dphi of Eq. bulk: compare with numpy's polynomial derivative."""
+    for phiA, phiB, beta in [(1.0, 0.0, 0.03), (1.0, -1.0, 0.00375), (0.7, -0.2, 1.3)]:
+        f = beta * np.poly1d([1.0, -phiA]) ** 2 * np.poly1d([1.0, -phiB]) ** 2
+        df = f.deriv()
+        for x in np.linspace(-1.5, 1.5, 31):
+            assert abs(oracle.dfdphi(x, beta, phiA, phiB) - df(x)) < 1e-13 * max(1.0, abs(df(x)))
+
+
+# ----------------------------------------------------------------------------- stencils
+
+def _symbols(kx, ky):
+    """Fourier symbols of the D2Q9-weighted stencils, worked out by hand:
+    d/dx -> i sin(kx)(2 + cos ky)/3, d/dy -> i sin(ky)(2 + cos kx)/3,
+    lap -> (4/3)(cos kx + cos ky) + (2/3) cos kx cos ky - 10/3."""
+    gx = np.sin(kx) * (2 + np.cos(ky)) / 3
+    gy = np.sin(ky) * (2 + np.cos(kx)) / 3
+    lap = 4 / 3 * (np.cos(kx) + np.cos(ky)) + 2 / 3 * np.cos(kx) * np.cos(ky) - 10 / 3
+    return gx, gy, lap
+
+
+@pytest.mark.parametrize("mx,my", [(1, 0), (0, 2), (3, 5), (7, 4)])
+def test_stencil_symbols_plane_wave(mx, my):
+    nx, ny = 16, 12
+    kx, ky = 2 * np.pi * mx / nx, 2 * np.pi * my / ny
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    th = kx * x + ky * y
+    psi = np.cos(th)
+    sgx, sgy, slap = _symbols(kx, ky)
+    gx, gy = oracle.grad(psi)
+    np.testing.assert_allclose(gx, -sgx * np.sin(th), atol=1e-14)
+    np.testing.assert_allclose(gy, -sgy * np.sin(th), atol=1e-14)
+    np.testing.assert_allclose(oracle.lap(psi), slap * psi, atol=1e-14)
+    # divergence of (cos th, 2 sin th)
+    d = oracle.div(psi, 2 * np.sin(th))
+    np.testing.assert_allclose(d, -sgx * np.sin(th) + 2 * sgy * np.cos(th), atol=1e-14)
+
+
+def test_stencils_exact_on_quadratics():
+    """Away from the periodic seam the stencils differentiate polynomials of degree <= 2 exactly."""
+    nx, ny = 12, 10
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    a = [0.3, -1.1, 0.7, 0.25, -0.4, 0.9]
+    psi = a[0] + a[1] * x + a[2] * y + a[3] * x * x + a[4] * x * y + a[5] * y * y
+    gx, gy = oracle.grad(psi)
+    L = oracle.lap(psi)
+    s = (slice(1, ny - 1), slice(1, nx - 1))
+    np.testing.assert_allclose(gx[s], (a[1] + 2 * a[3] * x + a[4] * y)[s], atol=1e-12)
+    np.testing.assert_allclose(gy[s], (a[2] + a[4] * x + 2 * a[5] * y)[s], atol=1e-12)
+    np.testing.assert_allclose(L[s], 2 * a[3] + 2 * a[5], atol=1e-12)
+
+
+def test_stencils_mirror_walls():
+    """With walls, a field even about both walls (y = -1/2 and ny - 1/2) sees the same values as its
+    periodic extension, so the stencils reproduce the plane-wave symbols on every row."""
+    nx, ny = 16, 10
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    kx, ky = 2 * np.pi * 3 / nx, 2 * np.pi / ny
+    psi = np.cos(kx * x) * np.cos(ky * (y + 0.5))
+    sgx, sgy, slap = _symbols(kx, ky)
+    gx, gy = oracle.grad(psi, walls=1)
+    np.testing.assert_allclose(oracle.lap(psi, walls=1), slap * psi, atol=1e-14)
+    np.testing.assert_allclose(gx, -sgx * np.sin(kx * x) * np.cos(ky * (y + .5)), atol=1e-14)
+    np.testing.assert_allclose(gy, -sgy * np.cos(kx * x) * np.sin(ky * (y + .5)), atol=1e-14)
+
+
+def test_mu_and_force_on_quadratic_fields():
+    """Eq. mu on a quadratic phi and Eq. reFi's F1 (Eq. t0-phiu, grad p = 0) + F2 (Eq. mark3) with a
+    linear mu and uniform u, at interior nodes, against closed forms."""
+    nx, ny = 12, 12
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    p = wl.make_params(nx=nx, ny=ny, phiA=1.0, phiB=0.0, sigma=0.02, W=3.0, M=0.01, tau=0.9,
+                       rhoA=1.0, rhoB=0.3, model=2, vel=wl.VEL_UNIFORM, ux0=0.03, uy0=-0.02)
+    c = oracle.derive(p)
+    h = [0.5, 0.01, -0.02, 0.001, 0.002, -0.0015]  # phi = h0 + h1 x + h2 y + h3 x^2 + h4 xy + h5 y^2
+    phi = h[0] + h[1] * x + h[2] * y + h[3] * x * x + h[4] * x * y + h[5] * y * y
+    s = (slice(2, ny - 2), slice(2, nx - 2))
+    f = c.beta * np.poly1d([1.0, -1.0]) ** 2 * np.poly1d([1.0, 0.0]) ** 2
+    mu_expect = f.deriv()(phi) - c.kappa * (2 * h[3] + 2 * h[5])
+    np.testing.assert_allclose(oracle.mu(p, phi)[s], mu_expect[s], atol=1e-14)
+    m = 0.1 + 0.3 * x - 0.2 * y
+    ux, uy = np.full_like(phi, 0.03), np.full_like(phi, -0.02)
+    Fx, Fy = oracle.force(p, phi, m, ux, uy)
+    rho = c.a * phi + c.b
+    # F1 = -(phi^2/rho) grad mu ; F2 = K grad(u . grad phi) = K H u with H the Hessian of phi
+    Hxx, Hxy, Hyy = 2 * h[3], h[4], 2 * h[5]
+    F2x = c.K * (Hxx * 0.03 + Hxy * -0.02)
+    F2y = c.K * (Hxy * 0.03 + Hyy * -0.02)
+    np.testing.assert_allclose(Fx[s], (-phi ** 2 / rho * 0.3 + F2x)[s], atol=1e-15)
+    np.testing.assert_allclose(Fy[s], (-phi ** 2 / rho * -0.2 + F2y)[s], atol=1e-15)
+    # Model I drops F2
+    Fx1, Fy1 = oracle.force(dict(p, model=1), phi, m, ux, uy)
+    np.testing.assert_allclose(Fx1[s], (-phi ** 2 / rho * 0.3)[s], atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- the whole step, linearised
+
+def _amplification(p, c, phibar, kx, ky):
+    """9x9 matrix advancing a Fourier mode of the distributions by one step of Eq. LB, linearised about
+    the uniform state (phibar, mu = f'(phibar), uniform u).  Assembled here from: phi' = sum g';
+    mu' = f''(phibar) phi' - kappa lap phi'; F' = -(phibar^2/rho) grad mu' + K grad(div(phi' u));
+    g_eq' = dgeq/dphi phi' + dgeq/dmu mu'; collision; streaming multiplies direction i by e^{-i k.c_i}."""
+    ux, uy = p["ux0"], p["uy0"]
+    sgx, sgy, slap = _symbols(kx, ky)
+    f = c.beta * np.poly1d([1.0, -p["phiA"]]) ** 2 * np.poly1d([1.0, -p["phiB"]]) ** 2
+    f2 = f.deriv(2)(phibar)
+    rho = c.a * phibar + c.b
+    # g_eq is linear in phi and in mu at fixed u
+    dphi = oracle.geq(1.0, 0.0, ux, uy, c.eta)
+    dmu = oracle.geq(0.0, 1.0, ux, uy, c.eta)
+    Sx, Sy = oracle.source(1.0, 0.0), oracle.source(0.0, 1.0)
+    ones = np.ones(9)
+    mu_per_phi = f2 - c.kappa * slap
+    # force per unit phi-hat (complex): grad -> i (sgx, sgy)
+    Fx = -(phibar ** 2 / rho) * 1j * sgx * mu_per_phi
+    Fy = -(phibar ** 2 / rho) * 1j * sgy * mu_per_phi
+    if p["model"] == 2:
+        divu = 1j * (sgx * ux + sgy * uy)
+        Fx += c.K * 1j * sgx * divu
+        Fy += c.K * 1j * sgy * divu
+    tau = p["tau"]
+    geq_row = np.outer(dphi + dmu * mu_per_phi, ones)           # g_eq' = (.) phi', phi' = 1^T g'
+    S_row = np.outer(Sx * Fx + Sy * Fy, ones)
+    post = np.eye(9) - (np.eye(9) - geq_row) / tau + (1 - 1 / (2 * tau)) * S_row
+    shift = np.diag(np.exp(-1j * (C[:, 0] * kx + C[:, 1] * ky)))
+    return shift @ post
+
+
+@pytest.mark.parametrize("model,tau,rhoB,phibar", [(2, 1.0, 0.5, 0.35), (1, 0.8, 0.5, 0.6),
+                                                   (2, 0.5 + math.sqrt(3) / 6, 1.0, 0.2),
+                                                   (2, 1.3, 0.25, 0.8)])
+def test_step_matches_linear_amplification(model, tau, rhoB, phibar):
+    nx, ny, nsteps = 16, 12, 6
+    p = wl.make_params(nx=nx, ny=ny, model=model, tau=tau, rhoA=1.0, rhoB=rhoB, sigma=0.05, W=3.0,
+                       M=0.02, vel=wl.VEL_UNIFORM, ux0=0.04, uy0=-0.03)
+    c = oracle.derive(p)
+    mx, my = 3, 2
+    kx, ky = 2 * np.pi * mx / nx, 2 * np.pi * my / ny
+    A = _amplification(p, c, phibar, kx, ky)
+    r = np.random.default_rng(7)
+    v = r.normal(size=9) + 1j * r.normal(size=9)
+    gbar = oracle.geq(phibar, oracle.dfdphi(phibar, c.beta, 1.0, 0.0), 0.04, -0.03, c.eta)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    wave = np.exp(1j * (kx * x + ky * y))
+    pert = np.real(v[:, None, None] * wave[None])
+    eps = 1e-5
+    # central difference of two runs removes the even-order nonlinear remainder
+    gp = oracle.run(p, gbar[:, None, None] + eps * pert, nsteps)
+    gm = oracle.run(p, gbar[:, None, None] - eps * pert, nsteps)
+    got = (gp - gm) / (2 * eps)
+    want = np.real((np.linalg.matrix_power(A, nsteps) @ v)[:, None, None] * wave[None])
+    assert np.max(np.abs(got - want)) < 1e-8 * np.max(np.abs(want))
+
+
+# ----------------------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("vel,walls", [(wl.VEL_ROTATION, 0), (wl.VEL_VORTEX, 0), (wl.VEL_SHEAR, 1),
+                                       (wl.VEL_DEFORM, 0)])
+def test_mass_conserved(vel, walls):
+    """sum_i S_i = 0, sum_i g_eq = phi and streaming/bounce-back permute populations (Eqs. feqmoment,
+    conservation, macroscopicg), so sum_x phi is constant to rounding."""
+    nx, ny = 23, 19
+    p = wl.make_params(nx=nx, ny=ny, vel=vel, walls=walls, U0=0.03, xc=11, yc=9, half=11, Tper=50,
+                       shear=0.004, model=2, tau=0.9, M=0.02, rhoB=0.4, sigma=0.03, W=3.0)
+    phi0 = wl.random_smooth_phi(nx, ny, seed=3)
+    g0 = oracle.init(p, phi0)
+    m0 = oracle.phi_of(g0).sum()
+    phi, _ = oracle.simulate(p, phi0, 40)
+    assert abs(phi.sum() - m0) < 1e-13 * np.abs(phi0).sum()
+    assert abs(m0 - phi0.sum()) < 1e-13 * np.abs(phi0).sum()
+
+
+def test_translation_invariance_bitwise():
+    """With a uniform velocity the step commutes with integer shifts of the periodic lattice."""
+    p, phi0, _ = wl.translation(nx=20, U=0.04)
+    a, _ = oracle.simulate(p, phi0, 15)
+    b, _ = oracle.simulate(p, np.roll(phi0, (3, -5), axis=(0, 1)), 15)
+    assert np.array_equal(np.roll(a, (3, -5), axis=(0, 1)), b)
+
+
+def test_reflection_and_rotation_symmetry_at_rest():
+    """With u = 0 the scheme is symmetric under the lattice's reflections and 90-degree rotation."""
+    n = 18
+    p = wl.make_params(nx=n, ny=n, vel=wl.VEL_UNIFORM, model=2, tau=0.8, M=0.02, sigma=0.03, W=3.0)
+    phi0 = wl.random_smooth_phi(n, n, seed=11) + 0.2 * wl.circle_phi(n, n, 6.3, 8.1, 4.0, 3.0)
+    a, _ = oracle.simulate(p, phi0, 12)
+    b, _ = oracle.simulate(p, phi0[:, ::-1].copy(), 12)
+    np.testing.assert_allclose(b, a[:, ::-1], atol=1e-14)
+    c, _ = oracle.simulate(p, phi0.T.copy(), 12)
+    np.testing.assert_allclose(c, a.T, atol=1e-14)
+
+
+def test_uniform_state_is_fixed_point():
+    """A uniform phi with uniform u stays uniform: mu = f'(phi), F = 0, and streaming of a uniform field
+    is the identity."""
+    p = wl.make_params(nx=8, ny=6, vel=wl.VEL_UNIFORM, ux0=0.05, uy0=0.02, model=2, tau=0.7, M=0.01)
+    phi0 = np.full((6, 8), 0.37)
+    phi, _ = oracle.simulate(p, phi0, 10)
+    np.testing.assert_allclose(phi, 0.37, atol=1e-15)
+
+
+def test_planar_interface_is_nearly_stationary():
+    """Eq. analytical is the continuum equilibrium: at rest the discrete profile moves only by O(dx^2/W^2)
+    and the chemical potential it carries stays small."""
+    nx, ny = 4, 64
+    p = wl.make_params(nx=nx, ny=ny, vel=wl.VEL_UNIFORM, model=2, tau=1.0, M=0.02, W=5.0)
+    phi0 = wl.planar_phi(nx, ny, 16.0, 5.0)
+    c = oracle.derive(p)
+    assert np.max(np.abs(oracle.mu(p, phi0))) < 0.05 * c.beta
+    phi1, g1 = oracle.simulate(p, phi0, 1600)
+    phi2 = oracle.phi_of(oracle.run(p, g1, 1600, n0=1600))
+    assert np.max(np.abs(phi1 - phi0)) < 0.25 / 5.0 ** 2     # O(dx^2 / W^2)
+    assert np.max(np.abs(phi2 - phi1)) < 1e-3                # and it stays there
+
+
+def test_velocity_fields():
+    """Prescribed flows: the rotation is rigid about its centre; the vortex, reversing-shear and
+    deformation fields are divergence-free and reverse in time as stated; the shear flow moves the walls
+    at -/+ shear*ny/2."""
+    n = 64
+    rot = wl.make_params(nx=n, ny=n, vel=wl.VEL_ROTATION, U0=0.02, xc=32, yc=32, half=32)
+    ux, uy = oracle.velocity(rot, 40.0, 32.0, 0)
+    assert abs(ux) < 1e-18 and abs(uy - 0.02 * math.pi * 8 / 32) < 1e-16
+    h = 1e-5
+    for vel, T in [(wl.VEL_VORTEX, 100.0), (wl.VEL_REV_SHEAR, 100.0), (wl.VEL_DEFORM, 100.0)]:
+        p = wl.make_params(nx=n, ny=n, vel=vel, U0=0.03, Tper=T, nvort=4)
+        for (x, y) in [(3.3, 7.1), (20.0, 50.5), (41.7, 12.2)]:
+            dux = (oracle.velocity(p, x + h, y, 10)[0] - oracle.velocity(p, x - h, y, 10)[0]) / (2 * h)
+            duy = (oracle.velocity(p, x, y + h, 10)[1] - oracle.velocity(p, x, y - h, 10)[1]) / (2 * h)
+            assert abs(dux + duy) < 1e-9
+    vor = wl.make_params(nx=n, ny=n, vel=wl.VEL_VORTEX, U0=0.03, Tper=100.0)
+    a, b = oracle.velocity(vor, 10.0, 20.0, 0), oracle.velocity(vor, 10.0, 20.0, 100)
+    assert abs(a[0] + b[0]) < 1e-17 and abs(a[1] + b[1]) < 1e-17
+    rs = wl.make_params(nx=n, ny=n, vel=wl.VEL_REV_SHEAR, U0=0.03, Tper=100.0)
+    a, b = oracle.velocity(rs, 10.0, 20.0, 99), oracle.velocity(rs, 10.0, 20.0, 100)
+    assert a[0] == -b[0] and a[1] == -b[1]
+    sh = wl.make_params(nx=n, ny=n, vel=wl.VEL_SHEAR, shear=1e-4)
+    assert abs(oracle.velocity(sh, 0.0, -0.5, 0)[0] + 1e-4 * n / 2) < 1e-18
+    assert abs(oracle.velocity(sh, 0.0, n - 0.5, 0)[0] - 1e-4 * n / 2) < 1e-18
+
+
+def test_translation_returns_after_one_period():
+    """Sec. III.A: after one period the translated circle coincides with the initial one (small error,
+    mass conserved).  The configuration is the 100x100 translation workload at W = 4, tau = 0.8."""
+    p, phi0, T = wl.translation()
+    phi, _ = oracle.simulate(p, phi0, T)
+    ob = oracle.observe(phi, phi0)
+    assert ob["err_l2"] < 0.03
+    assert abs(ob["mass"] - phi0.sum()) < 1e-12 * phi0.sum()
+    assert 0.99 < ob["max"] < 1.02 and -0.02 < ob["min"] < 0.01
+
+
+@pytest.mark.slow
+def test_paper_printed_extrema_model2():
+    """Soft pin (Sec. III.A): the paper prints max/min phi = 1.0487 / -1.0361 for Model II at
+    tau_g = 0.5 + sqrt(3)/6 with matched densities, L0 = 200, U0 = 0.02, Pe = 200, W = 2, sigma = 0.01,
+    after 4T.  The oracle must land within a few percent of the overshoot."""
+    with open(os.path.join(GOLDEN, "paper_translation_extrema.json")) as fh:
+        ref = json.load(fh)
+    p, phi0, T = wl.paper_translation()
+    phi, _ = oracle.simulate(p, phi0, 4 * T)
+    ob = oracle.observe(phi, phi0)
+    assert abs(ob["max"] - ref["model2_max"]) < 0.02
+    assert abs(ob["min"] - ref["model2_min"]) < 0.02
