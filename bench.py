@@ -1,0 +1,297 @@
+"""Benchmark of the Cahn-Hilliard lattice Boltzmann step on one GB300.
+
+Workload: Zalesak's slotted disk on a 256 x 256 periodic lattice (disk radius 64 at (128, 160), slot
+16 x 80, W = 4, solid-body rotation with U0 = 0.02, M = 0.005, tau = 1, Model II).  One benchmark step is
+one full revolution, 12800 lattice steps, of the FP32 path; the FP64 path runs the same revolution
+beside it.  The metric is million lattice updates per second (MLUPS); the roofline fraction is the step
+kernel's algorithmic HBM bytes per launch over its average launch time, against the measured copy
+bandwidth.  A large-grid sweep (4096^2, inputs far larger than L2) reports the same kernel where HBM,
+not latency, bounds it.  L2 is flushed (a 512 MiB write) before every timed benchmark step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1805_00007_gb300 import workloads as wl  # noqa: E402
+
+REV_N = 256
+METRIC = "MLUPS and % HBM roofline (FP32 vs FP64 step) at stated phi error vs FP64 oracle"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1])); mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def oracle_baseline(p, phi0, nsteps):
+    """The FP64 oracle as it stands, on the host cores: lattice updates per second over nsteps."""
+    import oracle
+    g = oracle.init(p, phi0)
+    t0 = time.perf_counter()
+    oracle.run(p, g, nsteps)
+    dt = time.perf_counter() - t0
+    return p["nx"] * p["ny"] * nsteps / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    p, phi0, rev = wl.zalesak(n=REV_N)
+    sample = 150  # lattice steps of the 256^2 workload per benchmark step
+    for _ in range(args.warmup):
+        oracle_baseline(p, phi0, 5)
+    vals, tot = [], 0.0
+    for _ in range(args.steps):
+        v, dt = oracle_baseline(p, phi0, sample)
+        vals.append(v)
+        tot += dt
+    value = float(np.median(vals))
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "zalesak_256x256_fp64_oracle", "nx": REV_N, "ny": REV_N,
+                       "lattice_steps_per_step": sample, "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} lattice steps of the 256x256 Zalesak workload per step"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1805_00007_gb300 import abi
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_peak, peak_kind = peaks()
+
+    p, phi0, rev = wl.zalesak(n=REV_N)
+    nodes = REV_N * REV_N
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    def timed_revolutions(prec, k, w):
+        """Run w warm-up and k timed revolutions; returns (seconds per revolution, the simulation)."""
+        sim = abi.Simulation(p, phi0, prec=prec, stream=stream.cuda_stream)
+        for _ in range(w):
+            with torch.cuda.stream(stream):
+                flush_l2(flush)
+            sim.step(rev)
+        barrier()
+        total = 0.0
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(rev)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1) / 1e3
+        barrier()
+        return total / k, sim
+
+    # --- FP32 path: the headline value
+    with Clocks(local) as clk:
+        t32, sim32 = timed_revolutions("f32", args.steps, args.warmup)
+    t_max = t32
+    if world > 1:
+        t = torch.tensor([t32], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    info32 = sim32.info()
+    phi32 = sim32.phi()
+    sim32.close()
+
+    # --- FP64 path, same revolution
+    t64, sim64 = timed_revolutions("f64", max(1, args.steps // 2), 1)
+    info64 = sim64.info()
+    n_rev64 = args.steps // 2 + 1 + max(1, args.steps // 2)
+    phi64 = sim64.phi()
+    sim64.close()
+
+    lu_per_rev = nodes * rev
+    value = world * lu_per_rev / t_max / 1e6
+    launch32 = t32 / rev
+    achieved32 = info32["bytes_per_lu"] * nodes / launch32 / 1e9
+    achieved64 = info64["bytes_per_lu"] * nodes / (t64 / rev) / 1e9
+
+    # --- end to end through the C ABI with host buffers: init (H2D of phi0), one revolution, read phi (D2H)
+    e2e_times = []
+    for it in range(2 + max(1, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = abi.lb_ch_init(p, phi0, abi.LBCH_F32, stream.cuda_stream)
+        abi.lb_ch_step(h, rev)
+        out = abi.lb_ch_observe(h, 0, abi.LBCH_OBS_PHI, (REV_N, REV_N))
+        abi.lb_ch_free(h)
+        dt = time.perf_counter() - t0
+        if it >= 2:
+            e2e_times.append(dt)
+    e2e = world * lu_per_rev / statistics.median(e2e_times) / 1e6
+
+    # --- large-grid sweep: the same kernel with inputs far larger than L2 (HBM-bound regime)
+    sweep = {}
+    if not args.no_sweep:
+        for prec, n in (("f32", 4096), ("f64", 4096), ("f16s", 4096)):
+            pp = wl.make_params(nx=n, ny=n, vel=wl.VEL_ROTATION, U0=0.02, xc=n / 2, yc=n / 2, half=n / 2,
+                                W=4.0, M=0.005, tau=1.0)
+            f0 = wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
+            sim = abi.Simulation(pp, f0, prec=prec, stream=stream.cuda_stream)
+            sim.step(64)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nst = 128
+            e0.record(stream)
+            sim.step(nst)
+            e1.record(stream)
+            e1.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3 / nst
+            inf = sim.info()
+            gbs = inf["bytes_per_lu"] * n * n / dt / 1e9
+            sweep[f"{prec}_{n}"] = {"MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6,
+                                   "bytes_per_lu": inf["bytes_per_lu"], "achieved_gbs": gbs,
+                                   "frac": gbs / hbm_peak}
+            sim.close()
+
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        sample = 1200
+        v, dt = oracle_baseline(p, phi0, sample)
+        cpu = {"value": v, "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{sample} lattice steps of the 256x256 Zalesak workload ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "zalesak_256x256_one_revolution", "nx": REV_N, "ny": REV_N,
+                       "lattice_steps_per_step": rev, "model": "II", "l2": "flushed before each step",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "fp64": {"MLUPS": world * lu_per_rev / t64 / 1e6, "ms_per_step": 1e3 * t64,
+                     "achieved_gbs": achieved64, "frac": achieved64 / hbm_peak},
+            "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved32 / hbm_peak, "traffic": None,
+                         "kernel": "ch_step_kernel<float,float,float,32,16,256>",
+                         "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6},
+            "sweep_4096": sweep,
+            "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
+                    "d2h_bytes_per_step": phi0.nbytes},
+            "gpu_launches": args.steps * rev,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,145 @@
+/*
+ * lbch.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for the Cahn-Hilliard equation.
+ *
+ * Method: Zhang, Guo & Liang, "A high-order lattice Boltzmann model for the Cahn-Hilliard equation"
+ * (arXiv:1805.00007).  One step advances the D2Q9 distributions g_i of the order parameter phi by the
+ * single-relaxation-time equation of Eq. LB, with the equilibrium of Eq. geq, the source of Eq. liangFi
+ * and the force of Eq. reFi as the paper runs it (Remark III): F = (phi/rho)(-phi grad mu) for Model I,
+ * plus 3 c_s^2 K grad(div(phi u)) (Eq. mark3) for Model II.  The chemical potential is Eq. mu with the
+ * double well of Eq. bulk and the constants of Eq. betakappa; phi = sum_i g_i (Eq. macroscopicg).
+ *
+ * Conventions.  Lattice units (dx = dt = 1).  Node (i, j) sits at x = i, y = j; host fields are row-major
+ * double arrays of ny*nx values (index j*nx + i).  The domain is periodic in x; in y it is periodic, or
+ * (walls = 1) bounded by halfway bounce-back walls at y = -1/2 and y = ny - 1/2 that move with the
+ * prescribed velocity evaluated there.  The velocity field is prescribed (lbch_vel); it is evaluated at
+ * t = n for the step n -> n+1.
+ *
+ * Ownership.  The caller owns every host buffer it passes; the library copies what it needs before the
+ * call returns (lb_ch_init) or writes into it (lb_ch_observe).  The library owns all device memory of a
+ * handle and releases it in lb_ch_free.  A handle is bound to the CUDA device current at lb_ch_init and
+ * to one CUDA stream; calls on one handle must not run concurrently from several host threads.
+ *
+ * Errors.  Every entry point returns an lbch_status; nothing aborts.  LBCH_EINVAL for bad arguments
+ * (nothing is changed), LBCH_ENOMEM when device memory runs out, LBCH_ECUDA for any other CUDA error
+ * (the handle should then be freed), LBCH_ENONFINITE from lb_ch_observe when phi holds a NaN or Inf.
+ * lb_ch_last_error() gives a message for the most recent failure on the calling thread.
+ */
+#ifndef LBCH_H
+#define LBCH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBCH_OK = 0,
+    LBCH_EINVAL = 1,
+    LBCH_ENOMEM = 2,
+    LBCH_ECUDA = 3,
+    LBCH_ETIMEOUT = 4,
+    LBCH_ENONFINITE = 5
+} lbch_status;
+
+/* Storage and arithmetic precision of the lattice state.
+ *   LBCH_F64  : g and phi stored in double, double arithmetic.
+ *   LBCH_F32  : g and phi stored in float, float arithmetic (velocity tables built in double).
+ *   LBCH_F16S : shifted half storage -- phi kept in float, g_1..g_8 stored in half, g_0 not stored but
+ *               recovered as phi - sum_{i>0} g_i, so sum_i g_i = phi holds exactly; float arithmetic. */
+typedef enum { LBCH_F64 = 0, LBCH_F32 = 1, LBCH_F16S = 2 } lbch_prec;
+
+/* Prescribed velocity fields u(x, y, t) of the benchmark problems (paper Sec. III).
+ *   UNIFORM  : u = (ux0, uy0)                                          (diagonal translation, Sec. III.A)
+ *   ROTATION : u = (-U0 pi (y - yc)/half, U0 pi (x - xc)/half)          (Zalesak's disk, Sec. III.B)
+ *   VORTEX   : u = U0 (-sin^2(pi x/nx) sin(2 pi y/ny), sin(2 pi x/nx) sin^2(pi y/ny)) cos(pi t/Tper)
+ *   SHEAR    : u = (shear (y - (ny-1)/2), 0), used with walls = 1      (wall-driven shear flow)
+ *   REV_SHEAR: Eq. shear with L0 = nx, sign reversed for t >= Tper     (Sec. III.C)
+ *   DEFORM   : Eq. deformation with L0 = nx, n = nvort, T0 = Tper      (Sec. III.D) */
+typedef enum {
+    LBCH_VEL_UNIFORM = 0,
+    LBCH_VEL_ROTATION = 1,
+    LBCH_VEL_VORTEX = 2,
+    LBCH_VEL_SHEAR = 3,
+    LBCH_VEL_REV_SHEAR = 4,
+    LBCH_VEL_DEFORM = 5
+} lbch_vel;
+
+/* Quantities lb_ch_observe returns.  Sums are accumulated in double on the GPU in a fixed order, so
+ * repeated calls on the same state give identical results.
+ *   MASS    : sum_x phi                                                  (1 value)
+ *   ERR_L2  : ||E_phi||_2 = sqrt(sum (phi - phi0)^2 / sum phi0^2), Eq. err (1 value)
+ *   MAX/MIN : extreme values of phi (Sec. III.A prints them)              (1 value)
+ *   PHI     : the field phi as ny*nx doubles, row-major                   (nx*ny values)
+ *   STEP    : the step index n of the current state                       (1 value) */
+typedef enum {
+    LBCH_OBS_MASS = 0,
+    LBCH_OBS_ERR_L2 = 1,
+    LBCH_OBS_MAX = 2,
+    LBCH_OBS_MIN = 3,
+    LBCH_OBS_PHI = 4,
+    LBCH_OBS_STEP = 5
+} lbch_obs;
+
+/* Parameters of one problem instance, in the paper's notation.  The derived constants are computed by
+ * the library: beta, kappa (Eq. betakappa); eta from M = c_s^2 eta (tau - 1/2); a, b (Eq. rho);
+ * K = (tau - 1/6 - tau^2)/(tau - 1/2) (Eq. F2-1); and, when M <= 0, M = Ustar W / (Pe beta (phiA-phiB)^2)
+ * from the Peclet number of Sec. III.A. */
+typedef struct {
+    int nx, ny;          /* lattice size, each >= 4 */
+    int walls;           /* 0: periodic in y; 1: moving bounce-back walls at y = -1/2 and ny - 1/2 */
+    int model;           /* 1: Model I; 2: Model II (Eq. mark3 force added) */
+    int vel;             /* lbch_vel */
+    int nvort;           /* vortex count of the deformation field */
+    double phiA, phiB;   /* bulk values of phi */
+    double sigma, W;     /* surface tension, interface width */
+    double M;            /* mobility (if <= 0, derived from Pe and Ustar) */
+    double Pe, Ustar;    /* Peclet number and characteristic speed */
+    double tau;          /* relaxation time tau_g, > 1/2 */
+    double rhoA, rhoB;   /* bulk densities */
+    double U0, ux0, uy0; /* velocity amplitude; uniform velocity */
+    double xc, yc, half; /* rotation centre and half-length */
+    double Tper;         /* period or reversal time of time-dependent flows, in steps */
+    double shear;        /* shear rate */
+} lbch_params;
+
+typedef struct lbch_handle lbch_handle;
+
+/* Create a simulation of n_inst independent instances (an ensemble when n_inst > 1; instances may have
+ * different sizes and parameters but share the precision).  params: n_inst structs (host).  phi0: the
+ * initial order parameter of every instance, concatenated in instance order, each ny*nx row-major
+ * doubles (host).  The initial distributions are the equilibria of phi0, mu(phi0) and u(t = 0).
+ * stream: a cudaStream_t, or NULL for a stream the library creates.  On success *out receives the
+ * handle and the state is at step 0. */
+lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0, int prec,
+                       void* stream, lbch_handle** out);
+
+/* Advance every instance by nsteps >= 0 steps of Eq. LB.  Asynchronous on the handle's stream: the work
+ * is enqueued (in CUDA graphs of 64 steps when possible) and the call returns. */
+lbch_status lb_ch_step(lbch_handle* h, long nsteps);
+
+/* Read an observable of instance inst into out (host, sized as lbch_obs states).  Synchronises the
+ * handle's stream.  Returns LBCH_ENONFINITE (with out filled) when phi holds a NaN or Inf. */
+lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out);
+
+/* One scalar observable (MASS, ERR_L2, MAX or MIN) for every instance: out receives n_inst values. */
+lbch_status lb_ch_observe_all(lbch_handle* h, int what, double* out);
+
+/* Release every resource of the handle (safe on NULL). */
+lbch_status lb_ch_free(lbch_handle* h);
+
+/* Human-readable name of a status, and the message of the last failure on this thread. */
+const char* lb_ch_strerror(lbch_status s);
+const char* lb_ch_last_error(void);
+
+/* Device timing of the most recent lb_ch_step call's kernels is not tracked by the library; these two
+ * entry points expose what a caller needs to time or inspect the hot kernel directly.
+ * lb_ch_info: out[0] = total lattice nodes, out[1] = algorithmic HBM bytes per lattice update of the
+ * step kernel, out[2] = number of thread blocks of one step launch, out[3] = current step index. */
+lbch_status lb_ch_info(lbch_handle* h, double* out);
+
+/* The CUDA stream the handle enqueues on (a cudaStream_t). */
+void* lb_ch_stream(lbch_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBCH_H */

@@ -1,0 +1,191 @@
+"""Thin ctypes binding of the C ABI in include/lbch.h: the same entry points, argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module never computes any part of it.  If the
+library cannot be loaded the import of the entry points raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LBCH_OK, LBCH_EINVAL, LBCH_ENOMEM, LBCH_ECUDA, LBCH_ETIMEOUT, LBCH_ENONFINITE = range(6)
+LBCH_F64, LBCH_F32, LBCH_F16S = range(3)
+LBCH_OBS_MASS, LBCH_OBS_ERR_L2, LBCH_OBS_MAX, LBCH_OBS_MIN, LBCH_OBS_PHI, LBCH_OBS_STEP = range(6)
+PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
+
+# Exported symbols, as declared in include/lbch.h.
+SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free",
+           "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream")
+
+
+class lbch_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("walls", ctypes.c_int), ("model", ctypes.c_int),
+        ("vel", ctypes.c_int), ("nvort", ctypes.c_int),
+        ("phiA", ctypes.c_double), ("phiB", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("W", ctypes.c_double),
+        ("M", ctypes.c_double), ("Pe", ctypes.c_double), ("Ustar", ctypes.c_double),
+        ("tau", ctypes.c_double), ("rhoA", ctypes.c_double), ("rhoB", ctypes.c_double),
+        ("U0", ctypes.c_double), ("ux0", ctypes.c_double), ("uy0", ctypes.c_double),
+        ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("half", ctypes.c_double),
+        ("Tper", ctypes.c_double), ("shear", ctypes.c_double),
+    ]
+
+
+class LbchError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load liblbch.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise OSError(f"CUDA library not found at {path}")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    vp = ctypes.c_void_p
+    lib.lb_ch_init.argtypes = [P(lbch_params), ctypes.c_int, dp, ctypes.c_int, vp, P(vp)]
+    lib.lb_ch_step.argtypes = [vp, ctypes.c_long]
+    lib.lb_ch_observe.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    lib.lb_ch_observe_all.argtypes = [vp, ctypes.c_int, dp]
+    lib.lb_ch_free.argtypes = [vp]
+    lib.lb_ch_strerror.argtypes = [ctypes.c_int]
+    lib.lb_ch_strerror.restype = ctypes.c_char_p
+    lib.lb_ch_last_error.argtypes = []
+    lib.lb_ch_last_error.restype = ctypes.c_char_p
+    lib.lb_ch_info.argtypes = [vp, dp]
+    lib.lb_ch_stream.argtypes = [vp]
+    lib.lb_ch_stream.restype = vp
+    for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != LBCH_OK:
+        lib = load()
+        raise LbchError(status, where, lib.lb_ch_last_error().decode() or lib.lb_ch_strerror(status).decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_params(cfg) -> lbch_params:
+    p = lbch_params()
+    for name, ctype in lbch_params._fields_:
+        v = cfg[name]
+        setattr(p, name, int(v) if ctype is ctypes.c_int else float(v))
+    return p
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def lb_ch_init(params, phi0, prec=LBCH_F64, stream=None):
+    """params: one config dict or a list of them; phi0: one (ny, nx) array or a list.  Returns a handle."""
+    lib = load()
+    if isinstance(params, dict):
+        params, phi0 = [params], [phi0]
+    n = len(params)
+    arr = (lbch_params * n)(*[make_params(p) for p in params])
+    flat = np.ascontiguousarray(np.concatenate([np.ascontiguousarray(f, dtype=np.float64).ravel() for f in phi0]))
+    for p, f in zip(params, phi0):
+        if np.shape(f) != (p["ny"], p["nx"]):
+            raise ValueError(f"phi0 of shape {np.shape(f)} does not match ny x nx = {p['ny']} x {p['nx']}")
+    h = ctypes.c_void_p()
+    _check(lib.lb_ch_init(arr, n, _dptr(flat), int(prec), ctypes.c_void_p(stream or 0), ctypes.byref(h)),
+           "lb_ch_init")
+    return h
+
+
+def lb_ch_step(h, nsteps: int):
+    _check(load().lb_ch_step(h, int(nsteps)), "lb_ch_step")
+
+
+def lb_ch_observe(h, inst: int, what: int, shape=None):
+    if what == LBCH_OBS_PHI:
+        out = np.empty(shape, dtype=np.float64)
+    else:
+        out = np.empty(1, dtype=np.float64)
+    _check(load().lb_ch_observe(h, int(inst), int(what), _dptr(out)), "lb_ch_observe")
+    return out if what == LBCH_OBS_PHI else float(out[0])
+
+
+def lb_ch_observe_all(h, what: int, n_inst: int) -> np.ndarray:
+    out = np.empty(n_inst, dtype=np.float64)
+    _check(load().lb_ch_observe_all(h, int(what), _dptr(out)), "lb_ch_observe_all")
+    return out
+
+
+def lb_ch_free(h):
+    if h:
+        _check(load().lb_ch_free(h), "lb_ch_free")
+
+
+def lb_ch_info(h) -> dict:
+    out = np.zeros(4)
+    _check(load().lb_ch_info(h, _dptr(out)), "lb_ch_info")
+    return {"nodes": int(out[0]), "bytes_per_lu": out[1], "blocks": int(out[2]), "step": int(out[3])}
+
+
+def lb_ch_stream(h) -> int:
+    return load().lb_ch_stream(h) or 0
+
+
+# ----------------------------------------------------------------------------- convenience wrapper
+
+class Simulation:
+    """One handle: an instance or a ragged ensemble of instances advanced together."""
+
+    def __init__(self, params, phi0, prec="f64", stream=None):
+        self.params = [params] if isinstance(params, dict) else list(params)
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.h = lb_ch_init(self.params, [phi0] if isinstance(params, dict) else list(phi0), self.prec, stream)
+
+    def step(self, nsteps: int):
+        lb_ch_step(self.h, nsteps)
+        return self
+
+    def phi(self, inst: int = 0) -> np.ndarray:
+        p = self.params[inst]
+        return lb_ch_observe(self.h, inst, LBCH_OBS_PHI, (p["ny"], p["nx"]))
+
+    def observe(self, what: int, inst: int = 0) -> float:
+        return lb_ch_observe(self.h, inst, what)
+
+    def observe_all(self, what: int) -> np.ndarray:
+        return lb_ch_observe_all(self.h, what, len(self.params))
+
+    def info(self) -> dict:
+        return lb_ch_info(self.h)
+
+    def close(self):
+        if self.h:
+            lb_ch_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

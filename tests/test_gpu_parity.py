@@ -1,0 +1,176 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances (max |phi_gpu - phi_oracle| over every node):
+  FP64 path: 1e-12  (the same arithmetic in a different order, with FMA contraction on the GPU)
+  FP32 path: 1e-5   (single-precision state and arithmetic; the velocity tables are built in double)
+  F16S path: 2e-3 after 50 steps (half-precision populations; rounding of 2^-11 relative per step on
+             populations of size up to ~0.15, random-walk accumulated) -- see test_f16s_parity
+Sizes span several tiles (32 x 8 for FP64, 32 x 16 for FP32) with ragged tails in both directions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_00007_gb300 import abi
+from paper_1805_00007_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def _gpu(p, phi0, nsteps, prec):
+    with abi.Simulation(p, phi0, prec=prec) as sim:
+        sim.step(nsteps)
+        return sim.phi()
+
+
+def _maxdiff(a, b):
+    return float(np.max(np.abs(a - b)))
+
+
+def _cases():
+    n = 0
+    out = []
+    for vel in (wl.VEL_UNIFORM, wl.VEL_ROTATION, wl.VEL_VORTEX, wl.VEL_REV_SHEAR, wl.VEL_DEFORM, wl.VEL_SHEAR):
+        for model in (1, 2):
+            n += 1
+            out.append((vel, model, n))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("vel,model,seed", _cases())
+def test_small_grids_every_flow(prec, vel, model, seed):
+    nx, ny = 45, 37  # two tiles + ragged tail in x; several tiles + tail in y
+    walls = 1 if vel == wl.VEL_SHEAR else 0
+    p = wl.make_params(nx=nx, ny=ny, vel=vel, walls=walls, model=model, U0=0.03, ux0=0.03, uy0=-0.02,
+                       xc=22.0, yc=18.0, half=22.0, Tper=30.0, shear=2e-3, tau=0.85, M=0.02,
+                       sigma=0.02, W=3.0, rhoB=0.4, nvort=2)
+    phi0 = np.clip(wl.random_smooth_phi(nx, ny, seed) + 0.6 * wl.circle_phi(nx, ny, 20.3, 17.7, 9.0, 3.0) - 0.3,
+                   -0.2, 1.2)
+    nsteps = 50  # crosses the reversal time of the reversing shear
+    ref, _ = oracle.simulate(p, phi0, nsteps)
+    got = _gpu(p, phi0, nsteps, prec)
+    assert _maxdiff(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_zero_steps_is_initial_field(prec):
+    p, phi0, _ = wl.zalesak(n=40)
+    got = _gpu(p, phi0, 0, prec)
+    assert _maxdiff(got, phi0) <= (0.0 if prec == "f64" else 1e-7)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("nx,ny", [(4, 4), (5, 7), (33, 4), (4, 41), (64, 16), (31, 9)])
+def test_tiny_and_ragged_sizes(prec, nx, ny):
+    p = wl.make_params(nx=nx, ny=ny, vel=wl.VEL_ROTATION, U0=0.02, xc=nx / 2, yc=ny / 2, half=max(nx, ny) / 2,
+                       tau=1.0, M=0.02, sigma=0.02, W=3.0)
+    phi0 = wl.random_smooth_phi(nx, ny, seed=nx * 100 + ny)
+    ref, _ = oracle.simulate(p, phi0, 25)
+    assert _maxdiff(_gpu(p, phi0, 25, prec), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_translation_full_period(prec):
+    """The 100 x 100 diagonal translation for its whole period (2500 steps, CUDA graphs + tail steps)."""
+    p, phi0, T = wl.translation()
+    ref, _ = oracle.simulate(p, phi0, T)
+    with abi.Simulation(p, phi0, prec=prec) as sim:
+        sim.step(T)
+        got = sim.phi()
+        err = sim.observe(abi.LBCH_OBS_ERR_L2)
+        mass = sim.observe(abi.LBCH_OBS_MASS)
+        mx, mn = sim.observe(abi.LBCH_OBS_MAX), sim.observe(abi.LBCH_OBS_MIN)
+    assert _maxdiff(got, ref) <= TOL[prec]
+    ob = oracle.observe(ref, phi0)
+    assert abs(err - ob["err_l2"]) <= 0.01 * ob["err_l2"]
+    assert abs(mx - ob["max"]) <= TOL[prec] and abs(mn - ob["min"]) <= TOL[prec]
+    rel_mass = abs(mass - phi0.sum()) / phi0.sum()
+    assert rel_mass <= (1e-13 if prec == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_zalesak_full_grid(prec):
+    """256 x 256 Zalesak grid (the benchmark's launch configuration) for 200 steps."""
+    p, phi0, _ = wl.zalesak()
+    ref, _ = oracle.simulate(p, phi0, 200)
+    assert _maxdiff(_gpu(p, phi0, 200, prec), ref) <= TOL[prec]
+
+
+def test_single_vortex_full_grid():
+    p, phi0, _ = wl.single_vortex()
+    ref, _ = oracle.simulate(p, phi0, 30)
+    for prec in ("f64", "f32"):
+        assert _maxdiff(_gpu(p, phi0, 30, prec), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ragged_ensemble_matches_each_instance(prec):
+    """An ensemble of instances of different sizes and parameters in one launch equals each instance
+    simulated alone by the oracle."""
+    ens = wl.shear_ensemble(n_inst=7, sides=(16, 37, 64, 20), seed=5)
+    # make the shear visible at these small sizes
+    ens = [(dict(p, shear=p["shear"] * 40.0, Ustar=p["Ustar"] * 40.0), f) for p, f in ens]
+    params, fields = zip(*ens)
+    nsteps = 70
+    with abi.Simulation(list(params), list(fields), prec=prec) as sim:
+        sim.step(nsteps)
+        got = [sim.phi(k) for k in range(len(params))]
+        masses = sim.observe_all(abi.LBCH_OBS_MASS)
+    for k, (p, f) in enumerate(ens):
+        ref, _ = oracle.simulate(p, f, nsteps)
+        assert _maxdiff(got[k], ref) <= TOL[prec], k
+        assert abs(masses[k] - f.sum()) <= (1e-12 if prec == "f64" else 1e-4) * f.sum()
+
+
+def test_observables_match_oracle_definition():
+    p, phi0, _ = wl.zalesak(n=96)
+    ref, _ = oracle.simulate(p, phi0, 120)
+    ob = oracle.observe(ref, phi0)
+    with abi.Simulation(p, phi0, prec="f64") as sim:
+        sim.step(120)
+        assert abs(sim.observe(abi.LBCH_OBS_MASS) - ob["mass"]) <= 1e-11
+        assert abs(sim.observe(abi.LBCH_OBS_ERR_L2) - ob["err_l2"]) <= 1e-11
+        assert abs(sim.observe(abi.LBCH_OBS_MAX) - ob["max"]) <= 1e-12
+        assert abs(sim.observe(abi.LBCH_OBS_MIN) - ob["min"]) <= 1e-12
+        assert sim.observe(abi.LBCH_OBS_STEP) == 120
+        # reductions are deterministic: a second call gives the same bits
+        a = sim.observe(abi.LBCH_OBS_ERR_L2)
+        assert a == sim.observe(abi.LBCH_OBS_ERR_L2)
+
+
+def test_f16s_parity():
+    """Shifted half storage: phi in float, g_1..g_8 in half, g_0 implied by phi."""
+    p, phi0, _ = wl.zalesak(n=96)
+    ref, _ = oracle.simulate(p, phi0, 50)
+    with abi.Simulation(p, phi0, prec="f16s") as sim:
+        sim.step(50)
+        got = sim.phi()
+        mass = sim.observe(abi.LBCH_OBS_MASS)
+    assert _maxdiff(got, ref) <= 2e-3
+    assert abs(mass - phi0.sum()) <= 1e-5 * phi0.sum()
+
+
+def test_steps_split_across_calls_equal_one_call():
+    """Graph replays, single launches and their mix advance the same state (bitwise in FP64)."""
+    p, phi0, _ = wl.single_vortex(n=64, T=100)
+    with abi.Simulation(p, phi0, prec="f64") as a, abi.Simulation(p, phi0, prec="f64") as b:
+        a.step(131)
+        for k in (1, 64, 3, 63):
+            b.step(k)
+        assert np.array_equal(a.phi(), b.phi())
+
+
+def test_nonfinite_is_reported():
+    """A state that blows up (tau close to 1/2, huge velocity) is reported as LBCH_ENONFINITE."""
+    p = wl.make_params(nx=16, ny=16, vel=wl.VEL_UNIFORM, ux0=3.0, uy0=3.0, tau=0.5001, M=1.0, sigma=1.0, W=1.0)
+    phi0 = wl.random_smooth_phi(16, 16, seed=1, amp=2.0)
+    with abi.Simulation(p, phi0, prec="f64") as sim:
+        sim.step(400)
+        with pytest.raises(abi.LbchError) as ei:
+            sim.observe(abi.LBCH_OBS_MASS)
+        assert ei.value.status == abi.LBCH_ENONFINITE
