@@ -141,6 +141,50 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def sweep_params(n):
+    """A square rotation workload of side n (the Zalesak flow and parameters scaled to n)."""
+    pp = wl.make_params(nx=n, ny=n, vel=wl.VEL_ROTATION, U0=0.02, xc=n / 2, yc=n / 2, half=n / 2,
+                        W=4.0, M=0.005, tau=1.0)
+    return pp, wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
+
+
+def run_case(case, nsteps):
+    """One grid, no timing: the command ncu profiles."""
+    import torch
+    from paper_1805_00007_gb300 import abi
+    prec, n = case.split("_")
+    pp, f0 = sweep_params(int(n))
+    with abi.Simulation(pp, f0, prec=prec) as sim:
+        sim.step(nsteps)
+        torch.cuda.synchronize()
+        m = sim.observe(abi.LBCH_OBS_MASS)
+    print(json.dumps({"case": case, "steps": nsteps, "mass": m}))
+
+
+def accuracy(prec, p, phi0, nsteps):
+    """max |phi - phi_oracle| at the stored oracle sample nodes after the full run, and the relative
+    difference of ||E_phi||_2 (Eq. err); None when the stored oracle result is absent."""
+    path = os.path.join(ROOT, "tests", "golden", "zalesak_256.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        gold = json.load(fh)
+    if gold["nsteps"] != nsteps:
+        return None
+    from paper_1805_00007_gb300 import abi
+    with abi.Simulation(p, phi0, prec=prec) as sim:
+        sim.step(nsteps)
+        phi = sim.phi()
+        err = sim.observe(abi.LBCH_OBS_ERR_L2)
+        mass = sim.observe(abi.LBCH_OBS_MASS)
+    j, i = np.array(gold["nodes_j"]), np.array(gold["nodes_i"])
+    return {"max_abs_dphi_vs_oracle": float(np.max(np.abs(phi[j, i] - np.array(gold["phi"])))),
+            "err_l2": err, "err_l2_oracle": gold["err_l2"],
+            "err_l2_rel_diff": abs(err - gold["err_l2"]) / gold["err_l2"],
+            "mass_rel_drift": abs(mass - gold["mass0"]) / gold["mass0"],
+            "nodes_compared": int(j.size)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -149,9 +193,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="profiling case PREC_N (e.g. f32_4096): init and --case-steps steps of that grid only")
+    ap.add_argument("--case-steps", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args.case, args.case_steps)
 
     import torch
     import torch.distributed as dist
@@ -239,9 +288,7 @@ def main():
     sweep = {}
     if not args.no_sweep:
         for prec, n in (("f32", 4096), ("f64", 4096), ("f16s", 4096)):
-            pp = wl.make_params(nx=n, ny=n, vel=wl.VEL_ROTATION, U0=0.02, xc=n / 2, yc=n / 2, half=n / 2,
-                                W=4.0, M=0.005, tau=1.0)
-            f0 = wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
+            pp, f0 = sweep_params(n)
             sim = abi.Simulation(pp, f0, prec=prec, stream=stream.cuda_stream)
             sim.step(64)
             torch.cuda.synchronize()
@@ -259,6 +306,8 @@ def main():
                                    "frac": gbs / hbm_peak}
             sim.close()
 
+
+    acc = {prec: accuracy(prec, p, phi0, rev) for prec in ("f32", "f64", "f16s")} if rank == 0 else {}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -282,6 +331,7 @@ def main():
                          "kernel": "ch_step_kernel<float,float,float,32,16,256>",
                          "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6},
             "sweep_4096": sweep,
+            "accuracy_one_revolution": acc,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
                     "d2h_bytes_per_step": phi0.nbytes},
             "gpu_launches": args.steps * rev,

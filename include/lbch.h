@@ -42,9 +42,12 @@ typedef enum {
 
 /* Storage and arithmetic precision of the lattice state.
  *   LBCH_F64  : g and phi stored in double, double arithmetic.
- *   LBCH_F32  : g and phi stored in float, float arithmetic (velocity tables built in double).
+ *   LBCH_F32  : shifted float storage -- g_1..g_8 and g_0 - phi stored in float, phi in double; float
+ *               arithmetic on these small quantities, phi(t+1) = phi(t) + (float increment) summed in
+ *               double (velocity tables built in double).  88 bytes per lattice update.
  *   LBCH_F16S : shifted half storage -- phi kept in float, g_1..g_8 stored in half, g_0 not stored but
- *               recovered as phi - sum_{i>0} g_i, so sum_i g_i = phi holds exactly; float arithmetic. */
+ *               recovered as phi - sum_{i>0} g_i, so sum_i g_i = phi holds exactly; float arithmetic.
+ *               40 bytes per lattice update. */
 typedef enum { LBCH_F64 = 0, LBCH_F32 = 1, LBCH_F16S = 2 } lbch_prec;
 
 /* Prescribed velocity fields u(x, y, t) of the benchmark problems (paper Sec. III).
@@ -130,14 +133,22 @@ lbch_status lb_ch_free(lbch_handle* h);
 const char* lb_ch_strerror(lbch_status s);
 const char* lb_ch_last_error(void);
 
-/* Device timing of the most recent lb_ch_step call's kernels is not tracked by the library; these two
- * entry points expose what a caller needs to time or inspect the hot kernel directly.
- * lb_ch_info: out[0] = total lattice nodes, out[1] = algorithmic HBM bytes per lattice update of the
- * step kernel, out[2] = number of thread blocks of one step launch, out[3] = current step index. */
+/* Sizes for a caller who times the step kernel itself: out[0] = total lattice nodes, out[1] = algorithmic
+ * HBM bytes per lattice update of the step kernel (one read and one write of the stored populations and
+ * of phi), out[2] = persistent thread blocks of one step launch, out[3] = current step index. */
 lbch_status lb_ch_info(lbch_handle* h, double* out);
 
 /* The CUDA stream the handle enqueues on (a cudaStream_t). */
 void* lb_ch_stream(lbch_handle* h);
+
+/* Test hook for the failure path of the step kernel's bounded waits.  With hook
+ * LBCH_HOOK_SKIP_FIRST_LOAD and value != 0, the next step launches run without CUDA graphs and their
+ * first thread block never issues its first tile copy, so its bounded wait runs out (after about a
+ * second); the kernel then returns cleanly and the next lb_ch_observe reports LBCH_ETIMEOUT.  The
+ * handle's state is not advanced correctly afterwards and should be freed.  Not for production use. */
+enum { LBCH_HOOK_SKIP_FIRST_LOAD = 1 };
+lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
+
 
 #ifdef __cplusplus
 }

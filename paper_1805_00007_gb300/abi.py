@@ -19,7 +19,8 @@ PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
 
 # Exported symbols, as declared in include/lbch.h.
 SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free",
-           "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream")
+           "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream", "lb_ch_test_hook")
+LBCH_HOOK_SKIP_FIRST_LOAD = 1
 
 
 class lbch_params(ctypes.Structure):
@@ -69,7 +70,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_info.argtypes = [vp, dp]
     lib.lb_ch_stream.argtypes = [vp]
     lib.lb_ch_stream.restype = vp
-    for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info"):
+    lib.lb_ch_test_hook.argtypes = [vp, ctypes.c_int, ctypes.c_long]
+    for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
+                 "lb_ch_test_hook"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -139,7 +142,11 @@ def lb_ch_free(h):
 def lb_ch_info(h) -> dict:
     out = np.zeros(4)
     _check(load().lb_ch_info(h, _dptr(out)), "lb_ch_info")
-    return {"nodes": int(out[0]), "bytes_per_lu": out[1], "blocks": int(out[2]), "step": int(out[3])}
+    return {"nodes": int(out[0]), "bytes_per_lu": out[1], "grid": int(out[2]), "step": int(out[3])}
+
+
+def lb_ch_test_hook(h, hook: int, value: int):
+    _check(load().lb_ch_test_hook(h, int(hook), int(value)), "lb_ch_test_hook")
 
 
 def lb_ch_stream(h) -> int:

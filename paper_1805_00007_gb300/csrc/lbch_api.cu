@@ -1,18 +1,19 @@
 // lbch_api.cu -- host runtime of the C ABI declared in include/lbch.h.
 //
-// Owns the device state of a handle (ping-pong population planes and phi, the instance table, the step
-// counter, reduction scratch), derives the model constants from the parameters (Eqs. betakappa, rho,
-// F2-1, the mobility relation after Eq. phit3 and the Peclet number of Sec. III.A), launches the step
-// kernel -- replayed from CUDA graphs of 64 steps -- and the reductions behind lb_ch_observe.
+// Owns the device state of a handle: ping-pong population and phi arrays in the padded image layout,
+// the instance table, the separable velocity tables, the TMA tensor maps, the step counter and the
+// reduction scratch.  It derives the model constants from the parameters (Eqs. betakappa, rho, F2-1,
+// the mobility relation after Eq. phit3 and the Peclet number of Sec. III.A), launches the persistent
+// step kernel -- replayed from CUDA graphs of 64 steps -- and the reductions behind lb_ch_observe.
 #include "lbch.h"
 #include "lbch_kernels.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -33,7 +34,7 @@ lbch_status fail(lbch_status s, const char* fmt, ...)
 
 lbch_status cuda_fail(cudaError_t e, const char* what)
 {
-    cudaGetLastError();  // clear a sticky-free error so later calls on this thread are not confused
+    cudaGetLastError();  // clear a non-sticky error so later calls on this thread start clean
     return fail(e == cudaErrorMemoryAllocation ? LBCH_ENOMEM : LBCH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -45,10 +46,28 @@ lbch_status cuda_fail(cudaError_t e, const char* what)
 
 constexpr int kGraphChunk = 64;  // steps per captured graph (even, so the ping-pong parity is preserved)
 
-// Tile shapes of the step kernel per precision (output nodes per block; 256 threads).
+// Tile shapes of the step kernel per precision (output nodes per tile) and threads per CTA.
 constexpr int TX64 = 32, TY64 = 8;
 constexpr int TX32 = 32, TY32 = 16;
+constexpr int TX16 = 32, TY16 = 16;
 constexpr int NT = 256;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
 
 }  // namespace
 
@@ -59,60 +78,85 @@ struct lbch_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<InstDev> inst;
+    std::vector<long long> node_begin;  // first linear node index of each instance (+ total)
     InstDev* d_inst = nullptr;
-    long long plane = 0;        // elements per population plane (all instances, padded)
-    long long nodes = 0;        // lattice nodes (all instances, unpadded)
-    int total_tiles = 0;
-    int n_planes = 9;           // stored population planes
+    long long* d_node_begin = nullptr;
+    double* d_tabs = nullptr;   // velocity tables in double (init kernel, FP64 step)
+    float* d_tabs_f = nullptr;  // the same tables in float (float step kernels)
+    int pitch = 0;              // elements per stored row
+    int rows = 0;               // stored rows of all instances
+    int nq = 9;                 // stored population planes
+    int tx = 0, ty = 0;
     size_t g_elem = 8, phi_elem = 8;
+    long long nodes = 0;        // lattice nodes (all instances)
+    int total_tiles = 0;
+    int grid = 0;               // persistent CTAs per step launch
     void* g[2] = {nullptr, nullptr};
     void* phi[2] = {nullptr, nullptr};
-    double* phi0 = nullptr;     // initial field, double, pitched like phi
+    float* lo[2] = {nullptr, nullptr};  // low part of phi (float path)
+    double* phi0 = nullptr;     // initial field, double, padded layout
+    CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
     Ctl* ctl = nullptr;
     double* partials = nullptr; // reduction scratch: n_inst * chunks * RED_NV doubles
     double* result = nullptr;   // n_inst * RED_NV doubles
     int chunks = 0;
     long long n = 0;            // host mirror of the step index
+    int debug_skip = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    double* h_stage = nullptr;  // pinned host staging for observations
+    double* h_stage = nullptr;  // pinned host staging
     size_t h_stage_bytes = 0;
 };
 
 namespace {
 
+template <typename C> const C* tables(lbch_handle* h);
+template <> const double* tables<double>(lbch_handle* h) { return h->d_tabs; }
+template <> const float* tables<float>(lbch_handle* h) { return h->d_tabs_f; }
+
 template <typename C, typename S, typename P, int TX, int TY>
 cudaError_t launch_step_t(lbch_handle* h, int parity)
 {
-    using L = TileSmem<TX, TY, C>;
-    auto kern = ch_step_kernel<C, S, P, TX, TY, NT>;
-    StepArgs<S, P> a;
+    using L = StepShape<C, S, P, TX, TY>;
+    StepArgs<C, S, P> a;
     a.inst = h->d_inst;
+    a.tabs = tables<C>(h);
     a.n_inst = h->n_inst;
     a.total_tiles = h->total_tiles;
-    a.plane = h->plane;
-    a.g_in = static_cast<const S*>(h->g[parity]);
+    a.pitch = h->pitch;
+    a.debug_skip = h->debug_skip;
     a.g_out = static_cast<S*>(h->g[parity ^ 1]);
-    a.phi_in = static_cast<const P*>(h->phi[parity]);
     a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
+    a.lo_out = h->lo[parity ^ 1];
     a.ctl = h->ctl;
-    kern<<<h->total_tiles, NT, L::bytes, h->stream>>>(a);
+    ch_step_kernel<C, S, P, TX, TY, NT><<<h->grid, NT, L::BYTES, h->stream>>>(h->tm_g[parity], h->tm_phi[parity],
+                                                                              h->tm_lo[parity], a);
     return cudaGetLastError();
 }
 
-// Allow the step kernel of this handle's precision its dynamic shared memory (on the current device).
+// Dynamic shared memory of the step kernel, and the persistent grid that fits the device.
 template <typename C, typename S, typename P, int TX, int TY>
-cudaError_t prepare_step_t()
+cudaError_t prepare_step_t(lbch_handle* h)
 {
-    return cudaFuncSetAttribute(ch_step_kernel<C, S, P, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TileSmem<TX, TY, C>::bytes);
+    using L = StepShape<C, S, P, TX, TY>;
+    auto kern = ch_step_kernel<C, S, P, TX, TY, NT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    h->grid = std::max(1, std::min(h->total_tiles, per_sm * sms));
+    return cudaSuccess;
 }
 
-cudaError_t prepare_step(int prec)
+cudaError_t prepare_step(lbch_handle* h)
 {
-    switch (prec) {
-    case LBCH_F64: return prepare_step_t<double, double, double, TX64, TY64>();
-    case LBCH_F32: return prepare_step_t<float, float, float, TX32, TY32>();
-    default: return prepare_step_t<float, __half, float, TX32, TY32>();
+    switch (h->prec) {
+    case LBCH_F64: return prepare_step_t<double, double, double, TX64, TY64>(h);
+    case LBCH_F32: return prepare_step_t<float, float, float, TX32, TY32>(h);
+    default: return prepare_step_t<float, __half, float, TX16, TY16>(h);
     }
 }
 
@@ -121,13 +165,15 @@ cudaError_t launch_step(lbch_handle* h, int parity)
     switch (h->prec) {
     case LBCH_F64: return launch_step_t<double, double, double, TX64, TY64>(h, parity);
     case LBCH_F32: return launch_step_t<float, float, float, TX32, TY32>(h, parity);
-    default: return launch_step_t<float, __half, float, TX32, TY32>(h, parity);
+    default: return launch_step_t<float, __half, float, TX16, TY16>(h, parity);
     }
 }
 
 void tile_shape(int prec, int& tx, int& ty)
 {
-    if (prec == LBCH_F64) { tx = TX64; ty = TY64; } else { tx = TX32; ty = TY32; }
+    if (prec == LBCH_F64) { tx = TX64; ty = TY64; }
+    else if (prec == LBCH_F32) { tx = TX32; ty = TY32; }
+    else { tx = TX16; ty = TY16; }
 }
 
 lbch_status check_params(const lbch_params& p, int k)
@@ -153,19 +199,75 @@ void derive(const lbch_params& p, InstDev& d)
 {
     const double cs2 = 1.0 / 3.0;
     const double dphi = std::fabs(p.phiA - p.phiB);
-    d.beta = 12.0 * p.sigma / (p.W * dphi * dphi * dphi * dphi);      // Eq. betakappa
-    d.kappa = 3.0 * p.sigma * p.W / (2.0 * dphi * dphi);
+    Consts<double>& c = d.cd;
+    c.beta = 12.0 * p.sigma / (p.W * dphi * dphi * dphi * dphi);      // Eq. betakappa
+    c.kappa = 3.0 * p.sigma * p.W / (2.0 * dphi * dphi);
     double M = p.M > 0.0 ? p.M
-                         : p.Ustar * p.W / (p.Pe * d.beta * (p.phiA - p.phiB) * (p.phiA - p.phiB));  // Pe, Sec. III.A
-    d.eta = M / (cs2 * (p.tau - 0.5));                                  // M = c_s^2 eta (tau - 1/2)
-    d.a = (p.rhoA - p.rhoB) / (p.phiA - p.phiB);                        // Eq. rho
-    d.b = (p.rhoB * p.phiA - p.phiB * p.rhoA) / (p.phiA - p.phiB);
-    d.K = (p.tau - 1.0 / 6.0 - p.tau * p.tau) / (p.tau - 0.5);          // Eq. F2-1
-    d.tau = p.tau;
-    d.phiA = p.phiA; d.phiB = p.phiB;
-    d.U0 = p.U0; d.ux0 = p.ux0; d.uy0 = p.uy0; d.xc = p.xc; d.yc = p.yc; d.half = p.half;
-    d.Tper = p.Tper; d.shear = p.shear;
-    d.walls = p.walls; d.model = p.model; d.vel = p.vel; d.nvort = p.nvort;
+                         : p.Ustar * p.W / (p.Pe * c.beta * (p.phiA - p.phiB) * (p.phiA - p.phiB));  // Pe, Sec. III.A
+    c.eta = M / (cs2 * (p.tau - 0.5));                                  // M = c_s^2 eta (tau - 1/2)
+    c.a = (p.rhoA - p.rhoB) / (p.phiA - p.phiB);                        // Eq. rho
+    c.b = (p.rhoB * p.phiA - p.phiB * p.rhoA) / (p.phiA - p.phiB);
+    c.K = (p.tau - 1.0 / 6.0 - p.tau * p.tau) / (p.tau - 0.5);          // Eq. F2-1
+    c.itau = 1.0 / p.tau;
+    c.omt = 1.0 - 1.0 / p.tau;
+    c.src = 1.0 - 1.0 / (2.0 * p.tau);
+    c.phiA = p.phiA; c.phiB = p.phiB;
+    Consts<float>& f = d.cf;
+    f.beta = (float)c.beta; f.kappa = (float)c.kappa; f.eta = (float)c.eta; f.a = (float)c.a; f.b = (float)c.b;
+    f.K = (float)c.K; f.phiA = (float)c.phiA; f.phiB = (float)c.phiB;
+    f.itau = (float)c.itau; f.omt = (float)c.omt; f.src = (float)c.src;
+    d.Tper = p.Tper;
+    d.walls = p.walls; d.model = p.model; d.vel = p.vel;
+}
+
+// The prescribed flows are separable: ux = X1(x) Y1(y) T(t), uy = X2(x) Y2(y) T(t).  The tables are
+// indexed like the stored arrays: X1, X2 by stored column (domain x = column - GC, periodic images in
+// the ghost columns), Y1, Y2 by row of the instance's stored band (domain y = row - GR; periodic or
+// mirror images in the ghost rows, matching the stored phi), then Y1, Y2 at the walls y = -1/2, ny - 1/2.
+void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<double>& t)
+{
+    const double pi = 3.14159265358979323846;
+    const double Lx = (double)p.nx, Ly = (double)p.ny;
+    auto X = [&](double x, double& X1, double& X2) {
+        switch (p.vel) {
+        case LBCH_VEL_UNIFORM: X1 = 1.0; X2 = 1.0; break;
+        case LBCH_VEL_ROTATION: X1 = 1.0; X2 = p.U0 * pi * (x - p.xc) / p.half; break;
+        case LBCH_VEL_VORTEX: { double s = std::sin(pi * x / Lx); X1 = -p.U0 * s * s; X2 = p.U0 * std::sin(2.0 * pi * x / Lx); break; }
+        case LBCH_VEL_SHEAR: X1 = 1.0; X2 = 0.0; break;
+        case LBCH_VEL_REV_SHEAR: X1 = -p.U0 * pi * std::cos(pi * (x / Lx - 0.5)); X2 = p.U0 * pi * std::sin(pi * (x / Lx - 0.5)); break;
+        default: { double k = (double)p.nvort * pi; X1 = -p.U0 * std::sin(k * (x / Lx + 0.5)); X2 = -p.U0 * std::cos(k * (x / Lx + 0.5)); }
+        }
+    };
+    auto Y = [&](double y, double& Y1, double& Y2) {
+        switch (p.vel) {
+        case LBCH_VEL_UNIFORM: Y1 = p.ux0; Y2 = p.uy0; break;
+        case LBCH_VEL_ROTATION: Y1 = -p.U0 * pi * (y - p.yc) / p.half; Y2 = 1.0; break;
+        case LBCH_VEL_VORTEX: { double s = std::sin(pi * y / Ly); Y1 = std::sin(2.0 * pi * y / Ly); Y2 = s * s; break; }
+        case LBCH_VEL_SHEAR: Y1 = p.shear * (y - 0.5 * (double)(p.ny - 1)); Y2 = 0.0; break;
+        case LBCH_VEL_REV_SHEAR: Y1 = std::sin(pi * (y / Lx - 0.5)); Y2 = std::cos(pi * (y / Lx - 0.5)); break;
+        default: { double k = (double)p.nvort * pi; Y1 = std::sin(k * (y / Lx + 0.5)); Y2 = std::cos(k * (y / Lx + 0.5)); }
+        }
+    };
+    size_t b = t.size();
+    t.resize(b + 2 * (size_t)pitch + 2 * (size_t)ylen + 4, 0.0);
+    double* X1 = &t[b];
+    double* X2 = X1 + pitch;
+    double* Y1 = X2 + pitch;
+    double* Y2 = Y1 + ylen;
+    double* W = Y2 + ylen;
+    for (int col = 0; col < pitch; col++) {
+        int x = col - GC;
+        if (x < -GC || x >= p.nx + GC) continue;
+        X((double)(((x % p.nx) + p.nx) % p.nx), X1[col], X2[col]);
+    }
+    for (int k = 0; k < ylen; k++) {
+        int y = k - GR;
+        if (y < -GR || y >= p.ny + GR) continue;
+        int yy = p.walls ? (y < 0 ? -1 - y : (y >= p.ny ? 2 * p.ny - 1 - y : y)) : ((y % p.ny) + p.ny) % p.ny;
+        Y((double)yy, Y1[k], Y2[k]);
+    }
+    Y(-0.5, W[0], W[2]);
+    Y((double)p.ny - 0.5, W[1], W[3]);
 }
 
 void release(lbch_handle* h)
@@ -174,8 +276,12 @@ void release(lbch_handle* h)
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
         if (h->g[k]) cudaFree(h->g[k]);
         if (h->phi[k]) cudaFree(h->phi[k]);
+        if (h->lo[k]) cudaFree(h->lo[k]);
     }
     if (h->d_inst) cudaFree(h->d_inst);
+    if (h->d_tabs_f) cudaFree(h->d_tabs_f);
+    if (h->d_node_begin) cudaFree(h->d_node_begin);
+    if (h->d_tabs) cudaFree(h->d_tabs);
     if (h->phi0) cudaFree(h->phi0);
     if (h->ctl) cudaFree(h->ctl);
     if (h->partials) cudaFree(h->partials);
@@ -195,14 +301,60 @@ lbch_status stage(lbch_handle* h, size_t bytes)
     return LBCH_OK;
 }
 
+lbch_status encode_maps(lbch_handle* h)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(LBCH_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    CUtensorMapDataType gt = h->prec == LBCH_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : (h->prec == LBCH_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    CUtensorMapDataType pt = h->phi_elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    for (int k = 0; k < 2; k++) {
+        cuuint64_t gdim[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->nq, (cuuint64_t)h->rows};
+        cuuint64_t gstr[2] = {(cuuint64_t)h->pitch * h->g_elem, (cuuint64_t)h->pitch * h->g_elem * h->nq};
+        cuuint32_t gbox[3] = {(cuuint32_t)(h->tx + 8), (cuuint32_t)h->nq, (cuuint32_t)(h->ty + 2)};
+        cuuint32_t es[3] = {1, 1, 1};
+        CUresult r = enc(&h->tm_g[k], gt, 3, h->g[k], gdim, gstr, gbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of the populations: CUresult %d", (int)r);
+        cuuint64_t pdim[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->rows};
+        cuuint64_t pstr[1] = {(cuuint64_t)h->pitch * h->phi_elem};
+        cuuint32_t pbox[2] = {(cuuint32_t)(h->tx + 8), (cuuint32_t)(h->ty + 6)};
+        r = enc(&h->tm_phi[k], pt, 2, h->phi[k], pdim, pstr, pbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of phi: CUresult %d", (int)r);
+        if (h->lo[k]) {
+            cuuint32_t lbox[2] = {(cuuint32_t)h->tx, (cuuint32_t)h->ty};
+            cuuint64_t lstr[1] = {(cuuint64_t)h->pitch * 4};
+            r = enc(&h->tm_lo[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->lo[k], pdim, lstr, lbox, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of phi (low part): CUresult %d", (int)r);
+        } else {
+            h->tm_lo[k] = h->tm_phi[k];  // unused by the kernels without a low part
+        }
+    }
+    return LBCH_OK;
+}
+
+lbch_status check_err(lbch_handle* h)
+{
+    unsigned int err = 0;
+    CK(cudaMemcpyAsync(&err, &h->ctl->err, sizeof err, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (err) return fail(LBCH_ETIMEOUT, "a bounded wait for a TMA copy in the step kernel ran out (flags %u)", err);
+    return LBCH_OK;
+}
+
 lbch_status run_reduce(lbch_handle* h)
 {
     int parity = (int)(h->n & 1);
     dim3 grid(h->chunks, h->n_inst);
-    if (h->prec == LBCH_F64)
-        reduce_partials_kernel<double><<<grid, RED_NT, 0, h->stream>>>(h->d_inst, (const double*)h->phi[parity], h->phi0, h->partials, h->chunks);
+    if (h->phi_elem == 8)
+        reduce_partials_kernel<double><<<grid, RED_NT, 0, h->stream>>>(h->d_inst, (const double*)h->phi[parity], nullptr, h->phi0,
+                                                                       h->pitch, h->partials, h->chunks);
     else
-        reduce_partials_kernel<float><<<grid, RED_NT, 0, h->stream>>>(h->d_inst, (const float*)h->phi[parity], h->phi0, h->partials, h->chunks);
+        reduce_partials_kernel<float><<<grid, RED_NT, 0, h->stream>>>(h->d_inst, (const float*)h->phi[parity], h->lo[parity], h->phi0,
+                                                                      h->pitch, h->partials, h->chunks);
     CK(cudaGetLastError());
     reduce_final_kernel<<<h->n_inst, RED_NT, 0, h->stream>>>(h->partials, h->chunks, h->result);
     CK(cudaGetLastError());
@@ -229,15 +381,15 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     h->prec = prec;
     h->n_inst = n_inst;
     h->g_elem = prec == LBCH_F64 ? 8 : (prec == LBCH_F32 ? 4 : 2);
-    h->phi_elem = prec == LBCH_F64 ? 8 : 4;
-    h->n_planes = prec == LBCH_F16S ? 8 : 9;
-    int tx, ty;
-    tile_shape(prec, tx, ty);
+    h->phi_elem = prec == LBCH_F64 ? 8 : 4;  // the float path adds a float low part
+    h->nq = prec == LBCH_F16S ? 8 : 9;
+    tile_shape(prec, h->tx, h->ty);
 
-    // instance table: rows padded to 32 elements, each instance's block aligned to 64 elements
+    // layout: uniform pitch; instance k takes ny_k + 2 GR stored rows
     h->inst.resize(n_inst);
-    long long off = 0;
-    int tiles = 0;
+    h->node_begin.resize(n_inst + 1);
+    std::vector<double> tabs;
+    int tiles = 0, row = 0, max_w = 0;
     for (int k = 0; k < n_inst; k++) {
         const lbch_params& p = params[k];
         InstDev& d = h->inst[k];
@@ -245,17 +397,25 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         derive(p, d);
         d.nx = p.nx;
         d.ny = p.ny;
-        d.pitch = (p.nx + 31) / 32 * 32;
-        d.off = off;
-        d.tiles_x = (p.nx + tx - 1) / tx;
-        d.tiles_y = (p.ny + ty - 1) / ty;
+        d.row0 = row + GR;
+        d.tiles_x = (p.nx + h->tx - 1) / h->tx;
+        d.tiles_y = (p.ny + h->ty - 1) / h->ty;
         d.tile_begin = tiles;
         tiles += d.tiles_x * d.tiles_y;
-        off += ((long long)d.pitch * p.ny + 63) / 64 * 64;
+        row += p.ny + 2 * GR;
+        max_w = std::max(max_w, d.tiles_x * h->tx);
+        h->node_begin[k] = h->nodes;
         h->nodes += (long long)p.nx * p.ny;
     }
-    h->plane = off;
+    h->node_begin[n_inst] = h->nodes;
+    h->rows = row;
+    h->pitch = (max_w + 8 + 7) / 8 * 8;  // boxes reach 4 columns past the last tile; 16-byte rows for half
     h->total_tiles = tiles;
+    for (int k = 0; k < n_inst; k++) {
+        h->inst[k].tab = (int)tabs.size();
+        velocity_tables(params[k], h->pitch, h->inst[k].tiles_y * h->ty + 2 * GR, tabs);
+    }
+    std::vector<float> tabs_f(tabs.begin(), tabs.end());
 
     auto bail = [&](lbch_status s) { release(h); delete h; return s; };
     cudaError_t e;
@@ -265,21 +425,26 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         if (e != cudaSuccess) return bail(cuda_fail(e, #call));      \
     } while (0)
     CKI(cudaGetDevice(&h->device));
-    CKI(prepare_step(prec));
+    CKI(prepare_step(h));
     if (stream) {
         h->stream = static_cast<cudaStream_t>(stream);
     } else {
         CKI(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
         h->own_stream = true;
     }
-    size_t gbytes = (size_t)h->plane * h->n_planes * h->g_elem;
-    size_t pbytes = (size_t)h->plane * h->phi_elem;
+    const size_t cells = (size_t)h->rows * h->pitch;
+    const size_t gbytes = cells * h->nq * h->g_elem;
+    const size_t pbytes = cells * h->phi_elem;
     for (int k = 0; k < 2; k++) {
         CKI(cudaMalloc(&h->g[k], gbytes));
         CKI(cudaMalloc(&h->phi[k], pbytes));
+        if (prec == LBCH_F32) CKI(cudaMalloc(&h->lo[k], cells * sizeof(float)));
     }
-    CKI(cudaMalloc(&h->phi0, (size_t)h->plane * sizeof(double)));
+    CKI(cudaMalloc(&h->phi0, cells * sizeof(double)));
     CKI(cudaMalloc(&h->d_inst, sizeof(InstDev) * n_inst));
+    CKI(cudaMalloc(&h->d_node_begin, sizeof(long long) * (n_inst + 1)));
+    CKI(cudaMalloc(&h->d_tabs, sizeof(double) * tabs.size()));
+    CKI(cudaMalloc(&h->d_tabs_f, sizeof(float) * tabs_f.size()));
     CKI(cudaMalloc(&h->ctl, sizeof(Ctl)));
     long long max_nodes = 0;
     for (auto& d : h->inst) max_nodes = std::max(max_nodes, (long long)d.nx * d.ny);
@@ -287,41 +452,53 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     if (h->chunks < 1) h->chunks = 1;
     CKI(cudaMalloc(&h->partials, sizeof(double) * RED_NV * (size_t)h->chunks * n_inst));
     CKI(cudaMalloc(&h->result, sizeof(double) * RED_NV * (size_t)n_inst));
+    lbch_status st = encode_maps(h);
+    if (st != LBCH_OK) return bail(st);
 
-    // upload the initial field, pitched, through pinned staging
-    lbch_status s = stage(h, (size_t)h->plane * sizeof(double));
-    if (s != LBCH_OK) return bail(s);
-    std::memset(h->h_stage, 0, (size_t)h->plane * sizeof(double));
+    // the initial field in the padded layout, ghost frame included, through pinned staging
+    st = stage(h, cells * sizeof(double));
+    if (st != LBCH_OK) return bail(st);
+    std::memset(h->h_stage, 0, cells * sizeof(double));
     const double* src = phi0;
     for (int k = 0; k < n_inst; k++) {
         const InstDev& d = h->inst[k];
-        for (int j = 0; j < d.ny; j++)
-            std::memcpy(h->h_stage + d.off + (long long)j * d.pitch, src + (long long)j * d.nx, sizeof(double) * d.nx);
-        src += (long long)d.nx * d.ny;
+        for (int y = -GR; y < d.ny + GR; y++) {
+            int yy;
+            if (d.walls) yy = y < 0 ? -1 - y : (y >= d.ny ? 2 * d.ny - 1 - y : y);
+            else yy = ((y % d.ny) + d.ny) % d.ny;
+            yy = std::min(std::max(yy, 0), d.ny - 1);
+            double* rowp = h->h_stage + (size_t)(d.row0 + y) * h->pitch + GC;
+            for (int x = -GC; x < d.nx + GC; x++) rowp[x] = src[(size_t)yy * d.nx + (((x % d.nx) + d.nx) % d.nx)];
+        }
+        src += (size_t)d.nx * d.ny;
     }
-    CKI(cudaMemcpyAsync(h->phi0, h->h_stage, (size_t)h->plane * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CKI(cudaMemcpyAsync(h->phi0, h->h_stage, cells * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CKI(cudaMemcpyAsync(h->d_inst, h->inst.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice, h->stream));
+    CKI(cudaMemcpyAsync(h->d_node_begin, h->node_begin.data(), sizeof(long long) * (n_inst + 1), cudaMemcpyHostToDevice, h->stream));
+    CKI(cudaMemcpyAsync(h->d_tabs, tabs.data(), sizeof(double) * tabs.size(), cudaMemcpyHostToDevice, h->stream));
+    CKI(cudaMemcpyAsync(h->d_tabs_f, tabs_f.data(), sizeof(float) * tabs_f.size(), cudaMemcpyHostToDevice, h->stream));
     CKI(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
     for (int k = 0; k < 2; k++) {
         CKI(cudaMemsetAsync(h->g[k], 0, gbytes, h->stream));
         CKI(cudaMemsetAsync(h->phi[k], 0, pbytes, h->stream));
+        if (h->lo[k]) CKI(cudaMemsetAsync(h->lo[k], 0, cells * sizeof(float), h->stream));
     }
-    int nb = (int)((h->plane + 255) / 256);
+    int nb = (int)((h->nodes + 255) / 256);
     switch (prec) {
     case LBCH_F64:
-        init_kernel<double, double, double><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->phi0, h->plane,
-                                                                     (double*)h->g[0], (double*)h->phi[0], h->plane);
+        init_kernel<double, double, double><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->d_tabs, h->phi0, h->pitch,
+            h->ty, (double*)h->g[0], (double*)h->phi[0], nullptr, h->nodes, h->d_node_begin);
         break;
     case LBCH_F32:
-        init_kernel<float, float, float><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->phi0, h->plane,
-                                                                  (float*)h->g[0], (float*)h->phi[0], h->plane);
+        init_kernel<float, float, float><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->d_tabs, h->phi0, h->pitch,
+            h->ty, (float*)h->g[0], (float*)h->phi[0], h->lo[0], h->nodes, h->d_node_begin);
         break;
     default:
-        init_kernel<float, __half, float><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->phi0, h->plane,
-                                                                   (__half*)h->g[0], (float*)h->phi[0], h->plane);
+        init_kernel<float, __half, float><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->d_tabs, h->phi0, h->pitch,
+            h->ty, (__half*)h->g[0], (float*)h->phi[0], nullptr, h->nodes, h->d_node_begin);
     }
     CKI(cudaGetLastError());
-    CKI(cudaStreamSynchronize(h->stream));  // the pinned staging buffer is reused after this point
+    CKI(cudaStreamSynchronize(h->stream));  // the pinned staging buffer and the tables are reused after this
 #undef CKI
     *out = h;
     return LBCH_OK;
@@ -333,7 +510,7 @@ lbch_status lb_ch_step(lbch_handle* h, long nsteps)
     static const bool no_graph = std::getenv("LBCH_NO_GRAPH") != nullptr;
     while (nsteps > 0) {
         int parity = (int)(h->n & 1);
-        if (!no_graph && nsteps >= kGraphChunk) {
+        if (!no_graph && !h->debug_skip && nsteps >= kGraphChunk) {
             if (!h->graph[parity]) {
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -371,17 +548,25 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out)
         int parity = (int)(h->n & 1);
         lbch_status s = stage(h, (size_t)d.nx * d.ny * sizeof(double));
         if (s != LBCH_OK) return s;
-        const char* base = static_cast<const char*>(h->phi[parity]) + (size_t)d.off * h->phi_elem;
-        CK(cudaMemcpy2DAsync(h->h_stage, (size_t)d.nx * h->phi_elem, base, (size_t)d.pitch * h->phi_elem,
+        const size_t off = (size_t)d.row0 * h->pitch + GC;
+        const char* base = static_cast<const char*>(h->phi[parity]) + off * h->phi_elem;
+        CK(cudaMemcpy2DAsync(h->h_stage, (size_t)d.nx * h->phi_elem, base, (size_t)h->pitch * h->phi_elem,
                              (size_t)d.nx * h->phi_elem, d.ny, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
+        float* lo_host = nullptr;
+        if (h->lo[parity]) {  // the low part goes to the upper half of the staging buffer
+            lo_host = reinterpret_cast<float*>(h->h_stage) + (size_t)d.nx * d.ny;
+            CK(cudaMemcpy2DAsync(lo_host, (size_t)d.nx * 4, h->lo[parity] + off, (size_t)h->pitch * 4,
+                                 (size_t)d.nx * 4, d.ny, cudaMemcpyDeviceToHost, h->stream));
+        }
+        s = check_err(h);  // synchronises the stream
+        if (s != LBCH_OK) return s;
         long long N = (long long)d.nx * d.ny;
         bool finite = true;
         if (h->phi_elem == 8) {
             std::memcpy(out, h->h_stage, sizeof(double) * N);
         } else {
             const float* f = reinterpret_cast<const float*>(h->h_stage);
-            for (long long k = 0; k < N; k++) out[k] = (double)f[k];
+            for (long long k = 0; k < N; k++) out[k] = (double)f[k] + (lo_host ? (double)lo_host[k] : 0.0);
         }
         for (long long k = 0; k < N; k++) finite = finite && std::isfinite(out[k]);
         return finite ? LBCH_OK : fail(LBCH_ENONFINITE, "phi holds non-finite values");
@@ -391,7 +576,8 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out)
     if (s != LBCH_OK) return s;
     double r[RED_NV];
     CK(cudaMemcpyAsync(r, h->result + (size_t)inst * RED_NV, sizeof r, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    s = check_err(h);
+    if (s != LBCH_OK) return s;
     switch (what) {
     case LBCH_OBS_MASS: *out = r[0]; break;
     case LBCH_OBS_ERR_L2: *out = std::sqrt(r[1] / r[2]); break;
@@ -409,7 +595,8 @@ lbch_status lb_ch_observe_all(lbch_handle* h, int what, double* out)
     if (s != LBCH_OK) return s;
     std::vector<double> r((size_t)RED_NV * h->n_inst);
     CK(cudaMemcpyAsync(r.data(), h->result, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    s = check_err(h);
+    if (s != LBCH_OK) return s;
     bool nonfinite = false;
     for (int k = 0; k < h->n_inst; k++) {
         const double* v = &r[(size_t)k * RED_NV];
@@ -452,14 +639,22 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
 {
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     // algorithmic HBM bytes per lattice update: read + write of the stored populations and of phi
-    double bytes = 2.0 * (h->n_planes * (double)h->g_elem + (double)h->phi_elem);
+    double bytes = 2.0 * (h->nq * (double)h->g_elem + (double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
     out[0] = (double)h->nodes;
     out[1] = bytes;
-    out[2] = (double)h->total_tiles;
+    out[2] = (double)h->grid;
     out[3] = (double)h->n;
     return LBCH_OK;
 }
 
 void* lb_ch_stream(lbch_handle* h) { return h ? (void*)h->stream : nullptr; }
+
+lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
+{
+    if (!h) return fail(LBCH_EINVAL, "NULL handle");
+    if (hook != LBCH_HOOK_SKIP_FIRST_LOAD) return fail(LBCH_EINVAL, "unknown hook %d", hook);
+    h->debug_skip = value ? 1 : 0;
+    return LBCH_OK;
+}
 
 }  // extern "C"

@@ -1,129 +1,113 @@
 // lbch_kernels.cuh -- sm_103a device code of the Cahn-Hilliard lattice Boltzmann step.
 //
 // Method: Zhang, Guo & Liang, arXiv:1805.00007, Sec. II (Eqs. LB, geq, liangFi, macroscopicg, mu, bulk,
-// betakappa, rho, t0-phiu, mark3).  The step is one fused, memory-bound tile kernel; no tensor cores.
+// betakappa, rho, t0-phiu, mark3).  The step is one fused, memory-bound kernel; no tensor cores.
 //
-// Per step and tile (TX x TY output nodes) the kernel
-//   1. builds the wrapped/mirrored row and column maps and separable velocity tables for the tile + 3 halo,
-//   2. loads phi(t) on tile + 3 into shared memory (phi is stored, so g is never re-summed for the halo),
-//   3. computes mu = f'(phi) - kappa lap phi and D = div(phi u) on tile + 2,
-//   4. on tile + 1 computes grad mu, grad D, the force F, g_eq and S, reads g(t) and collides,
-//   5. pulls the post-collision populations g*_i(x - c_i) from shared memory for every tile node, applies
-//      halfway bounce-back at walls, and writes g(t+1) and phi(t+1) = sum_i g_i(t+1).
-// HBM traffic per lattice update is one read and one write of the 9 populations and of phi; the halo
-// re-reads of neighbouring tiles are served by L2.
+// Storage ("padded image layout").  Every stored row has the same pitch.  An instance occupies
+// ny + 2*GR consecutive stored rows; domain node (x, y) sits at stored row row0 + y, column GC + x.  The
+// ghost rows and columns around the domain hold copies of the nodes they stand for -- periodic images,
+// or mirror images next to walls -- written by the step that produces those nodes, so that the halo of
+// every tile is one contiguous box of the stored array.  The populations are interleaved by row:
+// g[(row * nq + q) * pitch + col], so one 3-D TMA box (columns x planes x rows) brings a tile's planes.
+// phi is a plain 2-D array phi[row * pitch + col].
+//
+// Per step a persistent CTA walks its tiles (TX x TY output nodes) with a two-stage TMA pipeline:
+// while tile k is computed, the population box (tile + 1 halo) and the phi box (tile + 3 halo) of the
+// next tile are in flight.  For each tile the CTA
+//   1. forms phi and the flux phi u on tile + 3 (velocity from per-instance separable tables),
+//   2. computes mu = f'(phi) - kappa lap phi and D = div(phi u) on tile + 2,
+//   3. on tile + 1 computes grad mu, grad D, the force F, g_eq and S and collides, in place in the box,
+//   4. pulls g*_i(x - c_i) from shared memory for every tile node (halfway bounce-back at walls) and
+//      stores g(t+1) and phi(t+1), with the ghost images the next step's boxes need.
+// HBM traffic per lattice update is one read and one write of the stored populations and of phi; the
+// overlap of neighbouring tiles' boxes is served from L2.
 #pragma once
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace lbch {
 
+constexpr int GC = 4;  // ghost columns on each side (keeps box starts 16-byte aligned)
+constexpr int GR = 3;  // ghost rows on each side (phi halo of the stencil chain)
+
 // ------------------------------------------------------------------------------------------ lattice
 // D2Q9 (Sec. II.B): c0=(0,0), c1=-c3=(1,0), c2=-c4=(0,1), c5=-c7=(1,1), c6=-c8=(-1,1).
 __host__ __device__ constexpr int cx(int q) { return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0); }
 __host__ __device__ constexpr int cy(int q) { return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0); }
 __host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 5 + 2) % 4) + 5); }
-// Weights w0 = 4/9, w1..4 = 1/9, w5..8 = 1/36, as exact fractions of the compute type.
+// Weights w0 = 4/9, w1..4 = 1/9, w5..8 = 1/36.
 template <typename C> __host__ __device__ constexpr C wq(int q) { return q == 0 ? C(4) / C(9) : (q <= 4 ? C(1) / C(9) : C(1) / C(36)); }
 
 enum Vel { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_SHEAR = 3, VEL_REV_SHEAR = 4, VEL_DEFORM = 5 };
 
-// Per-instance parameters and derived constants, resident in device memory.
-struct InstDev {
-    long long off;          // element offset of node (0, 0) inside every population plane
-    int nx, ny, pitch;      // lattice size and row pitch (elements)
-    int walls, model, vel, nvort;
-    int tiles_x, tiles_y, tile_begin;
-    int pad_;
-    double tau, beta, kappa, eta, a, b, K, phiA, phiB;
-    double U0, ux0, uy0, xc, yc, half, Tper, shear;
+// Derived constants of one instance in the arithmetic type of a kernel.
+template <typename C>
+struct Consts {
+    C beta, kappa, eta, a, b, K, phiA, phiB;
+    C itau, omt, src;  // 1/tau, 1 - 1/tau, 1 - 1/(2 tau)
 };
 
-// Step counter shared by the launches of one handle: the last block of each step advances `time`.
+// Per-instance parameters, derived constants and layout, resident in device memory.
+struct InstDev {
+    int nx, ny;
+    int row0;          // stored row of domain row 0 (the instance's first ghost row is row0 - GR)
+    int walls, model, vel;
+    int tiles_x, tiles_y, tile_begin;
+    int tab;           // offset of the velocity tables: X1, X2 [pitch]; Y1, Y2 [tiles_y*TY + 2 GR]; W[4]
+    double Tper;
+    Consts<double> cd;  // the constants in double (FP64 path, initial state)
+    Consts<float> cf;   // and rounded once to float (float paths)
+};
+
+template <typename C> __device__ __forceinline__ const Consts<C>& consts(const InstDev& I);
+template <> __device__ __forceinline__ const Consts<double>& consts<double>(const InstDev& I) { return I.cd; }
+template <> __device__ __forceinline__ const Consts<float>& consts<float>(const InstDev& I) { return I.cf; }
+
+// Step counter shared by the launches of one handle: the last CTA of each step advances `time`.
 struct Ctl {
     long long time;
     unsigned int done;
-    unsigned int err;
+    unsigned int err;   // bit 0: a TMA wait timed out
 };
 
-// ------------------------------------------------------------------------------------------ velocity
-// Every prescribed flow is a sum-free separable product: ux = X1(x) Y1(y) T(t), uy = X2(x) Y2(y) T(t).
-// The tables are evaluated in double and stored in the compute type.
-__device__ inline void vel_x(const InstDev& I, double x, double& X1, double& X2)
+// Time factor of the prescribed flows: u(x, y, t) = (X1(x) Y1(y), X2(x) Y2(y)) T(t).
+__host__ __device__ inline double vel_t(int vel, double Tper, long long n)
 {
     const double pi = 3.14159265358979323846;
-    const double L = (double)I.nx;
-    switch (I.vel) {
-    case VEL_UNIFORM: X1 = 1.0; X2 = 1.0; break;
-    case VEL_ROTATION: X1 = 1.0; X2 = I.U0 * pi * (x - I.xc) / I.half; break;
-    case VEL_VORTEX: { double s = sin(pi * x / L); X1 = -I.U0 * s * s; X2 = I.U0 * sin(2.0 * pi * x / L); break; }
-    case VEL_SHEAR: X1 = 1.0; X2 = 0.0; break;
-    case VEL_REV_SHEAR: X1 = -I.U0 * pi * cos(pi * (x / L - 0.5)); X2 = I.U0 * pi * sin(pi * (x / L - 0.5)); break;
-    case VEL_DEFORM: { double k = (double)I.nvort * pi; X1 = -I.U0 * sin(k * (x / L + 0.5)); X2 = -I.U0 * cos(k * (x / L + 0.5)); break; }
-    default: X1 = 0.0; X2 = 0.0;
-    }
-}
-
-__device__ inline void vel_y(const InstDev& I, double y, double& Y1, double& Y2)
-{
-    const double pi = 3.14159265358979323846;
-    const double Lx = (double)I.nx, Ly = (double)I.ny;
-    switch (I.vel) {
-    case VEL_UNIFORM: Y1 = I.ux0; Y2 = I.uy0; break;
-    case VEL_ROTATION: Y1 = -I.U0 * pi * (y - I.yc) / I.half; Y2 = 1.0; break;
-    case VEL_VORTEX: { double s = sin(pi * y / Ly); Y1 = sin(2.0 * pi * y / Ly); Y2 = s * s; break; }
-    case VEL_SHEAR: Y1 = I.shear * (y - 0.5 * (double)(I.ny - 1)); Y2 = 0.0; break;
-    case VEL_REV_SHEAR: Y1 = sin(pi * (y / Lx - 0.5)); Y2 = cos(pi * (y / Lx - 0.5)); break;
-    case VEL_DEFORM: { double k = (double)I.nvort * pi; Y1 = sin(k * (y / Lx + 0.5)); Y2 = cos(k * (y / Lx + 0.5)); break; }
-    default: Y1 = 0.0; Y2 = 0.0;
-    }
-}
-
-__device__ inline double vel_t(const InstDev& I, long long n)
-{
-    const double pi = 3.14159265358979323846;
-    switch (I.vel) {
+    switch (vel) {
     case VEL_VORTEX:
-    case VEL_DEFORM: return cos(pi * (double)n / I.Tper);
-    case VEL_REV_SHEAR: return ((double)n < I.Tper) ? 1.0 : -1.0;
+    case VEL_DEFORM: return cos(pi * (double)n / Tper);
+    case VEL_REV_SHEAR: return ((double)n < Tper) ? 1.0 : -1.0;
     default: return 1.0;
     }
 }
 
-// ------------------------------------------------------------------------------------------ storage
+// ------------------------------------------------------------------------------------------ helpers
 template <typename T> __device__ __forceinline__ float to_f(T v) { return (float)v; }
 template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
-template <typename C, typename T> __device__ __forceinline__ C ld(const T* p) { return (C)to_f(*p); }
-template <> __device__ __forceinline__ double ld<double, double>(const double* p) { return *p; }
-template <typename T, typename C> __device__ __forceinline__ void st(T* p, C v) { *p = (T)v; }
-template <> __device__ __forceinline__ void st<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
+template <typename C, typename T> __device__ __forceinline__ C cvt(T v) { return (C)to_f(v); }
+template <> __device__ __forceinline__ double cvt<double, double>(double v) { return v; }
+template <typename T, typename C> __device__ __forceinline__ T to_s(C v) { return (T)v; }
+template <> __device__ __forceinline__ __half to_s<__half, float>(float v) { return __float2half_rn(v); }
 
-// Population plane q: shifted-half storage keeps only planes 1..8 (g0 is implied by phi).
-template <typename S> __device__ __forceinline__ long long plane_of(int q, long long plane)
+template <typename C> __device__ __forceinline__ C rcp(C v);
+template <> __device__ __forceinline__ float rcp<float>(float v) { return __frcp_rn(v); }
+// double reciprocal: a float seed refined by two Newton-Raphson steps r <- r (2 - v r); the error
+// squares at each step (2^-23 -> 2^-46 -> below double rounding)
+template <> __device__ __forceinline__ double rcp<double>(double v)
 {
-    return (sizeof(S) == 2) ? (long long)(q - 1) * plane : (long long)q * plane;
+    double r = (double)__frcp_rn((float)v);
+    r = r * fma(-v, r, 2.0);
+    r = r * fma(-v, r, 2.0);
+    return r;
 }
 
-template <typename S, typename P>
-struct StepArgs {
-    const InstDev* inst;
-    int n_inst;
-    int total_tiles;
-    long long plane;  // elements per population plane
-    const S* g_in;
-    S* g_out;
-    const P* phi_in;
-    P* phi_out;
-    Ctl* ctl;
-};
-
-__device__ __forceinline__ int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
-__device__ __forceinline__ int mirror_clamp(int j, int n)
+template <typename C> __device__ __forceinline__ C dfdphi(C phi, C beta, C phiA, C phiB)
 {
-    if (j < 0) j = -1 - j;
-    if (j >= n) j = 2 * n - 1 - j;
-    return j < 0 ? 0 : (j >= n ? n - 1 : j);
+    // d/dphi of beta (phi - phiA)^2 (phi - phiB)^2 (Eq. bulk)
+    return C(2) * beta * (phi - phiA) * (phi - phiB) * (C(2) * phi - phiA - phiB);
 }
 
 __device__ __forceinline__ int find_inst(const InstDev* inst, int n_inst, int tile)
@@ -136,223 +120,412 @@ __device__ __forceinline__ int find_inst(const InstDev* inst, int n_inst, int ti
     return lo;
 }
 
-template <typename C> __device__ __forceinline__ C dfdphi(C phi, C beta, C phiA, C phiB)
+__device__ __forceinline__ int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
+__device__ __forceinline__ int mirror(int j, int n)
 {
-    // d/dphi of beta (phi - phiA)^2 (phi - phiB)^2 (Eq. bulk)
-    return C(2) * beta * (phi - phiA) * (phi - phiB) * (C(2) * phi - phiA - phiB);
+    if (j < 0) j = -1 - j;
+    if (j >= n) j = 2 * n - 1 - j;
+    return j < 0 ? 0 : (j >= n ? n - 1 : j);
 }
 
-template <int TX, int TY, typename C>
-struct TileSmem {
-    static constexpr int PW = TX + 6, PH = TY + 6, MW = TX + 4, MH = TY + 4, GW = TX + 2, GH = TY + 2;
-    static constexpr int P = PW * PH, M = MW * MH, G = GW * GH;
-    // layout in units of C: phi, jx, jy [P]; mu, D [M]; post [9 G]; X1 X2 [PW]; Y1 Y2 [PH]; then ints
-    static constexpr int n_c = 3 * P + 2 * M + 9 * G + 2 * PW + 2 * PH;
-    static constexpr size_t bytes = sizeof(C) * n_c + sizeof(int) * (PW + PH) + 16;
-};
+// ------------------------------------------------------------------------------------------ TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll may suspend the thread for a short while).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit)
+{
+    for (unsigned k = 0; k < limit; k++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)), "l"(tm), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)), "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
 
 // ------------------------------------------------------------------------------------------ step
+// Storage types: S populations, P phi (the high part on the float path), C arithmetic.  The float path
+// (C = S = float) keeps phi as an unevaluated sum of two floats, phi = hi + lo: hi feeds the stencils,
+// lo is carried only at the node, and phi(t+1) = phi(t) + increment is formed with an exact TwoSum.
+template <typename C, typename S, typename P>
+struct StepArgs {
+    const InstDev* inst;
+    const C* tabs;       // velocity tables of all instances, indexed by stored column / instance row
+    int n_inst;
+    int total_tiles;
+    int pitch;           // elements per stored row
+    int debug_skip;      // test hook: when nonzero, CTA 0 never issues its first load (its wait runs out)
+    S* g_out;
+    P* phi_out;
+    float* lo_out;       // low part of phi on the float path
+    Ctl* ctl;
+};
+
+template <typename C, typename S, typename P, int TX, int TY>
+struct StepShape {
+    static constexpr bool FF = sizeof(C) == 4 && sizeof(S) == 4;  // float-float phi
+    static constexpr int NQ = (sizeof(S) == 2) ? 8 : 9;        // stored planes
+    static constexpr int BW = TX + 8;                          // box width (x0-4 .. x0+TX+3)
+    static constexpr int GBH = TY + 2, PBH = TY + 6;           // box heights
+    static constexpr int PW = TX + 6, PH = TY + 6;             // tile + 3
+    static constexpr int MW = TX + 4, MH = TY + 4;             // tile + 2
+    static constexpr int GW = TX + 2, GH = TY + 2;             // tile + 1
+    static constexpr int NP = PW * PH, NM = MW * MH, NG = GW * GH;  // region sizes
+    static constexpr unsigned GBOX_BYTES = GBH * NQ * BW * sizeof(S);
+    static constexpr unsigned PBOX_BYTES = PBH * BW * sizeof(P);
+    static constexpr unsigned LBOX_BYTES = FF ? TX * TY * 4 : 0;
+    __host__ __device__ static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr size_t OFF_P = a128(GBOX_BYTES), OFF_L = OFF_P + a128(PBOX_BYTES);
+    static constexpr size_t STAGE = OFF_L + a128(LBOX_BYTES);
+    static constexpr size_t WORK1 = a128(sizeof(C) * (2 * NP + 2 * NM));
+    static constexpr size_t WORK = WORK1 + (sizeof(S) == 2 ? a128(sizeof(C) * NG) : 0);  // + h*_0 (half path)
+    static constexpr size_t BYTES = 2 * STAGE + WORK + 128 + 128;  // mbarriers, alignment slack
+};
+
 template <typename C, typename S, typename P, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) ch_step_kernel(StepArgs<S, P> a)
+__global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(const __grid_constant__ CUtensorMap tm_g,
+                                                     const __grid_constant__ CUtensorMap tm_phi,
+                                                     const __grid_constant__ CUtensorMap tm_lo,
+                                                     StepArgs<C, S, P> a)
 {
-    using L = TileSmem<TX, TY, C>;
-    constexpr int PW = L::PW, MW = L::MW, GW = L::GW, MH = L::MH, PH = L::PH;
-    constexpr bool kHalf = sizeof(S) == 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s_phi = reinterpret_cast<C*>(smem_raw);
-    C* s_jx = s_phi + L::P;
-    C* s_jy = s_jx + L::P;
-    C* s_mu = s_jy + L::P;
-    C* s_D = s_mu + L::M;
-    C* s_post = s_D + L::M;
-    C* s_X1 = s_post + 9 * L::G;
-    C* s_X2 = s_X1 + PW;
-    C* s_Y1 = s_X2 + PW;
-    C* s_Y2 = s_Y1 + PH;
-    int* s_col = reinterpret_cast<int*>(s_Y2 + PH);
-    int* s_row = s_col + PW;
-    __shared__ int s_inst;
+    using L = StepShape<C, S, P, TX, TY>;
+    constexpr int NQ = L::NQ, BW = L::BW, PW = L::PW, MW = L::MW, MH = L::MH, GW = L::GW;
+    constexpr bool kHalf = sizeof(S) == 2;    // g_0 not stored: implied by phi
+    constexpr bool kShift = sizeof(C) == 4;   // float arithmetic on g_0 - phi instead of g_0
+    constexpr bool kFF = L::FF;
+    constexpr int QOFF = kHalf ? 1 : 0;       // stored plane of population q is q - QOFF
+    constexpr int NONE = -0x40000000;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    auto stage = [&](int k) { return base + (size_t)k * L::STAGE; };
+    C* s_ux = reinterpret_cast<C*>(base + 2 * L::STAGE);
+    C* s_uy = s_ux + L::NP;
+    C* s_mu = s_uy + L::NP;
+    C* s_D = s_mu + L::NM;
+    C* s_h0 = reinterpret_cast<C*>(base + 2 * L::STAGE + L::WORK1);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 2 * L::STAGE + L::WORK);
+
     __shared__ long long s_time;
+    __shared__ int s_tile_inst;
+    __shared__ C s_T;
 
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x;
     if (tid == 0) {
-        s_inst = find_inst(a.inst, a.n_inst, tile);
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
         s_time = a.ctl->time;
     }
     __syncthreads();
-    const InstDev& I = a.inst[s_inst];
-    const int nx = I.nx, ny = I.ny, pitch = I.pitch, walls = I.walls, model = I.model;
-    const long long off = I.off, plane = a.plane;
-    const int local = tile - I.tile_begin;
-    const int x0 = (local % I.tiles_x) * TX;
-    const int y0 = (local / I.tiles_x) * TY;
     const long long n = s_time;
-    const C T = (C)vel_t(I, n);
 
-    // 1. row/column maps and separable velocity tables on tile + 3
-    for (int e = tid; e < PW + PH; e += NT) {
-        if (e < PW) {
-            int xw = wrap(x0 - 3 + e, nx);
-            double X1, X2;
-            vel_x(I, (double)xw, X1, X2);
-            s_col[e] = xw; s_X1[e] = (C)X1; s_X2[e] = (C)X2;
-        } else {
-            int r = e - PW;
-            int gy = y0 - 3 + r;
-            int yw = walls ? mirror_clamp(gy, ny) : wrap(gy, ny);
-            double Y1, Y2;
-            vel_y(I, (double)yw, Y1, Y2);
-            s_row[r] = yw; s_Y1[r] = (C)Y1; s_Y2[r] = (C)Y2;
+    // producer: thread 0 issues the boxes of tile t into stage s
+    auto issue = [&](int t, int s) {
+        int k = find_inst(a.inst, a.n_inst, t);
+        const InstDev& I = a.inst[k];
+        int local = t - I.tile_begin;
+        int x0 = (local % I.tiles_x) * TX, y0 = (local / I.tiles_x) * TY;
+        fence_proxy_async();
+        mbar_expect_tx(&mbar[s], L::GBOX_BYTES + L::PBOX_BYTES + L::LBOX_BYTES);
+        // box column origin: domain x0 - 4 is stored column x0 - 4 + GC = x0
+        tma_load_3d(stage(s), &tm_g, x0, 0, I.row0 + y0 - 1, &mbar[s]);
+        tma_load_2d(stage(s) + L::OFF_P, &tm_phi, x0, I.row0 + y0 - 3, &mbar[s]);
+        if (kFF) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, x0 + GC, I.row0 + y0, &mbar[s]);
+    };
+
+    const int stride = gridDim.x;
+    if (tid == 0) {
+        for (int j = 0; j < 2; j++) {
+            int t = blockIdx.x + j * stride;
+            if (t < a.total_tiles && !(a.debug_skip && blockIdx.x == 0 && j == 0)) issue(t, j);
         }
     }
-    __syncthreads();
 
-    // 2. phi(t) and the flux phi u on tile + 3
-    for (int e = tid; e < L::P; e += NT) {
-        int r = e / PW, c = e - r * PW;
-        long long gi = off + (long long)s_row[r] * pitch + s_col[c];
-        C ph = ld<C>(a.phi_in + gi);
-        s_phi[e] = ph;
-        s_jx[e] = ph * (s_X1[c] * s_Y1[r] * T);
-        s_jy[e] = ph * (s_X2[c] * s_Y2[r] * T);
-    }
-    __syncthreads();
-
-    // 3. mu = f'(phi) - kappa lap phi (Eq. mu) and D = div(phi u) on tile + 2
-    const C beta = (C)I.beta, kappa = (C)I.kappa, phiA = (C)I.phiA, phiB = (C)I.phiB;
-    for (int e = tid; e < L::M; e += NT) {
-        int r = e / MW, c = e - r * MW;
-        int p = (r + 1) * PW + (c + 1);
-        C ce = s_phi[p];
-        C ax = s_phi[p + 1] + s_phi[p - 1] + s_phi[p + PW] + s_phi[p - PW];
-        C dg = s_phi[p + PW + 1] + s_phi[p + PW - 1] + s_phi[p - PW + 1] + s_phi[p - PW - 1];
-        // lap = sum_k 2 w_k (psi_k - psi_c) / c_s^2 (isotropic central Laplacian)
-        C lap = (C(2) / C(3)) * (ax - C(4) * ce) + (C(1) / C(6)) * (dg - C(4) * ce);
-        s_mu[e] = dfdphi(ce, beta, phiA, phiB) - kappa * lap;
-        if (model == 2) {
-            // div = sum_k w_k c_k . (phi u)(x + c_k) / c_s^2
-            C ax1 = (s_jx[p + 1] - s_jx[p - 1]) + (s_jy[p + PW] - s_jy[p - PW]);
-            C dg1 = (s_jx[p + PW + 1] + s_jy[p + PW + 1]) + (-s_jx[p + PW - 1] + s_jy[p + PW - 1])
-                  + (-s_jx[p - PW - 1] - s_jy[p - PW - 1]) + (s_jx[p - PW + 1] - s_jy[p - PW + 1]);
-            s_D[e] = (C(1) / C(3)) * ax1 + (C(1) / C(12)) * dg1;
+    for (int it = 0;; it++) {
+        const int t = blockIdx.x + it * stride;
+        if (t >= a.total_tiles) break;
+        const int s = it & 1;
+        // every thread observes the completion of the stage's copies itself (bounded wait)
+        bool ok = mbar_wait_bounded(&mbar[s], (unsigned)((it >> 1) & 1), 1u << 22);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&a.ctl->err, 1u);
+                // let a copy already issued into the other stage land before the CTA exits (bounded)
+                if (t + stride < a.total_tiles)
+                    mbar_wait_bounded(&mbar[s ^ 1], (unsigned)(((it + 1) >> 1) & 1), 1u << 22);
+            }
+            break;  // skip the remaining tiles; the step counter below is still kept consistent
         }
-    }
-    if (walls && (y0 < 2 || y0 + TY + 2 > ny)) {
-        // every stencil operand takes at a ghost row the value at the mirror row: mu and D at rows
-        // -2, -1, ny, ny+1 are copied from rows 1, 0, ny-1, ny-2 (all inside this region)
+        if (tid == 0) {
+            int k = find_inst(a.inst, a.n_inst, t);
+            s_tile_inst = k;
+            s_T = (C)vel_t(a.inst[k].vel, a.inst[k].Tper, n);  // time factor of the flow, once per tile
+        }
         __syncthreads();
-        for (int e = tid; e < 4 * MW; e += NT) {
-            int k = e / MW, c = e - k * MW;
-            int gy = (k == 0) ? -2 : (k == 1) ? -1 : (k == 2) ? ny : ny + 1;
-            int r = gy - (y0 - 2);
-            int rm = (-1 - gy >= 0 ? -1 - gy : 2 * ny - 1 - gy) - (y0 - 2);
-            C vmu = 0, vD = 0;
-            bool ok = (r >= 0 && r < MH && rm >= 0 && rm < MH);
-            // mirror rows are interior rows (ny >= 4), so reads and writes never touch the same row
-            if (ok) { vmu = s_mu[rm * MW + c]; vD = s_D[rm * MW + c]; }
-            if (ok) { s_mu[r * MW + c] = vmu; if (model == 2) s_D[r * MW + c] = vD; }
-        }
-    }
-    __syncthreads();
+        const InstDev& I = a.inst[s_tile_inst];
+        const Consts<C>& K0 = consts<C>(I);
+        const int nx = I.nx, ny = I.ny, walls = I.walls, model = I.model;
+        const int local = t - I.tile_begin;
+        const int x0 = (local % I.tiles_x) * TX, y0 = (local / I.tiles_x) * TY;
+        const C T = s_T;
+        S* gb = reinterpret_cast<S*>(stage(s));
+        const P* pb = reinterpret_cast<const P*>(stage(s) + L::OFF_P);  // phi on tile + 3 at box column c + 1
+        // velocity tables: X by stored column, Y by row of the instance's stored band
+        const C* tX1 = a.tabs + I.tab;
+        const C* tX2 = tX1 + a.pitch;
+        const C* tY1 = tX2 + a.pitch;
+        const C* tY2 = tY1 + I.tiles_y * TY + 2 * GR;
+        const C* tW = tY2 + I.tiles_y * TY + 2 * GR;
 
-    // 4. force, equilibrium, source and collision on tile + 1
-    const C eta = (C)I.eta, ra = (C)I.a, rb = (C)I.b, K = (C)I.K;
-    const C inv_tau = C(1) / (C)I.tau;
-    const C src = C(1) - C(1) / (C(2) * (C)I.tau);
-    for (int e = tid; e < L::G; e += NT) {
-        int r = e / GW, c = e - r * GW;
-        int gy = y0 - 1 + r;
-        if (walls && (gy < 0 || gy >= ny)) {
-#pragma unroll
-            for (int q = 0; q < 9; q++) s_post[q * L::G + e] = C(0);
-            continue;
+        // 1. velocity on tile + 3
+        for (int e = tid; e < L::NP; e += NT) {
+            int r = e / PW, c = e - r * PW;
+            s_ux[e] = tX1[x0 + c + 1] * tY1[y0 + r] * T;   // stored column of P column c is x0 + c + 1
+            s_uy[e] = tX2[x0 + c + 1] * tY2[y0 + r] * T;
         }
-        int m = (r + 1) * MW + (c + 1);
-        int p = (r + 2) * PW + (c + 2);
-        // grad psi = sum_k w_k c_k psi(x + c_k) / c_s^2
-        C gmx = (C(1) / C(3)) * (s_mu[m + 1] - s_mu[m - 1])
-              + (C(1) / C(12)) * ((s_mu[m + MW + 1] - s_mu[m + MW - 1]) + (s_mu[m - MW + 1] - s_mu[m - MW - 1]));
-        C gmy = (C(1) / C(3)) * (s_mu[m + MW] - s_mu[m - MW])
-              + (C(1) / C(12)) * ((s_mu[m + MW + 1] + s_mu[m + MW - 1]) - (s_mu[m - MW + 1] + s_mu[m - MW - 1]));
-        C ph = s_phi[p];
-        C mu = s_mu[m];
-        C rho = ra * ph + rb;                     // Eq. rho
-        C fct = ph / rho;
-        C Fx = fct * (-ph * gmx);                 // F1 = (phi/rho)(Fs - grad p), Fs = -phi grad mu, grad p = 0
-        C Fy = fct * (-ph * gmy);
-        if (model == 2) {                         // F2 = 3 c_s^2 K grad(div(phi u)), Eq. mark3
-            C gDx = (C(1) / C(3)) * (s_D[m + 1] - s_D[m - 1])
-                  + (C(1) / C(12)) * ((s_D[m + MW + 1] - s_D[m + MW - 1]) + (s_D[m - MW + 1] - s_D[m - MW - 1]));
-            C gDy = (C(1) / C(3)) * (s_D[m + MW] - s_D[m - MW])
-                  + (C(1) / C(12)) * ((s_D[m + MW + 1] + s_D[m + MW - 1]) - (s_D[m - MW + 1] + s_D[m - MW - 1]));
-            Fx += K * gDx;
-            Fy += K * gDy;
+        __syncthreads();
+
+        // 2. mu (Eq. mu) and D = div(phi u) on tile + 2
+        const C beta = K0.beta, kappa = K0.kappa, phiA = K0.phiA, phiB = K0.phiB;
+        for (int e = tid; e < L::NM; e += NT) {
+            int r = e / MW, c = e - r * MW;
+            const P* q = pb + (r + 1) * BW + c + 2;
+            C ce = cvt<C>(q[0]);
+            C pE = cvt<C>(q[1]), pW = cvt<C>(q[-1]), pN = cvt<C>(q[BW]), pS = cvt<C>(q[-BW]);
+            C pNE = cvt<C>(q[BW + 1]), pNW = cvt<C>(q[BW - 1]), pSE = cvt<C>(q[-BW + 1]), pSW = cvt<C>(q[-BW - 1]);
+            C ax = (pE + pW) + (pN + pS);
+            C dg = (pNE + pNW) + (pSE + pSW);
+            // lap = sum_k 2 w_k (psi_k - psi_c) / c_s^2
+            C lap = (C(2) / C(3)) * (ax - C(4) * ce) + (C(1) / C(6)) * (dg - C(4) * ce);
+            s_mu[e] = dfdphi(ce, beta, phiA, phiB) - kappa * lap;
+            if (model == 2) {
+                // div = sum_k w_k c_k . (phi u)(x + c_k) / c_s^2
+                int p = (r + 1) * PW + (c + 1);
+                C ax1 = (pE * s_ux[p + 1] - pW * s_ux[p - 1]) + (pN * s_uy[p + PW] - pS * s_uy[p - PW]);
+                C dg1 = pNE * (s_ux[p + PW + 1] + s_uy[p + PW + 1]) + pNW * (s_uy[p + PW - 1] - s_ux[p + PW - 1])
+                      - pSW * (s_ux[p - PW - 1] + s_uy[p - PW - 1]) + pSE * (s_ux[p - PW + 1] - s_uy[p - PW + 1]);
+                s_D[e] = (C(1) / C(3)) * ax1 + (C(1) / C(12)) * dg1;
+            }
         }
-        C ux = s_X1[c + 2] * s_Y1[r + 2] * T;
-        C uy = s_X2[c + 2] * s_Y2[r + 2] * T;
-        long long gi = off + (long long)s_row[r + 2] * pitch + s_col[c + 2];
-        C g[9];
-        if (kHalf) {
-            C rest = C(0);
-#pragma unroll
-            for (int q = 1; q < 9; q++) { g[q] = ld<C>(a.g_in + plane_of<S>(q, plane) + gi); rest += g[q]; }
-            g[0] = ph - rest;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 9; q++) g[q] = ld<C>(a.g_in + plane_of<S>(q, plane) + gi);
+        if (walls && (y0 < 2 || y0 + TY + 2 > ny)) {
+            // every stencil operand takes at a ghost row the value at the mirror row: mu and D at rows
+            // -2, -1, ny, ny+1 are copied from rows 1, 0, ny-1, ny-2 (interior rows, as ny >= 4)
+            __syncthreads();
+            for (int e = tid; e < 4 * MW; e += NT) {
+                int k = e / MW, c = e - k * MW;
+                int gy = (k == 0) ? -2 : (k == 1) ? -1 : (k == 2) ? ny : ny + 1;
+                int r = gy - (y0 - 2);
+                int rm = (gy < 0 ? -1 - gy : 2 * ny - 1 - gy) - (y0 - 2);
+                if (r >= 0 && r < MH && rm >= 0 && rm < MH) {
+                    C vmu = s_mu[rm * MW + c], vD = s_D[rm * MW + c];
+                    s_mu[r * MW + c] = vmu;
+                    if (model == 2) s_D[r * MW + c] = vD;
+                }
+            }
         }
-        C uu = ux * ux + uy * uy;
-        C emu = eta * mu;
+        __syncthreads();
+
+        // 3. force, equilibrium, source and collision on tile + 1, written back into the box
+        const C eta = K0.eta, ra = K0.a, rb = K0.b, K = K0.K;
+        const C itau = K0.itau, omt = K0.omt, src = K0.src;
+        // per direction class (axis, diagonal): w/tau, 3 w/tau, 3 w (1 - 1/(2 tau))
+        const C k1a = wq<C>(1) * itau, k1d = wq<C>(5) * itau;
+        const C k2a = C(3) * k1a, k2d = C(3) * k1d;
+        const C k3a = C(3) * wq<C>(1) * src, k3d = C(3) * wq<C>(5) * src;
+        for (int e = tid; e < L::NG; e += NT) {
+            int r = e / GW, c = e - r * GW;
+            int gy = y0 - 1 + r;
+            if (walls && (gy < 0 || gy >= ny)) continue;  // ghost rows: never pulled (bounce-back)
+            int m = (r + 1) * MW + (c + 1);
+            int p = (r + 2) * PW + (c + 2);
+            // grad psi = sum_k w_k c_k psi(x + c_k) / c_s^2
+            C gmx = (C(1) / C(3)) * (s_mu[m + 1] - s_mu[m - 1])
+                  + (C(1) / C(12)) * ((s_mu[m + MW + 1] - s_mu[m + MW - 1]) + (s_mu[m - MW + 1] - s_mu[m - MW - 1]));
+            C gmy = (C(1) / C(3)) * (s_mu[m + MW] - s_mu[m - MW])
+                  + (C(1) / C(12)) * ((s_mu[m + MW + 1] + s_mu[m + MW - 1]) - (s_mu[m - MW + 1] + s_mu[m - MW - 1]));
+            C ph = cvt<C>(pb[(r + 2) * BW + c + 3]);
+            C mu = s_mu[m];
+            C fct = -ph * ph * rcp<C>(ra * ph + rb);  // F1 = (phi/rho)(-phi grad mu), rho = a phi + b
+            C Fx = fct * gmx, Fy = fct * gmy;
+            if (model == 2) {                         // F2 = 3 c_s^2 K grad(div(phi u)), Eq. mark3
+                C gDx = (C(1) / C(3)) * (s_D[m + 1] - s_D[m - 1])
+                      + (C(1) / C(12)) * ((s_D[m + MW + 1] - s_D[m + MW - 1]) + (s_D[m - MW + 1] - s_D[m - MW - 1]));
+                C gDy = (C(1) / C(3)) * (s_D[m + MW] - s_D[m - MW])
+                      + (C(1) / C(12)) * ((s_D[m + MW + 1] + s_D[m + MW - 1]) - (s_D[m - MW + 1] + s_D[m - MW - 1]));
+                Fx += K * gDx;
+                Fy += K * gDy;
+            }
+            C ux = s_ux[p], uy = s_uy[p];
+            // the node's populations in the box: row r, plane q - QOFF, column c + 3
+            S* gp = gb + (r * NQ) * BW + c + 3;
+            C g[9];
+            if (kHalf) {
+                C rest = C(0);
 #pragma unroll
-        for (int q = 0; q < 9; q++) {
-            C geq;
-            if (q == 0) {
-                geq = ph + (wq<C>(0) - C(1)) * emu - wq<C>(0) * ph * uu * C(1.5);   // Eq. geq, i = 0
+                for (int q = 1; q < 9; q++) { g[q] = cvt<C>(gp[(q - QOFF) * BW]); rest += g[q]; }
+                g[0] = -rest;  // g_0 - phi
             } else {
+#pragma unroll
+                for (int q = 0; q < 9; q++) g[q] = cvt<C>(gp[q * BW]);
+            }
+            // Eq. LB as g* = (1 - 1/tau) g + g_eq/tau + (1 - 1/(2 tau)) S with Eq. geq and Eq. liangFi,
+            // split into the parts even and odd in c_i (S_i and the linear term of g_eq are odd)
+            C emu = eta * mu;
+            C uu = ux * ux + uy * uy;
+            C even = emu - C(1.5) * ph * uu;
+            C ph45 = C(4.5) * ph;
+            C g0eq = (kShift ? C(0) : ph) + (wq<C>(0) - C(1)) * emu - wq<C>(0) * C(1.5) * ph * uu;
+            C post[9];
+            post[0] = omt * g[0] + itau * g0eq;
+            // pairs (q, opp q): (1,3) c=(1,0); (2,4) c=(0,1); (5,7) c=(1,1); (6,8) c=(-1,1)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int q = (k == 0) ? 1 : (k == 1) ? 2 : (k == 2) ? 5 : 6;
+                const int o = opp(q);
                 C cu = (C)cx(q) * ux + (C)cy(q) * uy;
-                geq = wq<C>(q) * emu + wq<C>(q) * ph * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+                C cF = (C)cx(q) * Fx + (C)cy(q) * Fy;
+                C k1 = (q < 5) ? k1a : k1d, k2 = (q < 5) ? k2a : k2d, k3 = (q < 5) ? k3a : k3d;
+                C A = k1 * fma(ph45 * cu, cu, even);
+                C B = fma(k2, ph * cu, k3 * cF);
+                post[q] = fma(omt, g[q], A + B);
+                post[o] = fma(omt, g[o], A - B);
             }
-            C Sq = C(3) * wq<C>(q) * ((C)cx(q) * Fx + (C)cy(q) * Fy);              // Eq. liangFi
-            s_post[q * L::G + e] = g[q] - (g[q] - geq) * inv_tau + src * Sq;       // Eq. LB
-        }
-    }
-    __syncthreads();
-
-    // 5. pull streaming from shared memory, bounce-back at walls, write g(t+1), phi(t+1)
-    for (int e = tid; e < TX * TY; e += NT) {
-        int r = e / TX, c = e - r * TX;
-        int gx = x0 + c, gy = y0 + r;
-        if (gx >= nx || gy >= ny) continue;
-        int b = (r + 1) * GW + (c + 1);
-        long long gi = off + (long long)gy * pitch + gx;
-        C phin = C(0);
-        C v[9];
+            if (kHalf) s_h0[e] = post[0];
 #pragma unroll
-        for (int q = 0; q < 9; q++) {
-            int sy = gy - cy(q);
-            if (walls && (sy < 0 || sy >= ny)) {
-                // halfway bounce-back: the population that left along -c_q returns along c_q, plus the
-                // moving-wall term 2 w_q phi (c_q . u_w) / c_s^2
-                double X1, X2, Y1, Y2;
-                vel_x(I, (double)gx, X1, X2);
-                vel_y(I, sy < 0 ? -0.5 : (double)ny - 0.5, Y1, Y2);
-                C uwx = (C)X1 * (C)Y1 * T, uwy = (C)X2 * (C)Y2 * T;
-                C ph = s_phi[(r + 3) * PW + (c + 3)];
-                v[q] = s_post[opp(q) * L::G + b]
-                     + C(2) * wq<C>(q) * ph * ((C)cx(q) * uwx + (C)cy(q) * uwy) * C(3);
+            for (int q = QOFF; q < 9; q++) gp[(q - QOFF) * BW] = to_s<S>(post[q]);
+        }
+        __syncthreads();
+
+        // 4. pull streaming from the box, bounce-back at walls; store g(t+1), phi(t+1) and ghost images
+        const int pitch = a.pitch;
+        const float* lb = reinterpret_cast<const float*>(stage(s) + L::OFF_L);
+        for (int e = tid; e < TX * TY; e += NT) {
+            int r = e / TX, c = e - r * TX;
+            int gx = x0 + c, gy = y0 + r;
+            if (gx >= nx || gy >= ny) continue;
+            C v[9];
+            C sumq = C(0);
+#pragma unroll
+            for (int q = 0; q < 9; q++) {
+                if (q == 0) {
+                    v[0] = kHalf ? s_h0[(r + 1) * GW + (c + 1)] : cvt<C>(gb[((r + 1) * NQ) * BW + c + 4]);
+                    if (!kShift) sumq += v[0];
+                    continue;
+                }
+                int sy = gy - cy(q);
+                if (walls && (sy < 0 || sy >= ny)) {
+                    // halfway bounce-back: the population that left along -c_q returns along c_q, plus
+                    // the moving-wall term 2 w_q phi (c_q . u_w) / c_s^2
+                    int wi = sy < 0 ? 0 : 1;
+                    C uwx = tX1[gx + GC] * tW[wi] * T, uwy = tX2[gx + GC] * tW[2 + wi] * T;
+                    C ph = cvt<C>(pb[(r + 3) * BW + c + 4]);
+                    v[q] = cvt<C>(gb[((r + 1) * NQ + opp(q) - QOFF) * BW + c + 4])
+                         + C(6) * wq<C>(q) * ph * ((C)cx(q) * uwx + (C)cy(q) * uwy);
+                } else {
+                    v[q] = cvt<C>(gb[((r + 1 - cy(q)) * NQ + q - QOFF) * BW + c + 4 - cx(q)]);
+                }
+                sumq += v[q];
+            }
+            P hi;
+            float lo = 0.0f;
+            if (kFF) {
+                // g_0(t+1) = phi(t) + v_0 stays at the node: phi(t+1) = phi(t) + (v_0 + sum_{q>0} g_q(t+1));
+                // hi + lo absorbs the increment exactly (TwoSum); g_0 - phi is stored as -sum_{q>0} g_q
+                float h = (float)pb[(r + 3) * BW + c + 4];
+                float tt = lb[r * TX + c] + (float)(v[0] + sumq);
+                float sm = h + tt;
+                float bb = sm - h;
+                lo = (h - (sm - bb)) + (tt - bb);
+                hi = (P)sm;
+                v[0] = -sumq;
+            } else if (kShift) {
+                // half path: phi(t+1) = phi(t) + v_0 + sum_{q>0} g_q(t+1) in float; g_0 stays implied
+                hi = (P)((float)pb[(r + 3) * BW + c + 4] + (float)(v[0] + sumq));
             } else {
-                v[q] = s_post[q * L::G + b - cy(q) * GW - cx(q)];
+                hi = (P)sumq;
             }
-            phin += v[q];
-        }
+            // positions to write: the node and its images in the ghost columns/rows (phi three deep,
+            // the populations one deep; images in y only for periodic y, mirror images for walls)
+            const int xa = gx < 3 ? gx + nx : NONE, xb = gx >= nx - 3 ? gx - nx : NONE;
+            const int ya = gy < 3 ? (walls ? -1 - gy : gy + ny) : NONE;
+            const int yb = gy >= ny - 3 ? (walls ? 2 * ny - 1 - gy : gy - ny) : NONE;
 #pragma unroll
-        for (int q = (kHalf ? 1 : 0); q < 9; q++) st(a.g_out + plane_of<S>(q, plane) + gi, v[q]);
-        st(a.phi_out + gi, phin);
+            for (int iy = 0; iy < 3; iy++) {
+                const int yy = iy == 0 ? gy : (iy == 1 ? ya : yb);
+                if (yy == NONE) continue;
+#pragma unroll
+                for (int ix = 0; ix < 3; ix++) {
+                    const int xx = ix == 0 ? gx : (ix == 1 ? xa : xb);
+                    if (xx == NONE) continue;
+                    long long idx = (long long)(I.row0 + yy) * pitch + GC + xx;
+                    a.phi_out[idx] = hi;
+                    if (kFF && ix == 0 && iy == 0) a.lo_out[idx] = lo;
+                }
+            }
+            const int gxa = gx == 0 ? nx : (gx == nx - 1 ? -1 : NONE);
+            const int gya = walls ? NONE : (gy == 0 ? ny : (gy == ny - 1 ? -1 : NONE));
+#pragma unroll
+            for (int iy = 0; iy < 2; iy++) {
+                const int yy = iy == 0 ? gy : gya;
+                if (yy == NONE) continue;
+#pragma unroll
+                for (int ix = 0; ix < 2; ix++) {
+                    const int xx = ix == 0 ? gx : gxa;
+                    if (xx == NONE) continue;
+                    S* o = a.g_out + ((long long)(I.row0 + yy) * NQ) * pitch + GC + xx;
+#pragma unroll
+                    for (int q = QOFF; q < 9; q++) o[(q - QOFF) * pitch] = to_s<S>(v[q]);
+                }
+            }
+        }
+        __syncthreads();  // the stage and the work arrays are free again
+
+        if (tid == 0) {
+            int t2 = t + 2 * stride;
+            if (t2 < a.total_tiles) issue(t2, s);
+        }
     }
 
-    // the last block of the launch advances the step counter read by the next launch
-    __syncthreads();
+    // the last CTA of the launch advances the step counter read by the next launch
     if (tid == 0) {
         __threadfence();
         unsigned int prev = atomicAdd(&a.ctl->done, 1u);
@@ -365,52 +538,71 @@ __global__ void __launch_bounds__(NT) ch_step_kernel(StepArgs<S, P> a)
 }
 
 // ------------------------------------------------------------------------------------------ init
-// g_i(x, 0) = g_i^eq(phi0, mu(phi0), u(x, 0)); phi(0) = phi0.  One thread per node.
+// g_i(x, 0) = g_i^eq(phi0, mu(phi0), u(x, 0)); phi(0) = phi0 (hi + lo on the float path); the ghost
+// images are written too.  phi0 arrives in the padded layout with its ghost frame filled; the
+// velocity tables are the double ones, indexed like the step kernel's.
 template <typename C, typename S, typename P>
-__global__ void init_kernel(const InstDev* inst, int n_inst, const double* phi0, long long plane,
-                            S* g, P* phi, long long total_nodes_padded)
+__global__ void init_kernel(const InstDev* inst, int n_inst, const double* tabs, const double* phi0, int pitch,
+                            int ty, S* g, P* phi, float* lo, long long nodes_total, const long long* node_begin)
 {
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= total_nodes_padded) return;
-    int lo = 0, hi = n_inst - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (inst[mid].off <= k) lo = mid; else hi = mid - 1;
+    if (k >= nodes_total) return;
+    int lo_i = 0, hi_i = n_inst - 1;
+    while (lo_i < hi_i) {
+        int mid = (lo_i + hi_i + 1) >> 1;
+        if (node_begin[mid] <= k) lo_i = mid; else hi_i = mid - 1;
     }
-    const InstDev& I = inst[lo];
-    long long loc = k - I.off;
-    int j = (int)(loc / I.pitch), i = (int)(loc - (long long)j * I.pitch);
-    if (j >= I.ny || i >= I.nx) return;
-    auto at = [&](int di, int dj) -> double {
-        int ii = wrap(i + di, I.nx);
-        int jj = I.walls ? mirror_clamp(j + dj, I.ny) : wrap(j + dj, I.ny);
-        return phi0[I.off + (long long)jj * I.pitch + ii];
+    const InstDev& I = inst[lo_i];
+    const int NQ = (sizeof(S) == 2) ? 8 : 9, QOFF = (sizeof(S) == 2) ? 1 : 0;
+    long long loc = k - node_begin[lo_i];
+    int y = (int)(loc / I.nx), x = (int)(loc - (long long)y * I.nx);
+    auto at = [&](int dx, int dy) -> double {
+        int xx = wrap(x + dx, I.nx);
+        int yy = I.walls ? mirror(y + dy, I.ny) : wrap(y + dy, I.ny);
+        return phi0[(long long)(I.row0 + yy) * pitch + GC + xx];
     };
     double c0 = at(0, 0);
     double ax = at(1, 0) + at(-1, 0) + at(0, 1) + at(0, -1);
     double dg = at(1, 1) + at(-1, 1) + at(1, -1) + at(-1, -1);
     double lap = (2.0 / 3.0) * (ax - 4.0 * c0) + (1.0 / 6.0) * (dg - 4.0 * c0);
-    C mu = (C)(dfdphi<double>(c0, I.beta, I.phiA, I.phiB) - I.kappa * lap);
-    double X1, X2, Y1, Y2;
-    vel_x(I, (double)i, X1, X2);
-    vel_y(I, (double)j, Y1, Y2);
-    double T = vel_t(I, 0);
-    C ux = (C)(X1 * Y1 * T), uy = (C)(X2 * Y2 * T);
-    C ph = (C)c0, eta = (C)I.eta;
+    C mu = (C)(dfdphi<double>(c0, I.cd.beta, I.cd.phiA, I.cd.phiB) - I.cd.kappa * lap);
+    const double* tX1 = tabs + I.tab;
+    const double* tX2 = tX1 + pitch;
+    const double* tY1 = tX2 + pitch;
+    const double* tY2 = tY1 + I.tiles_y * ty + 2 * GR;
+    double T = vel_t(I.vel, I.Tper, 0);
+    C ux = (C)(tX1[x + GC] * tY1[y + GR] * T), uy = (C)(tX2[x + GC] * tY2[y + GR] * T);
+    C ph = (C)c0, eta = (C)I.cd.eta;
     C uu = ux * ux + uy * uy;
+    C v[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        C geq;
         if (q == 0) {
-            geq = ph + (wq<C>(0) - C(1)) * eta * mu - wq<C>(0) * ph * uu * C(1.5);
+            // the float paths store g_0 - phi
+            v[q] = (sizeof(C) == 4 ? C(0) : ph) + (wq<C>(0) - C(1)) * eta * mu - wq<C>(0) * C(1.5) * ph * uu;
         } else {
             C cu = (C)cx(q) * ux + (C)cy(q) * uy;
-            geq = wq<C>(q) * eta * mu + wq<C>(q) * ph * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+            v[q] = wq<C>(q) * eta * mu + wq<C>(q) * ph * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
         }
-        if (sizeof(S) == 2 && q == 0) continue;
-        st(g + plane_of<S>(q, plane) + k, geq);
     }
-    st(phi + k, ph);
+    const P hi = (P)c0;
+    if (lo) lo[(long long)(I.row0 + y) * pitch + GC + x] = (float)(c0 - (double)hi);
+    const int NONE = -0x40000000;
+    const int xa = x < 3 ? x + I.nx : NONE, xb = x >= I.nx - 3 ? x - I.nx : NONE;
+    const int ya = y < 3 ? (I.walls ? -1 - y : y + I.ny) : NONE;
+    const int yb = y >= I.ny - 3 ? (I.walls ? 2 * I.ny - 1 - y : y - I.ny) : NONE;
+    for (int iy = 0; iy < 3; iy++) {
+        const int yy = iy == 0 ? y : (iy == 1 ? ya : yb);
+        if (yy == NONE) continue;
+        for (int ix = 0; ix < 3; ix++) {
+            const int xx = ix == 0 ? x : (ix == 1 ? xa : xb);
+            if (xx == NONE) continue;
+            long long row = I.row0 + yy;
+            phi[row * pitch + GC + xx] = hi;
+            S* o = g + (row * NQ) * pitch + GC + xx;
+            for (int q = QOFF; q < 9; q++) o[(q - QOFF) * pitch] = to_s<S>(v[q]);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------ reductions
@@ -463,18 +655,18 @@ __device__ inline void block_reduce(double* v, double (*sh)[RED_NV])
 }
 
 template <typename P>
-__global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const InstDev* inst, const P* phi,
-                                                                 const double* phi0, double* partials,
-                                                                 int chunks)
+__global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const InstDev* inst, const P* phi, const float* lo,
+                                                                 const double* phi0, int pitch,
+                                                                 double* partials, int chunks)
 {
     __shared__ double sh[RED_NT / 32][RED_NV];
     const InstDev& I = inst[blockIdx.y];
     const long long N = (long long)I.nx * I.ny;
     double v[RED_NV] = {0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
     for (long long k = (long long)blockIdx.x * RED_NT + threadIdx.x; k < N; k += (long long)chunks * RED_NT) {
-        int j = (int)(k / I.nx), i = (int)(k - (long long)j * I.nx);
-        long long gi = I.off + (long long)j * I.pitch + i;
-        double p = (double)phi[gi], p0 = phi0[gi];
+        int y = (int)(k / I.nx), x = (int)(k - (long long)y * I.nx);
+        long long gi = (long long)(I.row0 + y) * pitch + GC + x;
+        double p = (double)phi[gi] + (lo ? (double)lo[gi] : 0.0), p0 = phi0[gi];
         if (!isfinite(p)) { v[5] += 1.0; continue; }
         v[0] += p; v[1] += (p - p0) * (p - p0); v[2] += p0 * p0;
         v[3] = fmax(v[3], p); v[4] = fmin(v[4], p);
