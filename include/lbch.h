@@ -149,6 +149,27 @@ void* lb_ch_stream(lbch_handle* h);
 enum { LBCH_HOOK_SKIP_FIRST_LOAD = 1 };
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
 
+/* Statistics of a caller-owned field without allocating anything (the paper has no counterpart; this
+ * serves callers that may not allocate device memory, e.g. code running inside another framework's
+ * memory pool or a plugin restricted to the buffers it is handed).
+ *
+ * phi, phi0: device pointers to ny rows of nx doubles, row r starting at element r * pitch.
+ * out: device pointer to 6 doubles, written asynchronously on `stream` (a cudaStream_t, NULL = legacy
+ * default stream): out[0] = sum phi, out[1] = sum (phi - phi0)^2, out[2] = sum phi0^2 (so that
+ * ||E_phi||_2 of Eq. err is sqrt(out[1] / out[2])), out[3] = max phi, out[4] = min phi, out[5] = number
+ * of non-finite phi values (left out of the other five).  The values equal those lb_ch_observe reports
+ * for the same field up to the order of the floating-point sums.
+ *
+ * The per-block partial sums go to a file-scope device array of LBCH_NOALLOC_MAX_BLOCKS x 6 doubles
+ * (48 KiB), which every GPU that loads this library holds until the process exits.  The first call on a
+ * device looks up that array's device address (with the device current) and caches it; make that first
+ * call before any stream capture.  Calls share the array: each overwrites what it uses, but calls that
+ * overlap on the GPU race.  Fields of more than LBCH_NOALLOC_MAX_NODES nodes are rejected with
+ * LBCH_EINVAL; no cudaMalloc, cudaFree or allocating library routine is ever called. */
+#define LBCH_NOALLOC_MAX_BLOCKS 1024
+#define LBCH_NOALLOC_MAX_NODES (1LL << 31)
+lbch_status lb_ch_field_stats_noalloc(const double* phi, const double* phi0, int nx, int ny, int pitch,
+                                      double* out, void* stream);
 
 #ifdef __cplusplus
 }

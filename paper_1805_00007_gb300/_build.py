@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbch.so")
-SOURCES = [os.path.join(CSRC, "lbch_api.cu")]
+SOURCES = [os.path.join(CSRC, "lbch_api.cu"), os.path.join(CSRC, "lbch_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(ROOT, "include", "lbch.h")]
 

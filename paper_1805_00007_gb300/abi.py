@@ -19,7 +19,8 @@ PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
 
 # Exported symbols, as declared in include/lbch.h.
 SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free",
-           "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream", "lb_ch_test_hook")
+           "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream", "lb_ch_test_hook",
+           "lb_ch_field_stats_noalloc")
 LBCH_HOOK_SKIP_FIRST_LOAD = 1
 
 
@@ -71,8 +72,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_stream.argtypes = [vp]
     lib.lb_ch_stream.restype = vp
     lib.lb_ch_test_hook.argtypes = [vp, ctypes.c_int, ctypes.c_long]
+    lib.lb_ch_field_stats_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
-                 "lb_ch_test_hook"):
+                 "lb_ch_test_hook", "lb_ch_field_stats_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -147,6 +149,15 @@ def lb_ch_info(h) -> dict:
 
 def lb_ch_test_hook(h, hook: int, value: int):
     _check(load().lb_ch_test_hook(h, int(hook), int(value)), "lb_ch_test_hook")
+
+
+def lb_ch_field_stats_noalloc(phi_ptr: int, phi0_ptr: int, nx: int, ny: int, pitch: int, out_ptr: int,
+                              stream: int = 0):
+    """Statistics of a caller-owned device field (device pointers as integers) into a caller-owned
+    device array of 6 doubles, without any device allocation."""
+    _check(load().lb_ch_field_stats_noalloc(ctypes.c_void_p(phi_ptr), ctypes.c_void_p(phi0_ptr), int(nx), int(ny),
+                                            int(pitch), ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream or 0)),
+           "lb_ch_field_stats_noalloc")
 
 
 def lb_ch_stream(h) -> int:

@@ -71,6 +71,13 @@ EncodeTiledFn encode_fn()
 
 }  // namespace
 
+// Used by the allocation-free entry point (another translation unit) to report its failures through
+// lb_ch_last_error(); not exported.
+__attribute__((visibility("hidden"))) void lbch_set_last_error(const char* msg)
+{
+    snprintf(g_msg, sizeof g_msg, "%s", msg);
+}
+
 struct lbch_handle {
     int device = 0;
     int prec = LBCH_F64;

@@ -1,0 +1,84 @@
+"""The allocation-free statistics entry point, checked against lb_ch_observe.
+
+lb_ch_field_stats_noalloc exists for callers that may not allocate device memory (code that runs while
+another framework owns the memory pool, or plugins restricted to the buffers they are given): it keeps
+its partial sums in a fixed device array of the library instead of allocating scratch.  This file runs
+last so that a failure here leaves every other test already run.  The device buffers below are the
+test's own (allocated with torch); the entry point itself allocates nothing.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1805_00007_gb300 import abi
+from paper_1805_00007_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _reference(p, phi0, nsteps):
+    with abi.Simulation(p, phi0, prec="f64") as sim:
+        sim.step(nsteps)
+        phi = sim.phi()
+        ref = {w: sim.observe(w) for w in (abi.LBCH_OBS_MASS, abi.LBCH_OBS_ERR_L2, abi.LBCH_OBS_MAX,
+                                           abi.LBCH_OBS_MIN)}
+    return phi, ref
+
+
+def _noalloc(phi, phi0, pad=0):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ny, nx = phi.shape
+    pitch = nx + pad
+    a = np.zeros((ny, pitch)); a[:, :nx] = phi
+    b = np.zeros((ny, pitch)); b[:, :nx] = phi0
+    d_phi = torch.from_numpy(a).to(dev)
+    d_phi0 = torch.from_numpy(b).to(dev)
+    out = torch.full((6,), float("nan"), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    abi.lb_ch_field_stats_noalloc(d_phi.data_ptr(), d_phi0.data_ptr(), nx, ny, pitch, out.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    return out.cpu().numpy()
+
+
+def _check(o, ref):
+    tol = 1e-12  # the FP64 parity tolerance; only the order of the sums differs
+    assert abs(o[0] - ref[abi.LBCH_OBS_MASS]) <= tol * abs(ref[abi.LBCH_OBS_MASS])
+    assert abs(math.sqrt(o[1] / o[2]) - ref[abi.LBCH_OBS_ERR_L2]) <= tol * ref[abi.LBCH_OBS_ERR_L2]
+    assert o[3] == ref[abi.LBCH_OBS_MAX] and o[4] == ref[abi.LBCH_OBS_MIN]
+    assert o[5] == 0.0
+
+
+def test_noalloc_matches_observe_on_two_calls_in_a_row():
+    p, phi0, _ = wl.zalesak(n=96)
+    phi, ref = _reference(p, phi0, 150)
+    first = _noalloc(phi, phi0)
+    _check(first, ref)
+    second = _noalloc(phi, phi0)          # the shared partials array is reused
+    _check(second, ref)
+    assert np.array_equal(first, second)  # same blocks, same order: the same bits
+
+
+def test_noalloc_other_size_and_pitch_after_a_larger_call():
+    p, phi0, _ = wl.single_vortex(n=512, T=100)
+    phi_big, ref_big = _reference(p, phi0, 20)
+    _check(_noalloc(phi_big, phi0), ref_big)
+    q, f0, _ = wl.translation(nx=40)
+    phi_small, ref_small = _reference(q, f0, 30)
+    _check(_noalloc(phi_small, f0, pad=24), ref_small)  # fewer blocks than the previous call
+
+
+def test_noalloc_rejects_bad_arguments():
+    dev = torch.device("cuda", torch.cuda.current_device())
+    buf = torch.zeros(16, dtype=torch.float64, device=dev)
+    out = torch.zeros(6, dtype=torch.float64, device=dev)
+    cases = [((buf.data_ptr(), buf.data_ptr(), 1 << 16, 1 << 16, 1 << 16), "maximum"),  # too many nodes
+             ((buf.data_ptr(), buf.data_ptr(), 4, 4, 3), "pitch"),                       # pitch < nx
+             ((0, buf.data_ptr(), 4, 4, 4), "device pointers")]                          # NULL field
+    for args, words in cases:
+        with pytest.raises(abi.LbchError) as ei:
+            abi.lb_ch_field_stats_noalloc(*args, out.data_ptr(), 0)
+        assert ei.value.status == abi.LBCH_EINVAL
+        assert words in str(ei.value)
