@@ -307,6 +307,30 @@ def main():
             sim.close()
 
 
+    # --- the ragged ensemble: 256 wall-bounded shear instances (23.1 M nodes) advanced in one launch per step
+    ensemble = {}
+    if not args.no_sweep:
+        ens = wl.shear_ensemble()
+        eparams, efields = zip(*ens)
+        enodes = sum(q["nx"] * q["ny"] for q in eparams)
+        for prec in ("f32", "f16s"):
+            sim = abi.Simulation(list(eparams), list(efields), prec=prec, stream=stream.cuda_stream)
+            sim.step(64)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nst = 128
+            e0.record(stream)
+            sim.step(nst)
+            e1.record(stream)
+            e1.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3 / nst
+            inf = sim.info()
+            gbs = inf["bytes_per_lu"] * enodes / dt / 1e9
+            ensemble[prec] = {"instances": len(eparams), "nodes": enodes, "MLUPS": enodes / dt / 1e6,
+                              "us_per_launch": dt * 1e6, "bytes_per_lu": inf["bytes_per_lu"],
+                              "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+            sim.close()
+
     acc = {prec: accuracy(prec, p, phi0, rev) for prec in ("f32", "f64", "f16s")} if rank == 0 else {}
 
     cpu = None
@@ -331,6 +355,7 @@ def main():
                          "kernel": "ch_step_kernel<float,float,float,32,16,256>",
                          "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6},
             "sweep_4096": sweep,
+            "ensemble_shear_256": ensemble,
             "accuracy_one_revolution": acc,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
                     "d2h_bytes_per_step": phi0.nbytes},

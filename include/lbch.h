@@ -141,6 +141,31 @@ lbch_status lb_ch_info(lbch_handle* h, double* out);
 /* The CUDA stream the handle enqueues on (a cudaStream_t). */
 void* lb_ch_stream(lbch_handle* h);
 
+/* ---- checkpoints and the differentiable adjoint (single-instance, periodic handles) ----
+ *
+ * The step's Jacobian depends on the populations only through phi (Eq. LB with Eqs. geq, liangFi,
+ * mu, t0-phiu, mark3 are linear in g except through phi = sum g), so reverse mode needs, for every
+ * forward step n, the forward phi(n) (a tape entry) and nothing else.  The adjoint type is double for
+ * LBCH_F64 handles and float otherwise; every array below is a device pointer the caller owns.
+ *
+ * lb_ch_state_bytes / lb_ch_state_save / lb_ch_state_load: the full state (populations, phi, step
+ * index) to and from a caller buffer of lb_ch_state_bytes() bytes -- the checkpoints of a segmented
+ * (square-root) reverse sweep.  Loading also restores the step index.
+ * lb_ch_tape_phi: phi of the current state into dst (nx*ny values, row-major, adjoint type).
+ * lb_ch_adjoint_begin: lambda = dL/dg_q(T) = dL/dphi(T) for every q (dL_dphiT: nx*ny values).
+ * lb_ch_adjoint_step: one step backwards: lambda_n from lambda_{n+1}, given phi_n (the forward phi at
+ *   step n) and n; accumulates dL/ds, where the prescribed velocity is s times the configured one.
+ * lb_ch_adjoint_end: the adjoint of the initial equilibria: dL/dphi0 into dL_dphi0 (nx*ny values)
+ *   and dL/ds (at s = 1) into *dL_ds (host).  Synchronises the stream.
+ * Walls and ensembles are rejected with LBCH_EINVAL. */
+lbch_status lb_ch_state_bytes(lbch_handle* h, long long* bytes);
+lbch_status lb_ch_state_save(lbch_handle* h, void* dst);
+lbch_status lb_ch_state_load(lbch_handle* h, const void* src);
+lbch_status lb_ch_tape_phi(lbch_handle* h, void* dst);
+lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT);
+lbch_status lb_ch_adjoint_step(lbch_handle* h, const void* phi_n, long n);
+lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
+
 /* Test hook for the failure path of the step kernel's bounded waits.  With hook
  * LBCH_HOOK_SKIP_FIRST_LOAD and value != 0, the next step launches run without CUDA graphs and their
  * first thread block never issues its first tile copy, so its bounded wait runs out (after about a

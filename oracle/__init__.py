@@ -100,6 +100,12 @@ def lib() -> ctypes.CDLL:
         _lib.ora_run.argtypes = [P(_Params), dp, ctypes.c_long, ctypes.c_long]
         _lib.ora_run.restype = ctypes.c_int
         _lib.ora_observe.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        _lib.ora_d2fdphi2.argtypes = [ctypes.c_double] * 4
+        _lib.ora_d2fdphi2.restype = ctypes.c_double
+        _lib.ora_adjoint_step.argtypes = [P(_Params), dp, dp, dp, ctypes.c_long, dp]
+        _lib.ora_adjoint_step.restype = ctypes.c_int
+        _lib.ora_adjoint_init.argtypes = [P(_Params), dp, dp, dp, dp]
+        _lib.ora_adjoint_init.restype = ctypes.c_int
     return _lib
 
 
@@ -250,3 +256,29 @@ def simulate(cfg, phi0, nsteps: int, n0: int = 0):
     """phi after nsteps steps from the initial field phi0 (initial g from the equilibria)."""
     g = run(cfg, init(cfg, phi0), nsteps, n0)
     return phi_of(g), g
+
+
+def d2fdphi2(phi, beta, phiA, phiB) -> float:
+    return lib().ora_d2fdphi2(phi, beta, phiA, phiB)
+
+
+def adjoint(cfg, phi0, nsteps: int, dL_dphiT):
+    """Reverse-mode gradient of a loss of phi(nsteps): given dL/dphi(T), returns (dL/dphi0, dL/ds) where the
+    velocity field is s * u (derivative at s = 1).  Stores every forward state (small grids only)."""
+    p = params(cfg)
+    phi0 = _f64(phi0)
+    N = p.nx * p.ny
+    states = [init(cfg, phi0)]
+    for n in range(nsteps):
+        states.append(step(cfg, states[-1], n))
+    lam = np.repeat(_f64(dL_dphiT)[None], 9, axis=0).copy()   # phi = sum_q g_q
+    dLds = ctypes.c_double(0.0)
+    for n in range(nsteps - 1, -1, -1):
+        out = np.zeros_like(lam)
+        rc = lib().ora_adjoint_step(ctypes.byref(p), _ptr(states[n]), _ptr(lam), _ptr(out), n, ctypes.byref(dLds))
+        if rc != 0:
+            raise ValueError("the oracle adjoint supports periodic domains only")
+        lam = out
+    dphi0 = np.zeros((p.ny, p.nx))
+    lib().ora_adjoint_init(ctypes.byref(p), _ptr(phi0), _ptr(np.ascontiguousarray(lam)), _ptr(dphi0), ctypes.byref(dLds))
+    return dphi0, dLds.value

@@ -410,3 +410,181 @@ void ora_observe(int nx, int ny, const double* phi, const double* phi0, double* 
     out[4] = e;
     out[5] = r;
 }
+
+/* ---------------------------------------------------------------- adjoint (reverse mode) of the step
+ *
+ * For a loss L of the final state, lambda_q(x) = dL/dg_q(x).  The step of Eq. LB is
+ *   phi = sum_q g_q;  mu = f'(phi) - kappa lap phi;  F = -(phi^2/rho) grad mu [+ K grad div(phi u)];
+ *   post_q = (1 - 1/tau) g_q + g_eq_q(phi, mu, u)/tau + (1 - 1/(2 tau)) S_q(F);  g'_q(x + c_q) = post_q(x),
+ * and its adjoint runs these operations backwards with every linear map transposed.  The transposed
+ * stencils are written out as (A^T v)(x) = sum_k A_k v(x - c_k).  The velocity field enters as u = s u_ref;
+ * dLds accumulates dL/ds at s = 1.  Periodic domains only (returns -2 when walls are set).
+ */
+
+/* f''(phi) for the double well of Eq. bulk. */
+double ora_d2fdphi2(double phi, double beta, double phiA, double phiB)
+{
+    return 2.0 * beta * ((phi - phiB) * (2.0 * phi - phiA - phiB) + (phi - phiA) * (2.0 * phi - phiA - phiB)
+                         + 2.0 * (phi - phiA) * (phi - phiB));
+}
+
+/* Partial derivatives of Eq. geq at one node: dphi[q], dmu[q], dux[q], duy[q]. */
+static void geq_partials(double phi, double ux, double uy, double eta, double* dphi, double* dmu, double* dux,
+                         double* duy)
+{
+    double uu = ux * ux + uy * uy;
+    dphi[0] = 1.0 - WQ[0] * uu / (2.0 * CS2);
+    dmu[0] = (WQ[0] - 1.0) * eta;
+    dux[0] = -WQ[0] * phi * ux / CS2;
+    duy[0] = -WQ[0] * phi * uy / CS2;
+    for (int q = 1; q < Q; q++) {
+        double cu = CX[q] * ux + CY[q] * uy;
+        dphi[q] = WQ[q] * (cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+        dmu[q] = WQ[q] * eta;
+        dux[q] = WQ[q] * phi * (CX[q] / CS2 + cu * CX[q] / (CS2 * CS2) - ux / CS2);
+        duy[q] = WQ[q] * phi * (CY[q] / CS2 + cu * CY[q] / (CS2 * CS2) - uy / CS2);
+    }
+}
+
+/* (G^T v)(x) for the isotropic gradient G: sum_k w_k c_k v(x - c_k) / c_s^2, one component. */
+static double gradT(int nx, int ny, const double* v, int i, int j, int comp)
+{
+    double s = 0.0;
+    for (int k = 1; k < Q; k++) {
+        long m = nbr(nx, ny, 0, i, j, -CX[k], -CY[k]);
+        s += WQ[k] * (comp == 0 ? CX[k] : CY[k]) * v[m];
+    }
+    return s / CS2;
+}
+
+/* (L^T v)(x) for the isotropic Laplacian L: sum_k 2 w_k (v(x - c_k) - v(x)) / c_s^2. */
+static double lapT(int nx, int ny, const double* v, int i, int j)
+{
+    double c = v[(long)j * nx + i], s = 0.0;
+    for (int k = 1; k < Q; k++) s += 2.0 * WQ[k] * (v[nbr(nx, ny, 0, i, j, -CX[k], -CY[k])] - c);
+    return s / CS2;
+}
+
+/* lambda_n from lambda_{n+1} for the step n -> n+1 taken from state gin (the forward g at step n). */
+int ora_adjoint_step(const ora_params* p, const double* gin, const double* lam_next, double* lam, long n,
+                     double* dLds)
+{
+    if (p->walls) return -2;
+    ora_consts c;
+    ora_derive(p, &c);
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double* phi = (double*)malloc(sizeof(double) * N);
+    double* mu = (double*)malloc(sizeof(double) * N);
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* gmx = (double*)malloc(sizeof(double) * N);
+    double* gmy = (double*)malloc(sizeof(double) * N);
+    double* gmubx = (double*)malloc(sizeof(double) * N);   /* adjoint of grad mu */
+    double* gmuby = (double*)malloc(sizeof(double) * N);
+    double* Fbx = (double*)malloc(sizeof(double) * N);     /* adjoint of F */
+    double* Fby = (double*)malloc(sizeof(double) * N);
+    double* phib = (double*)malloc(sizeof(double) * N);    /* adjoint of phi */
+    double* mub = (double*)malloc(sizeof(double) * N);     /* adjoint of mu */
+    double* Db = (double*)malloc(sizeof(double) * N);      /* adjoint of D = div(phi u) */
+    double* ubx = (double*)malloc(sizeof(double) * N);     /* adjoint of u */
+    double* uby = (double*)malloc(sizeof(double) * N);
+
+    /* forward quantities at step n */
+    ora_phi(nx, ny, gin, phi);
+    ora_mu(p, &c, phi, mu);
+    ora_velocity_field(p, n, ux, uy);
+    ora_grad(nx, ny, 0, mu, gmx, gmy);
+
+    /* streaming reversed, collision, g_eq, S and F1 (local) */
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long x = (long)j * nx + i;
+            double pb[Q], dphi[Q], dmu[Q], dux[Q], duy[Q];
+            for (int q = 0; q < Q; q++) pb[q] = lam_next[q * N + nbr(nx, ny, 0, i, j, CX[q], CY[q])];
+            geq_partials(phi[x], ux[x], uy[x], c.eta, dphi, dmu, dux, duy);
+            double fbx = 0.0, fby = 0.0, pl = 0.0, ml = 0.0, bx = 0.0, by = 0.0;
+            for (int q = 0; q < Q; q++) {
+                lam[q * N + x] = (1.0 - 1.0 / p->tau) * pb[q];
+                double geqb = pb[q] / p->tau;
+                double Sb = (1.0 - 1.0 / (2.0 * p->tau)) * pb[q];
+                fbx += Sb * WQ[q] * CX[q] / CS2;      /* S_q = w_q c_q . F / c_s^2 */
+                fby += Sb * WQ[q] * CY[q] / CS2;
+                pl += geqb * dphi[q];
+                ml += geqb * dmu[q];
+                bx += geqb * dux[q];
+                by += geqb * duy[q];
+            }
+            double rho = c.a * phi[x] + c.b;
+            double coef = phi[x] * phi[x] / rho;                         /* F1 = -coef grad mu */
+            double dcoef = phi[x] * (c.a * phi[x] + 2.0 * c.b) / (rho * rho);
+            gmubx[x] = -coef * fbx;
+            gmuby[x] = -coef * fby;
+            pl += -dcoef * (fbx * gmx[x] + fby * gmy[x]);
+            Fbx[x] = fbx; Fby[x] = fby;
+            phib[x] = pl; mub[x] = ml; ubx[x] = bx; uby[x] = by;
+        }
+    /* grad mu = G mu  ->  mu_bar += G^T grad_mu_bar;  F2 = K G D  ->  D_bar = K G^T F_bar */
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long x = (long)j * nx + i;
+            mub[x] += gradT(nx, ny, gmubx, i, j, 0) + gradT(nx, ny, gmuby, i, j, 1);
+            Db[x] = (p->model == 2) ? 3.0 * CS2 * c.K * (gradT(nx, ny, Fbx, i, j, 0) + gradT(nx, ny, Fby, i, j, 1)) : 0.0;
+        }
+    /* mu = f'(phi) - kappa L phi;  D = G . (phi u)  ->  j_bar = G^T D_bar */
+    double acc = 0.0;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long x = (long)j * nx + i;
+            double pb = phib[x] + ora_d2fdphi2(phi[x], c.beta, p->phiA, p->phiB) * mub[x] - c.kappa * lapT(nx, ny, mub, i, j);
+            if (p->model == 2) {
+                double jbx = gradT(nx, ny, Db, i, j, 0), jby = gradT(nx, ny, Db, i, j, 1);
+                pb += ux[x] * jbx + uy[x] * jby;
+                ubx[x] += phi[x] * jbx;
+                uby[x] += phi[x] * jby;
+            }
+            acc += ubx[x] * ux[x] + uby[x] * uy[x];   /* u = s u_ref: du/ds = u */
+            for (int q = 0; q < Q; q++) lam[q * N + x] += pb;  /* phi = sum_q g_q */
+        }
+    *dLds += acc;
+    free(phi); free(mu); free(ux); free(uy); free(gmx); free(gmy); free(gmubx); free(gmuby); free(Fbx); free(Fby);
+    free(phib); free(mub); free(Db); free(ubx); free(uby);
+    return 0;
+}
+
+/* Adjoint of the initial state g_q(x, 0) = g_eq_q(phi0, mu(phi0), u(x, 0)): dL/dphi0 from lambda_0. */
+int ora_adjoint_init(const ora_params* p, const double* phi0, const double* lam0, double* dphi0, double* dLds)
+{
+    if (p->walls) return -2;
+    ora_consts c;
+    ora_derive(p, &c);
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* mub = (double*)malloc(sizeof(double) * N);
+    ora_velocity_field(p, 0, ux, uy);
+    double acc = 0.0;
+    for (long x = 0; x < N; x++) {
+        double dphi[Q], dmu[Q], dux[Q], duy[Q];
+        geq_partials(phi0[x], ux[x], uy[x], c.eta, dphi, dmu, dux, duy);
+        double pl = 0.0, ml = 0.0, bx = 0.0, by = 0.0;
+        for (int q = 0; q < Q; q++) {
+            pl += lam0[q * N + x] * dphi[q];
+            ml += lam0[q * N + x] * dmu[q];
+            bx += lam0[q * N + x] * dux[q];
+            by += lam0[q * N + x] * duy[q];
+        }
+        dphi0[x] = pl;
+        mub[x] = ml;
+        acc += bx * ux[x] + by * uy[x];
+    }
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long x = (long)j * nx + i;
+            dphi0[x] += ora_d2fdphi2(phi0[x], c.beta, p->phiA, p->phiB) * mub[x] - c.kappa * lapT(nx, ny, mub, i, j);
+        }
+    *dLds += acc;
+    free(ux); free(uy); free(mub);
+    return 0;
+}

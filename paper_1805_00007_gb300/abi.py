@@ -20,7 +20,8 @@ PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
 # Exported symbols, as declared in include/lbch.h.
 SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free",
            "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream", "lb_ch_test_hook",
-           "lb_ch_field_stats_noalloc")
+           "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
+           "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end")
 LBCH_HOOK_SKIP_FIRST_LOAD = 1
 
 
@@ -73,8 +74,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_stream.restype = vp
     lib.lb_ch_test_hook.argtypes = [vp, ctypes.c_int, ctypes.c_long]
     lib.lb_ch_field_stats_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.lb_ch_state_bytes.argtypes = [vp, P(ctypes.c_longlong)]
+    lib.lb_ch_state_save.argtypes = [vp, vp]
+    lib.lb_ch_state_load.argtypes = [vp, vp]
+    lib.lb_ch_tape_phi.argtypes = [vp, vp]
+    lib.lb_ch_adjoint_begin.argtypes = [vp, vp]
+    lib.lb_ch_adjoint_step.argtypes = [vp, vp, ctypes.c_long]
+    lib.lb_ch_adjoint_end.argtypes = [vp, vp, dp]
     for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
-                 "lb_ch_test_hook", "lb_ch_field_stats_noalloc"):
+                 "lb_ch_test_hook", "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save",
+                 "lb_ch_state_load", "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step",
+                 "lb_ch_adjoint_end"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -157,7 +167,40 @@ def lb_ch_field_stats_noalloc(phi_ptr: int, phi0_ptr: int, nx: int, ny: int, pit
     device array of 6 doubles, without any device allocation."""
     _check(load().lb_ch_field_stats_noalloc(ctypes.c_void_p(phi_ptr), ctypes.c_void_p(phi0_ptr), int(nx), int(ny),
                                             int(pitch), ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream or 0)),
-           "lb_ch_field_stats_noalloc")
+           "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
+           "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end")
+
+
+def lb_ch_state_bytes(h) -> int:
+    out = ctypes.c_longlong(0)
+    _check(load().lb_ch_state_bytes(h, ctypes.byref(out)), "lb_ch_state_bytes")
+    return out.value
+
+
+def lb_ch_state_save(h, dst_ptr: int):
+    _check(load().lb_ch_state_save(h, ctypes.c_void_p(dst_ptr)), "lb_ch_state_save")
+
+
+def lb_ch_state_load(h, src_ptr: int):
+    _check(load().lb_ch_state_load(h, ctypes.c_void_p(src_ptr)), "lb_ch_state_load")
+
+
+def lb_ch_tape_phi(h, dst_ptr: int):
+    _check(load().lb_ch_tape_phi(h, ctypes.c_void_p(dst_ptr)), "lb_ch_tape_phi")
+
+
+def lb_ch_adjoint_begin(h, dphiT_ptr: int):
+    _check(load().lb_ch_adjoint_begin(h, ctypes.c_void_p(dphiT_ptr)), "lb_ch_adjoint_begin")
+
+
+def lb_ch_adjoint_step(h, phi_n_ptr: int, n: int):
+    _check(load().lb_ch_adjoint_step(h, ctypes.c_void_p(phi_n_ptr), int(n)), "lb_ch_adjoint_step")
+
+
+def lb_ch_adjoint_end(h, dphi0_ptr: int) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().lb_ch_adjoint_end(h, ctypes.c_void_p(dphi0_ptr), ctypes.byref(out)), "lb_ch_adjoint_end")
+    return out.value
 
 
 def lb_ch_stream(h) -> int:

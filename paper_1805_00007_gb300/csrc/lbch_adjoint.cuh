@@ -1,0 +1,290 @@
+// lbch_adjoint.cuh -- reverse-mode adjoint of the step kernel (one instance, periodic domain).
+//
+// For a loss L of phi(T), lambda_q(x) = dL/dg_q(x).  One forward step (Eq. LB with Eqs. geq, liangFi,
+// mu, t0-phiu, mark3) is
+//   phi = sum_q g_q;  mu = f'(phi) - kappa lap phi;  F = -(phi^2/rho) grad mu [+ K grad div(phi u)];
+//   post_q = (1 - 1/tau) g_q + g_eq_q(phi, mu, u)/tau + (1 - 1/(2 tau)) S_q(F);  g'_q(x + c_q) = post_q(x).
+// Its Jacobian depends on the populations only through phi, so the backward sweep needs the forward phi
+// of each step (a tape) and nothing else.  The transpose of every linear map is applied explicitly:
+// streaming becomes a gather from x + c_q, the gradient stencil G becomes (G^T v)(x) = sum_k w_k c_k
+// v(x - c_k)/c_s^2, the Laplacian L becomes (L^T v)(x) = sum_k 2 w_k (v(x - c_k) - v(x))/c_s^2.  The velocity
+// is u = s u_ref and dL/ds (at s = 1) is accumulated in double.
+//
+// Layout: plain arrays over the instance, node index y*nx + x; lambda is [9][N].  Five one-thread-per-node
+// kernels per adjoint step (forward mu; local adjoints; mu_bar and D_bar; phi_bar and the new lambda;
+// the dL/ds reduction), written for clarity first.
+#pragma once
+#include "lbch_kernels.cuh"
+
+namespace lbch {
+namespace adj {
+
+struct AdjArgs {
+    int nx, ny, model;
+    int pitch;                 // of the velocity tables' X part
+    int ylen;                  // length of each Y table
+    long long n;               // forward step index of this adjoint step
+};
+
+__device__ __forceinline__ int wp(int i, int n) { return i >= n ? i - n : (i < 0 ? i + n : i); }
+
+template <typename C>
+__device__ __forceinline__ void vel_at(const InstDev& I, const double* tabs, const AdjArgs& a, int x, int y,
+                                       double T, C& ux, C& uy)
+{
+    const double* tX1 = tabs + I.tab;
+    const double* tX2 = tX1 + a.pitch;
+    const double* tY1 = tX2 + a.pitch;
+    const double* tY2 = tY1 + a.ylen;
+    ux = (C)(tX1[x + GC] * tY1[y + GR] * T);
+    uy = (C)(tX2[x + GC] * tY2[y + GR] * T);
+}
+
+template <typename C> __device__ __forceinline__ C d2f(C phi, C beta, C phiA, C phiB)
+{
+    // f''(phi) of f = beta (phi - phiA)^2 (phi - phiB)^2 (Eq. bulk)
+    return C(2) * beta * ((phi - phiB) * (C(2) * phi - phiA - phiB) + (phi - phiA) * (C(2) * phi - phiA - phiB)
+                          + C(2) * (phi - phiA) * (phi - phiB));
+}
+
+// Partial derivatives of Eq. geq with respect to phi, mu and u at one node.
+template <typename C>
+__device__ __forceinline__ void geq_partials(C phi, C ux, C uy, C eta, C* dphi, C* dmu, C* dux, C* duy)
+{
+    C uu = ux * ux + uy * uy;
+    dphi[0] = C(1) - wq<C>(0) * C(1.5) * uu;
+    dmu[0] = (wq<C>(0) - C(1)) * eta;
+    dux[0] = -wq<C>(0) * phi * C(3) * ux;
+    duy[0] = -wq<C>(0) * phi * C(3) * uy;
+#pragma unroll
+    for (int q = 1; q < 9; q++) {
+        C cu = (C)cx(q) * ux + (C)cy(q) * uy;
+        dphi[q] = wq<C>(q) * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+        dmu[q] = wq<C>(q) * eta;
+        dux[q] = wq<C>(q) * phi * (C(3) * (C)cx(q) + C(9) * cu * (C)cx(q) - C(3) * ux);
+        duy[q] = wq<C>(q) * phi * (C(3) * (C)cy(q) + C(9) * cu * (C)cy(q) - C(3) * uy);
+    }
+}
+
+// (G^T v)(x), component comp, on the periodic lattice.
+template <typename C>
+__device__ __forceinline__ C gradT(const C* v, int nx, int ny, int x, int y, int comp)
+{
+    C s = C(0);
+#pragma unroll
+    for (int k = 1; k < 9; k++) {
+        int xs = wp(x - cx(k), nx), ys = wp(y - cy(k), ny);
+        s += wq<C>(k) * (C)(comp == 0 ? cx(k) : cy(k)) * v[(long long)ys * nx + xs];
+    }
+    return C(3) * s;
+}
+
+// (L^T v)(x) on the periodic lattice.
+template <typename C>
+__device__ __forceinline__ C lapT(const C* v, int nx, int ny, int x, int y)
+{
+    C c = v[(long long)y * nx + x], s = C(0);
+#pragma unroll
+    for (int k = 1; k < 9; k++) {
+        int xs = wp(x - cx(k), nx), ys = wp(y - cy(k), ny);
+        s += C(2) * wq<C>(k) * (v[(long long)ys * nx + xs] - c);
+    }
+    return C(3) * s;
+}
+
+// forward mu = f'(phi) - kappa lap phi at step n
+template <typename C>
+__global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const C* phi, C* mu)
+{
+    const InstDev& I = inst[0];
+    const Consts<C>& K0 = consts<C>(I);
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)a.nx * a.ny) return;
+    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    C c = phi[k], s = C(0);
+#pragma unroll
+    for (int q = 1; q < 9; q++) {
+        int xs = wp(x + cx(q), a.nx), ys = wp(y + cy(q), a.ny);
+        s += C(2) * wq<C>(q) * (phi[(long long)ys * a.nx + xs] - c);
+    }
+    mu[k] = dfdphi(c, K0.beta, K0.phiA, K0.phiB) - K0.kappa * C(3) * s;
+}
+
+// local adjoints of streaming, collision, g_eq, S and F1
+template <typename C>
+__global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const C* phi,
+                             const C* mu, const C* lam_next, C* lam, C* gmb, C* Fb, C* phib, C* mub, C* ub)
+{
+    const InstDev& I = inst[0];
+    const Consts<C>& K0 = consts<C>(I);
+    const long long N = (long long)a.nx * a.ny;
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    C ph = phi[k];
+    C ux, uy;
+    vel_at(I, tabs, a, x, y, T, ux, uy);
+    // grad mu at x
+    C gx = C(0), gy = C(0);
+#pragma unroll
+    for (int q = 1; q < 9; q++) {
+        C m = mu[(long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
+        gx += wq<C>(q) * (C)cx(q) * m;
+        gy += wq<C>(q) * (C)cy(q) * m;
+    }
+    gx *= C(3);
+    gy *= C(3);
+    C dphi[9], dmu[9], dux[9], duy[9];
+    geq_partials(ph, ux, uy, K0.eta, dphi, dmu, dux, duy);
+    C fbx = C(0), fby = C(0), pl = C(0), ml = C(0), bx = C(0), by = C(0);
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        // reverse streaming: post_q(x) was sent to x + c_q
+        C pb = lam_next[q * N + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
+        lam[q * N + k] = K0.omt * pb;
+        C geqb = pb * K0.itau;
+        C Sb = K0.src * pb;
+        fbx += Sb * C(3) * wq<C>(q) * (C)cx(q);  // S_q = w_q c_q . F / c_s^2
+        fby += Sb * C(3) * wq<C>(q) * (C)cy(q);
+        pl += geqb * dphi[q];
+        ml += geqb * dmu[q];
+        bx += geqb * dux[q];
+        by += geqb * duy[q];
+    }
+    C rho = K0.a * ph + K0.b;
+    C coef = ph * ph / rho;                                  // F1 = -coef grad mu
+    C dcoef = ph * (K0.a * ph + C(2) * K0.b) / (rho * rho);
+    gmb[k] = -coef * fbx;
+    gmb[N + k] = -coef * fby;
+    Fb[k] = fbx;
+    Fb[N + k] = fby;
+    phib[k] = pl - dcoef * (fbx * gx + fby * gy);
+    mub[k] = ml;
+    ub[k] = bx;
+    ub[N + k] = by;
+}
+
+// mu_bar += G^T grad_mu_bar;  D_bar = 3 c_s^2 K G^T F_bar
+template <typename C>
+__global__ void transpose1_kernel(const InstDev* inst, AdjArgs a, const C* gmb, const C* Fb, C* mub, C* Db)
+{
+    const InstDev& I = inst[0];
+    const Consts<C>& K0 = consts<C>(I);
+    const long long N = (long long)a.nx * a.ny;
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    mub[k] += gradT(gmb, a.nx, a.ny, x, y, 0) + gradT(gmb + N, a.nx, a.ny, x, y, 1);
+    Db[k] = (a.model == 2) ? K0.K * (gradT(Fb, a.nx, a.ny, x, y, 0) + gradT(Fb + N, a.nx, a.ny, x, y, 1)) : C(0);
+}
+
+// phi_bar = local + f''(phi) mu_bar - kappa L^T mu_bar + u . G^T D_bar; lambda_q += phi_bar; dL/ds per node
+template <typename C>
+__global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const C* phi,
+                                  const C* phib, const C* mub, const C* Db, const C* ub, C* lam, double* ds)
+{
+    const InstDev& I = inst[0];
+    const Consts<C>& K0 = consts<C>(I);
+    const long long N = (long long)a.nx * a.ny;
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    C ph = phi[k];
+    C ux, uy;
+    vel_at(I, tabs, a, x, y, T, ux, uy);
+    C pb = phib[k] + d2f(ph, K0.beta, K0.phiA, K0.phiB) * mub[k] - K0.kappa * lapT(mub, a.nx, a.ny, x, y);
+    C bx = ub[k], by = ub[N + k];
+    if (a.model == 2) {
+        C jbx = gradT(Db, a.nx, a.ny, x, y, 0), jby = gradT(Db, a.nx, a.ny, x, y, 1);
+        pb += ux * jbx + uy * jby;
+        bx += ph * jbx;
+        by += ph * jby;
+    }
+    ds[k] = (double)bx * (double)ux + (double)by * (double)uy;  // u = s u_ref: du/ds = u
+#pragma unroll
+    for (int q = 0; q < 9; q++) lam[q * N + k] += pb;           // phi = sum_q g_q
+}
+
+// adjoint of the initial equilibria: dL/dphi0 (two kernels: local, then the mu transpose)
+template <typename C>
+__global__ void init_local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const double* phi0,
+                                  int pitch0, const C* lam, C* mub, C* dphi0, double* ds)
+{
+    const InstDev& I = inst[0];
+    const Consts<C>& K0 = consts<C>(I);
+    const long long N = (long long)a.nx * a.ny;
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    C ph = (C)phi0[(long long)(I.row0 + y) * pitch0 + GC + x];
+    C ux, uy;
+    vel_at(I, tabs, a, x, y, T, ux, uy);
+    C dphi[9], dmu[9], dux[9], duy[9];
+    geq_partials(ph, ux, uy, K0.eta, dphi, dmu, dux, duy);
+    C pl = C(0), ml = C(0), bx = C(0), by = C(0);
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        C l = lam[q * N + k];
+        pl += l * dphi[q];
+        ml += l * dmu[q];
+        bx += l * dux[q];
+        by += l * duy[q];
+    }
+    dphi0[k] = pl;
+    mub[k] = ml;
+    ds[k] = (double)bx * (double)ux + (double)by * (double)uy;
+}
+
+template <typename C>
+__global__ void init_transpose_kernel(const InstDev* inst, AdjArgs a, const double* phi0, int pitch0, const C* mub,
+                                      C* dphi0)
+{
+    const InstDev& I = inst[0];
+    const Consts<C>& K0 = consts<C>(I);
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)a.nx * a.ny) return;
+    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    C ph = (C)phi0[(long long)(I.row0 + y) * pitch0 + GC + x];
+    dphi0[k] += d2f(ph, K0.beta, K0.phiA, K0.phiB) * mub[k] - K0.kappa * lapT(mub, a.nx, a.ny, x, y);
+}
+
+// deterministic sum of ds[0..N) into *acc (one block, fixed order), executed once per adjoint step
+__global__ void __launch_bounds__(256) sum_into_kernel(const double* ds, long long N, double* acc)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (long long k = threadIdx.x; k < N; k += 256) s += ds[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *acc += sh[0];
+}
+
+// phi of the instance (padded storage, plus the low part on the float path) into a plain array
+template <typename P, typename C>
+__global__ void tape_kernel(const InstDev* inst, int pitch, const P* phi, const float* lo, C* out)
+{
+    const InstDev& I = inst[0];
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)I.nx * I.ny) return;
+    int y = (int)(k / I.nx), x = (int)(k - (long long)y * I.nx);
+    long long gi = (long long)(I.row0 + y) * pitch + GC + x;
+    out[k] = (C)((double)phi[gi] + (lo ? (double)lo[gi] : 0.0));
+}
+
+// lambda_T: dL/dg_q = dL/dphi(T) for every q
+template <typename C>
+__global__ void adj_begin_kernel(long long N, const C* dphiT, C* lam)
+{
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    C v = dphiT[k];
+#pragma unroll
+    for (int q = 0; q < 9; q++) lam[q * N + k] = v;
+}
+
+}  // namespace adj
+}  // namespace lbch

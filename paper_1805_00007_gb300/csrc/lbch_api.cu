@@ -6,6 +6,7 @@
 // the mobility relation after Eq. phit3 and the Peclet number of Sec. III.A), launches the persistent
 // step kernel -- replayed from CUDA graphs of 64 steps -- and the reductions behind lb_ch_observe.
 #include "lbch.h"
+#include "lbch_adjoint.cuh"
 #include "lbch_kernels.cuh"
 
 #include <algorithm>
@@ -112,6 +113,11 @@ struct lbch_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double* h_stage = nullptr;  // pinned host staging
     size_t h_stage_bytes = 0;
+    // adjoint workspace (instance 0), allocated by the first lb_ch_adjoint_begin
+    void* adj = nullptr;        // one block: lambda[2] (9N each), mu, grad_mu_bar (2N), F_bar (2N), phi_bar,
+                                // mu_bar, D_bar, u_bar (2N) in the adjoint type; then ds (N) and dL/ds, double
+    size_t adj_elem = 8;
+    int adj_par = 0;            // which lambda holds the current adjoint
 };
 
 namespace {
@@ -294,6 +300,7 @@ void release(lbch_handle* h)
     if (h->partials) cudaFree(h->partials);
     if (h->result) cudaFree(h->result);
     if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->adj) cudaFree(h->adj);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -366,6 +373,103 @@ lbch_status run_reduce(lbch_handle* h)
     reduce_final_kernel<<<h->n_inst, RED_NT, 0, h->stream>>>(h->partials, h->chunks, h->result);
     CK(cudaGetLastError());
     return LBCH_OK;
+}
+
+// ----------------------------------------------------------------------------- state and adjoint helpers
+
+size_t state_bytes(const lbch_handle* h)
+{
+    const size_t cells = (size_t)h->rows * h->pitch;
+    size_t b = 256;  // header: the step index
+    b += (cells * h->nq * h->g_elem + 255) / 256 * 256;
+    b += (cells * h->phi_elem + 255) / 256 * 256;
+    if (h->lo[0]) b += (cells * 4 + 255) / 256 * 256;
+    return b;
+}
+
+struct AdjView {  // pointers into the adjoint workspace
+    void* lam[2];
+    void *mu, *gmb, *Fb, *phib, *mub, *Db, *ub;
+    double* ds;
+    double* dLds;
+};
+
+AdjView adj_view(lbch_handle* h)
+{
+    const size_t N = (size_t)h->inst[0].nx * h->inst[0].ny, e = h->adj_elem;
+    char* p = static_cast<char*>(h->adj);
+    AdjView v;
+    auto take = [&](size_t n) { void* r = p; p += (n * e + 255) / 256 * 256; return r; };
+    v.lam[0] = take(9 * N);
+    v.lam[1] = take(9 * N);
+    v.mu = take(N);
+    v.gmb = take(2 * N);
+    v.Fb = take(2 * N);
+    v.phib = take(N);
+    v.mub = take(N);
+    v.Db = take(N);
+    v.ub = take(2 * N);
+    v.ds = reinterpret_cast<double*>(p);
+    p += (N * 8 + 255) / 256 * 256;
+    v.dLds = reinterpret_cast<double*>(p);
+    return v;
+}
+
+size_t adj_bytes(const lbch_handle* h)
+{
+    const size_t N = (size_t)h->inst[0].nx * h->inst[0].ny, e = h->adj_elem;
+    auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+    return 2 * r(9 * N * e) + r(N * e) + 2 * r(2 * N * e) + 3 * r(N * e) + r(2 * N * e) + r(N * 8) + 256;
+}
+
+adj::AdjArgs adj_args(const lbch_handle* h, long long n)
+{
+    adj::AdjArgs a;
+    a.nx = h->inst[0].nx;
+    a.ny = h->inst[0].ny;
+    a.model = h->inst[0].model;
+    a.pitch = h->pitch;
+    a.ylen = h->inst[0].tiles_y * h->ty + 2 * GR;
+    a.n = n;
+    return a;
+}
+
+template <typename C>
+cudaError_t adjoint_step_t(lbch_handle* h, const C* phi_n, long long n)
+{
+    AdjView v = adj_view(h);
+    adj::AdjArgs a = adj_args(h, n);
+    const long long N = (long long)a.nx * a.ny;
+    const int nb = (int)((N + 255) / 256);
+    const double T = vel_t(h->inst[0].vel, h->inst[0].Tper, n);
+    const C* lam_next = static_cast<const C*>(v.lam[h->adj_par]);
+    C* lam = static_cast<C*>(v.lam[h->adj_par ^ 1]);
+    adj::fwd_mu_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, phi_n, (C*)v.mu);
+    adj::local_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.mu, lam_next, lam,
+                                                    (C*)v.gmb, (C*)v.Fb, (C*)v.phib, (C*)v.mub, (C*)v.ub);
+    adj::transpose1_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, (const C*)v.gmb, (const C*)v.Fb, (C*)v.mub,
+                                                         (C*)v.Db);
+    adj::transpose2_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib,
+                                                         (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam, v.ds);
+    adj::sum_into_kernel<<<1, 256, 0, h->stream>>>(v.ds, N, v.dLds);
+    h->adj_par ^= 1;
+    return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t adjoint_end_t(lbch_handle* h, C* dphi0)
+{
+    AdjView v = adj_view(h);
+    adj::AdjArgs a = adj_args(h, 0);
+    const long long N = (long long)a.nx * a.ny;
+    const int nb = (int)((N + 255) / 256);
+    const double T = vel_t(h->inst[0].vel, h->inst[0].Tper, 0);
+    const C* lam = static_cast<const C*>(v.lam[h->adj_par]);
+    adj::init_local_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, h->phi0, h->pitch, lam,
+                                                         (C*)v.mub, dphi0, v.ds);
+    adj::init_transpose_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, h->phi0, h->pitch, (const C*)v.mub, dphi0);
+    adj::sum_into_kernel<<<1, 256, 0, h->stream>>>(v.ds, N, v.dLds);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -655,6 +759,114 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
 }
 
 void* lb_ch_stream(lbch_handle* h) { return h ? (void*)h->stream : nullptr; }
+
+lbch_status lb_ch_state_bytes(lbch_handle* h, long long* bytes)
+{
+    if (!h || !bytes) return fail(LBCH_EINVAL, "NULL handle or output");
+    *bytes = (long long)state_bytes(h);
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_state_save(lbch_handle* h, void* dst)
+{
+    if (!h || !dst) return fail(LBCH_EINVAL, "NULL handle or buffer");
+    const int par = (int)(h->n & 1);
+    const size_t cells = (size_t)h->rows * h->pitch;
+    char* p = static_cast<char*>(dst);
+    long long n = h->n;
+    CK(cudaMemcpyAsync(p, &n, sizeof n, cudaMemcpyHostToDevice, h->stream));
+    p += 256;
+    size_t gb = cells * h->nq * h->g_elem, pb = cells * h->phi_elem;
+    CK(cudaMemcpyAsync(p, h->g[par], gb, cudaMemcpyDeviceToDevice, h->stream));
+    p += (gb + 255) / 256 * 256;
+    CK(cudaMemcpyAsync(p, h->phi[par], pb, cudaMemcpyDeviceToDevice, h->stream));
+    p += (pb + 255) / 256 * 256;
+    if (h->lo[par]) CK(cudaMemcpyAsync(p, h->lo[par], cells * 4, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // the step index was copied from a host variable
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_state_load(lbch_handle* h, const void* src)
+{
+    if (!h || !src) return fail(LBCH_EINVAL, "NULL handle or buffer");
+    const char* p = static_cast<const char*>(src);
+    long long n = 0;
+    CK(cudaMemcpyAsync(&n, p, sizeof n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (n < 0) return fail(LBCH_EINVAL, "buffer does not hold a saved state");
+    const int par = (int)(n & 1);
+    const size_t cells = (size_t)h->rows * h->pitch;
+    p += 256;
+    size_t gb = cells * h->nq * h->g_elem, pb = cells * h->phi_elem;
+    CK(cudaMemcpyAsync(h->g[par], p, gb, cudaMemcpyDeviceToDevice, h->stream));
+    p += (gb + 255) / 256 * 256;
+    CK(cudaMemcpyAsync(h->phi[par], p, pb, cudaMemcpyDeviceToDevice, h->stream));
+    p += (pb + 255) / 256 * 256;
+    if (h->lo[par]) CK(cudaMemcpyAsync(h->lo[par], p, cells * 4, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(&h->ctl->time, &n, sizeof n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->n = n;
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_tape_phi(lbch_handle* h, void* dst)
+{
+    if (!h || !dst) return fail(LBCH_EINVAL, "NULL handle or buffer");
+    if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
+    const int par = (int)(h->n & 1);
+    const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
+    const int nb = (int)((N + 255) / 256);
+    if (h->prec == LBCH_F64)
+        adj::tape_kernel<double, double><<<nb, 256, 0, h->stream>>>(h->d_inst, h->pitch, (const double*)h->phi[par],
+                                                                    nullptr, (double*)dst);
+    else
+        adj::tape_kernel<float, float><<<nb, 256, 0, h->stream>>>(h->d_inst, h->pitch, (const float*)h->phi[par],
+                                                                  h->lo[par], (float*)dst);
+    CK(cudaGetLastError());
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
+{
+    if (!h || !dL_dphiT) return fail(LBCH_EINVAL, "NULL handle or gradient");
+    if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
+    if (h->inst[0].walls) return fail(LBCH_EINVAL, "the adjoint supports periodic domains only");
+    h->adj_elem = h->prec == LBCH_F64 ? 8 : 4;
+    if (!h->adj) CK(cudaMalloc(&h->adj, adj_bytes(h)));
+    AdjView v = adj_view(h);
+    const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
+    const int nb = (int)((N + 255) / 256);
+    h->adj_par = 0;
+    if (h->adj_elem == 8)
+        adj::adj_begin_kernel<double><<<nb, 256, 0, h->stream>>>(N, (const double*)dL_dphiT, (double*)v.lam[0]);
+    else
+        adj::adj_begin_kernel<float><<<nb, 256, 0, h->stream>>>(N, (const float*)dL_dphiT, (float*)v.lam[0]);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(v.dLds, 0, sizeof(double), h->stream));
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_adjoint_step(lbch_handle* h, const void* phi_n, long n)
+{
+    if (!h || !phi_n || n < 0) return fail(LBCH_EINVAL, "NULL handle, NULL phi or negative step");
+    if (!h->adj) return fail(LBCH_EINVAL, "lb_ch_adjoint_begin was not called");
+    cudaError_t e = h->adj_elem == 8 ? adjoint_step_t<double>(h, (const double*)phi_n, n)
+                                     : adjoint_step_t<float>(h, (const float*)phi_n, n);
+    CK(e);
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds)
+{
+    if (!h || !dL_dphi0 || !dL_ds) return fail(LBCH_EINVAL, "NULL handle or output");
+    if (!h->adj) return fail(LBCH_EINVAL, "lb_ch_adjoint_begin was not called");
+    cudaError_t e = h->adj_elem == 8 ? adjoint_end_t<double>(h, (double*)dL_dphi0)
+                                     : adjoint_end_t<float>(h, (float*)dL_dphi0);
+    CK(e);
+    CK(cudaMemcpyAsync(dL_ds, adj_view(h).dLds, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBCH_OK;
+}
 
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
 {
