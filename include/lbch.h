@@ -145,13 +145,15 @@ void* lb_ch_stream(lbch_handle* h);
  *
  * The step's Jacobian depends on the populations only through phi (Eq. LB with Eqs. geq, liangFi,
  * mu, t0-phiu, mark3 are linear in g except through phi = sum g), so reverse mode needs, for every
- * forward step n, the forward phi(n) (a tape entry) and nothing else.  The adjoint type is double for
- * LBCH_F64 handles and float otherwise; every array below is a device pointer the caller owns.
+ * forward step n, the forward phi(n) (a tape entry) and nothing else.  The tape type is the forward
+ * path's: double for LBCH_F64 handles, float otherwise.  Gradients (dL_dphiT, dL_dphi0) are double for
+ * every precision, and the adjoint itself is carried in double.  Every array below is a device pointer
+ * the caller owns.
  *
  * lb_ch_state_bytes / lb_ch_state_save / lb_ch_state_load: the full state (populations, phi, step
  * index) to and from a caller buffer of lb_ch_state_bytes() bytes -- the checkpoints of a segmented
  * (square-root) reverse sweep.  Loading also restores the step index.
- * lb_ch_tape_phi: phi of the current state into dst (nx*ny values, row-major, adjoint type).
+ * lb_ch_tape_phi: phi of the current state into dst (nx*ny values, row-major, tape type).
  * lb_ch_adjoint_begin: lambda = dL/dg_q(T) = dL/dphi(T) for every q (dL_dphiT: nx*ny values).
  * lb_ch_adjoint_step: one step backwards: lambda_n from lambda_{n+1}, given phi_n (the forward phi at
  *   step n) and n; accumulates dL/ds, where the prescribed velocity is s times the configured one.

@@ -48,25 +48,25 @@ class _Evolve(torch.autograd.Function):
             n += k
         phiT = torch.from_numpy(sim.phi()).to(device=phi0.device, dtype=phi0.dtype)
         ctx.sim, ctx.ckpts, ctx.scale, ctx.dev = sim, ckpts, s, dev
-        ctx.adt = torch.float64 if prec in ("f64", abi.LBCH_F64) else torch.float32
+        ctx.tape_dtype = torch.float64 if prec in ("f64", abi.LBCH_F64) else torch.float32
         ctx.phi0_meta = (phi0.device, phi0.dtype)
         return phiT
 
     @staticmethod
     def backward(ctx, grad_phiT):
-        sim, dev, adt = ctx.sim, ctx.dev, ctx.adt
+        sim, dev, tdt = ctx.sim, ctx.dev, ctx.tape_dtype
         ny, nx = grad_phiT.shape
-        g = grad_phiT.detach().to(device=dev, dtype=adt).contiguous()
+        g = grad_phiT.detach().to(device=dev, dtype=torch.float64).contiguous()
         abi.lb_ch_adjoint_begin(sim.h, g.data_ptr())
         for n0, n1, buf in reversed(ctx.ckpts):
             abi.lb_ch_state_load(sim.h, buf.data_ptr())
-            tape = torch.empty((n1 - n0, ny, nx), dtype=adt, device=dev)
+            tape = torch.empty((n1 - n0, ny, nx), dtype=tdt, device=dev)
             for k in range(n1 - n0):
                 abi.lb_ch_tape_phi(sim.h, tape[k].data_ptr())
                 sim.step(1)
             for k in range(n1 - n0 - 1, -1, -1):
                 abi.lb_ch_adjoint_step(sim.h, tape[k].data_ptr(), n0 + k)
-        dphi0 = torch.empty((ny, nx), dtype=adt, device=dev)
+        dphi0 = torch.empty((ny, nx), dtype=torch.float64, device=dev)
         dLds = abi.lb_ch_adjoint_end(sim.h, dphi0.data_ptr())
         sim.close()
         ctx.ckpts = None

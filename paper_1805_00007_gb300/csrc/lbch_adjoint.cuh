@@ -10,7 +10,10 @@
 // v(x - c_k)/c_s^2, the Laplacian L becomes (L^T v)(x) = sum_k 2 w_k (v(x - c_k) - v(x))/c_s^2.  The velocity
 // is u = s u_ref and dL/ds (at s = 1) is accumulated in double.
 //
-// Layout: plain arrays over the instance, node index y*nx + x; lambda is [9][N].  Five one-thread-per-node
+// Layout: plain arrays over the instance, node index y*nx + x; lambda is [9][N].  The adjoint is carried
+// in double for every storage precision (at tau = 1 all nine lambda_q are equal and dL/du is formed from
+// differences of neighbouring lambda, which float storage would round away); the tape keeps the
+// forward phi in the precision of the forward path, so the gradient is that of the path actually run.  Five one-thread-per-node
 // kernels per adjoint step (forward mu; local adjoints; mu_bar and D_bar; phi_bar and the new lambda;
 // the dL/ds reduction), written for clarity first.
 #pragma once
@@ -92,27 +95,27 @@ __device__ __forceinline__ C lapT(const C* v, int nx, int ny, int x, int y)
     return C(3) * s;
 }
 
-// forward mu = f'(phi) - kappa lap phi at step n
-template <typename C>
-__global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const C* phi, C* mu)
+// forward mu = f'(phi) - kappa lap phi at step n (phi from the tape, of type TP)
+template <typename C, typename TP>
+__global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const TP* phi, C* mu)
 {
     const InstDev& I = inst[0];
     const Consts<C>& K0 = consts<C>(I);
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)a.nx * a.ny) return;
     int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
-    C c = phi[k], s = C(0);
+    C c = (C)phi[k], s = C(0);
 #pragma unroll
     for (int q = 1; q < 9; q++) {
         int xs = wp(x + cx(q), a.nx), ys = wp(y + cy(q), a.ny);
-        s += C(2) * wq<C>(q) * (phi[(long long)ys * a.nx + xs] - c);
+        s += C(2) * wq<C>(q) * ((C)phi[(long long)ys * a.nx + xs] - c);
     }
     mu[k] = dfdphi(c, K0.beta, K0.phiA, K0.phiB) - K0.kappa * C(3) * s;
 }
 
 // local adjoints of streaming, collision, g_eq, S and F1
-template <typename C>
-__global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const C* phi,
+template <typename C, typename TP>
+__global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
                              const C* mu, const C* lam_next, C* lam, C* gmb, C* Fb, C* phib, C* mub, C* ub)
 {
     const InstDev& I = inst[0];
@@ -121,7 +124,7 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
-    C ph = phi[k];
+    C ph = (C)phi[k];
     C ux, uy;
     vel_at(I, tabs, a, x, y, T, ux, uy);
     // grad mu at x
@@ -179,8 +182,8 @@ __global__ void transpose1_kernel(const InstDev* inst, AdjArgs a, const C* gmb, 
 }
 
 // phi_bar = local + f''(phi) mu_bar - kappa L^T mu_bar + u . G^T D_bar; lambda_q += phi_bar; dL/ds per node
-template <typename C>
-__global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const C* phi,
+template <typename C, typename TP>
+__global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
                                   const C* phib, const C* mub, const C* Db, const C* ub, C* lam, double* ds)
 {
     const InstDev& I = inst[0];
@@ -189,7 +192,7 @@ __global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjAr
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
-    C ph = phi[k];
+    C ph = (C)phi[k];
     C ux, uy;
     vel_at(I, tabs, a, x, y, T, ux, uy);
     C pb = phib[k] + d2f(ph, K0.beta, K0.phiA, K0.phiB) * mub[k] - K0.kappa * lapT(mub, a.nx, a.ny, x, y);

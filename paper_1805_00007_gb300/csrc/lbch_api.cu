@@ -434,8 +434,8 @@ adj::AdjArgs adj_args(const lbch_handle* h, long long n)
     return a;
 }
 
-template <typename C>
-cudaError_t adjoint_step_t(lbch_handle* h, const C* phi_n, long long n)
+template <typename C, typename TP>
+cudaError_t adjoint_step_t(lbch_handle* h, const TP* phi_n, long long n)
 {
     AdjView v = adj_view(h);
     adj::AdjArgs a = adj_args(h, n);
@@ -444,12 +444,12 @@ cudaError_t adjoint_step_t(lbch_handle* h, const C* phi_n, long long n)
     const double T = vel_t(h->inst[0].vel, h->inst[0].Tper, n);
     const C* lam_next = static_cast<const C*>(v.lam[h->adj_par]);
     C* lam = static_cast<C*>(v.lam[h->adj_par ^ 1]);
-    adj::fwd_mu_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, phi_n, (C*)v.mu);
-    adj::local_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.mu, lam_next, lam,
+    adj::fwd_mu_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, a, phi_n, (C*)v.mu);
+    adj::local_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.mu, lam_next, lam,
                                                     (C*)v.gmb, (C*)v.Fb, (C*)v.phib, (C*)v.mub, (C*)v.ub);
     adj::transpose1_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, (const C*)v.gmb, (const C*)v.Fb, (C*)v.mub,
                                                          (C*)v.Db);
-    adj::transpose2_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib,
+    adj::transpose2_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib,
                                                          (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam, v.ds);
     adj::sum_into_kernel<<<1, 256, 0, h->stream>>>(v.ds, N, v.dLds);
     h->adj_par ^= 1;
@@ -831,16 +831,13 @@ lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
     if (!h || !dL_dphiT) return fail(LBCH_EINVAL, "NULL handle or gradient");
     if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
     if (h->inst[0].walls) return fail(LBCH_EINVAL, "the adjoint supports periodic domains only");
-    h->adj_elem = h->prec == LBCH_F64 ? 8 : 4;
+    h->adj_elem = 8;  // the adjoint is carried in double for every storage precision
     if (!h->adj) CK(cudaMalloc(&h->adj, adj_bytes(h)));
     AdjView v = adj_view(h);
     const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
     const int nb = (int)((N + 255) / 256);
     h->adj_par = 0;
-    if (h->adj_elem == 8)
-        adj::adj_begin_kernel<double><<<nb, 256, 0, h->stream>>>(N, (const double*)dL_dphiT, (double*)v.lam[0]);
-    else
-        adj::adj_begin_kernel<float><<<nb, 256, 0, h->stream>>>(N, (const float*)dL_dphiT, (float*)v.lam[0]);
+    adj::adj_begin_kernel<double><<<nb, 256, 0, h->stream>>>(N, (const double*)dL_dphiT, (double*)v.lam[0]);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(v.dLds, 0, sizeof(double), h->stream));
     return LBCH_OK;
@@ -850,8 +847,8 @@ lbch_status lb_ch_adjoint_step(lbch_handle* h, const void* phi_n, long n)
 {
     if (!h || !phi_n || n < 0) return fail(LBCH_EINVAL, "NULL handle, NULL phi or negative step");
     if (!h->adj) return fail(LBCH_EINVAL, "lb_ch_adjoint_begin was not called");
-    cudaError_t e = h->adj_elem == 8 ? adjoint_step_t<double>(h, (const double*)phi_n, n)
-                                     : adjoint_step_t<float>(h, (const float*)phi_n, n);
+    cudaError_t e = h->prec == LBCH_F64 ? adjoint_step_t<double, double>(h, (const double*)phi_n, n)
+                                        : adjoint_step_t<double, float>(h, (const float*)phi_n, n);
     CK(e);
     return LBCH_OK;
 }
@@ -860,8 +857,7 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds)
 {
     if (!h || !dL_dphi0 || !dL_ds) return fail(LBCH_EINVAL, "NULL handle or output");
     if (!h->adj) return fail(LBCH_EINVAL, "lb_ch_adjoint_begin was not called");
-    cudaError_t e = h->adj_elem == 8 ? adjoint_end_t<double>(h, (double*)dL_dphi0)
-                                     : adjoint_end_t<float>(h, (float*)dL_dphi0);
+    cudaError_t e = adjoint_end_t<double>(h, (double*)dL_dphi0);
     CK(e);
     CK(cudaMemcpyAsync(dL_ds, adj_view(h).dLds, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));

@@ -29,7 +29,7 @@ def _grad(p, phi0, nsteps, prec, segment=None, ref=None):
     target = torch.tensor(phi0 if ref is None else ref, dtype=torch.float64)
     loss = 0.5 * torch.sum((phiT - target) ** 2)
     loss.backward()
-    return x.grad.numpy(), float(s.grad), float(loss), phiT.detach().numpy()
+    return x.grad.numpy(), float(s.grad.detach()), float(loss.detach()), phiT.detach().numpy()
 
 
 CASES = [
