@@ -26,7 +26,7 @@ _SRC = os.path.join(_HERE, "lbch_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblbch_oracle.so")
 
-VEL_UNIFORM, VEL_ROTATION, VEL_VORTEX, VEL_SHEAR, VEL_REV_SHEAR, VEL_DEFORM = range(6)
+VEL_UNIFORM, VEL_ROTATION, VEL_VORTEX, VEL_SHEAR, VEL_REV_SHEAR, VEL_DEFORM, VEL_COUPLED = range(7)
 
 
 class _Params(ctypes.Structure):
@@ -40,6 +40,7 @@ class _Params(ctypes.Structure):
         ("U0", ctypes.c_double), ("ux0", ctypes.c_double), ("uy0", ctypes.c_double),
         ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("half", ctypes.c_double),
         ("Tper", ctypes.c_double), ("shear", ctypes.c_double),
+        ("nu", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
     ]
 
 
@@ -106,6 +107,9 @@ def lib() -> ctypes.CDLL:
         _lib.ora_adjoint_step.restype = ctypes.c_int
         _lib.ora_adjoint_init.argtypes = [P(_Params), dp, dp, dp, dp]
         _lib.ora_adjoint_init.restype = ctypes.c_int
+        _lib.ora_ns_fields.argtypes = [P(_Params), dp, dp, dp, dp, dp]
+        _lib.ora_ns_init.argtypes = [P(_Params), dp, dp, dp, dp, dp]
+        _lib.ora_ns_step.argtypes = [P(_Params), dp, dp, dp, dp, ctypes.c_long]
     return _lib
 
 
@@ -282,3 +286,34 @@ def adjoint(cfg, phi0, nsteps: int, dL_dphiT):
     dphi0 = np.zeros((p.ny, p.nx))
     lib().ora_adjoint_init(ctypes.byref(p), _ptr(phi0), _ptr(np.ascontiguousarray(lam)), _ptr(dphi0), ctypes.byref(dLds))
     return dphi0, dLds.value
+
+
+def ns_init(cfg, phi0, ux0=None, uy0=None):
+    """Initial coupled state (f, g): g = g_eq(phi0, mu0, u0), f = f_eq(p = 0, rho(phi0), u0)."""
+    p = params(cfg)
+    phi0 = _f64(phi0)
+    ux0 = np.zeros_like(phi0) if ux0 is None else _f64(ux0)
+    uy0 = np.zeros_like(phi0) if uy0 is None else _f64(uy0)
+    f = np.zeros((9, p.ny, p.nx)); g = np.zeros((9, p.ny, p.nx))
+    lib().ora_ns_init(ctypes.byref(p), _ptr(phi0), _ptr(ux0), _ptr(uy0), _ptr(f), _ptr(g))
+    return f, g
+
+
+def ns_fields(cfg, f, g):
+    p = params(cfg)
+    f, g = _f64(f), _f64(g)
+    ux = np.zeros((p.ny, p.nx)); uy = np.zeros_like(ux); pr = np.zeros_like(ux)
+    lib().ora_ns_fields(ctypes.byref(p), _ptr(f), _ptr(g), _ptr(ux), _ptr(uy), _ptr(pr))
+    return ux, uy, pr
+
+
+def ns_simulate(cfg, phi0, nsteps: int, ux0=None, uy0=None):
+    """Coupled Cahn-Hilliard / Navier-Stokes run: returns (phi, ux, uy, p, f, g) after nsteps."""
+    p = params(cfg)
+    f, g = ns_init(cfg, phi0, ux0, uy0)
+    for n in range(nsteps):
+        fo = np.zeros_like(f); go = np.zeros_like(g)
+        lib().ora_ns_step(ctypes.byref(p), _ptr(f), _ptr(g), _ptr(fo), _ptr(go), n)
+        f, g = fo, go
+    ux, uy, pr = ns_fields(cfg, f, g)
+    return phi_of(g), ux, uy, pr, f, g

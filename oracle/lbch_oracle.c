@@ -42,7 +42,8 @@ static const double WQ[Q] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9
 static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 static const double CS2 = 1.0 / 3.0;
 
-enum { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_SHEAR = 3, VEL_REV_SHEAR = 4, VEL_DEFORM = 5 };
+enum { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_SHEAR = 3, VEL_REV_SHEAR = 4, VEL_DEFORM = 5,
+       VEL_COUPLED = 6 };
 
 /* Problem parameters, in the paper's notation.  Plain numbers; the derived constants are computed here. */
 typedef struct {
@@ -61,6 +62,8 @@ typedef struct {
     double xc, yc, half;/* rotation centre and half-length of the rotation field */
     double Tper;        /* period / reversal time of the time-dependent fields, in steps */
     double shear;       /* shear rate of the wall-driven shear flow */
+    double nu;          /* kinematic viscosity of the coupled flow (VEL_COUPLED) */
+    double gx, gy;      /* gravity of the coupled flow; buoyancy force -(rho - (rhoA + rhoB)/2) g */
 } ora_params;
 
 /* Constants the model derives from the parameters. */
@@ -587,4 +590,204 @@ int ora_adjoint_init(const ora_params* p, const double* phi0, const double* lam0
     *dLds += acc;
     free(ux); free(uy); free(mub);
     return 0;
+}
+
+
+/* ---------------------------------------------------------------- coupled Navier-Stokes step
+ *
+ * For flows that are not prescribed (Sec. III.E, Rayleigh-Taylor) the velocity comes from a second
+ * D2Q9 lattice Boltzmann equation for the Navier-Stokes equations (Eq. NS).  The paper calls that
+ * equation standard without writing it out; the oracle takes (reading R14) the incompressible,
+ * pressure-based single-relaxation-time form with the forcing of the phase-field literature it cites:
+ *   f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq)/tau_f + (1 - 1/(2 tau_f)) G_i,   tau_f = nu/c_s^2 + 1/2,
+ *   f_0^eq = (w_0 - 1) p/c_s^2 + rho s_0(u),  f_i^eq = w_i p/c_s^2 + rho s_i(u)  (i > 0),
+ *   s_i(u) = w_i [c_i.u/c_s^2 + (c_i.u)^2/(2 c_s^4) - u^2/(2 c_s^2)],  Gamma_i = w_i + s_i(u),
+ *   G_i = (c_i - u) . [Gamma_i F + (Gamma_i - w_i) c_s^2 grad rho] / c_s^2,
+ *   rho u = sum_i c_i f_i + F/2,   p = c_s^2/(1 - w_0) [sum_{i>0} f_i + (1/2) u . grad rho + rho s_0(u)],
+ * with rho = a phi + b (Eq. rho) and the total force
+ *   F = -phi grad mu - (rho - (rhoA + rhoB)/2) g + (d rho/d phi) M lap(mu) u        (Eq. NS, form c).
+ * The Cahn-Hilliard step then uses this u and F1 = (phi/rho)(-phi grad mu - grad p) (Eq. t0-phiu).
+ * Walls: both lattices bounce back halfway (no slip, u_w = 0); stencil operands at ghost rows take the
+ * mirror values (R7), p and the components of phi u included.
+ */
+
+/* equilibrium and forcing of the Navier-Stokes lattice at one node */
+static void ns_feq(double pr, double rho, double ux, double uy, double* feq)
+{
+    double uu = ux * ux + uy * uy;
+    for (int i = 0; i < Q; i++) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        double s = WQ[i] * (cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+        feq[i] = (i == 0 ? (WQ[0] - 1.0) : WQ[i]) * pr / CS2 + rho * s;
+    }
+}
+
+static void ns_forcing(double ux, double uy, double Fx, double Fy, double grx, double gry, double* G)
+{
+    double uu = ux * ux + uy * uy;
+    for (int i = 0; i < Q; i++) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        double s = WQ[i] * (cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+        double Gam = WQ[i] + s;
+        double ex = CX[i] - ux, ey = CY[i] - uy;
+        G[i] = (ex * (Gam * Fx + s * CS2 * grx) + ey * (Gam * Fy + s * CS2 * gry)) / CS2;
+    }
+}
+
+/* Macroscopic fields of the coupled state: phi, mu, grad mu, grad rho, lap mu, force F, u, p. */
+typedef struct {
+    double *phi, *mu, *gmx, *gmy, *grx, *gry, *lmu, *Fx, *Fy, *ux, *uy, *pr;
+} ns_fields;
+
+static void ns_alloc(ns_fields* w, long N)
+{
+    double** a[] = {&w->phi, &w->mu, &w->gmx, &w->gmy, &w->grx, &w->gry, &w->lmu, &w->Fx, &w->Fy, &w->ux, &w->uy, &w->pr};
+    for (int k = 0; k < 12; k++) *a[k] = (double*)malloc(sizeof(double) * N);
+}
+
+static void ns_free(ns_fields* w)
+{
+    double* a[] = {w->phi, w->mu, w->gmx, w->gmy, w->grx, w->gry, w->lmu, w->Fx, w->Fy, w->ux, w->uy, w->pr};
+    for (int k = 0; k < 12; k++) free(a[k]);
+}
+
+static void ns_compute_fields(const ora_params* p, const ora_consts* c, const double* f, const double* g, ns_fields* w)
+{
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double rbar = 0.5 * (p->rhoA + p->rhoB);
+    ora_phi(nx, ny, g, w->phi);                          /* Eq. macroscopicg */
+    ora_mu(p, c, w->phi, w->mu);                         /* Eq. mu */
+    ora_grad(nx, ny, p->walls, w->mu, w->gmx, w->gmy);
+    ora_grad(nx, ny, p->walls, w->phi, w->grx, w->gry);  /* grad rho = a grad phi (Eq. rho) */
+    ora_lap(nx, ny, p->walls, w->mu, w->lmu);
+    for (long x = 0; x < N; x++) {
+        double phi = w->phi[x], rho = c->a * phi + c->b;
+        w->grx[x] *= c->a;
+        w->gry[x] *= c->a;
+        double F0x = -phi * w->gmx[x] - (rho - rbar) * p->gx;
+        double F0y = -phi * w->gmy[x] - (rho - rbar) * p->gy;
+        double mx = 0.0, my = 0.0, sum1 = 0.0;
+        for (int i = 0; i < Q; i++) {
+            mx += CX[i] * f[i * N + x];
+            my += CY[i] * f[i * N + x];
+            if (i > 0) sum1 += f[i * N + x];
+        }
+        /* rho u = m + F/2 with F = F0 + a M lap(mu) u, solved for u */
+        double den = rho - 0.5 * c->a * c->M * w->lmu[x];
+        double ux = (mx + 0.5 * F0x) / den, uy = (my + 0.5 * F0y) / den;
+        w->ux[x] = ux;
+        w->uy[x] = uy;
+        w->Fx[x] = F0x + c->a * c->M * w->lmu[x] * ux;
+        w->Fy[x] = F0y + c->a * c->M * w->lmu[x] * uy;
+        double uu = ux * ux + uy * uy;
+        double s0 = WQ[0] * (-uu / (2.0 * CS2));
+        w->pr[x] = CS2 / (1.0 - WQ[0]) * (sum1 + 0.5 * (ux * w->grx[x] + uy * w->gry[x]) + rho * s0);
+    }
+}
+
+/* Macroscopic velocity and pressure of a coupled state (ux, uy, p), for observation. */
+void ora_ns_fields(const ora_params* p, const double* f, const double* g, double* ux, double* uy, double* pr)
+{
+    ora_consts c;
+    ora_derive(p, &c);
+    long N = (long)p->nx * p->ny;
+    ns_fields w;
+    ns_alloc(&w, N);
+    ns_compute_fields(p, &c, f, g, &w);
+    memcpy(ux, w.ux, sizeof(double) * N);
+    memcpy(uy, w.uy, sizeof(double) * N);
+    memcpy(pr, w.pr, sizeof(double) * N);
+    ns_free(&w);
+}
+
+/* Initial coupled state: g = g_eq(phi0, mu0, u0), f = f_eq(p = 0, rho(phi0), u0), u0 given per node. */
+void ora_ns_init(const ora_params* p, const double* phi0, const double* ux0, const double* uy0, double* f, double* g)
+{
+    ora_consts c;
+    ora_derive(p, &c);
+    long N = (long)p->nx * p->ny;
+    double* mu = (double*)malloc(sizeof(double) * N);
+    ora_mu(p, &c, phi0, mu);
+    for (long x = 0; x < N; x++) {
+        double geq[Q], feq[Q];
+        ora_geq(phi0[x], mu[x], ux0[x], uy0[x], c.eta, geq);
+        ns_feq(0.0, c.a * phi0[x] + c.b, ux0[x], uy0[x], feq);
+        for (int q = 0; q < Q; q++) {
+            g[q * N + x] = geq[q];
+            f[q * N + x] = feq[q];
+        }
+    }
+    free(mu);
+}
+
+/* One coupled step n -> n+1: the Cahn-Hilliard lattice g and the Navier-Stokes lattice f. */
+void ora_ns_step(const ora_params* p, const double* fin, const double* gin, double* fout, double* gout, long n)
+{
+    (void)n;
+    ora_consts c;
+    ora_derive(p, &c);
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double tauf = p->nu / CS2 + 0.5;
+    ns_fields w;
+    ns_alloc(&w, N);
+    ns_compute_fields(p, &c, fin, gin, &w);
+    double* gpx = (double*)malloc(sizeof(double) * N);
+    double* gpy = (double*)malloc(sizeof(double) * N);
+    double* Fx = (double*)malloc(sizeof(double) * N);
+    double* Fy = (double*)malloc(sizeof(double) * N);
+    ora_grad(nx, ny, p->walls, w.pr, gpx, gpy);
+    /* the Cahn-Hilliard force with the flow's pressure, Eqs. t0-phiu and mark3 */
+    for (long x = 0; x < N; x++) {
+        double phi = w.phi[x], rho = c.a * phi + c.b;
+        Fx[x] = phi / rho * (-phi * w.gmx[x] - gpx[x]);
+        Fy[x] = phi / rho * (-phi * w.gmy[x] - gpy[x]);
+    }
+    if (p->model == 2) {
+        double* jx = (double*)malloc(sizeof(double) * N);
+        double* jy = (double*)malloc(sizeof(double) * N);
+        double* D = (double*)malloc(sizeof(double) * N);
+        double* gDx = (double*)malloc(sizeof(double) * N);
+        double* gDy = (double*)malloc(sizeof(double) * N);
+        for (long x = 0; x < N; x++) {
+            jx[x] = w.phi[x] * w.ux[x];
+            jy[x] = w.phi[x] * w.uy[x];
+        }
+        ora_div(nx, ny, p->walls, jx, jy, D);
+        ora_grad(nx, ny, p->walls, D, gDx, gDy);
+        for (long x = 0; x < N; x++) {
+            Fx[x] += 3.0 * CS2 * c.K * gDx[x];
+            Fy[x] += 3.0 * CS2 * c.K * gDy[x];
+        }
+        free(jx); free(jy); free(D); free(gDx); free(gDy);
+    }
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long x = (long)j * nx + i;
+            double geq[Q], S[Q], feq[Q], G[Q];
+            double rho = c.a * w.phi[x] + c.b;
+            ora_geq(w.phi[x], w.mu[x], w.ux[x], w.uy[x], c.eta, geq);
+            ora_source(Fx[x], Fy[x], S);
+            ns_feq(w.pr[x], rho, w.ux[x], w.uy[x], feq);
+            ns_forcing(w.ux[x], w.uy[x], w.Fx[x], w.Fy[x], w.grx[x], w.gry[x], G);
+            for (int q = 0; q < Q; q++) {
+                double pg = gin[q * N + x] - (gin[q * N + x] - geq[q]) / p->tau + (1.0 - 1.0 / (2.0 * p->tau)) * S[q];
+                double pf = fin[q * N + x] - (fin[q * N + x] - feq[q]) / tauf + (1.0 - 1.0 / (2.0 * tauf)) * G[q];
+                int ii = ((i + CX[q]) % nx + nx) % nx;
+                int jj = j + CY[q];
+                if (!p->walls) {
+                    jj = ((jj % ny) + ny) % ny;
+                } else if (jj < 0 || jj >= ny) {
+                    /* halfway bounce-back at a wall at rest */
+                    gout[OPP[q] * N + x] = pg;
+                    fout[OPP[q] * N + x] = pf;
+                    continue;
+                }
+                gout[q * N + (long)jj * nx + ii] = pg;
+                fout[q * N + (long)jj * nx + ii] = pf;
+            }
+        }
+    free(gpx); free(gpy); free(Fx); free(Fy);
+    ns_free(&w);
 }

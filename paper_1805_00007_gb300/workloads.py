@@ -18,11 +18,11 @@ import numpy as np
 SEED_BASE = 20180501
 
 # Velocity-field codes, shared by the library's parameter struct and the oracle's.
-VEL_UNIFORM, VEL_ROTATION, VEL_VORTEX, VEL_SHEAR, VEL_REV_SHEAR, VEL_DEFORM = range(6)
+VEL_UNIFORM, VEL_ROTATION, VEL_VORTEX, VEL_SHEAR, VEL_REV_SHEAR, VEL_DEFORM, VEL_COUPLED = range(7)
 
 _DEFAULTS = dict(walls=0, model=2, vel=VEL_UNIFORM, nvort=4, phiA=1.0, phiB=0.0, sigma=0.01, W=4.0,
                  M=0.0, Pe=0.0, Ustar=0.0, tau=1.0, rhoA=1.0, rhoB=0.5, U0=0.0, ux0=0.0, uy0=0.0,
-                 xc=0.0, yc=0.0, half=1.0, Tper=1.0, shear=0.0)
+                 xc=0.0, yc=0.0, half=1.0, Tper=1.0, shear=0.0, nu=0.0, gx=0.0, gy=0.0)
 
 
 def make_params(**kw) -> dict:
@@ -153,6 +153,24 @@ def paper_translation(L0=200, U0=0.02, Pe=200.0, W=2.0, sigma=0.01, tau=0.5 + ma
                     tau=tau, phiA=1.0, phiB=-1.0, rhoA=1.0, rhoB=1.0 / rho_ratio, model=model)
     phi0 = circle_phi(L0, L0, L0 / 2, L0 / 2, L0 / 5, W, 1.0, -1.0)
     return p, phi0, int(round(L0 / U0))
+
+
+def rayleigh_taylor(nx=256, ny=1024, atwood=0.5, Re=3000.0, Pe=1000.0, W=5.0, sqrt_g_lambda=0.04,
+                    amp=0.1, sigma=5e-5, tau=1.0, model=2):
+    """Rayleigh-Taylor instability (Sec. III.E shape): heavy phase A (phi = 1) above y = ny/2 + amp nx
+    cos(2 pi x/nx), light phase B (phi = -1) below; periodic in x, no-slip walls in y; lambda = nx,
+    sqrt(g lambda) given, rho_h = 1, rho_l from the Atwood number, nu from Re = lambda sqrt(A g lambda/(1+A))/nu,
+    M from Pe with U* = sqrt(g lambda)."""
+    lam = float(nx)
+    g = sqrt_g_lambda ** 2 / lam
+    rho_h, rho_l = 1.0, (1.0 - atwood) / (1.0 + atwood)
+    nu = lam * math.sqrt(atwood * g * lam / (1.0 + atwood)) / Re
+    p = make_params(nx=nx, ny=ny, walls=1, vel=VEL_COUPLED, phiA=1.0, phiB=-1.0, rhoA=rho_h, rhoB=rho_l,
+                    sigma=sigma, W=W, Pe=Pe, Ustar=sqrt_g_lambda, tau=tau, model=model, nu=nu, gx=0.0, gy=g)
+    x, y = _grid(nx, ny)
+    h = ny / 2 + amp * nx * np.cos(2 * np.pi * x / nx)
+    phi0 = tanh_profile(y - h, W, 1.0, -1.0)
+    return p, phi0
 
 
 def random_smooth_phi(nx, ny, seed, amp=0.3, mean=0.5, modes=4) -> np.ndarray:
