@@ -56,14 +56,20 @@ typedef enum { LBCH_F64 = 0, LBCH_F32 = 1, LBCH_F16S = 2 } lbch_prec;
  *   VORTEX   : u = U0 (-sin^2(pi x/nx) sin(2 pi y/ny), sin(2 pi x/nx) sin^2(pi y/ny)) cos(pi t/Tper)
  *   SHEAR    : u = (shear (y - (ny-1)/2), 0), used with walls = 1      (wall-driven shear flow)
  *   REV_SHEAR: Eq. shear with L0 = nx, sign reversed for t >= Tper     (Sec. III.C)
- *   DEFORM   : Eq. deformation with L0 = nx, n = nvort, T0 = Tper      (Sec. III.D) */
+ *   DEFORM   : Eq. deformation with L0 = nx, n = nvort, T0 = Tper      (Sec. III.D)
+ *   COUPLED  : not prescribed -- solved by a second D2Q9 lattice for Eq. NS (the Rayleigh-Taylor
+ *              problem of Sec. III.E): the incompressible pressure-based single-relaxation-time form
+ *              with forcing, total force -phi grad mu - (rho - (rhoA+rhoB)/2)(gx, gy) + (d rho/d phi) M
+ *              lap(mu) u, and F1 = (phi/rho)(-phi grad mu - grad p) in the Cahn-Hilliard source.
+ *              Single-instance handles, LBCH_F64 or LBCH_F32 (plain float storage). */
 typedef enum {
     LBCH_VEL_UNIFORM = 0,
     LBCH_VEL_ROTATION = 1,
     LBCH_VEL_VORTEX = 2,
     LBCH_VEL_SHEAR = 3,
     LBCH_VEL_REV_SHEAR = 4,
-    LBCH_VEL_DEFORM = 5
+    LBCH_VEL_DEFORM = 5,
+    LBCH_VEL_COUPLED = 6
 } lbch_vel;
 
 /* Quantities lb_ch_observe returns.  Sums are accumulated in double on the GPU in a fixed order, so
@@ -72,14 +78,18 @@ typedef enum {
  *   ERR_L2  : ||E_phi||_2 = sqrt(sum (phi - phi0)^2 / sum phi0^2), Eq. err (1 value)
  *   MAX/MIN : extreme values of phi (Sec. III.A prints them)              (1 value)
  *   PHI     : the field phi as ny*nx doubles, row-major                   (nx*ny values)
- *   STEP    : the step index n of the current state                       (1 value) */
+ *   STEP    : the step index n of the current state                       (1 value)
+ *   U, P    : coupled handles only: the flow's velocity (ux field then uy field, 2*nx*ny values) and
+ *             pressure (nx*ny values) of the current state */
 typedef enum {
     LBCH_OBS_MASS = 0,
     LBCH_OBS_ERR_L2 = 1,
     LBCH_OBS_MAX = 2,
     LBCH_OBS_MIN = 3,
     LBCH_OBS_PHI = 4,
-    LBCH_OBS_STEP = 5
+    LBCH_OBS_STEP = 5,
+    LBCH_OBS_U = 6,
+    LBCH_OBS_P = 7
 } lbch_obs;
 
 /* Parameters of one problem instance, in the paper's notation.  The derived constants are computed by
@@ -102,6 +112,8 @@ typedef struct {
     double xc, yc, half; /* rotation centre and half-length */
     double Tper;         /* period or reversal time of time-dependent flows, in steps */
     double shear;        /* shear rate */
+    double nu;           /* LBCH_VEL_COUPLED: kinematic viscosity (tau_f = 3 nu + 1/2) */
+    double gx, gy;       /* LBCH_VEL_COUPLED: buoyancy force -(rho - (rhoA + rhoB)/2) (gx, gy) */
 } lbch_params;
 
 typedef struct lbch_handle lbch_handle;

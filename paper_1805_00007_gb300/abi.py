@@ -14,7 +14,7 @@ from . import _build
 
 LBCH_OK, LBCH_EINVAL, LBCH_ENOMEM, LBCH_ECUDA, LBCH_ETIMEOUT, LBCH_ENONFINITE = range(6)
 LBCH_F64, LBCH_F32, LBCH_F16S = range(3)
-LBCH_OBS_MASS, LBCH_OBS_ERR_L2, LBCH_OBS_MAX, LBCH_OBS_MIN, LBCH_OBS_PHI, LBCH_OBS_STEP = range(6)
+LBCH_OBS_MASS, LBCH_OBS_ERR_L2, LBCH_OBS_MAX, LBCH_OBS_MIN, LBCH_OBS_PHI, LBCH_OBS_STEP, LBCH_OBS_U, LBCH_OBS_P = range(8)
 PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
 
 # Exported symbols, as declared in include/lbch.h.
@@ -36,6 +36,7 @@ class lbch_params(ctypes.Structure):
         ("U0", ctypes.c_double), ("ux0", ctypes.c_double), ("uy0", ctypes.c_double),
         ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("half", ctypes.c_double),
         ("Tper", ctypes.c_double), ("shear", ctypes.c_double),
+        ("nu", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
     ]
 
 
@@ -132,12 +133,14 @@ def lb_ch_step(h, nsteps: int):
 
 
 def lb_ch_observe(h, inst: int, what: int, shape=None):
-    if what == LBCH_OBS_PHI:
+    if what in (LBCH_OBS_PHI, LBCH_OBS_P):
         out = np.empty(shape, dtype=np.float64)
+    elif what == LBCH_OBS_U:
+        out = np.empty((2,) + tuple(shape), dtype=np.float64)
     else:
         out = np.empty(1, dtype=np.float64)
     _check(load().lb_ch_observe(h, int(inst), int(what), _dptr(out)), "lb_ch_observe")
-    return out if what == LBCH_OBS_PHI else float(out[0])
+    return out if what in (LBCH_OBS_PHI, LBCH_OBS_P, LBCH_OBS_U) else float(out[0])
 
 
 def lb_ch_observe_all(h, what: int, n_inst: int) -> np.ndarray:
@@ -227,6 +230,15 @@ class Simulation:
 
     def observe(self, what: int, inst: int = 0) -> float:
         return lb_ch_observe(self.h, inst, what)
+
+    def velocity(self, inst: int = 0) -> np.ndarray:
+        """(2, ny, nx): the flow's velocity of a coupled handle."""
+        p = self.params[inst]
+        return lb_ch_observe(self.h, inst, LBCH_OBS_U, (p["ny"], p["nx"]))
+
+    def pressure(self, inst: int = 0) -> np.ndarray:
+        p = self.params[inst]
+        return lb_ch_observe(self.h, inst, LBCH_OBS_P, (p["ny"], p["nx"]))
 
     def observe_all(self, what: int) -> np.ndarray:
         return lb_ch_observe_all(self.h, what, len(self.params))

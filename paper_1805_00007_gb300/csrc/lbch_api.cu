@@ -8,6 +8,7 @@
 #include "lbch.h"
 #include "lbch_adjoint.cuh"
 #include "lbch_kernels.cuh"
+#include "lbch_ns.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -118,6 +119,11 @@ struct lbch_handle {
                                 // mu_bar, D_bar, u_bar (2N) in the adjoint type; then ds (N) and dL/ds, double
     size_t adj_elem = 8;
     int adj_par = 0;            // which lambda holds the current adjoint
+    // coupled Navier-Stokes state (LBCH_VEL_COUPLED): f[2], g[2] ([9][N]) and 11 node fields, one block
+    bool coupled = false;
+    void* ns = nullptr;
+    ns::NsConsts<double> nsd;
+    ns::NsConsts<float> nsf;
 };
 
 namespace {
@@ -173,8 +179,63 @@ cudaError_t prepare_step(lbch_handle* h)
     }
 }
 
+template <typename C> const ns::NsConsts<C>& ns_consts(const lbch_handle* h);
+template <> const ns::NsConsts<double>& ns_consts<double>(const lbch_handle* h) { return h->nsd; }
+template <> const ns::NsConsts<float>& ns_consts<float>(const lbch_handle* h) { return h->nsf; }
+template <typename C> const Consts<C>& ch_consts(const InstDev& I);
+template <> const Consts<double>& ch_consts<double>(const InstDev& I) { return I.cd; }
+template <> const Consts<float>& ch_consts<float>(const InstDev& I) { return I.cf; }
+
+template <typename C>
+ns::NsArgs<C> ns_args(lbch_handle* h, int parity)
+{
+    const InstDev& I = h->inst[0];
+    const size_t N = (size_t)I.nx * I.ny;
+    ns::NsArgs<C> a;
+    a.nx = I.nx; a.ny = I.ny; a.walls = I.walls; a.model = I.model; a.pitch = h->pitch; a.row0 = I.row0;
+    a.k = ch_consts<C>(I);
+    a.n = ns_consts<C>(h);
+    C* p = static_cast<C*>(h->ns);
+    C* f[2] = {p, p + 9 * N};
+    C* g[2] = {p + 18 * N, p + 27 * N};
+    a.f_in = f[parity]; a.f_out = f[parity ^ 1];
+    a.g_in = g[parity]; a.g_out = g[parity ^ 1];
+    C* w = p + 36 * N;
+    a.mu = w; a.ux = w + N; a.uy = w + 2 * N; a.pr = w + 3 * N; a.Fx = w + 4 * N; a.Fy = w + 5 * N;
+    a.grx = w + 6 * N; a.gry = w + 7 * N; a.gmx = w + 8 * N; a.gmy = w + 9 * N; a.D = w + 10 * N;
+    a.phi_in = static_cast<C*>(h->phi[parity]);
+    a.phi_out = static_cast<C*>(h->phi[parity ^ 1]);
+    return a;
+}
+
+// One coupled step: mu, the flow's moments and forces, div(phi u), collide-and-stream, phi(t+1).
+template <typename C>
+cudaError_t launch_ns_t(lbch_handle* h, int parity)
+{
+    ns::NsArgs<C> a = ns_args<C>(h, parity);
+    const int nb = (int)(((long long)a.nx * a.ny + 255) / 256);
+    ns::mu_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    ns::fields_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    if (a.model == 2) ns::div_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    ns::collide_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    ns::phi_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+// The flow's u and p of the current state (for observation): mu and fields kernels on it.
+template <typename C>
+cudaError_t ns_fields_t(lbch_handle* h, int parity)
+{
+    ns::NsArgs<C> a = ns_args<C>(h, parity);
+    const int nb = (int)(((long long)a.nx * a.ny + 255) / 256);
+    ns::mu_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    ns::fields_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(lbch_handle* h, int parity)
 {
+    if (h->coupled) return h->prec == LBCH_F64 ? launch_ns_t<double>(h, parity) : launch_ns_t<float>(h, parity);
     switch (h->prec) {
     case LBCH_F64: return launch_step_t<double, double, double, TX64, TY64>(h, parity);
     case LBCH_F32: return launch_step_t<float, float, float, TX32, TY32>(h, parity);
@@ -195,7 +256,8 @@ lbch_status check_params(const lbch_params& p, int k)
         return fail(LBCH_EINVAL, "instance %d: nx, ny must be in [4, 2^20] (got %d x %d)", k, p.nx, p.ny);
     if (!(p.tau > 0.5)) return fail(LBCH_EINVAL, "instance %d: tau must exceed 1/2", k);
     if (p.model != 1 && p.model != 2) return fail(LBCH_EINVAL, "instance %d: model must be 1 or 2", k);
-    if (p.vel < 0 || p.vel > 5) return fail(LBCH_EINVAL, "instance %d: unknown velocity field %d", k, p.vel);
+    if (p.vel < 0 || p.vel > 6) return fail(LBCH_EINVAL, "instance %d: unknown velocity field %d", k, p.vel);
+    if (p.vel == LBCH_VEL_COUPLED && !(p.nu > 0.0)) return fail(LBCH_EINVAL, "instance %d: coupled flow needs nu > 0", k);
     if (p.walls != 0 && p.walls != 1) return fail(LBCH_EINVAL, "instance %d: walls must be 0 or 1", k);
     if (p.phiA == p.phiB) return fail(LBCH_EINVAL, "instance %d: phiA == phiB", k);
     if (!(p.W > 0.0) || !(p.sigma >= 0.0)) return fail(LBCH_EINVAL, "instance %d: need W > 0, sigma >= 0", k);
@@ -243,6 +305,7 @@ void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<doub
     const double Lx = (double)p.nx, Ly = (double)p.ny;
     auto X = [&](double x, double& X1, double& X2) {
         switch (p.vel) {
+        case LBCH_VEL_COUPLED: X1 = 0.0; X2 = 0.0; break;  // the flow is solved, not prescribed
         case LBCH_VEL_UNIFORM: X1 = 1.0; X2 = 1.0; break;
         case LBCH_VEL_ROTATION: X1 = 1.0; X2 = p.U0 * pi * (x - p.xc) / p.half; break;
         case LBCH_VEL_VORTEX: { double s = std::sin(pi * x / Lx); X1 = -p.U0 * s * s; X2 = p.U0 * std::sin(2.0 * pi * x / Lx); break; }
@@ -253,6 +316,7 @@ void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<doub
     };
     auto Y = [&](double y, double& Y1, double& Y2) {
         switch (p.vel) {
+        case LBCH_VEL_COUPLED: Y1 = 0.0; Y2 = 0.0; break;
         case LBCH_VEL_UNIFORM: Y1 = p.ux0; Y2 = p.uy0; break;
         case LBCH_VEL_ROTATION: Y1 = -p.U0 * pi * (y - p.yc) / p.half; Y2 = 1.0; break;
         case LBCH_VEL_VORTEX: { double s = std::sin(pi * y / Ly); Y1 = std::sin(2.0 * pi * y / Ly); Y2 = s * s; break; }
@@ -301,6 +365,7 @@ void release(lbch_handle* h)
     if (h->result) cudaFree(h->result);
     if (h->h_stage) cudaFreeHost(h->h_stage);
     if (h->adj) cudaFree(h->adj);
+    if (h->ns) cudaFree(h->ns);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -487,9 +552,14 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         lbch_status s = check_params(params[k], k);
         if (s != LBCH_OK) return s;
     }
+    bool coupled = false;
+    for (int k = 0; k < n_inst; k++) coupled = coupled || params[k].vel == LBCH_VEL_COUPLED;
+    if (coupled && (n_inst != 1 || prec == LBCH_F16S))
+        return fail(LBCH_EINVAL, "the coupled flow needs a single instance in LBCH_F64 or LBCH_F32");
     lbch_handle* h = new (std::nothrow) lbch_handle();
     if (!h) return fail(LBCH_ENOMEM, "host allocation failed");
     h->prec = prec;
+    h->coupled = coupled;
     h->n_inst = n_inst;
     h->g_elem = prec == LBCH_F64 ? 8 : (prec == LBCH_F32 ? 4 : 2);
     h->phi_elem = prec == LBCH_F64 ? 8 : 4;  // the float path adds a float low part
@@ -609,6 +679,29 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
             h->ty, (__half*)h->g[0], (float*)h->phi[0], nullptr, h->nodes, h->d_node_begin);
     }
     CKI(cudaGetLastError());
+    if (coupled) {
+        const lbch_params& p = params[0];
+        const InstDev& d = h->inst[0];
+        double dphi = std::fabs(p.phiA - p.phiB);
+        double beta = 12.0 * p.sigma / (p.W * dphi * dphi * dphi * dphi);
+        double M = p.M > 0.0 ? p.M : p.Ustar * p.W / (p.Pe * beta * (p.phiA - p.phiB) * (p.phiA - p.phiB));
+        h->nsd.tauf = 3.0 * p.nu + 0.5;     // nu = c_s^2 (tau_f - 1/2)
+        h->nsd.gx = p.gx; h->nsd.gy = p.gy; h->nsd.M = M; h->nsd.rbar = 0.5 * (p.rhoA + p.rhoB);
+        h->nsf.tauf = (float)h->nsd.tauf; h->nsf.gx = (float)p.gx; h->nsf.gy = (float)p.gy;
+        h->nsf.M = (float)M; h->nsf.rbar = (float)h->nsd.rbar;
+        const size_t N = (size_t)d.nx * d.ny, esz = prec == LBCH_F64 ? 8 : 4;
+        CKI(cudaMalloc(&h->ns, 47 * N * esz));
+        CKI(cudaMemsetAsync(h->ns, 0, 47 * N * esz, h->stream));
+        const int nbn = (int)((N + 255) / 256);
+        if (prec == LBCH_F64) {
+            ns::NsArgs<double> a = ns_args<double>(h, 1);  // writes the parity-0 buffers
+            ns::init_kernel<double><<<nbn, 256, 0, h->stream>>>(a, h->phi0);
+        } else {
+            ns::NsArgs<float> a = ns_args<float>(h, 1);
+            ns::init_kernel<float><<<nbn, 256, 0, h->stream>>>(a, h->phi0);
+        }
+        CKI(cudaGetLastError());
+    }
     CKI(cudaStreamSynchronize(h->stream));  // the pinned staging buffer and the tables are reused after this
 #undef CKI
     *out = h;
@@ -682,6 +775,22 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out)
         for (long long k = 0; k < N; k++) finite = finite && std::isfinite(out[k]);
         return finite ? LBCH_OK : fail(LBCH_ENONFINITE, "phi holds non-finite values");
     }
+    if (what == LBCH_OBS_U || what == LBCH_OBS_P) {
+        if (!h->coupled) return fail(LBCH_EINVAL, "velocity and pressure are observable on coupled handles only");
+        const int parity = (int)(h->n & 1);
+        CK(h->prec == LBCH_F64 ? ns_fields_t<double>(h, parity) : ns_fields_t<float>(h, parity));
+        const size_t N = (size_t)h->inst[0].nx * h->inst[0].ny, e = h->prec == LBCH_F64 ? 8 : 4;
+        lbch_status s = stage(h, 2 * N * sizeof(double));
+        if (s != LBCH_OK) return s;
+        const char* w = static_cast<const char*>(h->ns) + 36 * N * e;  // mu, ux, uy, pr, ...
+        if (what == LBCH_OBS_U) CK(cudaMemcpyAsync(h->h_stage, w + N * e, 2 * N * e, cudaMemcpyDeviceToHost, h->stream));
+        else CK(cudaMemcpyAsync(h->h_stage, w + 3 * N * e, N * e, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const size_t cnt = what == LBCH_OBS_U ? 2 * N : N;
+        if (e == 8) std::memcpy(out, h->h_stage, cnt * 8);
+        else for (size_t k = 0; k < cnt; k++) out[k] = (double)reinterpret_cast<const float*>(h->h_stage)[k];
+        return LBCH_OK;
+    }
     if (what < LBCH_OBS_MASS || what > LBCH_OBS_MIN) return fail(LBCH_EINVAL, "unknown observable %d", what);
     lbch_status s = run_reduce(h);
     if (s != LBCH_OK) return s;
@@ -751,6 +860,10 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     // algorithmic HBM bytes per lattice update: read + write of the stored populations and of phi
     double bytes = 2.0 * (h->nq * (double)h->g_elem + (double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
+    if (h->coupled) {  // f and g read and written, phi read and written, u and p written and read
+        const double e = h->prec == LBCH_F64 ? 8.0 : 4.0;
+        bytes = 2.0 * (18.0 * e + e) + 2.0 * 3.0 * e;
+    }
     out[0] = (double)h->nodes;
     out[1] = bytes;
     out[2] = (double)h->grid;
@@ -770,6 +883,7 @@ lbch_status lb_ch_state_bytes(lbch_handle* h, long long* bytes)
 lbch_status lb_ch_state_save(lbch_handle* h, void* dst)
 {
     if (!h || !dst) return fail(LBCH_EINVAL, "NULL handle or buffer");
+    if (h->coupled) return fail(LBCH_EINVAL, "checkpoints are for prescribed-flow handles");
     const int par = (int)(h->n & 1);
     const size_t cells = (size_t)h->rows * h->pitch;
     char* p = static_cast<char*>(dst);
@@ -789,6 +903,7 @@ lbch_status lb_ch_state_save(lbch_handle* h, void* dst)
 lbch_status lb_ch_state_load(lbch_handle* h, const void* src)
 {
     if (!h || !src) return fail(LBCH_EINVAL, "NULL handle or buffer");
+    if (h->coupled) return fail(LBCH_EINVAL, "checkpoints are for prescribed-flow handles");
     const char* p = static_cast<const char*>(src);
     long long n = 0;
     CK(cudaMemcpyAsync(&n, p, sizeof n, cudaMemcpyDeviceToHost, h->stream));
@@ -831,6 +946,7 @@ lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
     if (!h || !dL_dphiT) return fail(LBCH_EINVAL, "NULL handle or gradient");
     if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
     if (h->inst[0].walls) return fail(LBCH_EINVAL, "the adjoint supports periodic domains only");
+    if (h->coupled) return fail(LBCH_EINVAL, "the adjoint supports prescribed flows only");
     h->adj_elem = 8;  // the adjoint is carried in double for every storage precision
     if (!h->adj) CK(cudaMalloc(&h->adj, adj_bytes(h)));
     AdjView v = adj_view(h);
