@@ -148,13 +148,14 @@ def sweep_params(n):
     return pp, wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
 
 
-def run_case(case, nsteps):
+def run_case(case, nsteps, tile=0):
     """One grid, no timing: the command ncu profiles."""
     import torch
     from paper_1805_00007_gb300 import abi
     prec, n = case.split("_")
     pp, f0 = sweep_params(int(n))
     with abi.Simulation(pp, f0, prec=prec) as sim:
+        abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, tile)
         sim.step(nsteps)
         torch.cuda.synchronize()
         m = sim.observe(abi.LBCH_OBS_MASS)
@@ -196,11 +197,12 @@ def main():
     ap.add_argument("--case", default=None,
                     help="profiling case PREC_N (e.g. f32_4096): init and --case-steps steps of that grid only")
     ap.add_argument("--case-steps", type=int, default=8)
+    ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
-        return run_case(args.case, args.case_steps)
+        return run_case(args.case, args.case_steps, args.case_tile)
 
     import torch
     import torch.distributed as dist
@@ -226,7 +228,7 @@ def main():
 
     def timed_revolutions(prec, k, w):
         """Run w warm-up and k timed revolutions; returns (seconds per revolution, the simulation)."""
-        sim = abi.Simulation(p, phi0, prec=prec, stream=stream.cuda_stream)
+        sim = abi.Simulation(p, phi0, prec=prec, stream=stream.cuda_stream, tune=True)
         for _ in range(w):
             with torch.cuda.stream(stream):
                 flush_l2(flush)
@@ -254,6 +256,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
     info32 = sim32.info()
+    tile32 = sim32.tile
     phi32 = sim32.phi()
     sim32.close()
 
@@ -289,7 +292,7 @@ def main():
     if not args.no_sweep:
         for prec, n in (("f32", 4096), ("f64", 4096), ("f16s", 4096)):
             pp, f0 = sweep_params(n)
-            sim = abi.Simulation(pp, f0, prec=prec, stream=stream.cuda_stream)
+            sim = abi.Simulation(pp, f0, prec=prec, stream=stream.cuda_stream, tune=True)
             sim.step(64)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -301,7 +304,7 @@ def main():
             dt = e0.elapsed_time(e1) / 1e3 / nst
             inf = sim.info()
             gbs = inf["bytes_per_lu"] * n * n / dt / 1e9
-            sweep[f"{prec}_{n}"] = {"MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6,
+            sweep[f"{prec}_{n}"] = {"MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6, "tile": sim.tile,
                                    "bytes_per_lu": inf["bytes_per_lu"], "achieved_gbs": gbs,
                                    "frac": gbs / hbm_peak}
             sim.close()
@@ -314,7 +317,7 @@ def main():
         eparams, efields = zip(*ens)
         enodes = sum(q["nx"] * q["ny"] for q in eparams)
         for prec in ("f32", "f16s"):
-            sim = abi.Simulation(list(eparams), list(efields), prec=prec, stream=stream.cuda_stream)
+            sim = abi.Simulation(list(eparams), list(efields), prec=prec, stream=stream.cuda_stream, tune=True)
             sim.step(64)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -326,7 +329,7 @@ def main():
             dt = e0.elapsed_time(e1) / 1e3 / nst
             inf = sim.info()
             gbs = inf["bytes_per_lu"] * enodes / dt / 1e9
-            ensemble[prec] = {"instances": len(eparams), "nodes": enodes, "MLUPS": enodes / dt / 1e6,
+            ensemble[prec] = {"instances": len(eparams), "nodes": enodes, "MLUPS": enodes / dt / 1e6, "tile": sim.tile,
                               "us_per_launch": dt * 1e6, "bytes_per_lu": inf["bytes_per_lu"],
                               "achieved_gbs": gbs, "frac": gbs / hbm_peak}
             sim.close()
@@ -352,7 +355,7 @@ def main():
                      "achieved_gbs": achieved64, "frac": achieved64 / hbm_peak},
             "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved32 / hbm_peak, "traffic": None,
-                         "kernel": "ch_step_kernel<float,float,float,32,16,256>",
+                         "kernel": f"ch_step_kernel<float,float,float,{tile32[0]},{tile32[1]},256>",
                          "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6},
             "sweep_4096": sweep,
             "ensemble_shear_256": ensemble,

@@ -153,6 +153,13 @@ lbch_status lb_ch_info(lbch_handle* h, double* out);
 /* The CUDA stream the handle enqueues on (a cudaStream_t). */
 void* lb_ch_stream(lbch_handle* h);
 
+/* Tile-shape autotuner.  The step kernel is built for several tile shapes (output nodes per thread
+ * block: 32x16, 32x8 and 16x8 for the float paths; 32x8 and 16x8 for LBCH_F64).  lb_ch_tune times
+ * `steps` steps of each shape on the handle's own problem, restores the state after each candidate,
+ * keeps the fastest, and reports its tile size in *tile_x, *tile_y (either may be NULL).  The result of
+ * the simulation does not depend on the shape.  Allocates a temporary state copy; synchronises. */
+lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y);
+
 /* ---- checkpoints and the differentiable adjoint (single-instance, periodic handles) ----
  *
  * The step's Jacobian depends on the populations only through phi (Eq. LB with Eqs. geq, liangFi,
@@ -184,8 +191,10 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
  * LBCH_HOOK_SKIP_FIRST_LOAD and value != 0, the next step launches run without CUDA graphs and their
  * first thread block never issues its first tile copy, so its bounded wait runs out (after about a
  * second); the kernel then returns cleanly and the next lb_ch_observe reports LBCH_ETIMEOUT.  The
- * handle's state is not advanced correctly afterwards and should be freed.  Not for production use. */
-enum { LBCH_HOOK_SKIP_FIRST_LOAD = 1 };
+ * handle's state is not advanced correctly afterwards and should be freed.  With hook
+ * LBCH_HOOK_TILE_SHAPE, value selects the tile shape by its index in the list lb_ch_tune describes
+ * (for tests that compare shapes).  Not for production use. */
+enum { LBCH_HOOK_SKIP_FIRST_LOAD = 1, LBCH_HOOK_TILE_SHAPE = 2 };
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
 
 /* Statistics of a caller-owned field without allocating anything (the paper has no counterpart; this

@@ -21,8 +21,8 @@ PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
 SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free",
            "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream", "lb_ch_test_hook",
            "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
-           "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end")
-LBCH_HOOK_SKIP_FIRST_LOAD = 1
+           "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune")
+LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE = 1, 2
 
 
 class lbch_params(ctypes.Structure):
@@ -82,10 +82,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_adjoint_begin.argtypes = [vp, vp]
     lib.lb_ch_adjoint_step.argtypes = [vp, vp, ctypes.c_long]
     lib.lb_ch_adjoint_end.argtypes = [vp, vp, dp]
+    lib.lb_ch_tune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]
     for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
                  "lb_ch_test_hook", "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save",
                  "lb_ch_state_load", "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step",
-                 "lb_ch_adjoint_end"):
+                 "lb_ch_adjoint_end", "lb_ch_tune"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -170,8 +171,7 @@ def lb_ch_field_stats_noalloc(phi_ptr: int, phi0_ptr: int, nx: int, ny: int, pit
     device array of 6 doubles, without any device allocation."""
     _check(load().lb_ch_field_stats_noalloc(ctypes.c_void_p(phi_ptr), ctypes.c_void_p(phi0_ptr), int(nx), int(ny),
                                             int(pitch), ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream or 0)),
-           "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
-           "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end")
+           "lb_ch_field_stats_noalloc")
 
 
 def lb_ch_state_bytes(h) -> int:
@@ -206,6 +206,13 @@ def lb_ch_adjoint_end(h, dphi0_ptr: int) -> float:
     return out.value
 
 
+def lb_ch_tune(h, steps: int = 20):
+    """Time every built tile shape on this handle's problem and keep the fastest; returns (tx, ty)."""
+    tx, ty = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().lb_ch_tune(h, int(steps), ctypes.byref(tx), ctypes.byref(ty)), "lb_ch_tune")
+    return tx.value, ty.value
+
+
 def lb_ch_stream(h) -> int:
     return load().lb_ch_stream(h) or 0
 
@@ -215,10 +222,11 @@ def lb_ch_stream(h) -> int:
 class Simulation:
     """One handle: an instance or a ragged ensemble of instances advanced together."""
 
-    def __init__(self, params, phi0, prec="f64", stream=None):
+    def __init__(self, params, phi0, prec="f64", stream=None, tune: bool = False):
         self.params = [params] if isinstance(params, dict) else list(params)
         self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         self.h = lb_ch_init(self.params, [phi0] if isinstance(params, dict) else list(phi0), self.prec, stream)
+        self.tile = lb_ch_tune(self.h) if tune else None
 
     def step(self, nsteps: int):
         lb_ch_step(self.h, nsteps)

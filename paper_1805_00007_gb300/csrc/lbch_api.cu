@@ -48,11 +48,16 @@ lbch_status cuda_fail(cudaError_t e, const char* what)
 
 constexpr int kGraphChunk = 64;  // steps per captured graph (even, so the ping-pong parity is preserved)
 
-// Tile shapes of the step kernel per precision (output nodes per tile) and threads per CTA.
-constexpr int TX64 = 32, TY64 = 8;
-constexpr int TX32 = 32, TY32 = 16;
-constexpr int TX16 = 32, TY16 = 16;
+// Tile shapes the step kernel is built for (output nodes per tile; 256 threads per CTA).  lb_ch_tune
+// times them on the handle's own problem and keeps the fastest; the first one is the default.  Every
+// TX divides 32 and every TY divides 16, so one storage layout serves all shapes.
 constexpr int NT = 256;
+constexpr int kMaxShapes = 3;
+struct Shape { int tx, ty; };
+constexpr Shape kShapes64[2] = {{32, 8}, {16, 8}};
+constexpr Shape kShapesF[3] = {{32, 16}, {32, 8}, {16, 8}};
+inline int n_shapes(int prec) { return prec == LBCH_F64 ? 2 : 3; }
+inline Shape shape_of(int prec, int k) { return prec == LBCH_F64 ? kShapes64[k] : kShapesF[k]; }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -95,16 +100,19 @@ struct lbch_handle {
     int pitch = 0;              // elements per stored row
     int rows = 0;               // stored rows of all instances
     int nq = 9;                 // stored population planes
-    int tx = 0, ty = 0;
     size_t g_elem = 8, phi_elem = 8;
     long long nodes = 0;        // lattice nodes (all instances)
-    int total_tiles = 0;
-    int grid = 0;               // persistent CTAs per step launch
+    int shape = 0;              // tile shape in use (index into the precision's shape list)
+    struct PerShape {           // what depends on the tile shape
+        int total_tiles = 0;
+        int grid = 0;           // persistent CTAs per step launch
+        int* d_tile_begin = nullptr;
+        CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
+    } ps[kMaxShapes];
     void* g[2] = {nullptr, nullptr};
     void* phi[2] = {nullptr, nullptr};
     float* lo[2] = {nullptr, nullptr};  // low part of phi (float path)
     double* phi0 = nullptr;     // initial field, double, padded layout
-    CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
     Ctl* ctl = nullptr;
     double* partials = nullptr; // reduction scratch: n_inst * chunks * RED_NV doubles
     double* result = nullptr;   // n_inst * RED_NV doubles
@@ -136,25 +144,27 @@ template <typename C, typename S, typename P, int TX, int TY>
 cudaError_t launch_step_t(lbch_handle* h, int parity)
 {
     using L = StepShape<C, S, P, TX, TY>;
+    const lbch_handle::PerShape& ps = h->ps[h->shape];
     StepArgs<C, S, P> a;
     a.inst = h->d_inst;
+    a.tile_begin = ps.d_tile_begin;
     a.tabs = tables<C>(h);
     a.n_inst = h->n_inst;
-    a.total_tiles = h->total_tiles;
+    a.total_tiles = ps.total_tiles;
     a.pitch = h->pitch;
     a.debug_skip = h->debug_skip;
     a.g_out = static_cast<S*>(h->g[parity ^ 1]);
     a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
     a.lo_out = h->lo[parity ^ 1];
     a.ctl = h->ctl;
-    ch_step_kernel<C, S, P, TX, TY, NT><<<h->grid, NT, L::BYTES, h->stream>>>(h->tm_g[parity], h->tm_phi[parity],
-                                                                              h->tm_lo[parity], a);
+    ch_step_kernel<C, S, P, TX, TY, NT><<<ps.grid, NT, L::BYTES, h->stream>>>(ps.tm_g[parity], ps.tm_phi[parity],
+                                                                             ps.tm_lo[parity], a);
     return cudaGetLastError();
 }
 
-// Dynamic shared memory of the step kernel, and the persistent grid that fits the device.
+// Dynamic shared memory of the step kernel, and the persistent grid that fits the device, for shape k.
 template <typename C, typename S, typename P, int TX, int TY>
-cudaError_t prepare_step_t(lbch_handle* h)
+cudaError_t prepare_step_t(lbch_handle* h, int k)
 {
     using L = StepShape<C, S, P, TX, TY>;
     auto kern = ch_step_kernel<C, S, P, TX, TY, NT>;
@@ -166,16 +176,21 @@ cudaError_t prepare_step_t(lbch_handle* h)
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    h->grid = std::max(1, std::min(h->total_tiles, per_sm * sms));
+    h->ps[k].grid = std::max(1, std::min(h->ps[k].total_tiles, per_sm * sms));
     return cudaSuccess;
 }
 
-cudaError_t prepare_step(lbch_handle* h)
+cudaError_t prepare_step(lbch_handle* h, int k)
 {
     switch (h->prec) {
-    case LBCH_F64: return prepare_step_t<double, double, double, TX64, TY64>(h);
-    case LBCH_F32: return prepare_step_t<float, float, float, TX32, TY32>(h);
-    default: return prepare_step_t<float, __half, float, TX16, TY16>(h);
+    case LBCH_F64:
+        return k == 0 ? prepare_step_t<double, double, double, 32, 8>(h, k) : prepare_step_t<double, double, double, 16, 8>(h, k);
+    case LBCH_F32:
+        return k == 0 ? prepare_step_t<float, float, float, 32, 16>(h, k)
+             : k == 1 ? prepare_step_t<float, float, float, 32, 8>(h, k) : prepare_step_t<float, float, float, 16, 8>(h, k);
+    default:
+        return k == 0 ? prepare_step_t<float, __half, float, 32, 16>(h, k)
+             : k == 1 ? prepare_step_t<float, __half, float, 32, 8>(h, k) : prepare_step_t<float, __half, float, 16, 8>(h, k);
     }
 }
 
@@ -236,18 +251,17 @@ cudaError_t ns_fields_t(lbch_handle* h, int parity)
 cudaError_t launch_step(lbch_handle* h, int parity)
 {
     if (h->coupled) return h->prec == LBCH_F64 ? launch_ns_t<double>(h, parity) : launch_ns_t<float>(h, parity);
+    const int k = h->shape;
     switch (h->prec) {
-    case LBCH_F64: return launch_step_t<double, double, double, TX64, TY64>(h, parity);
-    case LBCH_F32: return launch_step_t<float, float, float, TX32, TY32>(h, parity);
-    default: return launch_step_t<float, __half, float, TX16, TY16>(h, parity);
+    case LBCH_F64:
+        return k == 0 ? launch_step_t<double, double, double, 32, 8>(h, parity) : launch_step_t<double, double, double, 16, 8>(h, parity);
+    case LBCH_F32:
+        return k == 0 ? launch_step_t<float, float, float, 32, 16>(h, parity)
+             : k == 1 ? launch_step_t<float, float, float, 32, 8>(h, parity) : launch_step_t<float, float, float, 16, 8>(h, parity);
+    default:
+        return k == 0 ? launch_step_t<float, __half, float, 32, 16>(h, parity)
+             : k == 1 ? launch_step_t<float, __half, float, 32, 8>(h, parity) : launch_step_t<float, __half, float, 16, 8>(h, parity);
     }
-}
-
-void tile_shape(int prec, int& tx, int& ty)
-{
-    if (prec == LBCH_F64) { tx = TX64; ty = TY64; }
-    else if (prec == LBCH_F32) { tx = TX32; ty = TY32; }
-    else { tx = TX16; ty = TY16; }
 }
 
 lbch_status check_params(const lbch_params& p, int k)
@@ -357,6 +371,8 @@ void release(lbch_handle* h)
     }
     if (h->d_inst) cudaFree(h->d_inst);
     if (h->d_tabs_f) cudaFree(h->d_tabs_f);
+    for (int k = 0; k < kMaxShapes; k++)
+        if (h->ps[k].d_tile_begin) cudaFree(h->ps[k].d_tile_begin);
     if (h->d_node_begin) cudaFree(h->d_node_begin);
     if (h->d_tabs) cudaFree(h->d_tabs);
     if (h->phi0) cudaFree(h->phi0);
@@ -380,8 +396,10 @@ lbch_status stage(lbch_handle* h, size_t bytes)
     return LBCH_OK;
 }
 
-lbch_status encode_maps(lbch_handle* h)
+lbch_status encode_maps(lbch_handle* h, int sk)
 {
+    const Shape sh = shape_of(h->prec, sk);
+    lbch_handle::PerShape& ps = h->ps[sk];
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(LBCH_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     CUtensorMapDataType gt = h->prec == LBCH_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
@@ -390,26 +408,26 @@ lbch_status encode_maps(lbch_handle* h)
     for (int k = 0; k < 2; k++) {
         cuuint64_t gdim[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->nq, (cuuint64_t)h->rows};
         cuuint64_t gstr[2] = {(cuuint64_t)h->pitch * h->g_elem, (cuuint64_t)h->pitch * h->g_elem * h->nq};
-        cuuint32_t gbox[3] = {(cuuint32_t)(h->tx + 8), (cuuint32_t)h->nq, (cuuint32_t)(h->ty + 2)};
+        cuuint32_t gbox[3] = {(cuuint32_t)(sh.tx + 8), (cuuint32_t)h->nq, (cuuint32_t)(sh.ty + 2)};
         cuuint32_t es[3] = {1, 1, 1};
-        CUresult r = enc(&h->tm_g[k], gt, 3, h->g[k], gdim, gstr, gbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CUresult r = enc(&ps.tm_g[k], gt, 3, h->g[k], gdim, gstr, gbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of the populations: CUresult %d", (int)r);
         cuuint64_t pdim[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->rows};
         cuuint64_t pstr[1] = {(cuuint64_t)h->pitch * h->phi_elem};
-        cuuint32_t pbox[2] = {(cuuint32_t)(h->tx + 8), (cuuint32_t)(h->ty + 6)};
-        r = enc(&h->tm_phi[k], pt, 2, h->phi[k], pdim, pstr, pbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        cuuint32_t pbox[2] = {(cuuint32_t)(sh.tx + 8), (cuuint32_t)(sh.ty + 6)};
+        r = enc(&ps.tm_phi[k], pt, 2, h->phi[k], pdim, pstr, pbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of phi: CUresult %d", (int)r);
         if (h->lo[k]) {
-            cuuint32_t lbox[2] = {(cuuint32_t)h->tx, (cuuint32_t)h->ty};
+            cuuint32_t lbox[2] = {(cuuint32_t)sh.tx, (cuuint32_t)sh.ty};
             cuuint64_t lstr[1] = {(cuuint64_t)h->pitch * 4};
-            r = enc(&h->tm_lo[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->lo[k], pdim, lstr, lbox, es,
+            r = enc(&ps.tm_lo[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->lo[k], pdim, lstr, lbox, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of phi (low part): CUresult %d", (int)r);
         } else {
-            h->tm_lo[k] = h->tm_phi[k];  // unused by the kernels without a low part
+            ps.tm_lo[k] = ps.tm_phi[k];  // unused by the kernels without a low part
         }
     }
     return LBCH_OK;
@@ -494,7 +512,7 @@ adj::AdjArgs adj_args(const lbch_handle* h, long long n)
     a.ny = h->inst[0].ny;
     a.model = h->inst[0].model;
     a.pitch = h->pitch;
-    a.ylen = h->inst[0].tiles_y * h->ty + 2 * GR;
+    a.ylen = h->inst[0].ylen;
     a.n = n;
     return a;
 }
@@ -564,13 +582,12 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     h->g_elem = prec == LBCH_F64 ? 8 : (prec == LBCH_F32 ? 4 : 2);
     h->phi_elem = prec == LBCH_F64 ? 8 : 4;  // the float path adds a float low part
     h->nq = prec == LBCH_F16S ? 8 : 9;
-    tile_shape(prec, h->tx, h->ty);
 
     // layout: uniform pitch; instance k takes ny_k + 2 GR stored rows
     h->inst.resize(n_inst);
     h->node_begin.resize(n_inst + 1);
     std::vector<double> tabs;
-    int tiles = 0, row = 0, max_w = 0;
+    int row = 0, max_w = 0;
     for (int k = 0; k < n_inst; k++) {
         const lbch_params& p = params[k];
         InstDev& d = h->inst[k];
@@ -579,22 +596,29 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         d.nx = p.nx;
         d.ny = p.ny;
         d.row0 = row + GR;
-        d.tiles_x = (p.nx + h->tx - 1) / h->tx;
-        d.tiles_y = (p.ny + h->ty - 1) / h->ty;
-        d.tile_begin = tiles;
-        tiles += d.tiles_x * d.tiles_y;
+        d.ylen = (p.ny + 15) / 16 * 16 + 2 * GR;
         row += p.ny + 2 * GR;
-        max_w = std::max(max_w, d.tiles_x * h->tx);
+        max_w = std::max(max_w, (p.nx + 31) / 32 * 32);
         h->node_begin[k] = h->nodes;
         h->nodes += (long long)p.nx * p.ny;
     }
     h->node_begin[n_inst] = h->nodes;
     h->rows = row;
     h->pitch = (max_w + 8 + 7) / 8 * 8;  // boxes reach 4 columns past the last tile; 16-byte rows for half
-    h->total_tiles = tiles;
+    std::vector<int> tile_begin[kMaxShapes];
+    for (int sk = 0; sk < n_shapes(prec); sk++) {
+        const Shape sh = shape_of(prec, sk);
+        int t = 0;
+        for (int k = 0; k < n_inst; k++) {
+            tile_begin[sk].push_back(t);
+            t += ((params[k].nx + sh.tx - 1) / sh.tx) * ((params[k].ny + sh.ty - 1) / sh.ty);
+        }
+        tile_begin[sk].push_back(t);
+        h->ps[sk].total_tiles = t;
+    }
     for (int k = 0; k < n_inst; k++) {
         h->inst[k].tab = (int)tabs.size();
-        velocity_tables(params[k], h->pitch, h->inst[k].tiles_y * h->ty + 2 * GR, tabs);
+        velocity_tables(params[k], h->pitch, h->inst[k].ylen, tabs);
     }
     std::vector<float> tabs_f(tabs.begin(), tabs.end());
 
@@ -606,7 +630,11 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         if (e != cudaSuccess) return bail(cuda_fail(e, #call));      \
     } while (0)
     CKI(cudaGetDevice(&h->device));
-    CKI(prepare_step(h));
+    for (int sk = 0; sk < n_shapes(prec); sk++) {
+        CKI(prepare_step(h, sk));
+        CKI(cudaMalloc(&h->ps[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
+        CKI(cudaMemcpy(h->ps[sk].d_tile_begin, tile_begin[sk].data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice));
+    }
     if (stream) {
         h->stream = static_cast<cudaStream_t>(stream);
     } else {
@@ -633,7 +661,8 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     if (h->chunks < 1) h->chunks = 1;
     CKI(cudaMalloc(&h->partials, sizeof(double) * RED_NV * (size_t)h->chunks * n_inst));
     CKI(cudaMalloc(&h->result, sizeof(double) * RED_NV * (size_t)n_inst));
-    lbch_status st = encode_maps(h);
+    lbch_status st = LBCH_OK;
+    for (int sk = 0; sk < n_shapes(prec) && st == LBCH_OK; sk++) st = encode_maps(h, sk);
     if (st != LBCH_OK) return bail(st);
 
     // the initial field in the padded layout, ghost frame included, through pinned staging
@@ -668,15 +697,15 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     switch (prec) {
     case LBCH_F64:
         init_kernel<double, double, double><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->d_tabs, h->phi0, h->pitch,
-            h->ty, (double*)h->g[0], (double*)h->phi[0], nullptr, h->nodes, h->d_node_begin);
+            (double*)h->g[0], (double*)h->phi[0], nullptr, h->nodes, h->d_node_begin);
         break;
     case LBCH_F32:
         init_kernel<float, float, float><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->d_tabs, h->phi0, h->pitch,
-            h->ty, (float*)h->g[0], (float*)h->phi[0], h->lo[0], h->nodes, h->d_node_begin);
+            (float*)h->g[0], (float*)h->phi[0], h->lo[0], h->nodes, h->d_node_begin);
         break;
     default:
         init_kernel<float, __half, float><<<nb, 256, 0, h->stream>>>(h->d_inst, n_inst, h->d_tabs, h->phi0, h->pitch,
-            h->ty, (__half*)h->g[0], (float*)h->phi[0], nullptr, h->nodes, h->d_node_begin);
+            (__half*)h->g[0], (float*)h->phi[0], nullptr, h->nodes, h->d_node_begin);
     }
     CKI(cudaGetLastError());
     if (coupled) {
@@ -866,7 +895,7 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     }
     out[0] = (double)h->nodes;
     out[1] = bytes;
-    out[2] = (double)h->grid;
+    out[2] = (double)h->ps[h->shape].grid;
     out[3] = (double)h->n;
     return LBCH_OK;
 }
@@ -980,12 +1009,65 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds)
     return LBCH_OK;
 }
 
+lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
+{
+    if (!h || steps < 1) return fail(LBCH_EINVAL, "NULL handle or steps < 1");
+    const int ns = h->coupled ? 1 : n_shapes(h->prec);
+    if (ns > 1) {
+        long long bytes = 0;
+        lb_ch_state_bytes(h, &bytes);
+        void* backup = nullptr;
+        CK(cudaMalloc(&backup, (size_t)bytes));
+        lbch_status s = lb_ch_state_save(h, backup);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float best_ms = 0.0f;
+        int best = h->shape;
+        if (s == LBCH_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+            for (int k = 0; k < ns && s == LBCH_OK; k++) {
+                h->shape = k;
+                cudaError_t e = cudaSuccess;
+                for (int w = 0; w < 2 && e == cudaSuccess; w++) { e = launch_step(h, (int)(h->n & 1)); h->n++; }
+                e = e == cudaSuccess ? cudaEventRecord(e0, h->stream) : e;
+                for (int i = 0; i < steps && e == cudaSuccess; i++) { e = launch_step(h, (int)(h->n & 1)); h->n++; }
+                e = e == cudaSuccess ? cudaEventRecord(e1, h->stream) : e;
+                e = e == cudaSuccess ? cudaEventSynchronize(e1) : e;
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) s = cuda_fail(e, "timing a tile shape");
+                else if (k == 0 || ms < best_ms) { best_ms = ms; best = k; }
+                lbch_status r = lb_ch_state_load(h, backup);  // every candidate starts from the same state
+                if (s == LBCH_OK) s = r;
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(backup);
+        if (s != LBCH_OK) return s;
+        h->shape = best;
+        for (int k = 0; k < 2; k++)  // graphs captured earlier launch the previous shape's kernel
+            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+    }
+    const Shape sh = h->coupled ? Shape{0, 0} : shape_of(h->prec, h->shape);
+    if (tile_x) *tile_x = sh.tx;
+    if (tile_y) *tile_y = sh.ty;
+    return LBCH_OK;
+}
+
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
 {
     if (!h) return fail(LBCH_EINVAL, "NULL handle");
-    if (hook != LBCH_HOOK_SKIP_FIRST_LOAD) return fail(LBCH_EINVAL, "unknown hook %d", hook);
-    h->debug_skip = value ? 1 : 0;
-    return LBCH_OK;
+    if (hook == LBCH_HOOK_SKIP_FIRST_LOAD) {
+        h->debug_skip = value ? 1 : 0;
+        return LBCH_OK;
+    }
+    if (hook == LBCH_HOOK_TILE_SHAPE) {
+        if (h->coupled || value < 0 || value >= n_shapes(h->prec)) return fail(LBCH_EINVAL, "no tile shape %ld", value);
+        h->shape = (int)value;
+        for (int k = 0; k < 2; k++)
+            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        return LBCH_OK;
+    }
+    return fail(LBCH_EINVAL, "unknown hook %d", hook);
 }
 
 }  // extern "C"

@@ -54,8 +54,8 @@ struct InstDev {
     int nx, ny;
     int row0;          // stored row of domain row 0 (the instance's first ghost row is row0 - GR)
     int walls, model, vel;
-    int tiles_x, tiles_y, tile_begin;
-    int tab;           // offset of the velocity tables: X1, X2 [pitch]; Y1, Y2 [tiles_y*TY + 2 GR]; W[4]
+    int ylen;          // length of each Y velocity table: ny rounded up to 16, plus 2 GR ghost rows
+    int tab;           // offset of the velocity tables: X1, X2 [pitch]; Y1, Y2 [ylen]; W[4]
     double Tper;
     Consts<double> cd;  // the constants in double (FP64 path, initial state)
     Consts<float> cf;   // and rounded once to float (float paths)
@@ -110,12 +110,13 @@ template <typename C> __device__ __forceinline__ C dfdphi(C phi, C beta, C phiA,
     return C(2) * beta * (phi - phiA) * (phi - phiB) * (C(2) * phi - phiA - phiB);
 }
 
-__device__ __forceinline__ int find_inst(const InstDev* inst, int n_inst, int tile)
+// The instance owning tile `tile`: tile_begin[k] is the first tile of instance k for the launch's shape.
+__device__ __forceinline__ int find_inst(const int* tile_begin, int n_inst, int tile)
 {
     int lo = 0, hi = n_inst - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (inst[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+        if (tile_begin[mid] <= tile) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
@@ -188,6 +189,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
 template <typename C, typename S, typename P>
 struct StepArgs {
     const InstDev* inst;
+    const int* tile_begin;  // first tile of each instance for this launch's tile shape
     const C* tabs;       // velocity tables of all instances, indexed by stored column / instance row
     int n_inst;
     int total_tiles;
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
     __shared__ long long s_time;
     __shared__ int s_tile_inst;
     __shared__ C s_T;
+    __shared__ InstDev s_I;  // the current tile's instance, copied when the instance changes
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -254,16 +257,18 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         mbar_init(&mbar[1], 1);
         fence_mbar_init();
         s_time = a.ctl->time;
+        s_tile_inst = -1;
     }
     __syncthreads();
     const long long n = s_time;
 
     // producer: thread 0 issues the boxes of tile t into stage s
     auto issue = [&](int t, int s) {
-        int k = find_inst(a.inst, a.n_inst, t);
+        int k = find_inst(a.tile_begin, a.n_inst, t);
         const InstDev& I = a.inst[k];
-        int local = t - I.tile_begin;
-        int x0 = (local % I.tiles_x) * TX, y0 = (local / I.tiles_x) * TY;
+        int local = t - a.tile_begin[k];
+        int tiles_x = (I.nx + TX - 1) / TX;
+        int x0 = (local % tiles_x) * TX, y0 = (local / tiles_x) * TY;
         fence_proxy_async();
         mbar_expect_tx(&mbar[s], L::GBOX_BYTES + L::PBOX_BYTES + L::LBOX_BYTES);
         // box column origin: domain x0 - 4 is stored column x0 - 4 + GC = x0
@@ -296,16 +301,20 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             break;  // skip the remaining tiles; the step counter below is still kept consistent
         }
         if (tid == 0) {
-            int k = find_inst(a.inst, a.n_inst, t);
-            s_tile_inst = k;
-            s_T = (C)vel_t(a.inst[k].vel, a.inst[k].Tper, n);  // time factor of the flow, once per tile
+            int k = find_inst(a.tile_begin, a.n_inst, t);
+            if (k != s_tile_inst) {
+                s_I = a.inst[k];
+                s_tile_inst = k;
+                s_T = (C)vel_t(s_I.vel, s_I.Tper, n);  // time factor of the flow, once per instance
+            }
         }
         __syncthreads();
-        const InstDev& I = a.inst[s_tile_inst];
+        const InstDev& I = s_I;
         const Consts<C>& K0 = consts<C>(I);
         const int nx = I.nx, ny = I.ny, walls = I.walls, model = I.model;
-        const int local = t - I.tile_begin;
-        const int x0 = (local % I.tiles_x) * TX, y0 = (local / I.tiles_x) * TY;
+        const int local = t - a.tile_begin[s_tile_inst];
+        const int tiles_x = (nx + TX - 1) / TX;
+        const int x0 = (local % tiles_x) * TX, y0 = (local / tiles_x) * TY;
         const C T = s_T;
         S* gb = reinterpret_cast<S*>(stage(s));
         const P* pb = reinterpret_cast<const P*>(stage(s) + L::OFF_P);  // phi on tile + 3 at box column c + 1
@@ -313,8 +322,8 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         const C* tX1 = a.tabs + I.tab;
         const C* tX2 = tX1 + a.pitch;
         const C* tY1 = tX2 + a.pitch;
-        const C* tY2 = tY1 + I.tiles_y * TY + 2 * GR;
-        const C* tW = tY2 + I.tiles_y * TY + 2 * GR;
+        const C* tY2 = tY1 + I.ylen;
+        const C* tW = tY2 + I.ylen;
 
         // 1. velocity on tile + 3
         for (int e = tid; e < L::NP; e += NT) {
@@ -435,35 +444,44 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         }
         __syncthreads();
 
-        // 4. pull streaming from the box, bounce-back at walls; store g(t+1), phi(t+1) and ghost images
+        // 4. pull streaming from the box, bounce-back at walls; store g(t+1), phi(t+1) and ghost images.
+        //    Interior nodes (no wall neighbour, no ghost image) take a straight path without the checks.
         const int pitch = a.pitch;
         const float* lb = reinterpret_cast<const float*>(stage(s) + L::OFF_L);
         for (int e = tid; e < TX * TY; e += NT) {
             int r = e / TX, c = e - r * TX;
             int gx = x0 + c, gy = y0 + r;
             if (gx >= nx || gy >= ny) continue;
+            const bool wallrow = walls && (gy == 0 || gy == ny - 1);
+            const bool edge = gx < 3 || gx >= nx - 3 || gy < 3 || gy >= ny - 3;
+            const S* src = gb + ((r + 1) * NQ) * BW + c + 4;   // this node's box position, plane 0
             C v[9];
             C sumq = C(0);
+            v[0] = kHalf ? s_h0[(r + 1) * GW + (c + 1)] : cvt<C>(src[0]);
+            if (!kShift) sumq += v[0];
+            if (!wallrow) {
 #pragma unroll
-            for (int q = 0; q < 9; q++) {
-                if (q == 0) {
-                    v[0] = kHalf ? s_h0[(r + 1) * GW + (c + 1)] : cvt<C>(gb[((r + 1) * NQ) * BW + c + 4]);
-                    if (!kShift) sumq += v[0];
-                    continue;
+                for (int q = 1; q < 9; q++) {
+                    v[q] = cvt<C>(src[(-cy(q) * NQ + q - QOFF) * BW - cx(q)]);
+                    sumq += v[q];
                 }
-                int sy = gy - cy(q);
-                if (walls && (sy < 0 || sy >= ny)) {
-                    // halfway bounce-back: the population that left along -c_q returns along c_q, plus
-                    // the moving-wall term 2 w_q phi (c_q . u_w) / c_s^2
-                    int wi = sy < 0 ? 0 : 1;
-                    C uwx = tX1[gx + GC] * tW[wi] * T, uwy = tX2[gx + GC] * tW[2 + wi] * T;
-                    C ph = cvt<C>(pb[(r + 3) * BW + c + 4]);
-                    v[q] = cvt<C>(gb[((r + 1) * NQ + opp(q) - QOFF) * BW + c + 4])
-                         + C(6) * wq<C>(q) * ph * ((C)cx(q) * uwx + (C)cy(q) * uwy);
-                } else {
-                    v[q] = cvt<C>(gb[((r + 1 - cy(q)) * NQ + q - QOFF) * BW + c + 4 - cx(q)]);
+            } else {
+#pragma unroll
+                for (int q = 1; q < 9; q++) {
+                    int sy = gy - cy(q);
+                    if (sy < 0 || sy >= ny) {
+                        // halfway bounce-back: the population that left along -c_q returns along c_q, plus
+                        // the moving-wall term 2 w_q phi (c_q . u_w) / c_s^2
+                        int wi = sy < 0 ? 0 : 1;
+                        C uwx = tX1[gx + GC] * tW[wi] * T, uwy = tX2[gx + GC] * tW[2 + wi] * T;
+                        C ph = cvt<C>(pb[(r + 3) * BW + c + 4]);
+                        v[q] = cvt<C>(src[(opp(q) - QOFF) * BW])
+                             + C(6) * wq<C>(q) * ph * ((C)cx(q) * uwx + (C)cy(q) * uwy);
+                    } else {
+                        v[q] = cvt<C>(src[(-cy(q) * NQ + q - QOFF) * BW - cx(q)]);
+                    }
+                    sumq += v[q];
                 }
-                sumq += v[q];
             }
             P hi;
             float lo = 0.0f;
@@ -483,37 +501,38 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             } else {
                 hi = (P)sumq;
             }
-            // positions to write: the node and its images in the ghost columns/rows (phi three deep,
-            // the populations one deep; images in y only for periodic y, mirror images for walls)
-            const int xa = gx < 3 ? gx + nx : NONE, xb = gx >= nx - 3 ? gx - nx : NONE;
-            const int ya = gy < 3 ? (walls ? -1 - gy : gy + ny) : NONE;
-            const int yb = gy >= ny - 3 ? (walls ? 2 * ny - 1 - gy : gy - ny) : NONE;
+            const long long node = (long long)(I.row0 + gy) * pitch + GC + gx;
+            a.phi_out[node] = hi;
+            if (kFF) a.lo_out[node] = lo;
+            S* o = a.g_out + ((long long)(I.row0 + gy) * NQ) * pitch + GC + gx;
 #pragma unroll
-            for (int iy = 0; iy < 3; iy++) {
-                const int yy = iy == 0 ? gy : (iy == 1 ? ya : yb);
-                if (yy == NONE) continue;
-#pragma unroll
-                for (int ix = 0; ix < 3; ix++) {
-                    const int xx = ix == 0 ? gx : (ix == 1 ? xa : xb);
-                    if (xx == NONE) continue;
-                    long long idx = (long long)(I.row0 + yy) * pitch + GC + xx;
-                    a.phi_out[idx] = hi;
-                    if (kFF && ix == 0 && iy == 0) a.lo_out[idx] = lo;
+            for (int q = QOFF; q < 9; q++) o[(q - QOFF) * pitch] = to_s<S>(v[q]);
+            if (edge) {
+                // the node's images in the ghost columns/rows (phi three deep, the populations one deep;
+                // in y only for periodic y, mirror images next to walls)
+                const int xa = gx < 3 ? gx + nx : NONE, xb = gx >= nx - 3 ? gx - nx : NONE;
+                const int ya = gy < 3 ? (walls ? -1 - gy : gy + ny) : NONE;
+                const int yb = gy >= ny - 3 ? (walls ? 2 * ny - 1 - gy : gy - ny) : NONE;
+                for (int iy = 0; iy < 3; iy++) {
+                    const int yy = iy == 0 ? gy : (iy == 1 ? ya : yb);
+                    if (yy == NONE) continue;
+                    for (int ix = 0; ix < 3; ix++) {
+                        const int xx = ix == 0 ? gx : (ix == 1 ? xa : xb);
+                        if (xx == NONE || (ix == 0 && iy == 0)) continue;
+                        a.phi_out[(long long)(I.row0 + yy) * pitch + GC + xx] = hi;
+                    }
                 }
-            }
-            const int gxa = gx == 0 ? nx : (gx == nx - 1 ? -1 : NONE);
-            const int gya = walls ? NONE : (gy == 0 ? ny : (gy == ny - 1 ? -1 : NONE));
-#pragma unroll
-            for (int iy = 0; iy < 2; iy++) {
-                const int yy = iy == 0 ? gy : gya;
-                if (yy == NONE) continue;
-#pragma unroll
-                for (int ix = 0; ix < 2; ix++) {
-                    const int xx = ix == 0 ? gx : gxa;
-                    if (xx == NONE) continue;
-                    S* o = a.g_out + ((long long)(I.row0 + yy) * NQ) * pitch + GC + xx;
-#pragma unroll
-                    for (int q = QOFF; q < 9; q++) o[(q - QOFF) * pitch] = to_s<S>(v[q]);
+                const int gxa = gx == 0 ? nx : (gx == nx - 1 ? -1 : NONE);
+                const int gya = walls ? NONE : (gy == 0 ? ny : (gy == ny - 1 ? -1 : NONE));
+                for (int iy = 0; iy < 2; iy++) {
+                    const int yy = iy == 0 ? gy : gya;
+                    if (yy == NONE) continue;
+                    for (int ix = 0; ix < 2; ix++) {
+                        const int xx = ix == 0 ? gx : gxa;
+                        if (xx == NONE || (ix == 0 && iy == 0)) continue;
+                        S* oi = a.g_out + ((long long)(I.row0 + yy) * NQ) * pitch + GC + xx;
+                        for (int q = QOFF; q < 9; q++) oi[(q - QOFF) * pitch] = to_s<S>(v[q]);
+                    }
                 }
             }
         }
@@ -543,7 +562,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
 // velocity tables are the double ones, indexed like the step kernel's.
 template <typename C, typename S, typename P>
 __global__ void init_kernel(const InstDev* inst, int n_inst, const double* tabs, const double* phi0, int pitch,
-                            int ty, S* g, P* phi, float* lo, long long nodes_total, const long long* node_begin)
+                            S* g, P* phi, float* lo, long long nodes_total, const long long* node_begin)
 {
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nodes_total) return;
@@ -569,7 +588,7 @@ __global__ void init_kernel(const InstDev* inst, int n_inst, const double* tabs,
     const double* tX1 = tabs + I.tab;
     const double* tX2 = tX1 + pitch;
     const double* tY1 = tX2 + pitch;
-    const double* tY2 = tY1 + I.tiles_y * ty + 2 * GR;
+    const double* tY2 = tY1 + I.ylen;
     double T = vel_t(I.vel, I.Tper, 0);
     C ux = (C)(tX1[x + GC] * tY1[y + GR] * T), uy = (C)(tX2[x + GC] * tY2[y + GR] * T);
     C ph = (C)c0, eta = (C)I.cd.eta;

@@ -174,3 +174,34 @@ def test_nonfinite_is_reported():
         with pytest.raises(abi.LbchError) as ei:
             sim.observe(abi.LBCH_OBS_MASS)
         assert ei.value.status == abi.LBCH_ENONFINITE
+
+
+@pytest.mark.parametrize("prec,nshapes", [("f64", 2), ("f32", 3), ("f16s", 3)])
+def test_every_tile_shape_gives_the_same_bits(prec, nshapes):
+    """The result does not depend on the tile shape (each node's arithmetic is the same; only the halo
+    overlap between tiles changes), so every shape must reproduce the same bits; the autotuner then
+    only picks among equivalent kernels."""
+    ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=9)
+    params, fields = zip(*ens)
+    p, phi0, _ = wl.single_vortex(n=96, T=50)
+    outs = []
+    for k in range(nshapes):
+        with abi.Simulation(p, phi0, prec=prec) as sim, abi.Simulation(list(params), list(fields), prec=prec) as ens_sim:
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, k)
+            abi.lb_ch_test_hook(ens_sim.h, abi.LBCH_HOOK_TILE_SHAPE, k)
+            sim.step(70)
+            ens_sim.step(70)
+            outs.append([sim.phi()] + [ens_sim.phi(i) for i in range(3)])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_tune_keeps_the_state():
+    p, phi0, _ = wl.zalesak(n=128)
+    with abi.Simulation(p, phi0, prec="f32") as a, abi.Simulation(p, phi0, prec="f32", tune=True) as b:
+        assert b.tile in ((32, 16), (32, 8), (16, 8))
+        assert b.observe(abi.LBCH_OBS_STEP) == 0
+        a.step(100)
+        b.step(100)
+        assert np.array_equal(a.phi(), b.phi())
