@@ -128,7 +128,10 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
                        void* stream, lbch_handle** out);
 
 /* Advance every instance by nsteps >= 0 steps of Eq. LB.  Asynchronous on the handle's stream: the work
- * is enqueued (in CUDA graphs of 64 steps when possible) and the call returns. */
+ * is enqueued (in CUDA graphs of 64 steps when possible) and the call returns.  When every instance has
+ * tau_g = 1 (the paper's default), Eq. LB reduces to g* = g_eq + S/2 and the populations drop out of the
+ * step: the library then reads and writes phi only (the stored populations are left unchanged and are
+ * not part of the state), with the same results bit for bit. */
 lbch_status lb_ch_step(lbch_handle* h, long nsteps);
 
 /* Read an observable of instance inst into out (host, sized as lbch_obs states).  Synchronises the
@@ -193,8 +196,13 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
  * second); the kernel then returns cleanly and the next lb_ch_observe reports LBCH_ETIMEOUT.  The
  * handle's state is not advanced correctly afterwards and should be freed.  With hook
  * LBCH_HOOK_TILE_SHAPE, value selects the tile shape by its index in the list lb_ch_tune describes
- * (for tests that compare shapes).  Not for production use. */
-enum { LBCH_HOOK_SKIP_FIRST_LOAD = 1, LBCH_HOOK_TILE_SHAPE = 2 };
+ * (for tests that compare shapes).  With hook LBCH_HOOK_GENERAL_PATH and value != 0, handles whose
+ * instances all have tau_g = 1 run the general step kernel instead of the one that drops the
+ * populations (see lb_ch_step); the two give the same bits.  With hook LBCH_HOOK_NO_PDL and value != 0,
+ * step launches are ordinary stream-ordered launches instead of programmatic dependents of the previous
+ * step (whose launch and prologue overlap that step's tail); the results are the same bits.  Not for
+ * production use. */
+enum { LBCH_HOOK_SKIP_FIRST_LOAD = 1, LBCH_HOOK_TILE_SHAPE = 2, LBCH_HOOK_GENERAL_PATH = 3, LBCH_HOOK_NO_PDL = 4 };
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
 
 /* Statistics of a caller-owned field without allocating anything (the paper has no counterpart; this

@@ -103,6 +103,9 @@ struct lbch_handle {
     size_t g_elem = 8, phi_elem = 8;
     long long nodes = 0;        // lattice nodes (all instances)
     int shape = 0;              // tile shape in use (index into the precision's shape list)
+    bool tau1 = false;          // every instance has tau_g = 1: the populations drop out of the step
+    bool force_general = false; // test hook: use the general kernel even when tau1 holds
+    bool no_pdl = false;        // test hook: plain stream-ordered step launches
     struct PerShape {           // what depends on the tile shape
         int total_tiles = 0;
         int grid = 0;           // persistent CTAs per step launch
@@ -140,8 +143,8 @@ template <typename C> const C* tables(lbch_handle* h);
 template <> const double* tables<double>(lbch_handle* h) { return h->d_tabs; }
 template <> const float* tables<float>(lbch_handle* h) { return h->d_tabs_f; }
 
-template <typename C, typename S, typename P, int TX, int TY>
-cudaError_t launch_step_t(lbch_handle* h, int parity)
+template <typename C, typename S, typename P, int TX, int TY, bool TAU1>
+cudaError_t launch_step_v(lbch_handle* h, int parity)
 {
     using L = StepShape<C, S, P, TX, TY>;
     const lbch_handle::PerShape& ps = h->ps[h->shape];
@@ -157,9 +160,27 @@ cudaError_t launch_step_t(lbch_handle* h, int parity)
     a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
     a.lo_out = h->lo[parity ^ 1];
     a.ctl = h->ctl;
-    ch_step_kernel<C, S, P, TX, TY, NT><<<ps.grid, NT, L::BYTES, h->stream>>>(ps.tm_g[parity], ps.tm_phi[parity],
-                                                                             ps.tm_lo[parity], a);
-    return cudaGetLastError();
+    // a programmatic dependent of the previous launch in the stream (the kernel waits on it before it
+    // touches memory that launch writes), so its launch and prologue overlap the previous step's tail
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ps.grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = L::BYTES;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ch_step_kernel<C, S, P, TX, TY, NT, TAU1>, ps.tm_g[parity], ps.tm_phi[parity],
+                              ps.tm_lo[parity], a);
+}
+
+template <typename C, typename S, typename P, int TX, int TY>
+cudaError_t launch_step_t(lbch_handle* h, int parity)
+{
+    return (h->tau1 && !h->force_general) ? launch_step_v<C, S, P, TX, TY, true>(h, parity)
+                                          : launch_step_v<C, S, P, TX, TY, false>(h, parity);
 }
 
 // Dynamic shared memory of the step kernel, and the persistent grid that fits the device, for shape k.
@@ -167,8 +188,11 @@ template <typename C, typename S, typename P, int TX, int TY>
 cudaError_t prepare_step_t(lbch_handle* h, int k)
 {
     using L = StepShape<C, S, P, TX, TY>;
-    auto kern = ch_step_kernel<C, S, P, TX, TY, NT>;
+    auto kern = ch_step_kernel<C, S, P, TX, TY, NT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ch_step_kernel<C, S, P, TX, TY, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);
@@ -578,6 +602,8 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     if (!h) return fail(LBCH_ENOMEM, "host allocation failed");
     h->prec = prec;
     h->coupled = coupled;
+    h->tau1 = !coupled;
+    for (int k = 0; k < n_inst; k++) h->tau1 = h->tau1 && params[k].tau == 1.0;
     h->n_inst = n_inst;
     h->g_elem = prec == LBCH_F64 ? 8 : (prec == LBCH_F32 ? 4 : 2);
     h->phi_elem = prec == LBCH_F64 ? 8 : 4;  // the float path adds a float low part
@@ -596,7 +622,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         d.nx = p.nx;
         d.ny = p.ny;
         d.row0 = row + GR;
-        d.ylen = (p.ny + 15) / 16 * 16 + 2 * GR;
+        d.ylen = (p.ny + 15) / 16 * 16 + 8;  // the Y slice of a tile spans TY + 8 rows from its first halo row
         row += p.ny + 2 * GR;
         max_w = std::max(max_w, (p.nx + 31) / 32 * 32);
         h->node_begin[k] = h->nodes;
@@ -889,6 +915,8 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     // algorithmic HBM bytes per lattice update: read + write of the stored populations and of phi
     double bytes = 2.0 * (h->nq * (double)h->g_elem + (double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
+    if (h->tau1 && !h->force_general)  // only phi is read and written
+        bytes = 2.0 * ((double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
     if (h->coupled) {  // f and g read and written, phi read and written, u and p written and read
         const double e = h->prec == LBCH_F64 ? 8.0 : 4.0;
         bytes = 2.0 * (18.0 * e + e) + 2.0 * 3.0 * e;
@@ -1058,6 +1086,18 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
     if (!h) return fail(LBCH_EINVAL, "NULL handle");
     if (hook == LBCH_HOOK_SKIP_FIRST_LOAD) {
         h->debug_skip = value ? 1 : 0;
+        return LBCH_OK;
+    }
+    if (hook == LBCH_HOOK_NO_PDL) {
+        h->no_pdl = value != 0;
+        for (int k = 0; k < 2; k++)
+            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        return LBCH_OK;
+    }
+    if (hook == LBCH_HOOK_GENERAL_PATH) {
+        h->force_general = value != 0;
+        for (int k = 0; k < 2; k++)
+            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
         return LBCH_OK;
     }
     if (hook == LBCH_HOOK_TILE_SHAPE) {

@@ -165,12 +165,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// programmatic dependent launch: wait for the prerequisite grid to complete with its writes visible (a
+// no-op without a programmatic dependency), and allow the dependent grid to be scheduled
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar)
 {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
             "r"(smem_u32(dst)), "l"(tm), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// plain bulk copy (not tensor-mapped): 16-byte aligned source and destination, size a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -214,22 +227,30 @@ struct StepShape {
     static constexpr unsigned GBOX_BYTES = GBH * NQ * BW * sizeof(S);
     static constexpr unsigned PBOX_BYTES = PBH * BW * sizeof(P);
     static constexpr unsigned LBOX_BYTES = FF ? TX * TY * 4 : 0;
+    // velocity-table slices of the tile: X1, X2 over the box columns, Y1, Y2 over TY + 8 rows
+    static constexpr int YT = TY + 8;
+    static constexpr unsigned XT_BYTES = BW * sizeof(C), YT_BYTES = YT * sizeof(C);
+    static constexpr unsigned TAB_BYTES = 2 * XT_BYTES + 2 * YT_BYTES;
     __host__ __device__ static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t OFF_P = a128(GBOX_BYTES), OFF_L = OFF_P + a128(PBOX_BYTES);
-    static constexpr size_t STAGE = OFF_L + a128(LBOX_BYTES);
-    static constexpr size_t WORK1 = a128(sizeof(C) * (2 * NP + 2 * NM));
+    static constexpr size_t OFF_T = OFF_L + a128(LBOX_BYTES);
+    static constexpr size_t STAGE = OFF_T + a128(TAB_BYTES);
+    static constexpr size_t WORK1 = a128(sizeof(C) * (2 * NM));
     static constexpr size_t WORK = WORK1 + (sizeof(S) == 2 ? a128(sizeof(C) * NG) : 0);  // + h*_0 (half path)
     static constexpr size_t BYTES = 2 * STAGE + WORK + 128 + 128;  // mbarriers, alignment slack
 };
 
-template <typename C, typename S, typename P, int TX, int TY, int NT>
+// TAU1: the kernel for instances that all have tau_g = 1.  Then Eq. LB gives g* = g_eq + S/2: the
+// populations are multiplied by 1 - 1/tau = 0, so they are neither loaded nor stored -- the state is phi
+// alone, and the result is bit for bit the general kernel's (which multiplies them by exactly zero).
+template <typename C, typename S, typename P, int TX, int TY, int NT, bool TAU1 = false>
 __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(const __grid_constant__ CUtensorMap tm_g,
                                                      const __grid_constant__ CUtensorMap tm_phi,
                                                      const __grid_constant__ CUtensorMap tm_lo,
                                                      StepArgs<C, S, P> a)
 {
     using L = StepShape<C, S, P, TX, TY>;
-    constexpr int NQ = L::NQ, BW = L::BW, PW = L::PW, MW = L::MW, MH = L::MH, GW = L::GW;
+    constexpr int NQ = L::NQ, BW = L::BW, MW = L::MW, MH = L::MH, GW = L::GW;
     constexpr bool kHalf = sizeof(S) == 2;    // g_0 not stored: implied by phi
     constexpr bool kShift = sizeof(C) == 4;   // float arithmetic on g_0 - phi instead of g_0
     constexpr bool kFF = L::FF;
@@ -239,9 +260,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     auto stage = [&](int k) { return base + (size_t)k * L::STAGE; };
-    C* s_ux = reinterpret_cast<C*>(base + 2 * L::STAGE);
-    C* s_uy = s_ux + L::NP;
-    C* s_mu = s_uy + L::NP;
+    C* s_mu = reinterpret_cast<C*>(base + 2 * L::STAGE);
     C* s_D = s_mu + L::NM;
     C* s_h0 = reinterpret_cast<C*>(base + 2 * L::STAGE + L::WORK1);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 2 * L::STAGE + L::WORK);
@@ -256,9 +275,14 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         fence_mbar_init();
-        s_time = a.ctl->time;
         s_tile_inst = -1;
     }
+    // Launched as a programmatic dependent of the previous step: everything above overlaps its tail;
+    // nothing it writes (phi, g, the step counter) is touched before this wait.  The next step may then
+    // start its own prologue (it waits in turn before reading what this step writes).
+    grid_dependency_wait();
+    grid_launch_dependents();
+    if (tid == 0) s_time = a.ctl->time;
     __syncthreads();
     const long long n = s_time;
 
@@ -270,11 +294,19 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         int tiles_x = (I.nx + TX - 1) / TX;
         int x0 = (local % tiles_x) * TX, y0 = (local / tiles_x) * TY;
         fence_proxy_async();
-        mbar_expect_tx(&mbar[s], L::GBOX_BYTES + L::PBOX_BYTES + L::LBOX_BYTES);
+        mbar_expect_tx(&mbar[s], (TAU1 ? 0u : L::GBOX_BYTES) + L::PBOX_BYTES + L::LBOX_BYTES + L::TAB_BYTES);
         // box column origin: domain x0 - 4 is stored column x0 - 4 + GC = x0
-        tma_load_3d(stage(s), &tm_g, x0, 0, I.row0 + y0 - 1, &mbar[s]);
+        if (!TAU1) tma_load_3d(stage(s), &tm_g, x0, 0, I.row0 + y0 - 1, &mbar[s]);
         tma_load_2d(stage(s) + L::OFF_P, &tm_phi, x0, I.row0 + y0 - 3, &mbar[s]);
         if (kFF) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, x0 + GC, I.row0 + y0, &mbar[s]);
+        // the velocity tables of the box's columns and rows (the Y tables start at the box's first row)
+        const C* tX1 = a.tabs + I.tab;
+        const C* tY1 = tX1 + 2 * a.pitch;
+        unsigned char* tb = stage(s) + L::OFF_T;
+        bulk_load(tb, tX1 + x0, L::XT_BYTES, &mbar[s]);
+        bulk_load(tb + L::XT_BYTES, tX1 + a.pitch + x0, L::XT_BYTES, &mbar[s]);
+        bulk_load(tb + 2 * L::XT_BYTES, tY1 + y0, L::YT_BYTES, &mbar[s]);
+        bulk_load(tb + 2 * L::XT_BYTES + L::YT_BYTES, tY1 + I.ylen + y0, L::YT_BYTES, &mbar[s]);
     };
 
     const int stride = gridDim.x;
@@ -325,13 +357,12 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         const C* tY2 = tY1 + I.ylen;
         const C* tW = tY2 + I.ylen;
 
-        // 1. velocity on tile + 3
-        for (int e = tid; e < L::NP; e += NT) {
-            int r = e / PW, c = e - r * PW;
-            s_ux[e] = tX1[x0 + c + 1] * tY1[y0 + r] * T;   // stored column of P column c is x0 + c + 1
-            s_uy[e] = tX2[x0 + c + 1] * tY2[y0 + r] * T;
-        }
-        __syncthreads();
+        // the velocity-table slices arrived with the boxes: X by box column, Y by box row; the prescribed
+        // velocity at box (row, col) is (X1[col] Y1[row], X2[col] Y2[row]) T
+        const C* sX1 = reinterpret_cast<const C*>(stage(s) + L::OFF_T);
+        const C* sX2 = sX1 + BW;
+        const C* sY1 = sX2 + BW;
+        const C* sY2 = sY1 + L::YT;
 
         // 2. mu (Eq. mu) and D = div(phi u) on tile + 2
         const C beta = K0.beta, kappa = K0.kappa, phiA = K0.phiA, phiB = K0.phiB;
@@ -347,12 +378,16 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             C lap = (C(2) / C(3)) * (ax - C(4) * ce) + (C(1) / C(6)) * (dg - C(4) * ce);
             s_mu[e] = dfdphi(ce, beta, phiA, phiB) - kappa * lap;
             if (model == 2) {
-                // div = sum_k w_k c_k . (phi u)(x + c_k) / c_s^2
-                int p = (r + 1) * PW + (c + 1);
-                C ax1 = (pE * s_ux[p + 1] - pW * s_ux[p - 1]) + (pN * s_uy[p + PW] - pS * s_uy[p - PW]);
-                C dg1 = pNE * (s_ux[p + PW + 1] + s_uy[p + PW + 1]) + pNW * (s_uy[p + PW - 1] - s_ux[p + PW - 1])
-                      - pSW * (s_ux[p - PW - 1] + s_uy[p - PW - 1]) + pSE * (s_ux[p - PW + 1] - s_uy[p - PW + 1]);
-                s_D[e] = (C(1) / C(3)) * ax1 + (C(1) / C(12)) * dg1;
+                // div = sum_k w_k c_k . (phi u)(x + c_k) / c_s^2, with u from the separable tables (box
+                // columns c+1..c+3, rows r..r+2); D is linear in u, so the time factor T multiplies at the end
+                const C x1m = sX1[c + 1], x1c = sX1[c + 2], x1p = sX1[c + 3];
+                const C x2m = sX2[c + 1], x2c = sX2[c + 2], x2p = sX2[c + 3];
+                const C y1m = sY1[r], y1c = sY1[r + 1], y1p = sY1[r + 2];
+                const C y2m = sY2[r], y2c = sY2[r + 1], y2p = sY2[r + 2];
+                C ax1 = (pE * (x1p * y1c) - pW * (x1m * y1c)) + (pN * (x2c * y2p) - pS * (x2c * y2m));
+                C dg1 = pNE * (x1p * y1p + x2p * y2p) + pNW * (x2m * y2p - x1m * y1p)
+                      - pSW * (x1m * y1m + x2m * y2m) + pSE * (x1p * y1m - x2p * y2m);
+                s_D[e] = ((C(1) / C(3)) * ax1 + (C(1) / C(12)) * dg1) * T;
             }
         }
         if (walls && (y0 < 2 || y0 + TY + 2 > ny)) {
@@ -385,7 +420,6 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             int gy = y0 - 1 + r;
             if (walls && (gy < 0 || gy >= ny)) continue;  // ghost rows: never pulled (bounce-back)
             int m = (r + 1) * MW + (c + 1);
-            int p = (r + 2) * PW + (c + 2);
             // grad psi = sum_k w_k c_k psi(x + c_k) / c_s^2
             C gmx = (C(1) / C(3)) * (s_mu[m + 1] - s_mu[m - 1])
                   + (C(1) / C(12)) * ((s_mu[m + MW + 1] - s_mu[m + MW - 1]) + (s_mu[m - MW + 1] - s_mu[m - MW - 1]));
@@ -403,11 +437,14 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
                 Fx += K * gDx;
                 Fy += K * gDy;
             }
-            C ux = s_ux[p], uy = s_uy[p];
+            C ux = sX1[c + 3] * sY1[r + 2] * T, uy = sX2[c + 3] * sY2[r + 2] * T;  // box row r + 2, column c + 3
             // the node's populations in the box: row r, plane q - QOFF, column c + 3
             S* gp = gb + (r * NQ) * BW + c + 3;
             C g[9];
-            if (kHalf) {
+            if (TAU1) {
+#pragma unroll
+                for (int q = 0; q < 9; q++) g[q] = C(0);   // multiplied by 1 - 1/tau = 0 below
+            } else if (kHalf) {
                 C rest = C(0);
 #pragma unroll
                 for (int q = 1; q < 9; q++) { g[q] = cvt<C>(gp[(q - QOFF) * BW]); rest += g[q]; }
@@ -424,7 +461,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             C ph45 = C(4.5) * ph;
             C g0eq = (kShift ? C(0) : ph) + (wq<C>(0) - C(1)) * emu - wq<C>(0) * C(1.5) * ph * uu;
             C post[9];
-            post[0] = omt * g[0] + itau * g0eq;
+            post[0] = TAU1 ? g0eq : omt * g[0] + itau * g0eq;
             // pairs (q, opp q): (1,3) c=(1,0); (2,4) c=(0,1); (5,7) c=(1,1); (6,8) c=(-1,1)
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -435,8 +472,8 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
                 C k1 = (q < 5) ? k1a : k1d, k2 = (q < 5) ? k2a : k2d, k3 = (q < 5) ? k3a : k3d;
                 C A = k1 * fma(ph45 * cu, cu, even);
                 C B = fma(k2, ph * cu, k3 * cF);
-                post[q] = fma(omt, g[q], A + B);
-                post[o] = fma(omt, g[o], A - B);
+                post[q] = TAU1 ? A + B : fma(omt, g[q], A + B);
+                post[o] = TAU1 ? A - B : fma(omt, g[o], A - B);
             }
             if (kHalf) s_h0[e] = post[0];
 #pragma unroll
@@ -504,9 +541,11 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             const long long node = (long long)(I.row0 + gy) * pitch + GC + gx;
             a.phi_out[node] = hi;
             if (kFF) a.lo_out[node] = lo;
-            S* o = a.g_out + ((long long)(I.row0 + gy) * NQ) * pitch + GC + gx;
+            if (!TAU1) {
+                S* o = a.g_out + ((long long)(I.row0 + gy) * NQ) * pitch + GC + gx;
 #pragma unroll
-            for (int q = QOFF; q < 9; q++) o[(q - QOFF) * pitch] = to_s<S>(v[q]);
+                for (int q = QOFF; q < 9; q++) o[(q - QOFF) * pitch] = to_s<S>(v[q]);
+            }
             if (edge) {
                 // the node's images in the ghost columns/rows (phi three deep, the populations one deep;
                 // in y only for periodic y, mirror images next to walls)
@@ -524,7 +563,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
                 }
                 const int gxa = gx == 0 ? nx : (gx == nx - 1 ? -1 : NONE);
                 const int gya = walls ? NONE : (gy == 0 ? ny : (gy == ny - 1 ? -1 : NONE));
-                for (int iy = 0; iy < 2; iy++) {
+                for (int iy = 0; iy < (TAU1 ? 0 : 2); iy++) {
                     const int yy = iy == 0 ? gy : gya;
                     if (yy == NONE) continue;
                     for (int ix = 0; ix < 2; ix++) {
@@ -544,14 +583,14 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         }
     }
 
-    // the last CTA of the launch advances the step counter read by the next launch
+    // the last CTA of the launch advances the step counter read by the next launch.  No fence: the
+    // counter orders no other data, every CTA read the time before its increment, and the next launch
+    // reads it only after this grid has completed (kernel boundary or the dependency wait).
     if (tid == 0) {
-        __threadfence();
         unsigned int prev = atomicAdd(&a.ctl->done, 1u);
         if (prev == gridDim.x - 1) {
             a.ctl->done = 0u;
             a.ctl->time = n + 1;
-            __threadfence();
         }
     }
 }

@@ -205,3 +205,46 @@ def test_tune_keeps_the_state():
         a.step(100)
         b.step(100)
         assert np.array_equal(a.phi(), b.phi())
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16s"])
+def test_tau1_kernel_equals_general_kernel_bitwise(prec):
+    """At tau_g = 1 the populations drop out of Eq. LB (g* = g_eq + S/2).  The kernel that reads and writes
+    phi only must give the same bits as the general kernel, which multiplies the populations by zero --
+    for a periodic flow and for a ragged ensemble with moving walls."""
+    p, phi0, _ = wl.single_vortex(n=96, T=60)
+    ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=4)
+    ens = [(dict(q, shear=q["shear"] * 30.0, Ustar=q["Ustar"] * 30.0), f) for q, f in ens]
+    params, fields = zip(*ens)
+    res = []
+    for general in (0, 1):
+        with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(list(params), list(fields), prec=prec) as b:
+            abi.lb_ch_test_hook(a.h, abi.LBCH_HOOK_GENERAL_PATH, general)
+            abi.lb_ch_test_hook(b.h, abi.LBCH_HOOK_GENERAL_PATH, general)
+            a.step(90)
+            b.step(90)
+            res.append([a.phi()] + [b.phi(k) for k in range(3)])
+            bytes_lu = a.info()["bytes_per_lu"]
+            assert bytes_lu == ({"f64": 160.0, "f32": 88.0, "f16s": 40.0}[prec] if general else
+                                {"f64": 16.0, "f32": 16.0, "f16s": 8.0}[prec])
+    for x, y in zip(res[0], res[1]):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dependent_launch_gives_the_same_bits(prec):
+    """Step launches that overlap the previous step's tail (programmatic dependent launch) read the step
+    counter and the fields only after that step completes, so they reproduce the plain stream-ordered
+    launches bit for bit -- in a time-dependent flow, over graph replays and single launches, at tau_g = 1
+    and not."""
+    for tau in (1.0, 0.8):
+        p, phi0, _ = wl.single_vortex(n=96, T=60, tau=tau)
+        out = []
+        for no_pdl in (0, 1):
+            with abi.Simulation(p, phi0, prec=prec) as sim:
+                abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_NO_PDL, no_pdl)
+                for k in (64, 5, 128, 1):
+                    sim.step(k)
+                assert sim.observe(abi.LBCH_OBS_STEP) == 198
+                out.append(sim.phi())
+        assert np.array_equal(out[0], out[1])
