@@ -9,6 +9,7 @@
 #include "lbch_adjoint.cuh"
 #include "lbch_kernels.cuh"
 #include "lbch_ns.cuh"
+#include "lbch_sweep.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -58,6 +59,14 @@ constexpr Shape kShapes64[2] = {{32, 8}, {16, 8}};
 constexpr Shape kShapesF[3] = {{32, 16}, {32, 8}, {16, 8}};
 inline int n_shapes(int prec) { return prec == LBCH_F64 ? 2 : 3; }
 inline Shape shape_of(int prec, int k) { return prec == LBCH_F64 ? kShapes64[k] : kShapesF[k]; }
+
+// Configurations of the row-sweep kernel (tau_g = 1): TY output rows per warp, NW warps per CTA; a tile
+// is 56 columns by NW TY rows.  lb_ch_tune picks among them as among the tile shapes.
+struct SweepCfg { int ty, nw; };
+constexpr SweepCfg kSweep[4] = {{12, 4}, {6, 4}, {6, 2}, {3, 4}};
+constexpr int kSweepShapes = 4;
+constexpr int kSweepW = 56;
+inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw}; }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -111,7 +120,7 @@ struct lbch_handle {
         int grid = 0;           // persistent CTAs per step launch
         int* d_tile_begin = nullptr;
         CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
-    } ps[kMaxShapes];
+    } ps[kMaxShapes], sw[kSweepShapes];  // tile kernel shapes; row-sweep configurations (tm_g unused)
     void* g[2] = {nullptr, nullptr};
     void* phi[2] = {nullptr, nullptr};
     float* lo[2] = {nullptr, nullptr};  // low part of phi (float path)
@@ -179,8 +188,100 @@ cudaError_t launch_step_v(lbch_handle* h, int parity)
 template <typename C, typename S, typename P, int TX, int TY>
 cudaError_t launch_step_t(lbch_handle* h, int parity)
 {
-    return (h->tau1 && !h->force_general) ? launch_step_v<C, S, P, TX, TY, true>(h, parity)
-                                          : launch_step_v<C, S, P, TX, TY, false>(h, parity);
+    return launch_step_v<C, S, P, TX, TY, false>(h, parity);
+}
+
+// tau_g = 1 everywhere: the row-sweep kernel steps the handle (its shape index then names a sweep
+// configuration); otherwise the tile kernel does.
+inline bool use_sweep(const lbch_handle* h) { return h->tau1 && !h->force_general && !h->coupled; }
+inline int n_active(const lbch_handle* h) { return h->coupled ? 1 : (use_sweep(h) ? kSweepShapes : n_shapes(h->prec)); }
+inline const lbch_handle::PerShape& active_ps(const lbch_handle* h) { return use_sweep(h) ? h->sw[h->shape] : h->ps[h->shape]; }
+inline Shape active_tile(const lbch_handle* h)
+{
+    return h->coupled ? Shape{0, 0} : (use_sweep(h) ? sweep_tile(h->shape) : shape_of(h->prec, h->shape));
+}
+
+template <typename C, typename P, bool FF, int TY, int NW>
+cudaError_t launch_sweep_v(lbch_handle* h, int parity)
+{
+    using L = SweepShape<P, FF, TY, NW>;
+    const lbch_handle::PerShape& ps = h->sw[h->shape];
+    SweepArgs<C, P> a;
+    a.inst = h->d_inst;
+    a.tile_begin = ps.d_tile_begin;
+    a.tabs = tables<C>(h);
+    a.n_inst = h->n_inst;
+    a.total_tiles = ps.total_tiles;
+    a.pitch = h->pitch;
+    a.debug_skip = h->debug_skip;
+    a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
+    a.lo_out = h->lo[parity ^ 1];
+    a.ctl = h->ctl;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ps.grid);
+    cfg.blockDim = dim3(NW * 32);
+    cfg.dynamicSmemBytes = L::BYTES;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, P, FF, TY, NW>, ps.tm_phi[parity], ps.tm_lo[parity], a);
+}
+
+template <typename C, typename P, bool FF>
+cudaError_t launch_sweep_t(lbch_handle* h, int parity)
+{
+    switch (h->shape) {
+    case 0: return launch_sweep_v<C, P, FF, 12, 4>(h, parity);
+    case 1: return launch_sweep_v<C, P, FF, 6, 4>(h, parity);
+    case 2: return launch_sweep_v<C, P, FF, 6, 2>(h, parity);
+    default: return launch_sweep_v<C, P, FF, 3, 4>(h, parity);
+    }
+}
+
+cudaError_t launch_sweep(lbch_handle* h, int parity)
+{
+    switch (h->prec) {
+    case LBCH_F64: return launch_sweep_t<double, double, false>(h, parity);
+    case LBCH_F32: return launch_sweep_t<float, float, true>(h, parity);
+    default: return launch_sweep_t<float, float, false>(h, parity);
+    }
+}
+
+template <typename C, typename P, bool FF, int TY, int NW>
+cudaError_t prepare_sweep_v(lbch_handle* h, int k)
+{
+    using L = SweepShape<P, FF, TY, NW>;
+    auto kern = ch_sweep_kernel<C, P, FF, TY, NW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, L::BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    h->sw[k].grid = std::max(1, std::min(h->sw[k].total_tiles, per_sm * sms));
+    return cudaSuccess;
+}
+
+template <typename C, typename P, bool FF>
+cudaError_t prepare_sweep_t(lbch_handle* h, int k)
+{
+    return k == 0 ? prepare_sweep_v<C, P, FF, 12, 4>(h, k)
+         : k == 1 ? prepare_sweep_v<C, P, FF, 6, 4>(h, k)
+         : k == 2 ? prepare_sweep_v<C, P, FF, 6, 2>(h, k) : prepare_sweep_v<C, P, FF, 3, 4>(h, k);
+}
+
+cudaError_t prepare_sweep(lbch_handle* h, int k)
+{
+    switch (h->prec) {
+    case LBCH_F64: return prepare_sweep_t<double, double, false>(h, k);
+    case LBCH_F32: return prepare_sweep_t<float, float, true>(h, k);
+    default: return prepare_sweep_t<float, float, false>(h, k);
+    }
 }
 
 // Dynamic shared memory of the step kernel, and the persistent grid that fits the device, for shape k.
@@ -190,9 +291,6 @@ cudaError_t prepare_step_t(lbch_handle* h, int k)
     using L = StepShape<C, S, P, TX, TY>;
     auto kern = ch_step_kernel<C, S, P, TX, TY, NT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ch_step_kernel<C, S, P, TX, TY, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);
@@ -275,6 +373,7 @@ cudaError_t ns_fields_t(lbch_handle* h, int parity)
 cudaError_t launch_step(lbch_handle* h, int parity)
 {
     if (h->coupled) return h->prec == LBCH_F64 ? launch_ns_t<double>(h, parity) : launch_ns_t<float>(h, parity);
+    if (use_sweep(h)) return launch_sweep(h, parity);
     const int k = h->shape;
     switch (h->prec) {
     case LBCH_F64:
@@ -397,6 +496,8 @@ void release(lbch_handle* h)
     if (h->d_tabs_f) cudaFree(h->d_tabs_f);
     for (int k = 0; k < kMaxShapes; k++)
         if (h->ps[k].d_tile_begin) cudaFree(h->ps[k].d_tile_begin);
+    for (int k = 0; k < kSweepShapes; k++)
+        if (h->sw[k].d_tile_begin) cudaFree(h->sw[k].d_tile_begin);
     if (h->d_node_begin) cudaFree(h->d_node_begin);
     if (h->d_tabs) cudaFree(h->d_tabs);
     if (h->phi0) cudaFree(h->phi0);
@@ -453,6 +554,38 @@ lbch_status encode_maps(lbch_handle* h, int sk)
         } else {
             ps.tm_lo[k] = ps.tm_phi[k];  // unused by the kernels without a low part
         }
+    }
+    return LBCH_OK;
+}
+
+// The row-sweep kernel's boxes: phi over 64 columns and the tile's rows plus three halo rows on each
+// side; the low part of phi over the output rows.
+lbch_status encode_sweep_maps(lbch_handle* h, int sk)
+{
+    const Shape sh = sweep_tile(sk);
+    lbch_handle::PerShape& ps = h->sw[sk];
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(LBCH_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    CUtensorMapDataType pt = h->phi_elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint32_t es[2] = {1, 1};
+    cuuint64_t pdim[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->rows};
+    for (int k = 0; k < 2; k++) {
+        cuuint64_t pstr[1] = {(cuuint64_t)h->pitch * h->phi_elem};
+        cuuint32_t pbox[2] = {64u, (cuuint32_t)(sh.ty + 6)};
+        CUresult r = enc(&ps.tm_phi[k], pt, 2, h->phi[k], pdim, pstr, pbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of phi (row sweep): CUresult %d", (int)r);
+        if (h->lo[k]) {
+            cuuint64_t lstr[1] = {(cuuint64_t)h->pitch * 4};
+            cuuint32_t lbox[2] = {64u, (cuuint32_t)sh.ty};
+            r = enc(&ps.tm_lo[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->lo[k], pdim, lstr, lbox, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of phi, low part (row sweep): CUresult %d", (int)r);
+        } else {
+            ps.tm_lo[k] = ps.tm_phi[k];  // unused without a low part
+        }
+        ps.tm_g[k] = ps.tm_phi[k];
     }
     return LBCH_OK;
 }
@@ -642,6 +775,17 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         tile_begin[sk].push_back(t);
         h->ps[sk].total_tiles = t;
     }
+    std::vector<int> sweep_begin[kSweepShapes];
+    for (int sk = 0; sk < kSweepShapes; sk++) {
+        const Shape sh = sweep_tile(sk);
+        int t = 0;
+        for (int k = 0; k < n_inst; k++) {
+            sweep_begin[sk].push_back(t);
+            t += ((params[k].nx + sh.tx - 1) / sh.tx) * ((params[k].ny + sh.ty - 1) / sh.ty);
+        }
+        sweep_begin[sk].push_back(t);
+        h->sw[sk].total_tiles = t;
+    }
     for (int k = 0; k < n_inst; k++) {
         h->inst[k].tab = (int)tabs.size();
         velocity_tables(params[k], h->pitch, h->inst[k].ylen, tabs);
@@ -660,6 +804,14 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         CKI(prepare_step(h, sk));
         CKI(cudaMalloc(&h->ps[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
         CKI(cudaMemcpy(h->ps[sk].d_tile_begin, tile_begin[sk].data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice));
+    }
+    if (h->tau1) {
+        for (int sk = 0; sk < kSweepShapes; sk++) {
+            CKI(prepare_sweep(h, sk));
+            CKI(cudaMalloc(&h->sw[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
+            CKI(cudaMemcpy(h->sw[sk].d_tile_begin, sweep_begin[sk].data(), sizeof(int) * (n_inst + 1),
+                           cudaMemcpyHostToDevice));
+        }
     }
     if (stream) {
         h->stream = static_cast<cudaStream_t>(stream);
@@ -689,6 +841,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     CKI(cudaMalloc(&h->result, sizeof(double) * RED_NV * (size_t)n_inst));
     lbch_status st = LBCH_OK;
     for (int sk = 0; sk < n_shapes(prec) && st == LBCH_OK; sk++) st = encode_maps(h, sk);
+    for (int sk = 0; h->tau1 && sk < kSweepShapes && st == LBCH_OK; sk++) st = encode_sweep_maps(h, sk);
     if (st != LBCH_OK) return bail(st);
 
     // the initial field in the padded layout, ghost frame included, through pinned staging
@@ -923,7 +1076,7 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     }
     out[0] = (double)h->nodes;
     out[1] = bytes;
-    out[2] = (double)h->ps[h->shape].grid;
+    out[2] = (double)active_ps(h).grid;
     out[3] = (double)h->n;
     return LBCH_OK;
 }
@@ -1040,7 +1193,7 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds)
 lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
 {
     if (!h || steps < 1) return fail(LBCH_EINVAL, "NULL handle or steps < 1");
-    const int ns = h->coupled ? 1 : n_shapes(h->prec);
+    const int ns = n_active(h);
     if (ns > 1) {
         long long bytes = 0;
         lb_ch_state_bytes(h, &bytes);
@@ -1075,7 +1228,7 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
         for (int k = 0; k < 2; k++)  // graphs captured earlier launch the previous shape's kernel
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
     }
-    const Shape sh = h->coupled ? Shape{0, 0} : shape_of(h->prec, h->shape);
+    const Shape sh = active_tile(h);
     if (tile_x) *tile_x = sh.tx;
     if (tile_y) *tile_y = sh.ty;
     return LBCH_OK;
@@ -1095,13 +1248,14 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
         return LBCH_OK;
     }
     if (hook == LBCH_HOOK_GENERAL_PATH) {
+        if (h->force_general != (value != 0)) h->shape = 0;  // the shape index names the other kernel's list
         h->force_general = value != 0;
         for (int k = 0; k < 2; k++)
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
         return LBCH_OK;
     }
     if (hook == LBCH_HOOK_TILE_SHAPE) {
-        if (h->coupled || value < 0 || value >= n_shapes(h->prec)) return fail(LBCH_EINVAL, "no tile shape %ld", value);
+        if (h->coupled || value < 0 || value >= n_active(h)) return fail(LBCH_EINVAL, "no tile shape %ld", value);
         h->shape = (int)value;
         for (int k = 0; k < 2; k++)
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }

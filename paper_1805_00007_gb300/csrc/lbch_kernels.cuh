@@ -129,6 +129,132 @@ __device__ __forceinline__ int mirror(int j, int n)
     return j < 0 ? 0 : (j >= n ? n - 1 : j);
 }
 
+// ------------------------------------------------------------------------------------------ per-node arithmetic
+// Used by both forms of the step kernel (tiles in shared memory; row sweeps in registers), so that every
+// quantity is evaluated by the same operations in both.  Every product is an explicit rounded multiply
+// or an explicit fused multiply-add: the compiler's own contraction of a*b + c depends on how often a
+// product is reused, which differs between the two forms, and would change the last bits.
+__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// d/dphi of beta (phi - phiA)^2 (phi - phiB)^2 (Eq. bulk)
+template <typename C> __device__ __forceinline__ C node_dfdphi(C phi, C beta, C phiA, C phiB)
+{
+    const C s = op_fma(C(2), phi, -phiA) - phiB;
+    return op_mul(op_mul(op_mul(op_mul(C(2), beta), phi - phiA), phi - phiB), s);
+}
+
+// Eq. mu: mu = f'(phi) - kappa lap phi, with the isotropic nine-point Laplacian
+// lap psi = sum_k 2 w_k (psi(x + c_k) - psi(x)) / c_s^2.
+template <typename C>
+__device__ __forceinline__ C node_mu(C ce, C pE, C pW, C pN, C pS, C pNE, C pNW, C pSE, C pSW, C beta, C kappa,
+                                     C phiA, C phiB)
+{
+    const C ax = (pE + pW) + (pN + pS);
+    const C dg = (pNE + pNW) + (pSE + pSW);
+    const C lap = op_fma(C(2) / C(3), op_fma(C(-4), ce, ax), op_mul(C(1) / C(6), op_fma(C(-4), ce, dg)));
+    return op_fma(-kappa, lap, node_dfdphi(ce, beta, phiA, phiB));
+}
+
+// D = div(phi u) = sum_k w_k c_k . (phi u)(x + c_k) / c_s^2 for the separable flow u = (X1 Y1, X2 Y2) T:
+// x*m / x*c / x*p are the X tables at column offsets -1 / 0 / +1, y*m / y*c / y*p the Y tables at row
+// offsets -1 / 0 / +1.  D is linear in u, so the time factor T multiplies once at the end.
+template <typename C>
+__device__ __forceinline__ C node_div(C pE, C pW, C pN, C pS, C pNE, C pNW, C pSE, C pSW, C x1m, C x1p, C x2m, C x2c,
+                                      C x2p, C y1m, C y1c, C y1p, C y2m, C y2p, C T)
+{
+    // axis neighbours: (phi ux)(E) - (phi ux)(W) + (phi uy)(N) - (phi uy)(S)
+    const C ax1 = op_fma(pE, op_mul(x1p, y1c), -op_mul(pW, op_mul(x1m, y1c)))
+                + op_fma(pN, op_mul(x2c, y2p), -op_mul(pS, op_mul(x2c, y2m)));
+    // diagonal neighbours: c_k . (phi u)(x + c_k) for NE, NW, SW, SE
+    const C bNE = op_fma(x1p, y1p, op_mul(x2p, y2p));
+    const C bNW = op_fma(x2m, y2p, -op_mul(x1m, y1p));
+    const C bSW = op_fma(x1m, y1m, op_mul(x2m, y2m));
+    const C bSE = op_fma(x1p, y1m, -op_mul(x2p, y2m));
+    const C dg1 = op_fma(pSE, bSE, op_fma(-pSW, bSW, op_fma(pNW, bNW, op_mul(pNE, bNE))));
+    return op_mul(op_fma(C(1) / C(3), ax1, op_mul(C(1) / C(12), dg1)), T);
+}
+
+// Isotropic gradient grad psi = sum_k w_k c_k psi(x + c_k) / c_s^2.
+template <typename C>
+__device__ __forceinline__ void grad9(C E, C W, C N, C S, C NE, C NW, C SE, C SW, C& gx, C& gy)
+{
+    gx = op_fma(C(1) / C(3), E - W, op_mul(C(1) / C(12), (NE - NW) + (SE - SW)));
+    gy = op_fma(C(1) / C(3), N - S, op_mul(C(1) / C(12), (NE + NW) - (SE + SW)));
+}
+
+// The force: F1 = (phi / rho)(-phi grad mu) with rho = a phi + b (Eq. liangFi, with grad p = 0), plus
+// F2 = 3 c_s^2 K grad(div(phi u)) for Model II (Eq. mark3).
+template <typename C>
+__device__ __forceinline__ void node_force(C ph, C gmx, C gmy, C gDx, C gDy, bool model2, C ra, C rb, C K, C& Fx,
+                                           C& Fy)
+{
+    const C fct = op_mul(op_mul(-ph, ph), rcp<C>(op_fma(ra, ph, rb)));
+    Fx = op_mul(fct, gmx);
+    Fy = op_mul(fct, gmy);
+    if (model2) {
+        Fx = op_fma(K, gDx, Fx);
+        Fy = op_fma(K, gDy, Fy);
+    }
+}
+
+// The prescribed velocity X(x) Y(y) T at a node.
+template <typename C> __device__ __forceinline__ C node_u(C X, C Y, C T) { return op_mul(op_mul(X, Y), T); }
+
+// Eq. LB as g* = (1 - 1/tau) g + g_eq / tau + (1 - 1/(2 tau)) S, with Eq. geq and the source
+// S_i = w_i c_i . F / c_s^2 (Eq. liangFi), split into the parts even and odd in c_i.  With kShift the
+// rest population is carried as g_0 - phi.  With TAU1 (tau = 1) the populations g are not read.
+template <typename C, bool TAU1, bool kShift>
+__device__ __forceinline__ void collide9(C ph, C mu, C Fx, C Fy, C ux, C uy, const C* g, const Consts<C>& K0, C* post)
+{
+    const C itau = K0.itau, omt = K0.omt, src = K0.src;
+    // per direction class (axis, diagonal): w/tau, 3 w/tau, 3 w (1 - 1/(2 tau))
+    const C k1a = op_mul(wq<C>(1), itau), k1d = op_mul(wq<C>(5), itau);
+    const C k2a = op_mul(C(3), k1a), k2d = op_mul(C(3), k1d);
+    const C k3a = op_mul(C(3) * wq<C>(1), src), k3d = op_mul(C(3) * wq<C>(5), src);
+    const C emu = op_mul(K0.eta, mu);
+    const C phuu = op_mul(ph, op_fma(ux, ux, op_mul(uy, uy)));
+    const C even = op_fma(C(-1.5), phuu, emu);
+    const C ph45 = op_mul(C(4.5), ph);
+    C g0eq = op_fma(wq<C>(0) - C(1), emu, op_mul(-wq<C>(0) * C(1.5), phuu));
+    if (!kShift) g0eq = ph + g0eq;
+    post[0] = TAU1 ? g0eq : op_fma(omt, g[0], op_mul(itau, g0eq));
+    // pairs (q, opp q): (1,3) c=(1,0); (2,4) c=(0,1); (5,7) c=(1,1); (6,8) c=(-1,1)
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int q = (k == 0) ? 1 : (k == 1) ? 2 : (k == 2) ? 5 : 6;
+        const int o = opp(q);
+        const C cu = (k == 0) ? ux : (k == 1) ? uy : (k == 2) ? ux + uy : uy - ux;
+        const C cF = (k == 0) ? Fx : (k == 1) ? Fy : (k == 2) ? Fx + Fy : Fy - Fx;
+        const C k1 = (q < 5) ? k1a : k1d, k2 = (q < 5) ? k2a : k2d, k3 = (q < 5) ? k3a : k3d;
+        const C A = op_mul(k1, op_fma(op_mul(ph45, cu), cu, even));
+        const C B = op_fma(k2, op_mul(ph, cu), op_mul(k3, cF));
+        post[q] = TAU1 ? A + B : op_fma(omt, g[q], A + B);
+        post[o] = TAU1 ? A - B : op_fma(omt, g[o], A - B);
+    }
+}
+
+// Halfway bounce-back at a wall node: g_q arriving from the ghost row is the node's own post-collision
+// g_opp(q) plus the moving-wall term 2 w_q phi (c_q . u_w) / c_s^2.
+template <typename C, int q>
+__device__ __forceinline__ C bounce(C post_opp, C ph, C uwx, C uwy)
+{
+    const C cuw = cx(q) == 0 ? (cy(q) > 0 ? uwy : -uwy)
+                : (cy(q) == 0 ? (cx(q) > 0 ? uwx : -uwx)
+                : (cx(q) > 0 ? (cy(q) > 0 ? uwx + uwy : uwx - uwy) : (cy(q) > 0 ? uwy - uwx : -(uwx + uwy))));
+    return op_fma(op_mul(C(6) * wq<C>(q), ph), cuw, post_opp);
+}
+
+// Sum of the streamed populations g_1..g_8(t+1) at a node, grouped by the column they come from: the
+// three from x - 1 (1, 5, 8), the two from x (2, 4), the three from x + 1 (3, 6, 7).
+template <typename C>
+__device__ __forceinline__ C stream_sum(C v1, C v2, C v3, C v4, C v5, C v6, C v7, C v8)
+{
+    return (((v1 + v5) + v8) + (v2 + v4)) + ((v3 + v6) + v7);
+}
+
 // ------------------------------------------------------------------------------------------ TMA / mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -372,23 +498,10 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             C ce = cvt<C>(q[0]);
             C pE = cvt<C>(q[1]), pW = cvt<C>(q[-1]), pN = cvt<C>(q[BW]), pS = cvt<C>(q[-BW]);
             C pNE = cvt<C>(q[BW + 1]), pNW = cvt<C>(q[BW - 1]), pSE = cvt<C>(q[-BW + 1]), pSW = cvt<C>(q[-BW - 1]);
-            C ax = (pE + pW) + (pN + pS);
-            C dg = (pNE + pNW) + (pSE + pSW);
-            // lap = sum_k 2 w_k (psi_k - psi_c) / c_s^2
-            C lap = (C(2) / C(3)) * (ax - C(4) * ce) + (C(1) / C(6)) * (dg - C(4) * ce);
-            s_mu[e] = dfdphi(ce, beta, phiA, phiB) - kappa * lap;
-            if (model == 2) {
-                // div = sum_k w_k c_k . (phi u)(x + c_k) / c_s^2, with u from the separable tables (box
-                // columns c+1..c+3, rows r..r+2); D is linear in u, so the time factor T multiplies at the end
-                const C x1m = sX1[c + 1], x1c = sX1[c + 2], x1p = sX1[c + 3];
-                const C x2m = sX2[c + 1], x2c = sX2[c + 2], x2p = sX2[c + 3];
-                const C y1m = sY1[r], y1c = sY1[r + 1], y1p = sY1[r + 2];
-                const C y2m = sY2[r], y2c = sY2[r + 1], y2p = sY2[r + 2];
-                C ax1 = (pE * (x1p * y1c) - pW * (x1m * y1c)) + (pN * (x2c * y2p) - pS * (x2c * y2m));
-                C dg1 = pNE * (x1p * y1p + x2p * y2p) + pNW * (x2m * y2p - x1m * y1p)
-                      - pSW * (x1m * y1m + x2m * y2m) + pSE * (x1p * y1m - x2p * y2m);
-                s_D[e] = ((C(1) / C(3)) * ax1 + (C(1) / C(12)) * dg1) * T;
-            }
+            s_mu[e] = node_mu(ce, pE, pW, pN, pS, pNE, pNW, pSE, pSW, beta, kappa, phiA, phiB);
+            if (model == 2)  // the tables at box columns c+1..c+3 and box rows r..r+2
+                s_D[e] = node_div(pE, pW, pN, pS, pNE, pNW, pSE, pSW, sX1[c + 1], sX1[c + 3], sX2[c + 1], sX2[c + 2],
+                                  sX2[c + 3], sY1[r], sY1[r + 1], sY1[r + 2], sY2[r], sY2[r + 2], T);
         }
         if (walls && (y0 < 2 || y0 + TY + 2 > ny)) {
             // every stencil operand takes at a ghost row the value at the mirror row: mu and D at rows
@@ -409,35 +522,23 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         __syncthreads();
 
         // 3. force, equilibrium, source and collision on tile + 1, written back into the box
-        const C eta = K0.eta, ra = K0.a, rb = K0.b, K = K0.K;
-        const C itau = K0.itau, omt = K0.omt, src = K0.src;
-        // per direction class (axis, diagonal): w/tau, 3 w/tau, 3 w (1 - 1/(2 tau))
-        const C k1a = wq<C>(1) * itau, k1d = wq<C>(5) * itau;
-        const C k2a = C(3) * k1a, k2d = C(3) * k1d;
-        const C k3a = C(3) * wq<C>(1) * src, k3d = C(3) * wq<C>(5) * src;
+        const C ra = K0.a, rb = K0.b, K = K0.K;
         for (int e = tid; e < L::NG; e += NT) {
             int r = e / GW, c = e - r * GW;
             int gy = y0 - 1 + r;
             if (walls && (gy < 0 || gy >= ny)) continue;  // ghost rows: never pulled (bounce-back)
             int m = (r + 1) * MW + (c + 1);
-            // grad psi = sum_k w_k c_k psi(x + c_k) / c_s^2
-            C gmx = (C(1) / C(3)) * (s_mu[m + 1] - s_mu[m - 1])
-                  + (C(1) / C(12)) * ((s_mu[m + MW + 1] - s_mu[m + MW - 1]) + (s_mu[m - MW + 1] - s_mu[m - MW - 1]));
-            C gmy = (C(1) / C(3)) * (s_mu[m + MW] - s_mu[m - MW])
-                  + (C(1) / C(12)) * ((s_mu[m + MW + 1] + s_mu[m + MW - 1]) - (s_mu[m - MW + 1] + s_mu[m - MW - 1]));
+            C gmx, gmy, gDx = C(0), gDy = C(0);
+            grad9(s_mu[m + 1], s_mu[m - 1], s_mu[m + MW], s_mu[m - MW], s_mu[m + MW + 1], s_mu[m + MW - 1],
+                  s_mu[m - MW + 1], s_mu[m - MW - 1], gmx, gmy);
+            if (model == 2)
+                grad9(s_D[m + 1], s_D[m - 1], s_D[m + MW], s_D[m - MW], s_D[m + MW + 1], s_D[m + MW - 1],
+                      s_D[m - MW + 1], s_D[m - MW - 1], gDx, gDy);
             C ph = cvt<C>(pb[(r + 2) * BW + c + 3]);
             C mu = s_mu[m];
-            C fct = -ph * ph * rcp<C>(ra * ph + rb);  // F1 = (phi/rho)(-phi grad mu), rho = a phi + b
-            C Fx = fct * gmx, Fy = fct * gmy;
-            if (model == 2) {                         // F2 = 3 c_s^2 K grad(div(phi u)), Eq. mark3
-                C gDx = (C(1) / C(3)) * (s_D[m + 1] - s_D[m - 1])
-                      + (C(1) / C(12)) * ((s_D[m + MW + 1] - s_D[m + MW - 1]) + (s_D[m - MW + 1] - s_D[m - MW - 1]));
-                C gDy = (C(1) / C(3)) * (s_D[m + MW] - s_D[m - MW])
-                      + (C(1) / C(12)) * ((s_D[m + MW + 1] + s_D[m + MW - 1]) - (s_D[m - MW + 1] + s_D[m - MW - 1]));
-                Fx += K * gDx;
-                Fy += K * gDy;
-            }
-            C ux = sX1[c + 3] * sY1[r + 2] * T, uy = sX2[c + 3] * sY2[r + 2] * T;  // box row r + 2, column c + 3
+            C Fx, Fy;
+            node_force(ph, gmx, gmy, gDx, gDy, model == 2, ra, rb, K, Fx, Fy);
+            const C ux = node_u(sX1[c + 3], sY1[r + 2], T), uy = node_u(sX2[c + 3], sY2[r + 2], T);  // box row r+2, col c+3
             // the node's populations in the box: row r, plane q - QOFF, column c + 3
             S* gp = gb + (r * NQ) * BW + c + 3;
             C g[9];
@@ -453,28 +554,8 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
 #pragma unroll
                 for (int q = 0; q < 9; q++) g[q] = cvt<C>(gp[q * BW]);
             }
-            // Eq. LB as g* = (1 - 1/tau) g + g_eq/tau + (1 - 1/(2 tau)) S with Eq. geq and Eq. liangFi,
-            // split into the parts even and odd in c_i (S_i and the linear term of g_eq are odd)
-            C emu = eta * mu;
-            C uu = ux * ux + uy * uy;
-            C even = emu - C(1.5) * ph * uu;
-            C ph45 = C(4.5) * ph;
-            C g0eq = (kShift ? C(0) : ph) + (wq<C>(0) - C(1)) * emu - wq<C>(0) * C(1.5) * ph * uu;
             C post[9];
-            post[0] = TAU1 ? g0eq : omt * g[0] + itau * g0eq;
-            // pairs (q, opp q): (1,3) c=(1,0); (2,4) c=(0,1); (5,7) c=(1,1); (6,8) c=(-1,1)
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const int q = (k == 0) ? 1 : (k == 1) ? 2 : (k == 2) ? 5 : 6;
-                const int o = opp(q);
-                C cu = (C)cx(q) * ux + (C)cy(q) * uy;
-                C cF = (C)cx(q) * Fx + (C)cy(q) * Fy;
-                C k1 = (q < 5) ? k1a : k1d, k2 = (q < 5) ? k2a : k2d, k3 = (q < 5) ? k3a : k3d;
-                C A = k1 * fma(ph45 * cu, cu, even);
-                C B = fma(k2, ph * cu, k3 * cF);
-                post[q] = TAU1 ? A + B : fma(omt, g[q], A + B);
-                post[o] = TAU1 ? A - B : fma(omt, g[o], A - B);
-            }
+            collide9<C, TAU1, kShift>(ph, mu, Fx, Fy, ux, uy, g, K0, post);
             if (kHalf) s_h0[e] = post[0];
 #pragma unroll
             for (int q = QOFF; q < 9; q++) gp[(q - QOFF) * BW] = to_s<S>(post[q]);
@@ -493,33 +574,26 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             const bool edge = gx < 3 || gx >= nx - 3 || gy < 3 || gy >= ny - 3;
             const S* src = gb + ((r + 1) * NQ) * BW + c + 4;   // this node's box position, plane 0
             C v[9];
-            C sumq = C(0);
             v[0] = kHalf ? s_h0[(r + 1) * GW + (c + 1)] : cvt<C>(src[0]);
-            if (!kShift) sumq += v[0];
-            if (!wallrow) {
 #pragma unroll
-                for (int q = 1; q < 9; q++) {
-                    v[q] = cvt<C>(src[(-cy(q) * NQ + q - QOFF) * BW - cx(q)]);
-                    sumq += v[q];
+            for (int q = 1; q < 9; q++) v[q] = cvt<C>(src[(-cy(q) * NQ + q - QOFF) * BW - cx(q)]);
+            if (wallrow) {
+                // populations that would come from a ghost row are bounced back at the node
+                const C ph = cvt<C>(pb[(r + 3) * BW + c + 4]);
+                if (gy == 0) {
+                    const C uwx = node_u(tX1[gx + GC], tW[0], T), uwy = node_u(tX2[gx + GC], tW[2], T);
+                    v[2] = bounce<C, 2>(cvt<C>(src[(4 - QOFF) * BW]), ph, uwx, uwy);
+                    v[5] = bounce<C, 5>(cvt<C>(src[(7 - QOFF) * BW]), ph, uwx, uwy);
+                    v[6] = bounce<C, 6>(cvt<C>(src[(8 - QOFF) * BW]), ph, uwx, uwy);
                 }
-            } else {
-#pragma unroll
-                for (int q = 1; q < 9; q++) {
-                    int sy = gy - cy(q);
-                    if (sy < 0 || sy >= ny) {
-                        // halfway bounce-back: the population that left along -c_q returns along c_q, plus
-                        // the moving-wall term 2 w_q phi (c_q . u_w) / c_s^2
-                        int wi = sy < 0 ? 0 : 1;
-                        C uwx = tX1[gx + GC] * tW[wi] * T, uwy = tX2[gx + GC] * tW[2 + wi] * T;
-                        C ph = cvt<C>(pb[(r + 3) * BW + c + 4]);
-                        v[q] = cvt<C>(src[(opp(q) - QOFF) * BW])
-                             + C(6) * wq<C>(q) * ph * ((C)cx(q) * uwx + (C)cy(q) * uwy);
-                    } else {
-                        v[q] = cvt<C>(src[(-cy(q) * NQ + q - QOFF) * BW - cx(q)]);
-                    }
-                    sumq += v[q];
+                if (gy == ny - 1) {
+                    const C uwx = node_u(tX1[gx + GC], tW[1], T), uwy = node_u(tX2[gx + GC], tW[3], T);
+                    v[4] = bounce<C, 4>(cvt<C>(src[(2 - QOFF) * BW]), ph, uwx, uwy);
+                    v[7] = bounce<C, 7>(cvt<C>(src[(5 - QOFF) * BW]), ph, uwx, uwy);
+                    v[8] = bounce<C, 8>(cvt<C>(src[(6 - QOFF) * BW]), ph, uwx, uwy);
                 }
             }
+            const C sumq = stream_sum(v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8]);
             P hi;
             float lo = 0.0f;
             if (kFF) {
@@ -536,7 +610,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
                 // half path: phi(t+1) = phi(t) + v_0 + sum_{q>0} g_q(t+1) in float; g_0 stays implied
                 hi = (P)((float)pb[(r + 3) * BW + c + 4] + (float)(v[0] + sumq));
             } else {
-                hi = (P)sumq;
+                hi = (P)(v[0] + sumq);
             }
             const long long node = (long long)(I.row0 + gy) * pitch + GC + gx;
             a.phi_out[node] = hi;

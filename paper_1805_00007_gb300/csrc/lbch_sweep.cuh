@@ -1,0 +1,438 @@
+// lbch_sweep.cuh -- the step kernel as row sweeps in registers, for instances with tau_g = 1.
+//
+// At tau_g = 1, Eq. LB reduces to g* = g_eq + S / 2: the populations are multiplied by 1 - 1/tau = 0, so
+// the step maps phi(t) to phi(t+1) = sum_i g*_i(x - c_i) and nothing else is carried between steps.
+// Every quantity of the step at a node (mu, D = div(phi u), the gradients, the force, g*) depends only on
+// phi within three rows and three columns, so one warp can produce a strip of output rows by sweeping
+// upwards through it, one row per iteration, with everything the stencils need held in registers:
+//
+//   * a warp owns 64 consecutive columns, two per lane (a = 2 lane, b = 2 lane + 1, from domain column
+//     x0 - 4); its 56 middle columns (lanes 2..29) are output, the four on each side are halo;
+//   * the left neighbour of a and the right neighbour of b come from the adjacent lanes by shuffles;
+//   * the rows below stay in registers: iteration j loads phi of row yf = wy0 - 3 + j, computes mu and D
+//     of row yf - 1, collides row yf - 2 and completes phi(t+1) of row yf - 3;
+//   * streaming needs only three values from each side: the populations 1, 5, 8 that arrive from the
+//     column to the left are summed at their source node and cross one lane boundary as one number, as do
+//     3, 6, 7 from the right (the grouping of the sum is the one the tile kernel uses too).
+//
+// A CTA of NW warps stacks its warps vertically over a tile of 56 x (NW TY) output nodes and shares one
+// TMA box of phi (the tile plus three halo rows and four halo columns on each side; on the float path a
+// second box brings the low part of phi for the output rows).  Persistent CTAs walk the tiles with a
+// two-stage TMA pipeline, as the tile kernel does.  The velocity tables of the warp's columns are read
+// once per tile into registers; the Y tables of its rows arrive one row per lane and are broadcast by
+// shuffles.
+#pragma once
+#include <type_traits>
+
+#include "lbch_kernels.cuh"
+
+namespace lbch {
+
+template <typename C, typename P>
+struct SweepArgs {
+    const InstDev* inst;
+    const int* tile_begin;  // first tile of each instance (n_inst + 1 entries)
+    const C* tabs;          // velocity tables in the arithmetic type
+    int n_inst;
+    int total_tiles;
+    int pitch;
+    int debug_skip;         // test hook: CTA 0 never issues its first load (its wait runs out)
+    P* phi_out;
+    float* lo_out;          // low part of phi on the float-float path
+    Ctl* ctl;
+};
+
+template <typename P, bool FF, int TY, int NW>
+struct SweepShape {
+    static constexpr int W = 56;                 // output columns of a tile
+    static constexpr int BW = 64;                // box columns: x0 - 4 .. x0 + 59, two per lane
+    static constexpr int TH = NW * TY;           // output rows of a tile
+    static constexpr int PBH = TH + 6;           // phi box rows: y0 - 3 .. y0 + TH + 2
+    static constexpr unsigned PBOX_BYTES = PBH * BW * sizeof(P);
+    static constexpr unsigned LBOX_BYTES = FF ? TH * BW * 4 : 0;
+    __host__ __device__ static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
+    static constexpr size_t OFF_L = a128(PBOX_BYTES);
+    static constexpr size_t STAGE = OFF_L + a128(LBOX_BYTES);
+    static constexpr size_t BYTES = 2 * STAGE + 128 + 128;  // mbarriers, alignment slack
+};
+
+template <typename P> struct Pair;
+template <> struct Pair<float> { using T = float2; };
+template <> struct Pair<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C from_left(C v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <typename C> __device__ __forceinline__ C from_right(C v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// One row of the sweep.  A slot is reused every third row, so each field lives at most three rows.
+template <typename C>
+struct SwRow {
+    C pL, pa, pb, pR;              // phi: left neighbour of a, a, b, right neighbour of b
+    C mL, ma, mb, mR;              // mu, the same four columns
+    C dL, da, db, dR;              // D = div(phi u)
+    C y1, y2;                      // the Y velocity tables of the row
+    C u5a, u5b, u2a, u2b, u6a, u6b;         // g*_5, g*_2, g*_6 of the row: they stream to the row above
+    C Ra, Rb, Ca, Cb, La, Lb, v0a, v0b;     // partial sums of the populations arriving at the row
+    C e4a, e4b, e7a, e7b, e8a, e8b;         // at a top wall row: g_4, g_7, g_8 by bounce-back
+};
+
+// Writes phi(t+1) of domain node (x, y) into the ghost cells that stand for it (periodic images in x;
+// periodic or mirror images in y, three deep).
+template <typename P>
+__device__ __forceinline__ void store_images(P* phi_out, long long row0, int pitch, int nx, int ny, int walls, int x,
+                                             int y, P v)
+{
+    if (x >= 3 && x < nx - 3 && y >= 3 && y < ny - 3) return;
+    constexpr int NONE = -1000000;
+    const int xa = x < 3 ? x + nx : NONE, xb = x >= nx - 3 ? x - nx : NONE;
+    const int ya = y < 3 ? (walls ? -1 - y : y + ny) : NONE;
+    const int yb = y >= ny - 3 ? (walls ? 2 * ny - 1 - y : y - ny) : NONE;
+    for (int iy = 0; iy < 3; iy++) {
+        const int yy = iy == 0 ? y : (iy == 1 ? ya : yb);
+        if (yy == NONE) continue;
+        for (int ix = 0; ix < 3; ix++) {
+            const int xx = ix == 0 ? x : (ix == 1 ? xa : xb);
+            if (xx == NONE || (ix == 0 && iy == 0)) continue;
+            phi_out[(row0 + yy) * pitch + GC + xx] = v;
+        }
+    }
+}
+
+template <typename C, typename P, bool FF, int TY, int NW>
+__global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
+    ch_sweep_kernel(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lo,
+                    SweepArgs<C, P> a)
+{
+    static_assert(TY % 3 == 0, "the sweep advances three rows per unrolled step");
+    static_assert(TY + 6 <= 32, "the Y tables of a warp's rows are held one row per lane");
+    using L = SweepShape<P, FF, TY, NW>;
+    using P2 = typename Pair<P>::T;
+    constexpr int BW = L::BW, TH = L::TH;
+    constexpr bool kShift = sizeof(C) == 4;  // float arithmetic on g_0 - phi
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    auto stage = [&](int k) { return base + (size_t)k * L::STAGE; };
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 2 * L::STAGE);
+
+    __shared__ long long s_time;
+    __shared__ int s_tile_inst;
+    __shared__ C s_T;
+    __shared__ InstDev s_I;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int stride = gridDim.x;
+
+    // Where tile t lies, and this lane's velocity tables for it (constant data, so they are read before
+    // the waits): X by stored column (clamped: the clamped columns feed halo lanes only), Y by row of the
+    // instance's stored band, one row of the warp per lane.
+    int k_t = 0, x0 = 0, y0 = 0;
+    C X1m, X1a, X1b, X1p, X2m, X2a, X2b, X2p, ly1, ly2;
+    auto locate = [&](int t) {
+        k_t = find_inst(a.tile_begin, a.n_inst, t);
+        const InstDev* I = a.inst + k_t;
+        const int local = t - a.tile_begin[k_t];
+        const int tiles_x = (I->nx + L::W - 1) / L::W;
+        x0 = (local % tiles_x) * L::W;
+        y0 = (local / tiles_x) * TH;
+        const C* tX1 = a.tabs + I->tab;
+        const C* tX2 = tX1 + a.pitch;
+        const C* tY1 = tX2 + a.pitch;
+        const int sa = x0 + 2 * lane;
+        const int cm = max(sa - 1, 0), ca = min(sa, a.pitch - 1), cb = min(sa + 1, a.pitch - 1), cp = min(sa + 2, a.pitch - 1);
+        X1m = tX1[cm]; X1a = tX1[ca]; X1b = tX1[cb]; X1p = tX1[cp];
+        X2m = tX2[cm]; X2a = tX2[ca]; X2b = tX2[cb]; X2p = tX2[cp];
+        const int ylen = I->ylen;
+        const int yk = min(max(y0 + warp * TY - 3 + lane + GR, 0), ylen - 1);
+        ly1 = tY1[yk];
+        ly2 = tY1[ylen + yk];
+    };
+
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+        s_tile_inst = -1;
+        if ((int)blockIdx.x < a.total_tiles) {  // instance data are constant: read before the dependency wait
+            const int k = find_inst(a.tile_begin, a.n_inst, blockIdx.x);
+            s_I = a.inst[k];
+            s_tile_inst = k;
+        }
+    }
+    if ((int)blockIdx.x < a.total_tiles) locate(blockIdx.x);
+    // Launched as a programmatic dependent of the previous step: nothing that step writes (phi, the step
+    // counter) is read before this wait.
+    grid_dependency_wait();
+    grid_launch_dependents();
+    if (tid == 0) {
+        s_time = a.ctl->time;
+        if (s_tile_inst >= 0) s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time);
+    }
+    __syncthreads();
+    const long long n = s_time;
+
+    // producer: thread 0 issues the boxes of tile t into stage s
+    auto issue = [&](int t, int s) {
+        const int k = find_inst(a.tile_begin, a.n_inst, t);
+        const InstDev& I = a.inst[k];
+        const int local = t - a.tile_begin[k];
+        const int tiles_x = (I.nx + L::W - 1) / L::W;
+        const int bx = (local % tiles_x) * L::W, by = (local / tiles_x) * TH;
+        fence_proxy_async();
+        mbar_expect_tx(&mbar[s], L::PBOX_BYTES + L::LBOX_BYTES);
+        // box column origin: domain bx - 4 is stored column bx (a multiple of 4: 16-byte aligned)
+        tma_load_2d(stage(s), &tm_phi, bx, I.row0 + by - 3, &mbar[s]);
+        if (FF) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, bx, I.row0 + by, &mbar[s]);
+    };
+
+    if (tid == 0) {
+        for (int j = 0; j < 2; j++) {
+            const int t = blockIdx.x + j * stride;
+            if (t < a.total_tiles && !(a.debug_skip && blockIdx.x == 0 && j == 0)) issue(t, j);
+        }
+    }
+
+    // The sweep of one warp over its TY output rows of the tile in stage s.  WALLS: the instance has walls
+    // in y (bounce-back rows, mirror substitution) -- a separate body, so that periodic tiles carry none
+    // of that code.
+    auto sweep = [&](auto walls_t, int s) {
+        constexpr bool WALLS = decltype(walls_t)::value;
+        const InstDev& I = s_I;
+        const int nx = I.nx, ny = I.ny;
+        const int wy0 = y0 + warp * TY;  // the warp's first output row
+        if (wy0 >= ny) return;
+        const Consts<C>& K0 = consts<C>(I);
+        const C beta = K0.beta, kappa = K0.kappa, phiA = K0.phiA, phiB = K0.phiB;
+        const C ra = K0.a, rb = K0.b, K = K0.K;
+        const bool model2 = I.model == 2;
+        const C T = s_T;
+        const int pitch = a.pitch;
+        // this lane's column pair in the box, from the warp's first row (box row warp TY = domain wy0 - 3)
+        const P* box = reinterpret_cast<const P*>(stage(s)) + warp * TY * BW + 2 * lane;
+        const float* lbox = reinterpret_cast<const float*>(stage(s) + L::OFF_L) + warp * TY * BW + 2 * lane;
+        const int sa = x0 + 2 * lane;  // stored column of node a
+        const int xa = sa - GC, xb = xa + 1;
+        const bool va = lane >= 2 && lane < 30 && xa < nx, vb = lane >= 2 && lane < 30 && xb < nx;
+        const long long row0 = I.row0;
+        const C* tW = a.tabs + I.tab + 2 * pitch + 2 * I.ylen;  // Y1, Y2 at the walls y = -1/2, ny - 1/2
+
+        // One row: A is the slot of row yf (it held yf - 3), B of row yf - 1, Cs of row yf - 2.  MU: mu and D
+        // of row yf - 1; COL: collide row yf - 2; OUT: complete phi(t+1) of row yf - 3.  The three flags
+        // are false only while the pipeline fills.
+        auto row_step = [&](auto mu_t, auto col_t, auto out_t, const int j, SwRow<C>& A, SwRow<C>& B, SwRow<C>& Cs) {
+            constexpr bool MU = decltype(mu_t)::value, COL = decltype(col_t)::value, OUT = decltype(out_t)::value;
+            const int yf = wy0 - 3 + j;
+            {
+                const P2 v = *reinterpret_cast<const P2*>(box + j * BW);
+                A.pa = cvt<C>(v.x);
+                A.pb = cvt<C>(v.y);
+                A.pL = from_left(A.pb);
+                A.pR = from_right(A.pa);
+                A.y1 = __shfl_sync(0xffffffffu, ly1, j);
+                A.y2 = __shfl_sync(0xffffffffu, ly2, j);
+            }
+            if constexpr (MU) {
+                B.ma = node_mu(B.pa, B.pb, B.pL, A.pa, Cs.pa, A.pb, A.pL, Cs.pb, Cs.pL, beta, kappa, phiA, phiB);
+                B.mb = node_mu(B.pb, B.pR, B.pa, A.pb, Cs.pb, A.pR, A.pa, Cs.pR, Cs.pa, beta, kappa, phiA, phiB);
+                B.mL = from_left(B.mb);
+                B.mR = from_right(B.ma);
+                if (model2) {
+                    B.da = node_div(B.pb, B.pL, A.pa, Cs.pa, A.pb, A.pL, Cs.pb, Cs.pL, X1m, X1b, X2m, X2a, X2b,
+                                    Cs.y1, B.y1, A.y1, Cs.y2, A.y2, T);
+                    B.db = node_div(B.pR, B.pa, A.pb, Cs.pb, A.pR, A.pa, Cs.pR, Cs.pa, X1a, X1p, X2a, X2b, X2p,
+                                    Cs.y1, B.y1, A.y1, Cs.y2, A.y2, T);
+                    B.dL = from_left(B.db);
+                    B.dR = from_right(B.da);
+                }
+            }
+            const int yc = yf - 2;
+            C p8a = C(0), p8b = C(0), p7a = C(0), p7b = C(0), p4a = C(0), p4b = C(0);
+            if constexpr (COL) {
+                // at a wall, the ghost rows are not collided (nothing is pulled from them)
+                if (!WALLS || (yc >= 0 && yc < ny)) {
+                    if constexpr (WALLS) {
+                        // next to a wall, mu and D of the ghost row take the values of the mirror row (yc);
+                        // the ghost row's own values are used by no other node
+                        if (yc == 0) { A.mL = Cs.mL; A.ma = Cs.ma; A.mb = Cs.mb; A.mR = Cs.mR;
+                                       A.dL = Cs.dL; A.da = Cs.da; A.db = Cs.db; A.dR = Cs.dR; }
+                        if (yc == ny - 1) { B.mL = Cs.mL; B.ma = Cs.ma; B.mb = Cs.mb; B.mR = Cs.mR;
+                                            B.dL = Cs.dL; B.da = Cs.da; B.db = Cs.db; B.dR = Cs.dR; }
+                    }
+                    C gmxa, gmya, gmxb, gmyb, gDxa = C(0), gDya = C(0), gDxb = C(0), gDyb = C(0);
+                    grad9(Cs.mb, Cs.mL, B.ma, A.ma, B.mb, B.mL, A.mb, A.mL, gmxa, gmya);
+                    grad9(Cs.mR, Cs.ma, B.mb, A.mb, B.mR, B.ma, A.mR, A.ma, gmxb, gmyb);
+                    if (model2) {
+                        grad9(Cs.db, Cs.dL, B.da, A.da, B.db, B.dL, A.db, A.dL, gDxa, gDya);
+                        grad9(Cs.dR, Cs.da, B.db, A.db, B.dR, B.da, A.dR, A.da, gDxb, gDyb);
+                    }
+                    C Fxa, Fya, Fxb, Fyb;
+                    node_force(Cs.pa, gmxa, gmya, gDxa, gDya, model2, ra, rb, K, Fxa, Fya);
+                    node_force(Cs.pb, gmxb, gmyb, gDxb, gDyb, model2, ra, rb, K, Fxb, Fyb);
+                    C pa_[9], pb_[9];
+                    collide9<C, true, kShift>(Cs.pa, Cs.ma, Fxa, Fya, node_u(X1a, Cs.y1, T), node_u(X2a, Cs.y2, T), pa_,
+                                              K0, pa_);
+                    collide9<C, true, kShift>(Cs.pb, Cs.mb, Fxb, Fyb, node_u(X1b, Cs.y1, T), node_u(X2b, Cs.y2, T), pb_,
+                                              K0, pb_);
+                    Cs.u5a = pa_[5]; Cs.u5b = pb_[5];
+                    Cs.u2a = pa_[2]; Cs.u2b = pb_[2];
+                    Cs.u6a = pa_[6]; Cs.u6b = pb_[6];
+                    // (g_1 + g_5) and (g_3 + g_6) at their source nodes; g_2 from the row below
+                    Cs.Ra = pa_[1] + A.u5a; Cs.Rb = pb_[1] + A.u5b;
+                    Cs.La = pa_[3] + A.u6a; Cs.Lb = pb_[3] + A.u6b;
+                    Cs.Ca = A.u2a; Cs.Cb = A.u2b;
+                    Cs.v0a = pa_[0];
+                    Cs.v0b = pb_[0];
+                    if constexpr (WALLS) {
+                        if (yc == 0) {
+                            // bottom wall row: 2, 5, 6 would come from the ghost row; they bounce back at the
+                            // node, so the sums from the sides are formed here, at the destination
+                            const C uxa = node_u(X1a, tW[0], T), uya = node_u(X2a, tW[2], T);
+                            const C uxb = node_u(X1b, tW[0], T), uyb = node_u(X2b, tW[2], T);
+                            Cs.Ra = from_left(pb_[1]) + bounce<C, 5>(pa_[7], Cs.pa, uxa, uya);
+                            Cs.Rb = pa_[1] + bounce<C, 5>(pb_[7], Cs.pb, uxb, uyb);
+                            Cs.La = pb_[3] + bounce<C, 6>(pa_[8], Cs.pa, uxa, uya);
+                            Cs.Lb = from_right(pa_[3]) + bounce<C, 6>(pb_[8], Cs.pb, uxb, uyb);
+                            Cs.Ca = bounce<C, 2>(pa_[4], Cs.pa, uxa, uya);
+                            Cs.Cb = bounce<C, 2>(pb_[4], Cs.pb, uxb, uyb);
+                        }
+                        if (yc == ny - 1) {
+                            // top wall row: 4, 7, 8 would come from the ghost row above
+                            const C uxa = node_u(X1a, tW[1], T), uya = node_u(X2a, tW[3], T);
+                            const C uxb = node_u(X1b, tW[1], T), uyb = node_u(X2b, tW[3], T);
+                            Cs.e4a = bounce<C, 4>(pa_[2], Cs.pa, uxa, uya); Cs.e4b = bounce<C, 4>(pb_[2], Cs.pb, uxb, uyb);
+                            Cs.e7a = bounce<C, 7>(pa_[5], Cs.pa, uxa, uya); Cs.e7b = bounce<C, 7>(pb_[5], Cs.pb, uxb, uyb);
+                            Cs.e8a = bounce<C, 8>(pa_[6], Cs.pa, uxa, uya); Cs.e8b = bounce<C, 8>(pb_[6], Cs.pb, uxb, uyb);
+                        }
+                    }
+                    p8a = pa_[8]; p8b = pb_[8];
+                    p7a = pa_[7]; p7b = pb_[7];
+                    p4a = pa_[4]; p4b = pb_[4];
+                }
+            }
+            if constexpr (OUT) {
+                // phi(t+1) of row yo = yf - 3 (slot A), with g*_4, g*_7, g*_8 of row yo + 1 just computed
+                const int yo = yf - 3;
+                C Ra, Rb, Ca, Cb, La, Lb;
+                if (WALLS && yo == ny - 1) {
+                    // top wall row (no collision above): the sums (g_1 + g_5), (g_3 + g_6) cross to their
+                    // destinations, where the bounced-back 8, 7 and 4 complete them
+                    Ra = from_left(A.Rb) + A.e8a; Rb = A.Ra + A.e8b;
+                    La = A.Lb + A.e7a; Lb = from_right(A.La) + A.e7b;
+                    Ca = A.Ca + A.e4a; Cb = A.Cb + A.e4b;
+                } else if (WALLS && yo == 0) {
+                    // bottom wall row: the sums are already at the destinations
+                    Ra = A.Ra + from_left(p8b); Rb = A.Rb + p8a;
+                    La = A.La + p7b; Lb = A.Lb + from_right(p7a);
+                    Ca = A.Ca + p4a; Cb = A.Cb + p4b;
+                } else {
+                    const C Rsa = A.Ra + p8a, Rsb = A.Rb + p8b, Lsa = A.La + p7a, Lsb = A.Lb + p7b;
+                    Ra = from_left(Rsb); Rb = Rsa;
+                    La = Lsb; Lb = from_right(Lsa);
+                    Ca = A.Ca + p4a; Cb = A.Cb + p4b;
+                }
+                const C suma = (Ra + Ca) + La, sumb = (Rb + Cb) + Lb;  // the grouping of stream_sum
+                P hia, hib;
+                float loa = 0.0f, lob = 0.0f;
+                if constexpr (FF) {
+                    // phi(t+1) = phi(t) + (g*_0 - phi(t)) + sum_{q>0}; hi + lo absorbs it exactly (TwoSum)
+                    const P2 hv = *reinterpret_cast<const P2*>(box + (j - 3) * BW);
+                    const float2 lv = *reinterpret_cast<const float2*>(lbox + (j - 6) * BW);
+                    {
+                        const float h = (float)hv.x, tt = lv.x + (float)(A.v0a + suma);
+                        const float sm = h + tt, bb = sm - h;
+                        loa = (h - (sm - bb)) + (tt - bb);
+                        hia = (P)sm;
+                    }
+                    {
+                        const float h = (float)hv.y, tt = lv.y + (float)(A.v0b + sumb);
+                        const float sm = h + tt, bb = sm - h;
+                        lob = (h - (sm - bb)) + (tt - bb);
+                        hib = (P)sm;
+                    }
+                } else if constexpr (kShift) {
+                    const P2 hv = *reinterpret_cast<const P2*>(box + (j - 3) * BW);
+                    hia = (P)((float)hv.x + (float)(A.v0a + suma));
+                    hib = (P)((float)hv.y + (float)(A.v0b + sumb));
+                } else {
+                    hia = (P)(A.v0a + suma);
+                    hib = (P)(A.v0b + sumb);
+                }
+                if (yo < ny) {
+                    const long long node = (row0 + yo) * pitch + sa;
+                    if (va && vb) {
+                        P2 o;
+                        o.x = hia;
+                        o.y = hib;
+                        *reinterpret_cast<P2*>(a.phi_out + node) = o;
+                        if (FF) *reinterpret_cast<float2*>(a.lo_out + node) = make_float2(loa, lob);
+                    } else if (va) {
+                        a.phi_out[node] = hia;
+                        if (FF) a.lo_out[node] = loa;
+                    }
+                    if (va) store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xa, yo, hia);
+                    if (vb) store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xb, yo, hib);
+                }
+            }
+        };
+
+        using F = std::false_type;
+        using Tr = std::true_type;
+        SwRow<C> r0 = {}, r1 = {}, r2 = {};
+        // the pipeline fills: rows wy0 - 3 .. wy0 + 2 enter; mu from the third, collisions from the fifth
+        row_step(F(), F(), F(), 0, r0, r1, r2);
+        row_step(F(), F(), F(), 1, r2, r0, r1);
+        row_step(Tr(), F(), F(), 2, r1, r2, r0);
+        row_step(Tr(), F(), F(), 3, r0, r1, r2);
+        row_step(Tr(), Tr(), F(), 4, r2, r0, r1);
+        row_step(Tr(), Tr(), F(), 5, r1, r2, r0);
+        // steady state: one output row per row entering
+#pragma unroll 1
+        for (int j = 6; j < TY + 6; j += 3) {
+            row_step(Tr(), Tr(), Tr(), j, r0, r1, r2);
+            row_step(Tr(), Tr(), Tr(), j + 1, r2, r0, r1);
+            row_step(Tr(), Tr(), Tr(), j + 2, r1, r2, r0);
+        }
+    };
+
+    for (int it = 0;; it++) {
+        const int t = blockIdx.x + it * stride;
+        if (t >= a.total_tiles) break;
+        const int s = it & 1;
+        if (it > 0) locate(t);  // the table loads are in flight during the wait
+        const bool ok = mbar_wait_bounded(&mbar[s], (unsigned)((it >> 1) & 1), 1u << 22);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(&a.ctl->err, 1u);
+                // let a copy already issued into the other stage land before the CTA exits (bounded)
+                if (t + stride < a.total_tiles)
+                    mbar_wait_bounded(&mbar[s ^ 1], (unsigned)(((it + 1) >> 1) & 1), 1u << 22);
+            }
+            break;
+        }
+        if (tid == 0 && k_t != s_tile_inst) {
+            s_I = a.inst[k_t];
+            s_tile_inst = k_t;
+            s_T = (C)vel_t(s_I.vel, s_I.Tper, n);
+        }
+        __syncthreads();
+        if (s_I.walls) sweep(std::true_type(), s);
+        else sweep(std::false_type(), s);
+        __syncthreads();  // the stage is free again
+
+        if (tid == 0) {
+            const int t2 = t + 2 * stride;
+            if (t2 < a.total_tiles) issue(t2, s);
+        }
+    }
+
+    // the last CTA of the launch advances the step counter read by the next launch (no fence: the
+    // counter orders no other data, and the next launch reads it only after this grid has completed)
+    if (tid == 0) {
+        const unsigned int prev = atomicAdd(&a.ctl->done, 1u);
+        if (prev == gridDim.x - 1) {
+            a.ctl->done = 0u;
+            a.ctl->time = n + 1;
+        }
+    }
+}
+
+}  // namespace lbch

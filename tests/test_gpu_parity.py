@@ -176,19 +176,22 @@ def test_nonfinite_is_reported():
         assert ei.value.status == abi.LBCH_ENONFINITE
 
 
-@pytest.mark.parametrize("prec,nshapes", [("f64", 2), ("f32", 3), ("f16s", 3)])
-def test_every_tile_shape_gives_the_same_bits(prec, nshapes):
+@pytest.mark.parametrize("prec,nshapes,general", [("f64", 2, 1), ("f32", 3, 1), ("f16s", 3, 1),
+                                                 ("f64", 4, 0), ("f32", 4, 0), ("f16s", 4, 0)])
+def test_every_tile_shape_gives_the_same_bits(prec, nshapes, general):
     """The result does not depend on the tile shape (each node's arithmetic is the same; only the halo
     overlap between tiles changes), so every shape must reproduce the same bits; the autotuner then
-    only picks among equivalent kernels."""
+    only picks among equivalent kernels.  Both kernel forms: the tile kernel (general path) and the
+    row-sweep kernel that steps tau_g = 1 handles."""
     ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=9)
     params, fields = zip(*ens)
     p, phi0, _ = wl.single_vortex(n=96, T=50)
     outs = []
     for k in range(nshapes):
         with abi.Simulation(p, phi0, prec=prec) as sim, abi.Simulation(list(params), list(fields), prec=prec) as ens_sim:
-            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, k)
-            abi.lb_ch_test_hook(ens_sim.h, abi.LBCH_HOOK_TILE_SHAPE, k)
+            for h in (sim.h, ens_sim.h):
+                abi.lb_ch_test_hook(h, abi.LBCH_HOOK_GENERAL_PATH, general)
+                abi.lb_ch_test_hook(h, abi.LBCH_HOOK_TILE_SHAPE, k)
             sim.step(70)
             ens_sim.step(70)
             outs.append([sim.phi()] + [ens_sim.phi(i) for i in range(3)])
@@ -200,7 +203,7 @@ def test_every_tile_shape_gives_the_same_bits(prec, nshapes):
 def test_tune_keeps_the_state():
     p, phi0, _ = wl.zalesak(n=128)
     with abi.Simulation(p, phi0, prec="f32") as a, abi.Simulation(p, phi0, prec="f32", tune=True) as b:
-        assert b.tile in ((32, 16), (32, 8), (16, 8))
+        assert b.tile in ((56, 48), (56, 24), (56, 12))  # the row-sweep configurations (tau_g = 1)
         assert b.observe(abi.LBCH_OBS_STEP) == 0
         a.step(100)
         b.step(100)
@@ -209,9 +212,11 @@ def test_tune_keeps_the_state():
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16s"])
 def test_tau1_kernel_equals_general_kernel_bitwise(prec):
-    """At tau_g = 1 the populations drop out of Eq. LB (g* = g_eq + S/2).  The kernel that reads and writes
-    phi only must give the same bits as the general kernel, which multiplies the populations by zero --
-    for a periodic flow and for a ragged ensemble with moving walls."""
+    """At tau_g = 1 the populations drop out of Eq. LB (g* = g_eq + S/2).  The row-sweep kernel, which reads
+    and writes phi only, must give the same bits as the tile kernel on the general path, which multiplies
+    the populations by zero -- for a periodic flow and for a ragged ensemble with moving walls.  On the
+    half-storage path the general kernel rounds the streamed populations to half; the sweep keeps them in
+    float, so there the two agree to the half rounding only (and the sweep is the closer to the oracle)."""
     p, phi0, _ = wl.single_vortex(n=96, T=60)
     ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=4)
     ens = [(dict(q, shear=q["shear"] * 30.0, Ustar=q["Ustar"] * 30.0), f) for q, f in ens]
@@ -227,8 +232,14 @@ def test_tau1_kernel_equals_general_kernel_bitwise(prec):
             bytes_lu = a.info()["bytes_per_lu"]
             assert bytes_lu == ({"f64": 160.0, "f32": 88.0, "f16s": 40.0}[prec] if general else
                                 {"f64": 16.0, "f32": 16.0, "f16s": 8.0}[prec])
-    for x, y in zip(res[0], res[1]):
-        assert np.array_equal(x, y)
+    if prec != "f16s":
+        for x, y in zip(res[0], res[1]):
+            assert np.array_equal(x, y)
+    else:
+        ref, _ = oracle.simulate(p, phi0, 90)
+        assert _maxdiff(res[0][0], ref) <= _maxdiff(res[1][0], ref) + 1e-6
+        for x, y in zip(res[0], res[1]):
+            assert _maxdiff(x, y) <= 2e-3
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
