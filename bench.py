@@ -141,10 +141,10 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def sweep_params(n):
+def sweep_params(n, tau=1.0):
     """A square rotation workload of side n (the Zalesak flow and parameters scaled to n)."""
     pp = wl.make_params(nx=n, ny=n, vel=wl.VEL_ROTATION, U0=0.02, xc=n / 2, yc=n / 2, half=n / 2,
-                        W=4.0, M=0.005, tau=1.0)
+                        W=4.0, M=0.005, tau=tau)
     return pp, wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
 
 
@@ -152,8 +152,10 @@ def run_case(case, nsteps, tile=0):
     """One grid, no timing: the command ncu profiles."""
     import torch
     from paper_1805_00007_gb300 import abi
-    prec, n = case.split("_")
-    pp, f0 = sweep_params(int(n))
+    parts = case.split("_")
+    prec, n = parts[0], int(parts[1])
+    tau = float(parts[2]) if len(parts) > 2 else 1.0
+    pp, f0 = sweep_params(n, tau)
     with abi.Simulation(pp, f0, prec=prec) as sim:
         abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, tile)
         sim.step(nsteps)
@@ -195,7 +197,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default=None,
-                    help="profiling case PREC_N (e.g. f32_4096): init and --case-steps steps of that grid only")
+                    help="profiling case PREC_N[_TAU] (e.g. f32_4096, f32_4096_0.8): init and --case-steps steps "
+                         "of that grid only")
     ap.add_argument("--case-steps", type=int, default=8)
     ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case")
     args = ap.parse_args()
@@ -290,8 +293,9 @@ def main():
     # --- large-grid sweep: the same kernel with inputs far larger than L2 (HBM-bound regime)
     sweep = {}
     if not args.no_sweep:
-        for prec, n in (("f32", 4096), ("f64", 4096), ("f16s", 4096)):
-            pp, f0 = sweep_params(n)
+        for prec, n, tau in (("f32", 4096, 1.0), ("f64", 4096, 1.0), ("f16s", 4096, 1.0),
+                             ("f32", 4096, 0.8), ("f64", 4096, 0.8), ("f16s", 4096, 0.8)):
+            pp, f0 = sweep_params(n, tau)
             sim = abi.Simulation(pp, f0, prec=prec, stream=stream.cuda_stream, tune=True)
             sim.step(64)
             torch.cuda.synchronize()
@@ -304,7 +308,7 @@ def main():
             dt = e0.elapsed_time(e1) / 1e3 / nst
             inf = sim.info()
             gbs = inf["bytes_per_lu"] * n * n / dt / 1e9
-            sweep[f"{prec}_{n}"] = {"MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6, "tile": sim.tile,
+            sweep[f"{prec}_{n}" + ("" if tau == 1.0 else f"_tau{tau}")] = {"MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6, "tile": sim.tile,
                                    "bytes_per_lu": inf["bytes_per_lu"], "achieved_gbs": gbs,
                                    "frac": gbs / hbm_peak}
             sim.close()

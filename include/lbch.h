@@ -197,12 +197,21 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
  * handle's state is not advanced correctly afterwards and should be freed.  With hook
  * LBCH_HOOK_TILE_SHAPE, value selects the tile shape by its index in the list lb_ch_tune describes
  * (for tests that compare shapes).  With hook LBCH_HOOK_GENERAL_PATH and value != 0, handles whose
- * instances all have tau_g = 1 run the general step kernel instead of the one that drops the
- * populations (see lb_ch_step); the two give the same bits.  With hook LBCH_HOOK_NO_PDL and value != 0,
+ * instances all have tau_g = 1 keep and stream the populations instead of dropping them (see
+ * lb_ch_step); the two give the same bits.  With hook LBCH_HOOK_TILE_KERNEL and value != 0, the steps
+ * run the tile kernel (each tile's stencil fields staged in shared memory) instead of the row sweep, with
+ * the populations; the tile shape hook then indexes its own list of shapes, and the results are the same
+ * bits again.  With hook LBCH_HOOK_NO_PDL and value != 0,
  * step launches are ordinary stream-ordered launches instead of programmatic dependents of the previous
  * step (whose launch and prologue overlap that step's tail); the results are the same bits.  Not for
  * production use. */
-enum { LBCH_HOOK_SKIP_FIRST_LOAD = 1, LBCH_HOOK_TILE_SHAPE = 2, LBCH_HOOK_GENERAL_PATH = 3, LBCH_HOOK_NO_PDL = 4 };
+enum {
+    LBCH_HOOK_SKIP_FIRST_LOAD = 1,
+    LBCH_HOOK_TILE_SHAPE = 2,
+    LBCH_HOOK_GENERAL_PATH = 3,
+    LBCH_HOOK_NO_PDL = 4,
+    LBCH_HOOK_TILE_KERNEL = 5
+};
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
 
 /* Statistics of a caller-owned field without allocating anything (the paper has no counterpart; this

@@ -22,7 +22,7 @@ SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb
            "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream", "lb_ch_test_hook",
            "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
            "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune")
-LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL = 1, 2, 3, 4
+LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL = 1, 2, 3, 4, 5
 
 
 class lbch_params(ctypes.Structure):

@@ -113,11 +113,13 @@ struct lbch_handle {
     long long nodes = 0;        // lattice nodes (all instances)
     int shape = 0;              // tile shape in use (index into the precision's shape list)
     bool tau1 = false;          // every instance has tau_g = 1: the populations drop out of the step
-    bool force_general = false; // test hook: use the general kernel even when tau1 holds
+    bool force_general = false; // test hook: keep the populations even when tau1 holds
+    bool force_tile = false;    // test hook: step with the tile kernel instead of the row sweep
     bool no_pdl = false;        // test hook: plain stream-ordered step launches
     struct PerShape {           // what depends on the tile shape
         int total_tiles = 0;
         int grid = 0;           // persistent CTAs per step launch
+        int grid_gen = 0;       // row sweep with the populations (the tile kernel uses grid)
         int* d_tile_begin = nullptr;
         CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
     } ps[kMaxShapes], sw[kSweepShapes];  // tile kernel shapes; row-sweep configurations (tm_g unused)
@@ -191,22 +193,27 @@ cudaError_t launch_step_t(lbch_handle* h, int parity)
     return launch_step_v<C, S, P, TX, TY, false>(h, parity);
 }
 
-// tau_g = 1 everywhere: the row-sweep kernel steps the handle (its shape index then names a sweep
-// configuration); otherwise the tile kernel does.
-inline bool use_sweep(const lbch_handle* h) { return h->tau1 && !h->force_general && !h->coupled; }
+// The row-sweep kernel steps the handle (its shape index then names a sweep configuration), without the
+// populations when every instance has tau_g = 1; the tile kernel only when a test asks for it.
+inline bool use_sweep(const lbch_handle* h) { return !h->force_tile && !h->coupled; }
+inline bool sweep_gen(const lbch_handle* h) { return !h->tau1 || h->force_general; }
 inline int n_active(const lbch_handle* h) { return h->coupled ? 1 : (use_sweep(h) ? kSweepShapes : n_shapes(h->prec)); }
 inline const lbch_handle::PerShape& active_ps(const lbch_handle* h) { return use_sweep(h) ? h->sw[h->shape] : h->ps[h->shape]; }
+inline int active_grid(const lbch_handle* h)
+{
+    return use_sweep(h) && sweep_gen(h) ? h->sw[h->shape].grid_gen : active_ps(h).grid;
+}
 inline Shape active_tile(const lbch_handle* h)
 {
     return h->coupled ? Shape{0, 0} : (use_sweep(h) ? sweep_tile(h->shape) : shape_of(h->prec, h->shape));
 }
 
-template <typename C, typename P, bool FF, int TY, int NW>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
 cudaError_t launch_sweep_v(lbch_handle* h, int parity)
 {
-    using L = SweepShape<P, FF, TY, NW>;
+    using L = SweepShape<P, S, FF, TY, NW, GEN>;
     const lbch_handle::PerShape& ps = h->sw[h->shape];
-    SweepArgs<C, P> a;
+    SweepArgs<C, S, P> a;
     a.inst = h->d_inst;
     a.tile_begin = ps.d_tile_begin;
     a.tabs = tables<C>(h);
@@ -217,8 +224,11 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
     a.lo_out = h->lo[parity ^ 1];
     a.ctl = h->ctl;
+    a.g_in = static_cast<const S*>(h->g[parity]);
+    a.g_out = static_cast<S*>(h->g[parity ^ 1]);
+    a.rows = h->rows;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ps.grid);
+    cfg.gridDim = dim3(GEN ? ps.grid_gen : ps.grid);
     cfg.blockDim = dim3(NW * 32);
     cfg.dynamicSmemBytes = L::BYTES;
     cfg.stream = h->stream;
@@ -227,34 +237,42 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, P, FF, TY, NW>, ps.tm_phi[parity], ps.tm_lo[parity], a);
+    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>, ps.tm_phi[parity], ps.tm_lo[parity], a);
 }
 
-template <typename C, typename P, bool FF>
+template <typename C, typename S, typename P, bool FF, int TY, int NW>
+cudaError_t launch_sweep_g(lbch_handle* h, int parity)
+{
+    return sweep_gen(h) ? launch_sweep_v<C, S, P, FF, TY, NW, true>(h, parity)
+                        : launch_sweep_v<C, S, P, FF, TY, NW, false>(h, parity);
+}
+
+template <typename C, typename S, typename P, bool FF>
 cudaError_t launch_sweep_t(lbch_handle* h, int parity)
 {
     switch (h->shape) {
-    case 0: return launch_sweep_v<C, P, FF, 12, 4>(h, parity);
-    case 1: return launch_sweep_v<C, P, FF, 6, 4>(h, parity);
-    case 2: return launch_sweep_v<C, P, FF, 6, 2>(h, parity);
-    default: return launch_sweep_v<C, P, FF, 3, 4>(h, parity);
+    case 0: return launch_sweep_g<C, S, P, FF, 12, 4>(h, parity);
+    case 1: return launch_sweep_g<C, S, P, FF, 6, 4>(h, parity);
+    case 2: return launch_sweep_g<C, S, P, FF, 6, 2>(h, parity);
+    default: return launch_sweep_g<C, S, P, FF, 3, 4>(h, parity);
     }
 }
 
 cudaError_t launch_sweep(lbch_handle* h, int parity)
 {
     switch (h->prec) {
-    case LBCH_F64: return launch_sweep_t<double, double, false>(h, parity);
-    case LBCH_F32: return launch_sweep_t<float, float, true>(h, parity);
-    default: return launch_sweep_t<float, float, false>(h, parity);
+    case LBCH_F64: return launch_sweep_t<double, double, double, false>(h, parity);
+    case LBCH_F32: return launch_sweep_t<float, float, float, true>(h, parity);
+    default: return launch_sweep_t<float, __half, float, false>(h, parity);
     }
 }
 
-template <typename C, typename P, bool FF, int TY, int NW>
+// Dynamic shared memory of one sweep kernel and the persistent grid that fits the device.
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
 cudaError_t prepare_sweep_v(lbch_handle* h, int k)
 {
-    using L = SweepShape<P, FF, TY, NW>;
-    auto kern = ch_sweep_kernel<C, P, FF, TY, NW>;
+    using L = SweepShape<P, S, FF, TY, NW, GEN>;
+    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -263,24 +281,32 @@ cudaError_t prepare_sweep_v(lbch_handle* h, int k)
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    h->sw[k].grid = std::max(1, std::min(h->sw[k].total_tiles, per_sm * sms));
+    (GEN ? h->sw[k].grid_gen : h->sw[k].grid) = std::max(1, std::min(h->sw[k].total_tiles, per_sm * sms));
     return cudaSuccess;
 }
 
-template <typename C, typename P, bool FF>
+template <typename C, typename S, typename P, bool FF, int TY, int NW>
+cudaError_t prepare_sweep_g(lbch_handle* h, int k)
+{
+    cudaError_t e = prepare_sweep_v<C, S, P, FF, TY, NW, true>(h, k);
+    if (e == cudaSuccess && h->tau1) e = prepare_sweep_v<C, S, P, FF, TY, NW, false>(h, k);
+    return e;
+}
+
+template <typename C, typename S, typename P, bool FF>
 cudaError_t prepare_sweep_t(lbch_handle* h, int k)
 {
-    return k == 0 ? prepare_sweep_v<C, P, FF, 12, 4>(h, k)
-         : k == 1 ? prepare_sweep_v<C, P, FF, 6, 4>(h, k)
-         : k == 2 ? prepare_sweep_v<C, P, FF, 6, 2>(h, k) : prepare_sweep_v<C, P, FF, 3, 4>(h, k);
+    return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4>(h, k)
+         : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4>(h, k)
+         : k == 2 ? prepare_sweep_g<C, S, P, FF, 6, 2>(h, k) : prepare_sweep_g<C, S, P, FF, 3, 4>(h, k);
 }
 
 cudaError_t prepare_sweep(lbch_handle* h, int k)
 {
     switch (h->prec) {
-    case LBCH_F64: return prepare_sweep_t<double, double, false>(h, k);
-    case LBCH_F32: return prepare_sweep_t<float, float, true>(h, k);
-    default: return prepare_sweep_t<float, float, false>(h, k);
+    case LBCH_F64: return prepare_sweep_t<double, double, double, false>(h, k);
+    case LBCH_F32: return prepare_sweep_t<float, float, float, true>(h, k);
+    default: return prepare_sweep_t<float, __half, float, false>(h, k);
     }
 }
 
@@ -805,7 +831,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         CKI(cudaMalloc(&h->ps[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
         CKI(cudaMemcpy(h->ps[sk].d_tile_begin, tile_begin[sk].data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice));
     }
-    if (h->tau1) {
+    if (!coupled) {
         for (int sk = 0; sk < kSweepShapes; sk++) {
             CKI(prepare_sweep(h, sk));
             CKI(cudaMalloc(&h->sw[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
@@ -841,7 +867,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     CKI(cudaMalloc(&h->result, sizeof(double) * RED_NV * (size_t)n_inst));
     lbch_status st = LBCH_OK;
     for (int sk = 0; sk < n_shapes(prec) && st == LBCH_OK; sk++) st = encode_maps(h, sk);
-    for (int sk = 0; h->tau1 && sk < kSweepShapes && st == LBCH_OK; sk++) st = encode_sweep_maps(h, sk);
+    for (int sk = 0; !coupled && sk < kSweepShapes && st == LBCH_OK; sk++) st = encode_sweep_maps(h, sk);
     if (st != LBCH_OK) return bail(st);
 
     // the initial field in the padded layout, ghost frame included, through pinned staging
@@ -1076,7 +1102,7 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     }
     out[0] = (double)h->nodes;
     out[1] = bytes;
-    out[2] = (double)active_ps(h).grid;
+    out[2] = (double)active_grid(h);
     out[3] = (double)h->n;
     return LBCH_OK;
 }
@@ -1247,8 +1273,15 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
         return LBCH_OK;
     }
+    if (hook == LBCH_HOOK_TILE_KERNEL) {
+        if (h->coupled) return fail(LBCH_EINVAL, "the coupled flow has no tile kernel");
+        if (h->force_tile != (value != 0)) h->shape = 0;  // the shape index names the other kernel's list
+        h->force_tile = value != 0;
+        for (int k = 0; k < 2; k++)
+            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        return LBCH_OK;
+    }
     if (hook == LBCH_HOOK_GENERAL_PATH) {
-        if (h->force_general != (value != 0)) h->shape = 0;  // the shape index names the other kernel's list
         h->force_general = value != 0;
         for (int k = 0; k < 2; k++)
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }

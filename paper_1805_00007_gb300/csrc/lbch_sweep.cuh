@@ -21,6 +21,12 @@
 // two-stage TMA pipeline, as the tile kernel does.  The velocity tables of the warp's columns are read
 // once per tile into registers; the Y tables of its rows arrive one row per lane and are broadcast by
 // shuffles.
+//
+// GEN (any tau_g): the populations are read and written as well.  Each lane copies its own columns of
+// the population planes of the rows it will collide into a three-row ring in shared memory, two rows
+// ahead (cp.async, one group per row); after the collision the nine g* of a node reach their
+// destinations individually -- 1, 5, 8 from the lane to the left, 3, 6, 7 from the right, 2 and 4 from
+// the rows below and above -- and g(t+1) is stored plane by plane.
 #pragma once
 #include <type_traits>
 
@@ -28,7 +34,7 @@
 
 namespace lbch {
 
-template <typename C, typename P>
+template <typename C, typename S, typename P>
 struct SweepArgs {
     const InstDev* inst;
     const int* tile_begin;  // first tile of each instance (n_inst + 1 entries)
@@ -40,9 +46,12 @@ struct SweepArgs {
     P* phi_out;
     float* lo_out;          // low part of phi on the float-float path
     Ctl* ctl;
+    const S* g_in;          // populations (GEN): g[(row * nq + plane) * pitch + column]
+    S* g_out;
+    int rows;               // stored rows of the population arrays
 };
 
-template <typename P, bool FF, int TY, int NW>
+template <typename P, typename S, bool FF, int TY, int NW, bool GEN>
 struct SweepShape {
     static constexpr int W = 56;                 // output columns of a tile
     static constexpr int BW = 64;                // box columns: x0 - 4 .. x0 + 59, two per lane
@@ -53,12 +62,47 @@ struct SweepShape {
     __host__ __device__ static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t OFF_L = a128(PBOX_BYTES);
     static constexpr size_t STAGE = OFF_L + a128(LBOX_BYTES);
-    static constexpr size_t BYTES = 2 * STAGE + 128 + 128;  // mbarriers, alignment slack
+    static constexpr int NQ = sizeof(S) == 2 ? 8 : 9;  // stored population planes
+    static constexpr int RING = 3;                      // population rows in flight per warp
+    static constexpr size_t RING_BYTES = GEN ? (size_t)RING * NQ * BW * sizeof(S) : 0;  // per warp
+    static constexpr size_t OFF_RING = 2 * STAGE;
+    static constexpr size_t OFF_MBAR = OFF_RING + NW * RING_BYTES;
+    static constexpr size_t BYTES = OFF_MBAR + 128 + 128;  // mbarriers, alignment slack
 };
 
 template <typename P> struct Pair;
 template <> struct Pair<float> { using T = float2; };
 template <> struct Pair<double> { using T = double2; };
+template <> struct Pair<__half> { using T = __half2; };
+
+template <typename C, typename S2> __device__ __forceinline__ void unpair(S2 v, C& x, C& y) { x = cvt<C>(v.x); y = cvt<C>(v.y); }
+template <typename C> __device__ __forceinline__ void unpair(__half2 v, C& x, C& y)
+{
+    x = (C)__low2float(v);
+    y = (C)__high2float(v);
+}
+template <typename S, typename C> __device__ __forceinline__ typename Pair<S>::T mkpair(C x, C y)
+{
+    typename Pair<S>::T v;
+    v.x = (S)x;
+    v.y = (S)y;
+    return v;
+}
+template <> __device__ __forceinline__ __half2 mkpair<__half, float>(float x, float y) { return __floats2half2_rn(x, y); }
+
+// Per-thread asynchronous copy of one column pair of a population row into shared memory; with
+// src_bytes = 0 nothing is read and the destination is zero-filled.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_pair(void* dst, const void* src, unsigned src_bytes)
+{
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES), "r"(src_bytes)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <typename C> __device__ __forceinline__ C from_left(C v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 template <typename C> __device__ __forceinline__ C from_right(C v) { return __shfl_down_sync(0xffffffffu, v, 1); }
@@ -73,6 +117,7 @@ struct SwRow {
     C u5a, u5b, u2a, u2b, u6a, u6b;         // g*_5, g*_2, g*_6 of the row: they stream to the row above
     C Ra, Rb, Ca, Cb, La, Lb, v0a, v0b;     // partial sums of the populations arriving at the row
     C e4a, e4b, e7a, e7b, e8a, e8b;         // at a top wall row: g_4, g_7, g_8 by bounce-back
+    C n0a, n0b, n1a, n1b, n2a, n2b, n3a, n3b, n4a, n4b, n5a, n5b, n6a, n6b, n7a, n7b, n8a, n8b;  // GEN: g(t+1) of the row
 };
 
 // Writes phi(t+1) of domain node (x, y) into the ghost cells that stand for it (periodic images in x;
@@ -97,22 +142,49 @@ __device__ __forceinline__ void store_images(P* phi_out, long long row0, int pit
     }
 }
 
-template <typename C, typename P, bool FF, int TY, int NW>
+// Writes g(t+1) of domain node (x, y) into the ghost cells that stand for it, one deep: periodic images
+// in x, and in y unless the instance has walls there.
+template <typename S, typename C, int QOFF, bool WALLS>
+__device__ __forceinline__ void store_g_images(S* g_out, long long row0, int pitch, int nx, int ny, int x, int y,
+                                               const C* v)
+{
+    constexpr int NONE = -1000000;
+    const int gxa = x == 0 ? nx : (x == nx - 1 ? -1 : NONE);
+    const int gya = WALLS ? NONE : (y == 0 ? ny : (y == ny - 1 ? -1 : NONE));
+    if (gxa == NONE && gya == NONE) return;
+    constexpr int NQ = 9 - QOFF;
+    for (int iy = 0; iy < 2; iy++) {
+        const int yy = iy == 0 ? y : gya;
+        if (yy == NONE) continue;
+        for (int ix = 0; ix < 2; ix++) {
+            const int xx = ix == 0 ? x : gxa;
+            if (xx == NONE || (ix == 0 && iy == 0)) continue;
+            S* o = g_out + ((row0 + yy) * NQ) * pitch + GC + xx;
+#pragma unroll
+            for (int q = QOFF; q < 9; q++) o[(long long)(q - QOFF) * pitch] = to_s<S>(v[q]);
+        }
+    }
+}
+
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
 __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     ch_sweep_kernel(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lo,
-                    SweepArgs<C, P> a)
+                    SweepArgs<C, S, P> a)
 {
     static_assert(TY % 3 == 0, "the sweep advances three rows per unrolled step");
     static_assert(TY + 6 <= 32, "the Y tables of a warp's rows are held one row per lane");
-    using L = SweepShape<P, FF, TY, NW>;
+    using L = SweepShape<P, S, FF, TY, NW, GEN>;
     using P2 = typename Pair<P>::T;
-    constexpr int BW = L::BW, TH = L::TH;
-    constexpr bool kShift = sizeof(C) == 4;  // float arithmetic on g_0 - phi
+    using S2 = typename Pair<S>::T;
+    constexpr int BW = L::BW, TH = L::TH, NQ = L::NQ, RING = L::RING;
+    constexpr bool kShift = sizeof(C) == 4;     // float arithmetic on g_0 - phi
+    constexpr bool kHalf = sizeof(S) == 2;      // half storage: g_0 not stored (implied by phi)
+    constexpr int QOFF = kHalf ? 1 : 0;         // stored plane of population q is q - QOFF
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     auto stage = [&](int k) { return base + (size_t)k * L::STAGE; };
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 2 * L::STAGE);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + L::OFF_MBAR);
 
     __shared__ long long s_time;
     __shared__ int s_tile_inst;
@@ -214,6 +286,28 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         const bool va = lane >= 2 && lane < 30 && xa < nx, vb = lane >= 2 && lane < 30 && xb < nx;
         const long long row0 = I.row0;
         const C* tW = a.tabs + I.tab + 2 * pitch + 2 * I.ylen;  // Y1, Y2 at the walls y = -1/2, ny - 1/2
+        // GEN: this warp's ring of population rows ([slot][plane][64 columns]); collision row k of the
+        // warp is domain row wy0 - 1 + k and lives in slot k % RING
+        [[maybe_unused]] S* ring = reinterpret_cast<S*>(base + L::OFF_RING + warp * L::RING_BYTES) + 2 * lane;
+        auto g_fetch = [&](int k) {
+            if constexpr (GEN) {
+                if (k <= TY + 1) {
+                    const long long row = row0 + wy0 - 1 + k;
+                    const bool ok = row < a.rows && sa < pitch;
+                    const S* src = a.g_in + (ok ? (row * NQ) * pitch + sa : 0);
+                    S* dst = ring + (k % RING) * NQ * BW;
+#pragma unroll
+                    for (int q = 0; q < NQ; q++)
+                        cp_async_pair<2 * sizeof(S)>(dst + q * BW, src + (ok ? (long long)q * pitch : 0), ok ? 2 * sizeof(S) : 0);
+                }
+                cp_async_commit();  // one group per row (empty past the last row), so the waits stay uniform
+            }
+        };
+        if constexpr (GEN) {
+            g_fetch(0);
+            g_fetch(1);
+            g_fetch(2);
+        }
 
         // One row: A is the slot of row yf (it held yf - 3), B of row yf - 1, Cs of row yf - 2.  MU: mu and D
         // of row yf - 1; COL: collide row yf - 2; OUT: complete phi(t+1) of row yf - 3.  The three flags
@@ -247,6 +341,28 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             const int yc = yf - 2;
             C p8a = C(0), p8b = C(0), p7a = C(0), p7b = C(0), p4a = C(0), p4b = C(0);
             if constexpr (COL) {
+                // GEN: the populations g(t) of row yc (collision row k = j - 4 of the warp)
+                C ga[9], gb[9];
+                if constexpr (GEN) {
+                    const int k = j - 4;
+                    cp_async_wait<RING - 1>();  // row k has landed; the RING - 1 rows after it may be in flight
+                    const S* rg = ring + (k % RING) * NQ * BW;
+                    if constexpr (kHalf) {
+                        C resta = C(0), restb = C(0);
+#pragma unroll
+                        for (int q = 1; q < 9; q++) {
+                            unpair(*reinterpret_cast<const S2*>(rg + (q - 1) * BW), ga[q], gb[q]);
+                            resta += ga[q];
+                            restb += gb[q];
+                        }
+                        ga[0] = -resta;  // g_0 - phi
+                        gb[0] = -restb;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 9; q++) unpair(*reinterpret_cast<const S2*>(rg + q * BW), ga[q], gb[q]);
+                    }
+                    g_fetch(k + RING);  // the values are in registers: the slot takes row k + RING
+                }
                 // at a wall, the ghost rows are not collided (nothing is pulled from them)
                 if (!WALLS || (yc >= 0 && yc < ny)) {
                     if constexpr (WALLS) {
@@ -268,10 +384,48 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                     node_force(Cs.pa, gmxa, gmya, gDxa, gDya, model2, ra, rb, K, Fxa, Fya);
                     node_force(Cs.pb, gmxb, gmyb, gDxb, gDyb, model2, ra, rb, K, Fxb, Fyb);
                     C pa_[9], pb_[9];
-                    collide9<C, true, kShift>(Cs.pa, Cs.ma, Fxa, Fya, node_u(X1a, Cs.y1, T), node_u(X2a, Cs.y2, T), pa_,
+                    collide9<C, !GEN, kShift>(Cs.pa, Cs.ma, Fxa, Fya, node_u(X1a, Cs.y1, T), node_u(X2a, Cs.y2, T), ga,
                                               K0, pa_);
-                    collide9<C, true, kShift>(Cs.pb, Cs.mb, Fxb, Fyb, node_u(X1b, Cs.y1, T), node_u(X2b, Cs.y2, T), pb_,
+                    collide9<C, !GEN, kShift>(Cs.pb, Cs.mb, Fxb, Fyb, node_u(X1b, Cs.y1, T), node_u(X2b, Cs.y2, T), gb,
                                               K0, pb_);
+                    if constexpr (GEN && kHalf) {
+                        // the streamed populations are stored in half: they travel rounded (g*_0 stays at the
+                        // node, in float)
+#pragma unroll
+                        for (int q = 1; q < 9; q++) {
+                            pa_[q] = (C)__half2float(__float2half_rn((float)pa_[q]));
+                            pb_[q] = (C)__half2float(__float2half_rn((float)pb_[q]));
+                        }
+                    }
+                    if constexpr (GEN) {
+                        // g*_q reaches node x + c_q: the row above takes 2, 5, 6; this row 0, 1, 3; the row
+                        // below 4, 7, 8 (1, 5, 8 from the lane to the left, 3, 6, 7 from the right)
+                        B.n2a = pa_[2]; B.n2b = pb_[2];
+                        B.n5a = from_left(pb_[5]); B.n5b = pa_[5];
+                        B.n6a = pb_[6]; B.n6b = from_right(pa_[6]);
+                        Cs.n0a = pa_[0]; Cs.n0b = pb_[0];
+                        Cs.n1a = from_left(pb_[1]); Cs.n1b = pa_[1];
+                        Cs.n3a = pb_[3]; Cs.n3b = from_right(pa_[3]);
+                        A.n4a = pa_[4]; A.n4b = pb_[4];
+                        A.n7a = pb_[7]; A.n7b = from_right(pa_[7]);
+                        A.n8a = from_left(pb_[8]); A.n8b = pa_[8];
+                        if constexpr (WALLS) {
+                            if (yc == 0) {  // bottom wall: 2, 5, 6 of this row bounce back at the node
+                                const C uxa = node_u(X1a, tW[0], T), uya = node_u(X2a, tW[2], T);
+                                const C uxb = node_u(X1b, tW[0], T), uyb = node_u(X2b, tW[2], T);
+                                Cs.n2a = bounce<C, 2>(pa_[4], Cs.pa, uxa, uya); Cs.n2b = bounce<C, 2>(pb_[4], Cs.pb, uxb, uyb);
+                                Cs.n5a = bounce<C, 5>(pa_[7], Cs.pa, uxa, uya); Cs.n5b = bounce<C, 5>(pb_[7], Cs.pb, uxb, uyb);
+                                Cs.n6a = bounce<C, 6>(pa_[8], Cs.pa, uxa, uya); Cs.n6b = bounce<C, 6>(pb_[8], Cs.pb, uxb, uyb);
+                            }
+                            if (yc == ny - 1) {  // top wall: 4, 7, 8 of this row
+                                const C uxa = node_u(X1a, tW[1], T), uya = node_u(X2a, tW[3], T);
+                                const C uxb = node_u(X1b, tW[1], T), uyb = node_u(X2b, tW[3], T);
+                                Cs.n4a = bounce<C, 4>(pa_[2], Cs.pa, uxa, uya); Cs.n4b = bounce<C, 4>(pb_[2], Cs.pb, uxb, uyb);
+                                Cs.n7a = bounce<C, 7>(pa_[5], Cs.pa, uxa, uya); Cs.n7b = bounce<C, 7>(pb_[5], Cs.pb, uxb, uyb);
+                                Cs.n8a = bounce<C, 8>(pa_[6], Cs.pa, uxa, uya); Cs.n8b = bounce<C, 8>(pb_[6], Cs.pb, uxb, uyb);
+                            }
+                        }
+                    } else {
                     Cs.u5a = pa_[5]; Cs.u5b = pb_[5];
                     Cs.u2a = pa_[2]; Cs.u2b = pb_[2];
                     Cs.u6a = pa_[6]; Cs.u6b = pb_[6];
@@ -306,9 +460,73 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                     p8a = pa_[8]; p8b = pb_[8];
                     p7a = pa_[7]; p7b = pb_[7];
                     p4a = pa_[4]; p4b = pb_[4];
+                    }
                 }
             }
-            if constexpr (OUT) {
+            if constexpr (OUT && GEN) {
+                // g(t+1) and phi(t+1) of row yo = yf - 3 (slot A): every population has arrived
+                const int yo = yf - 3;
+                const C suma = stream_sum(A.n1a, A.n2a, A.n3a, A.n4a, A.n5a, A.n6a, A.n7a, A.n8a);
+                const C sumb = stream_sum(A.n1b, A.n2b, A.n3b, A.n4b, A.n5b, A.n6b, A.n7b, A.n8b);
+                P hia, hib;
+                float loa = 0.0f, lob = 0.0f;
+                C g0a = A.n0a, g0b = A.n0b;  // the stored rest population
+                if constexpr (FF) {
+                    const P2 hv = *reinterpret_cast<const P2*>(box + (j - 3) * BW);
+                    const float2 lv = *reinterpret_cast<const float2*>(lbox + (j - 6) * BW);
+                    {
+                        const float h = (float)hv.x, tt = lv.x + (float)(A.n0a + suma);
+                        const float sm = h + tt, bb = sm - h;
+                        loa = (h - (sm - bb)) + (tt - bb);
+                        hia = (P)sm;
+                    }
+                    {
+                        const float h = (float)hv.y, tt = lv.y + (float)(A.n0b + sumb);
+                        const float sm = h + tt, bb = sm - h;
+                        lob = (h - (sm - bb)) + (tt - bb);
+                        hib = (P)sm;
+                    }
+                    g0a = -suma;  // g_0 - phi(t+1) = -sum_{q>0} g_q(t+1)
+                    g0b = -sumb;
+                } else if constexpr (kShift) {
+                    const P2 hv = *reinterpret_cast<const P2*>(box + (j - 3) * BW);
+                    hia = (P)((float)hv.x + (float)(A.n0a + suma));
+                    hib = (P)((float)hv.y + (float)(A.n0b + sumb));
+                } else {
+                    hia = (P)(A.n0a + suma);
+                    hib = (P)(A.n0b + sumb);
+                }
+                if (yo < ny) {
+                    const long long node = (row0 + yo) * pitch + sa;
+                    const C va_[9] = {g0a, A.n1a, A.n2a, A.n3a, A.n4a, A.n5a, A.n6a, A.n7a, A.n8a};
+                    const C vb_[9] = {g0b, A.n1b, A.n2b, A.n3b, A.n4b, A.n5b, A.n6b, A.n7b, A.n8b};
+                    S* go = a.g_out + ((row0 + yo) * NQ) * pitch + sa;
+                    if (va && vb) {
+                        P2 o;
+                        o.x = hia;
+                        o.y = hib;
+                        *reinterpret_cast<P2*>(a.phi_out + node) = o;
+                        if (FF) *reinterpret_cast<float2*>(a.lo_out + node) = make_float2(loa, lob);
+#pragma unroll
+                        for (int q = QOFF; q < 9; q++)
+                            *reinterpret_cast<S2*>(go + (long long)(q - QOFF) * pitch) = mkpair<S>(va_[q], vb_[q]);
+                    } else if (va) {
+                        a.phi_out[node] = hia;
+                        if (FF) a.lo_out[node] = loa;
+#pragma unroll
+                        for (int q = QOFF; q < 9; q++) go[(long long)(q - QOFF) * pitch] = to_s<S>(va_[q]);
+                    }
+                    if (va) {
+                        store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xa, yo, hia);
+                        store_g_images<S, C, QOFF, WALLS>(a.g_out, row0, pitch, nx, ny, xa, yo, va_);
+                    }
+                    if (vb) {
+                        store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xb, yo, hib);
+                        store_g_images<S, C, QOFF, WALLS>(a.g_out, row0, pitch, nx, ny, xb, yo, vb_);
+                    }
+                }
+            }
+            if constexpr (OUT && !GEN) {
                 // phi(t+1) of row yo = yf - 3 (slot A), with g*_4, g*_7, g*_8 of row yo + 1 just computed
                 const int yo = yf - 3;
                 C Ra, Rb, Ca, Cb, La, Lb;
@@ -391,6 +609,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             row_step(Tr(), Tr(), Tr(), j + 1, r2, r0, r1);
             row_step(Tr(), Tr(), Tr(), j + 2, r1, r2, r0);
         }
+        if constexpr (GEN) cp_async_wait<0>();  // (only empty groups remain)
     };
 
     for (int it = 0;; it++) {

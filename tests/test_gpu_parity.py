@@ -176,13 +176,14 @@ def test_nonfinite_is_reported():
         assert ei.value.status == abi.LBCH_ENONFINITE
 
 
-@pytest.mark.parametrize("prec,nshapes,general", [("f64", 2, 1), ("f32", 3, 1), ("f16s", 3, 1),
-                                                 ("f64", 4, 0), ("f32", 4, 0), ("f16s", 4, 0)])
-def test_every_tile_shape_gives_the_same_bits(prec, nshapes, general):
+@pytest.mark.parametrize("prec,nshapes,tile,general", [("f64", 2, 1, 1), ("f32", 3, 1, 1), ("f16s", 3, 1, 1),
+                                                      ("f64", 4, 0, 1), ("f32", 4, 0, 1), ("f16s", 4, 0, 1),
+                                                      ("f64", 4, 0, 0), ("f32", 4, 0, 0), ("f16s", 4, 0, 0)])
+def test_every_tile_shape_gives_the_same_bits(prec, nshapes, tile, general):
     """The result does not depend on the tile shape (each node's arithmetic is the same; only the halo
     overlap between tiles changes), so every shape must reproduce the same bits; the autotuner then
-    only picks among equivalent kernels.  Both kernel forms: the tile kernel (general path) and the
-    row-sweep kernel that steps tau_g = 1 handles."""
+    only picks among equivalent kernels.  Every kernel form: the tile kernel, and the row sweep with
+    and without the populations."""
     ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=9)
     params, fields = zip(*ens)
     p, phi0, _ = wl.single_vortex(n=96, T=50)
@@ -190,6 +191,7 @@ def test_every_tile_shape_gives_the_same_bits(prec, nshapes, general):
     for k in range(nshapes):
         with abi.Simulation(p, phi0, prec=prec) as sim, abi.Simulation(list(params), list(fields), prec=prec) as ens_sim:
             for h in (sim.h, ens_sim.h):
+                abi.lb_ch_test_hook(h, abi.LBCH_HOOK_TILE_KERNEL, tile)
                 abi.lb_ch_test_hook(h, abi.LBCH_HOOK_GENERAL_PATH, general)
                 abi.lb_ch_test_hook(h, abi.LBCH_HOOK_TILE_SHAPE, k)
             sim.step(70)
@@ -208,6 +210,28 @@ def test_tune_keeps_the_state():
         a.step(100)
         b.step(100)
         assert np.array_equal(a.phi(), b.phi())
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16s"])
+def test_kernel_forms_give_the_same_bits(prec):
+    """The row sweep with the populations (any tau_g) against the tile kernel, at tau_g = 0.8 and 1.3, for
+    a periodic time-dependent flow and for a ragged ensemble with moving walls: the same arithmetic per
+    node in another order of work, so the same bits -- on the half-storage path too."""
+    for tau in (0.8, 1.3):
+        p, phi0, _ = wl.single_vortex(n=96, T=60, tau=tau)
+        ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=4, tau=tau)
+        ens = [(dict(q, shear=q["shear"] * 30.0, Ustar=q["Ustar"] * 30.0), f) for q, f in ens]
+        params, fields = zip(*ens)
+        res = []
+        for tile in (0, 1):
+            with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(list(params), list(fields), prec=prec) as b:
+                abi.lb_ch_test_hook(a.h, abi.LBCH_HOOK_TILE_KERNEL, tile)
+                abi.lb_ch_test_hook(b.h, abi.LBCH_HOOK_TILE_KERNEL, tile)
+                a.step(90)
+                b.step(90)
+                res.append([a.phi()] + [b.phi(k) for k in range(3)])
+        for x, y in zip(res[0], res[1]):
+            assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16s"])
