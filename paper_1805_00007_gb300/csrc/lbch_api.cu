@@ -7,9 +7,9 @@
 // step kernel -- replayed from CUDA graphs of 64 steps -- and the reductions behind lb_ch_observe.
 #include "lbch.h"
 #include "lbch_adjoint.cuh"
+#include "lbch_internal.h"
 #include "lbch_kernels.cuh"
 #include "lbch_ns.cuh"
-#include "lbch_sweep.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -53,20 +53,11 @@ constexpr int kGraphChunk = 64;  // steps per captured graph (even, so the ping-
 // times them on the handle's own problem and keeps the fastest; the first one is the default.  Every
 // TX divides 32 and every TY divides 16, so one storage layout serves all shapes.
 constexpr int NT = 256;
-constexpr int kMaxShapes = 3;
-struct Shape { int tx, ty; };
 constexpr Shape kShapes64[2] = {{32, 8}, {16, 8}};
 constexpr Shape kShapesF[3] = {{32, 16}, {32, 8}, {16, 8}};
 inline int n_shapes(int prec) { return prec == LBCH_F64 ? 2 : 3; }
 inline Shape shape_of(int prec, int k) { return prec == LBCH_F64 ? kShapes64[k] : kShapesF[k]; }
 
-// Configurations of the row-sweep kernel (tau_g = 1): TY output rows per warp, NW warps per CTA; a tile
-// is 56 columns by NW TY rows.  lb_ch_tune picks among them as among the tile shapes.
-struct SweepCfg { int ty, nw; };
-constexpr SweepCfg kSweep[4] = {{12, 4}, {6, 4}, {6, 2}, {3, 4}};
-constexpr int kSweepShapes = 4;
-constexpr int kSweepW = 56;
-inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw}; }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -94,65 +85,9 @@ __attribute__((visibility("hidden"))) void lbch_set_last_error(const char* msg)
     snprintf(g_msg, sizeof g_msg, "%s", msg);
 }
 
-struct lbch_handle {
-    int device = 0;
-    int prec = LBCH_F64;
-    int n_inst = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::vector<InstDev> inst;
-    std::vector<long long> node_begin;  // first linear node index of each instance (+ total)
-    InstDev* d_inst = nullptr;
-    long long* d_node_begin = nullptr;
-    double* d_tabs = nullptr;   // velocity tables in double (init kernel, FP64 step)
-    float* d_tabs_f = nullptr;  // the same tables in float (float step kernels)
-    int pitch = 0;              // elements per stored row
-    int rows = 0;               // stored rows of all instances
-    int nq = 9;                 // stored population planes
-    size_t g_elem = 8, phi_elem = 8;
-    long long nodes = 0;        // lattice nodes (all instances)
-    int shape = 0;              // tile shape in use (index into the precision's shape list)
-    bool tau1 = false;          // every instance has tau_g = 1: the populations drop out of the step
-    bool force_general = false; // test hook: keep the populations even when tau1 holds
-    bool force_tile = false;    // test hook: step with the tile kernel instead of the row sweep
-    bool no_pdl = false;        // test hook: plain stream-ordered step launches
-    struct PerShape {           // what depends on the tile shape
-        int total_tiles = 0;
-        int grid = 0;           // persistent CTAs per step launch
-        int grid_gen = 0;       // row sweep with the populations (the tile kernel uses grid)
-        int* d_tile_begin = nullptr;
-        CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
-    } ps[kMaxShapes], sw[kSweepShapes];  // tile kernel shapes; row-sweep configurations (tm_g unused)
-    void* g[2] = {nullptr, nullptr};
-    void* phi[2] = {nullptr, nullptr};
-    float* lo[2] = {nullptr, nullptr};  // low part of phi (float path)
-    double* phi0 = nullptr;     // initial field, double, padded layout
-    Ctl* ctl = nullptr;
-    double* partials = nullptr; // reduction scratch: n_inst * chunks * RED_NV doubles
-    double* result = nullptr;   // n_inst * RED_NV doubles
-    int chunks = 0;
-    long long n = 0;            // host mirror of the step index
-    int debug_skip = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    double* h_stage = nullptr;  // pinned host staging
-    size_t h_stage_bytes = 0;
-    // adjoint workspace (instance 0), allocated by the first lb_ch_adjoint_begin
-    void* adj = nullptr;        // one block: lambda[2] (9N each), mu, grad_mu_bar (2N), F_bar (2N), phi_bar,
-                                // mu_bar, D_bar, u_bar (2N) in the adjoint type; then ds (N) and dL/ds, double
-    size_t adj_elem = 8;
-    int adj_par = 0;            // which lambda holds the current adjoint
-    // coupled Navier-Stokes state (LBCH_VEL_COUPLED): f[2], g[2] ([9][N]) and 11 node fields, one block
-    bool coupled = false;
-    void* ns = nullptr;
-    ns::NsConsts<double> nsd;
-    ns::NsConsts<float> nsf;
-};
 
 namespace {
 
-template <typename C> const C* tables(lbch_handle* h);
-template <> const double* tables<double>(lbch_handle* h) { return h->d_tabs; }
-template <> const float* tables<float>(lbch_handle* h) { return h->d_tabs_f; }
 
 template <typename C, typename S, typename P, int TX, int TY, bool TAU1>
 cudaError_t launch_step_v(lbch_handle* h, int parity)
@@ -196,7 +131,6 @@ cudaError_t launch_step_t(lbch_handle* h, int parity)
 // The row-sweep kernel steps the handle (its shape index then names a sweep configuration), without the
 // populations when every instance has tau_g = 1; the tile kernel only when a test asks for it.
 inline bool use_sweep(const lbch_handle* h) { return !h->force_tile && !h->coupled; }
-inline bool sweep_gen(const lbch_handle* h) { return !h->tau1 || h->force_general; }
 inline int n_active(const lbch_handle* h) { return h->coupled ? 1 : (use_sweep(h) ? kSweepShapes : n_shapes(h->prec)); }
 inline const lbch_handle::PerShape& active_ps(const lbch_handle* h) { return use_sweep(h) ? h->sw[h->shape] : h->ps[h->shape]; }
 inline int active_grid(const lbch_handle* h)
@@ -208,105 +142,21 @@ inline Shape active_tile(const lbch_handle* h)
     return h->coupled ? Shape{0, 0} : (use_sweep(h) ? sweep_tile(h->shape) : shape_of(h->prec, h->shape));
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
-cudaError_t launch_sweep_v(lbch_handle* h, int parity)
-{
-    using L = SweepShape<P, S, FF, TY, NW, GEN>;
-    const lbch_handle::PerShape& ps = h->sw[h->shape];
-    SweepArgs<C, S, P> a;
-    a.inst = h->d_inst;
-    a.tile_begin = ps.d_tile_begin;
-    a.tabs = tables<C>(h);
-    a.n_inst = h->n_inst;
-    a.total_tiles = ps.total_tiles;
-    a.pitch = h->pitch;
-    a.debug_skip = h->debug_skip;
-    a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
-    a.lo_out = h->lo[parity ^ 1];
-    a.ctl = h->ctl;
-    a.g_in = static_cast<const S*>(h->g[parity]);
-    a.g_out = static_cast<S*>(h->g[parity ^ 1]);
-    a.rows = h->rows;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(GEN ? ps.grid_gen : ps.grid);
-    cfg.blockDim = dim3(NW * 32);
-    cfg.dynamicSmemBytes = L::BYTES;
-    cfg.stream = h->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>, ps.tm_phi[parity], ps.tm_lo[parity], a);
-}
-
-template <typename C, typename S, typename P, bool FF, int TY, int NW>
-cudaError_t launch_sweep_g(lbch_handle* h, int parity)
-{
-    return sweep_gen(h) ? launch_sweep_v<C, S, P, FF, TY, NW, true>(h, parity)
-                        : launch_sweep_v<C, S, P, FF, TY, NW, false>(h, parity);
-}
-
-template <typename C, typename S, typename P, bool FF>
-cudaError_t launch_sweep_t(lbch_handle* h, int parity)
-{
-    switch (h->shape) {
-    case 0: return launch_sweep_g<C, S, P, FF, 12, 4>(h, parity);
-    case 1: return launch_sweep_g<C, S, P, FF, 6, 4>(h, parity);
-    case 2: return launch_sweep_g<C, S, P, FF, 6, 2>(h, parity);
-    default: return launch_sweep_g<C, S, P, FF, 3, 4>(h, parity);
-    }
-}
-
 cudaError_t launch_sweep(lbch_handle* h, int parity)
 {
     switch (h->prec) {
-    case LBCH_F64: return launch_sweep_t<double, double, double, false>(h, parity);
-    case LBCH_F32: return launch_sweep_t<float, float, float, true>(h, parity);
-    default: return launch_sweep_t<float, __half, float, false>(h, parity);
+    case LBCH_F64: return lbch_launch_sweep_f64(h, parity);
+    case LBCH_F32: return lbch_launch_sweep_f32(h, parity);
+    default: return lbch_launch_sweep_f16s(h, parity);
     }
-}
-
-// Dynamic shared memory of one sweep kernel and the persistent grid that fits the device.
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
-cudaError_t prepare_sweep_v(lbch_handle* h, int k)
-{
-    using L = SweepShape<P, S, FF, TY, NW, GEN>;
-    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, L::BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    (GEN ? h->sw[k].grid_gen : h->sw[k].grid) = std::max(1, std::min(h->sw[k].total_tiles, per_sm * sms));
-    return cudaSuccess;
-}
-
-template <typename C, typename S, typename P, bool FF, int TY, int NW>
-cudaError_t prepare_sweep_g(lbch_handle* h, int k)
-{
-    cudaError_t e = prepare_sweep_v<C, S, P, FF, TY, NW, true>(h, k);
-    if (e == cudaSuccess && h->tau1) e = prepare_sweep_v<C, S, P, FF, TY, NW, false>(h, k);
-    return e;
-}
-
-template <typename C, typename S, typename P, bool FF>
-cudaError_t prepare_sweep_t(lbch_handle* h, int k)
-{
-    return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4>(h, k)
-         : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4>(h, k)
-         : k == 2 ? prepare_sweep_g<C, S, P, FF, 6, 2>(h, k) : prepare_sweep_g<C, S, P, FF, 3, 4>(h, k);
 }
 
 cudaError_t prepare_sweep(lbch_handle* h, int k)
 {
     switch (h->prec) {
-    case LBCH_F64: return prepare_sweep_t<double, double, double, false>(h, k);
-    case LBCH_F32: return prepare_sweep_t<float, float, float, true>(h, k);
-    default: return prepare_sweep_t<float, __half, float, false>(h, k);
+    case LBCH_F64: return lbch_prepare_sweep_f64(h, k);
+    case LBCH_F32: return lbch_prepare_sweep_f32(h, k);
+    default: return lbch_prepare_sweep_f16s(h, k);
     }
 }
 
@@ -616,6 +466,37 @@ lbch_status encode_sweep_maps(lbch_handle* h, int sk)
     return LBCH_OK;
 }
 
+// The row sweep's ring fills: one row of the population planes (64 columns x nq planes), and one row of
+// the low part of phi.
+lbch_status encode_row_maps(lbch_handle* h)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(LBCH_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    CUtensorMapDataType gt = h->prec == LBCH_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : (h->prec == LBCH_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    for (int k = 0; k < 2; k++) {
+        cuuint64_t gdim[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->nq, (cuuint64_t)h->rows};
+        cuuint64_t gstr[2] = {(cuuint64_t)h->pitch * h->g_elem, (cuuint64_t)h->pitch * h->g_elem * h->nq};
+        cuuint32_t gbox[3] = {64u, (cuuint32_t)h->nq, 1u};
+        cuuint32_t es[3] = {1, 1, 1};
+        CUresult r = enc(&h->tm_grow[k], gt, 3, h->g[k], gdim, gstr, gbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of a population row: CUresult %d", (int)r);
+        if (h->lo[k]) {
+            cuuint64_t ldim[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->rows};
+            cuuint64_t lstr[1] = {(cuuint64_t)h->pitch * 4};
+            cuuint32_t lbox[2] = {64u, 1u};
+            r = enc(&h->tm_lorow[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h->lo[k], ldim, lstr, lbox, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return fail(LBCH_ECUDA, "tensor map of a row of phi's low part: CUresult %d", (int)r);
+        } else {
+            h->tm_lorow[k] = h->tm_grow[k];  // unused without a low part
+        }
+    }
+    return LBCH_OK;
+}
+
 lbch_status check_err(lbch_handle* h)
 {
     unsigned int err = 0;
@@ -868,6 +749,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     lbch_status st = LBCH_OK;
     for (int sk = 0; sk < n_shapes(prec) && st == LBCH_OK; sk++) st = encode_maps(h, sk);
     for (int sk = 0; !coupled && sk < kSweepShapes && st == LBCH_OK; sk++) st = encode_sweep_maps(h, sk);
+    if (!coupled && st == LBCH_OK) st = encode_row_maps(h);
     if (st != LBCH_OK) return bail(st);
 
     // the initial field in the padded layout, ghost frame included, through pinned staging

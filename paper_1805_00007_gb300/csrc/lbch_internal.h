@@ -1,0 +1,91 @@
+// lbch_internal.h -- the handle of the C ABI and what the translation units of the library share.
+#pragma once
+#include <algorithm>
+#include <vector>
+
+#include "lbch.h"
+#include "lbch_kernels.cuh"
+#include "lbch_ns.cuh"
+
+constexpr int kMaxShapes = 3;
+struct Shape { int tx, ty; };
+
+// Configurations of the row-sweep kernel (tau_g = 1): TY output rows per warp, NW warps per CTA; a tile
+// is 56 columns by NW TY rows.  lb_ch_tune picks among them as among the tile shapes.
+struct SweepCfg { int ty, nw; };
+constexpr SweepCfg kSweep[4] = {{12, 4}, {6, 4}, {6, 2}, {3, 4}};
+constexpr int kSweepShapes = 4;
+constexpr int kSweepW = 56;
+inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw}; }
+
+struct lbch_handle {
+    int device = 0;
+    int prec = LBCH_F64;
+    int n_inst = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<lbch::InstDev> inst;
+    std::vector<long long> node_begin;  // first linear node index of each instance (+ total)
+    lbch::InstDev* d_inst = nullptr;
+    long long* d_node_begin = nullptr;
+    double* d_tabs = nullptr;   // velocity tables in double (init kernel, FP64 step)
+    float* d_tabs_f = nullptr;  // the same tables in float (float step kernels)
+    int pitch = 0;              // elements per stored row
+    int rows = 0;               // stored rows of all instances
+    int nq = 9;                 // stored population planes
+    size_t g_elem = 8, phi_elem = 8;
+    long long nodes = 0;        // lattice nodes (all instances)
+    int shape = 0;              // tile shape in use (index into the precision's shape list)
+    bool tau1 = false;          // every instance has tau_g = 1: the populations drop out of the step
+    bool force_general = false; // test hook: keep the populations even when tau1 holds
+    bool force_tile = false;    // test hook: step with the tile kernel instead of the row sweep
+    bool no_pdl = false;        // test hook: plain stream-ordered step launches
+    struct PerShape {           // what depends on the tile shape
+        int total_tiles = 0;
+        int grid = 0;           // persistent CTAs per step launch
+        int grid_gen = 0;       // row sweep with the populations (the tile kernel uses grid)
+        int* d_tile_begin = nullptr;
+        CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
+    } ps[kMaxShapes], sw[kSweepShapes];  // tile kernel shapes; row-sweep configurations (tm_g unused)
+    CUtensorMap tm_grow[2], tm_lorow[2];  // one row of the populations / of phi's low part (row sweep)
+    void* g[2] = {nullptr, nullptr};
+    void* phi[2] = {nullptr, nullptr};
+    float* lo[2] = {nullptr, nullptr};  // low part of phi (float path)
+    double* phi0 = nullptr;     // initial field, double, padded layout
+    lbch::Ctl* ctl = nullptr;
+    double* partials = nullptr; // reduction scratch: n_inst * chunks * RED_NV doubles
+    double* result = nullptr;   // n_inst * RED_NV doubles
+    int chunks = 0;
+    long long n = 0;            // host mirror of the step index
+    int debug_skip = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double* h_stage = nullptr;  // pinned host staging
+    size_t h_stage_bytes = 0;
+    // adjoint workspace (instance 0), allocated by the first lb_ch_adjoint_begin
+    void* adj = nullptr;        // one block: lambda[2] (9N each), mu, grad_mu_bar (2N), F_bar (2N), phi_bar,
+                                // mu_bar, D_bar, u_bar (2N) in the adjoint type; then ds (N) and dL/ds, double
+    size_t adj_elem = 8;
+    int adj_par = 0;            // which lambda holds the current adjoint
+    // coupled Navier-Stokes state (LBCH_VEL_COUPLED): f[2], g[2] ([9][N]) and 11 node fields, one block
+    bool coupled = false;
+    void* ns = nullptr;
+    lbch::ns::NsConsts<double> nsd;
+    lbch::ns::NsConsts<float> nsf;
+};
+
+// The velocity tables in the arithmetic type of a step kernel.
+template <typename C> inline const C* tables(lbch_handle* h);
+template <> inline const double* tables<double>(lbch_handle* h) { return h->d_tabs; }
+template <> inline const float* tables<float>(lbch_handle* h) { return h->d_tabs_f; }
+
+// The row sweep keeps the populations unless every instance has tau_g = 1 (and no test asks for them).
+inline bool sweep_gen(const lbch_handle* h) { return !h->tau1 || h->force_general; }
+
+// Row-sweep launches and set-up, one translation unit per precision (lbch_sweep_*.cu).
+#define LBCH_INTERNAL __attribute__((visibility("hidden")))
+LBCH_INTERNAL cudaError_t lbch_launch_sweep_f64(lbch_handle* h, int parity);
+LBCH_INTERNAL cudaError_t lbch_launch_sweep_f32(lbch_handle* h, int parity);
+LBCH_INTERNAL cudaError_t lbch_launch_sweep_f16s(lbch_handle* h, int parity);
+LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f64(lbch_handle* h, int k);
+LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f32(lbch_handle* h, int k);
+LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f16s(lbch_handle* h, int k);

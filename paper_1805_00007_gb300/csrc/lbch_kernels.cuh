@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const InstDev* 
     }
 }
 
-__global__ void __launch_bounds__(RED_NT) reduce_final_kernel(const double* partials, int chunks, double* result)
+static __global__ void __launch_bounds__(RED_NT) reduce_final_kernel(const double* partials, int chunks, double* result)
 {
     __shared__ double sh[RED_NT / 32][RED_NV];
     double v[RED_NV] = {0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};

@@ -22,11 +22,12 @@
 // once per tile into registers; the Y tables of its rows arrive one row per lane and are broadcast by
 // shuffles.
 //
-// GEN (any tau_g): the populations are read and written as well.  Each lane copies its own columns of
-// the population planes of the rows it will collide into a three-row ring in shared memory, two rows
-// ahead (cp.async, one group per row); after the collision the nine g* of a node reach their
-// destinations individually -- 1, 5, 8 from the lane to the left, 3, 6, 7 from the right, 2 and 4 from
-// the rows below and above -- and g(t+1) is stored plane by plane.
+// GEN (any tau_g): the populations are read and written as well.  Each warp keeps a four-slot ring of
+// the rows it will collide in shared memory: one TMA box per row (64 columns x the population planes,
+// plus the low part of phi on the float-float path), issued by lane 0 three rows ahead on the slot's
+// mbarrier.  After the collision the nine g* of a node reach their destinations individually -- 1, 5, 8
+// from the lane to the left, 3, 6, 7 from the right, 2 and 4 from the rows below and above -- and
+// g(t+1) is stored plane by plane.
 #pragma once
 #include <type_traits>
 
@@ -46,8 +47,7 @@ struct SweepArgs {
     P* phi_out;
     float* lo_out;          // low part of phi on the float-float path
     Ctl* ctl;
-    const S* g_in;          // populations (GEN): g[(row * nq + plane) * pitch + column]
-    S* g_out;
+    S* g_out;               // populations (GEN): g[(row * nq + plane) * pitch + column]
     int rows;               // stored rows of the population arrays
 };
 
@@ -58,16 +58,19 @@ struct SweepShape {
     static constexpr int TH = NW * TY;           // output rows of a tile
     static constexpr int PBH = TH + 6;           // phi box rows: y0 - 3 .. y0 + TH + 2
     static constexpr unsigned PBOX_BYTES = PBH * BW * sizeof(P);
-    static constexpr unsigned LBOX_BYTES = FF ? TH * BW * 4 : 0;
+    static constexpr unsigned LBOX_BYTES = (FF && !GEN) ? TH * BW * 4 : 0;  // GEN: the low part rides in the ring
     __host__ __device__ static constexpr size_t a128(size_t b) { return (b + 127) / 128 * 128; }
     static constexpr size_t OFF_L = a128(PBOX_BYTES);
     static constexpr size_t STAGE = OFF_L + a128(LBOX_BYTES);
     static constexpr int NQ = sizeof(S) == 2 ? 8 : 9;  // stored population planes
-    static constexpr int RING = 3;                      // population rows in flight per warp
-    static constexpr size_t RING_BYTES = GEN ? (size_t)RING * NQ * BW * sizeof(S) : 0;  // per warp
+    static constexpr int RING = 4;                      // ring slots per warp (rows k .. k + 3)
+    static constexpr int NPL = NQ + (FF ? 1 : 0);       // planes per ring row: the populations, the low part of phi
+    static constexpr int CH = BW * (int)sizeof(S) / 16; // 16-byte chunks per plane row
+    static constexpr size_t RING_BYTES = GEN ? (size_t)RING * NPL * BW * sizeof(S) : 0;  // per warp
+    static constexpr unsigned ROW_BYTES = NQ * BW * sizeof(S) + (FF ? BW * 4 : 0);  // one ring fill
     static constexpr size_t OFF_RING = 2 * STAGE;
     static constexpr size_t OFF_MBAR = OFF_RING + NW * RING_BYTES;
-    static constexpr size_t BYTES = OFF_MBAR + 128 + 128;  // mbarriers, alignment slack
+    static constexpr size_t BYTES = OFF_MBAR + 256 + 128;  // mbarriers (2 for the stages, RING per warp), slack
 };
 
 template <typename P> struct Pair;
@@ -90,19 +93,6 @@ template <typename S, typename C> __device__ __forceinline__ typename Pair<S>::T
 }
 template <> __device__ __forceinline__ __half2 mkpair<__half, float>(float x, float y) { return __floats2half2_rn(x, y); }
 
-// Per-thread asynchronous copy of one column pair of a population row into shared memory; with
-// src_bytes = 0 nothing is read and the destination is zero-filled.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_pair(void* dst, const void* src, unsigned src_bytes)
-{
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES), "r"(src_bytes)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <typename C> __device__ __forceinline__ C from_left(C v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 template <typename C> __device__ __forceinline__ C from_right(C v) { return __shfl_down_sync(0xffffffffu, v, 1); }
@@ -169,6 +159,7 @@ __device__ __forceinline__ void store_g_images(S* g_out, long long row0, int pit
 template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
 __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     ch_sweep_kernel(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lo,
+                    const __grid_constant__ CUtensorMap tm_grow, const __grid_constant__ CUtensorMap tm_lorow,
                     SweepArgs<C, S, P> a)
 {
     static_assert(TY % 3 == 0, "the sweep advances three rows per unrolled step");
@@ -176,7 +167,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
     using P2 = typename Pair<P>::T;
     using S2 = typename Pair<S>::T;
-    constexpr int BW = L::BW, TH = L::TH, NQ = L::NQ, RING = L::RING;
+    constexpr int BW = L::BW, TH = L::TH, NQ = L::NQ, RING = L::RING, NPL = L::NPL;
     constexpr bool kShift = sizeof(C) == 4;     // float arithmetic on g_0 - phi
     constexpr bool kHalf = sizeof(S) == 2;      // half storage: g_0 not stored (implied by phi)
     constexpr int QOFF = kHalf ? 1 : 0;         // stored plane of population q is q - QOFF
@@ -220,8 +211,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     };
 
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int b = 0; b < 2 + (GEN ? NW * RING : 0); b++) mbar_init(&mbar[b], 1);
         fence_mbar_init();
         s_tile_inst = -1;
         if ((int)blockIdx.x < a.total_tiles) {  // instance data are constant: read before the dependency wait
@@ -253,7 +243,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         mbar_expect_tx(&mbar[s], L::PBOX_BYTES + L::LBOX_BYTES);
         // box column origin: domain bx - 4 is stored column bx (a multiple of 4: 16-byte aligned)
         tma_load_2d(stage(s), &tm_phi, bx, I.row0 + by - 3, &mbar[s]);
-        if (FF) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, bx, I.row0 + by, &mbar[s]);
+        if (FF && !GEN) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, bx, I.row0 + by, &mbar[s]);
     };
 
     if (tid == 0) {
@@ -262,6 +252,12 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             if (t < a.total_tiles && !(a.debug_skip && blockIdx.x == 0 && j == 0)) issue(t, j);
         }
     }
+
+    // GEN: this warp's ring.  Fill n goes to slot n % RING and completes phase n / RING of the slot's
+    // mbarrier; the fills and their uses run in the same row order, tile after tile.
+    uint64_t* rbar = mbar + 2 + warp * RING;
+    int fills = 0, uses = 0;
+    bool ring_ok = true;
 
     // The sweep of one warp over its TY output rows of the tile in stage s.  WALLS: the instance has walls
     // in y (bounce-back rows, mirror substitution) -- a separate body, so that periodic tiles carry none
@@ -286,21 +282,23 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         const bool va = lane >= 2 && lane < 30 && xa < nx, vb = lane >= 2 && lane < 30 && xb < nx;
         const long long row0 = I.row0;
         const C* tW = a.tabs + I.tab + 2 * pitch + 2 * I.ylen;  // Y1, Y2 at the walls y = -1/2, ny - 1/2
-        // GEN: this warp's ring of population rows ([slot][plane][64 columns]); collision row k of the
-        // warp is domain row wy0 - 1 + k and lives in slot k % RING
-        [[maybe_unused]] S* ring = reinterpret_cast<S*>(base + L::OFF_RING + warp * L::RING_BYTES) + 2 * lane;
+        // GEN: the ring of rows ([slot][plane][64 columns]: the population planes, then the low part of
+        // phi on the float-float path).  Collision row k of the warp is domain row wy0 - 1 + k; its slot is
+        // filled three rows before its collision and refilled after its phi(t+1) is written.
+        [[maybe_unused]] S* ring = reinterpret_cast<S*>(base + L::OFF_RING + warp * L::RING_BYTES);
         auto g_fetch = [&](int k) {
             if constexpr (GEN) {
-                if (k <= TY + 1) {
-                    const long long row = row0 + wy0 - 1 + k;
-                    const bool ok = row < a.rows && sa < pitch;
-                    const S* src = a.g_in + (ok ? (row * NQ) * pitch + sa : 0);
-                    S* dst = ring + (k % RING) * NQ * BW;
-#pragma unroll
-                    for (int q = 0; q < NQ; q++)
-                        cp_async_pair<2 * sizeof(S)>(dst + q * BW, src + (ok ? (long long)q * pitch : 0), ok ? 2 * sizeof(S) : 0);
+                if (k <= TY + 1 && ring_ok) {  // after a lost copy nothing more is issued
+                    if (lane == 0) {
+                        const int slot = fills % RING, row = (int)row0 + wy0 - 1 + k;
+                        S* dst = ring + slot * NPL * BW;
+                        fence_proxy_async();  // the slot's previous contents were read through the generic proxy
+                        mbar_expect_tx(&rbar[slot], L::ROW_BYTES);
+                        tma_load_3d(dst, &tm_grow, x0, 0, row, &rbar[slot]);
+                        if (FF) tma_load_2d(dst + NQ * BW, &tm_lorow, x0, row, &rbar[slot]);
+                    }
+                    fills++;
                 }
-                cp_async_commit();  // one group per row (empty past the last row), so the waits stay uniform
             }
         };
         if constexpr (GEN) {
@@ -344,9 +342,11 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                 // GEN: the populations g(t) of row yc (collision row k = j - 4 of the warp)
                 C ga[9], gb[9];
                 if constexpr (GEN) {
-                    const int k = j - 4;
-                    cp_async_wait<RING - 1>();  // row k has landed; the RING - 1 rows after it may be in flight
-                    const S* rg = ring + (k % RING) * NQ * BW;
+                    // row k = j - 4 has landed (bounded wait; a lost copy is reported, not waited for)
+                    const int slot = uses % RING;
+                    if (ring_ok) ring_ok = mbar_wait_bounded(&rbar[slot], (unsigned)((uses / RING) & 1), 1u << 22);
+                    uses++;
+                    const S* rg = ring + slot * NPL * BW + 2 * lane;
                     if constexpr (kHalf) {
                         C resta = C(0), restb = C(0);
 #pragma unroll
@@ -361,7 +361,6 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
 #pragma unroll
                         for (int q = 0; q < 9; q++) unpair(*reinterpret_cast<const S2*>(rg + q * BW), ga[q], gb[q]);
                     }
-                    g_fetch(k + RING);  // the values are in registers: the slot takes row k + RING
                 }
                 // at a wall, the ghost rows are not collided (nothing is pulled from them)
                 if (!WALLS || (yc >= 0 && yc < ny)) {
@@ -473,7 +472,9 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                 C g0a = A.n0a, g0b = A.n0b;  // the stored rest population
                 if constexpr (FF) {
                     const P2 hv = *reinterpret_cast<const P2*>(box + (j - 3) * BW);
-                    const float2 lv = *reinterpret_cast<const float2*>(lbox + (j - 6) * BW);
+                    // the low part of row yo = the previous collision row, one slot back
+                    const float2 lv = *reinterpret_cast<const float2*>(
+                        reinterpret_cast<const float*>(ring) + ((uses - 2) % RING) * NPL * BW + NQ * BW + 2 * lane);
                     {
                         const float h = (float)hv.x, tt = lv.x + (float)(A.n0a + suma);
                         const float sm = h + tt, bb = sm - h;
@@ -525,6 +526,12 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                         store_g_images<S, C, QOFF, WALLS>(a.g_out, row0, pitch, nx, ny, xb, yo, vb_);
                     }
                 }
+            }
+            if constexpr (COL && GEN) {
+                // the slot of collision row j - 5 (read by the collision before and the output just done)
+                // takes row j - 1 = k + 3
+                __syncwarp();
+                g_fetch(j - 1);
             }
             if constexpr (OUT && !GEN) {
                 // phi(t+1) of row yo = yf - 3 (slot A), with g*_4, g*_7, g*_8 of row yo + 1 just computed
@@ -609,7 +616,6 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             row_step(Tr(), Tr(), Tr(), j + 1, r2, r0, r1);
             row_step(Tr(), Tr(), Tr(), j + 2, r1, r2, r0);
         }
-        if constexpr (GEN) cp_async_wait<0>();  // (only empty groups remain)
     };
 
     for (int it = 0;; it++) {
@@ -635,11 +641,20 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         __syncthreads();
         if (s_I.walls) sweep(std::true_type(), s);
         else sweep(std::false_type(), s);
+        if (GEN && !ring_ok && lane == 0) atomicOr(&a.ctl->err, 1u);
         __syncthreads();  // the stage is free again
 
         if (tid == 0) {
             const int t2 = t + 2 * stride;
             if (t2 < a.total_tiles) issue(t2, s);
+        }
+    }
+
+    // GEN, after a ring wait gave up: the copies still in flight (at most one per slot) land before exit
+    if (GEN && !ring_ok && lane == 0) {
+        for (int b = 0; b < RING; b++) {
+            const int nb = fills - 1 - ((fills - 1 - b) % RING + RING) % RING;  // the last fill into slot b
+            if (nb >= 0) mbar_wait_bounded(&rbar[b], (unsigned)((nb / RING) & 1), 1u << 22);
         }
     }
 

@@ -1,0 +1,12 @@
+// lbch_sweep_f64.cu -- the row-sweep step kernels of the f64 path.
+#include "lbch_sweep_launch.cuh"
+
+cudaError_t lbch_launch_sweep_f64(lbch_handle* h, int parity)
+{
+    return lbch::launch_sweep_t<double, double, double, false>(h, parity);
+}
+
+cudaError_t lbch_prepare_sweep_f64(lbch_handle* h, int k)
+{
+    return lbch::prepare_sweep_t<double, double, double, false>(h, k);
+}

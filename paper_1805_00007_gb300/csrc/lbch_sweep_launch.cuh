@@ -1,0 +1,93 @@
+// lbch_sweep_launch.cuh -- launch and set-up of the row-sweep kernel for one precision; included by the
+// per-precision translation units, so that their kernels compile in parallel.
+#pragma once
+#include "lbch_internal.h"
+#include "lbch_sweep.cuh"
+
+namespace lbch {
+
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
+cudaError_t launch_sweep_v(lbch_handle* h, int parity)
+{
+    using L = SweepShape<P, S, FF, TY, NW, GEN>;
+    const lbch_handle::PerShape& ps = h->sw[h->shape];
+    SweepArgs<C, S, P> a;
+    a.inst = h->d_inst;
+    a.tile_begin = ps.d_tile_begin;
+    a.tabs = tables<C>(h);
+    a.n_inst = h->n_inst;
+    a.total_tiles = ps.total_tiles;
+    a.pitch = h->pitch;
+    a.debug_skip = h->debug_skip;
+    a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
+    a.lo_out = h->lo[parity ^ 1];
+    a.ctl = h->ctl;
+    a.g_out = static_cast<S*>(h->g[parity ^ 1]);
+    a.rows = h->rows;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(GEN ? ps.grid_gen : ps.grid);
+    cfg.blockDim = dim3(NW * 32);
+    cfg.dynamicSmemBytes = L::BYTES;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>, ps.tm_phi[parity], ps.tm_lo[parity],
+                              h->tm_grow[parity], h->tm_lorow[parity], a);
+}
+
+template <typename C, typename S, typename P, bool FF, int TY, int NW>
+cudaError_t launch_sweep_g(lbch_handle* h, int parity)
+{
+    return sweep_gen(h) ? launch_sweep_v<C, S, P, FF, TY, NW, true>(h, parity)
+                        : launch_sweep_v<C, S, P, FF, TY, NW, false>(h, parity);
+}
+
+template <typename C, typename S, typename P, bool FF>
+cudaError_t launch_sweep_t(lbch_handle* h, int parity)
+{
+    switch (h->shape) {
+    case 0: return launch_sweep_g<C, S, P, FF, 12, 4>(h, parity);
+    case 1: return launch_sweep_g<C, S, P, FF, 6, 4>(h, parity);
+    case 2: return launch_sweep_g<C, S, P, FF, 6, 2>(h, parity);
+    default: return launch_sweep_g<C, S, P, FF, 3, 4>(h, parity);
+    }
+}
+
+// Dynamic shared memory of one sweep kernel and the persistent grid that fits the device.
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
+cudaError_t prepare_sweep_v(lbch_handle* h, int k)
+{
+    using L = SweepShape<P, S, FF, TY, NW, GEN>;
+    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, L::BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    (GEN ? h->sw[k].grid_gen : h->sw[k].grid) = std::max(1, std::min(h->sw[k].total_tiles, per_sm * sms));
+    return cudaSuccess;
+}
+
+template <typename C, typename S, typename P, bool FF, int TY, int NW>
+cudaError_t prepare_sweep_g(lbch_handle* h, int k)
+{
+    cudaError_t e = prepare_sweep_v<C, S, P, FF, TY, NW, true>(h, k);
+    if (e == cudaSuccess && h->tau1) e = prepare_sweep_v<C, S, P, FF, TY, NW, false>(h, k);
+    return e;
+}
+
+template <typename C, typename S, typename P, bool FF>
+cudaError_t prepare_sweep_t(lbch_handle* h, int k)
+{
+    return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4>(h, k)
+         : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4>(h, k)
+         : k == 2 ? prepare_sweep_g<C, S, P, FF, 6, 2>(h, k) : prepare_sweep_g<C, S, P, FF, 3, 4>(h, k);
+}
+
+}  // namespace lbch
