@@ -5,14 +5,17 @@ Workload: Zalesak's slotted disk on a 256 x 256 periodic lattice (disk radius 64
 one full revolution, 12800 lattice steps, of the FP32 path; the FP64 path runs the same revolution
 beside it.  The metric is million lattice updates per second (MLUPS); the roofline fraction is the step
 kernel's algorithmic HBM bytes per launch over its average launch time, against the measured copy
-bandwidth.  A large-grid sweep (4096^2, inputs far larger than L2) reports the same kernel where HBM,
-not latency, bounds it.  L2 is flushed (a 512 MiB write) before every timed benchmark step.
+bandwidth, with the FP32 arithmetic roofline beside it.  A large-grid sweep (4096^2, inputs far larger
+than L2) reports the kernels where HBM or arithmetic, not latency, bounds them: at tau_g = 1 (phi only,
+16 B per update) and at tau_g = 0.8 (the populations too, 88 B per update on the FP32 path).  L2 is
+flushed (a 512 MiB write) before every timed benchmark step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -29,6 +32,33 @@ from paper_1805_00007_gb300 import workloads as wl  # noqa: E402
 
 REV_N = 256
 METRIC = "MLUPS and % HBM roofline (FP32 vs FP64 step) at stated phi error vs FP64 oracle"
+
+# FP32 operations per lattice update of the row-sweep step at tau_g = 1, Model II, float-float phi: the
+# operations of the per-node helpers (a fused multiply-add counts 2): mu 23, D = div(phi u) 34, grad mu and
+# grad D 28, force 11, velocity 4, equilibrium + source + collision 55, streaming sum and TwoSum 14.
+FLOPS_PER_LU_TAU1 = 169
+SMS, FP32_LANES_PER_SM = 152, 128
+
+# DRAM bytes (read + write) per launch of the headline kernel, from the ncu capture summarised in
+# profiles/ (kernel source hash, bytes); reported only while the kernel sources still hash the same.
+TRAFFIC = {"hash": None, "bytes_per_launch": None, "profile": None}
+KERNEL_SOURCES = ("lbch_kernels.cuh", "lbch_sweep.cuh", "lbch_sweep_launch.cuh")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1805_00007_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_name(k: dict, prec: str) -> str:
+    types = {"f32": "float,float,float,FF=1", "f64": "double,double,double,FF=0", "f16s": "float,__half,float,FF=0"}[prec]
+    if k["form"] in ("sweep", "sweep_tau1"):
+        nw = k["threads"] // 32
+        return f"ch_sweep_kernel<{types},TY={k['rows_per_warp']},NW={nw},GEN={int(k['form'] == 'sweep')}>"
+    return f"ch_step_kernel<{types},tile={k['tile'][0]}x{k['tile'][1]}>"
 
 
 def peaks():
@@ -156,12 +186,14 @@ def run_case(case, nsteps, tile=0):
     prec, n = parts[0], int(parts[1])
     tau = float(parts[2]) if len(parts) > 2 else 1.0
     pp, f0 = sweep_params(n, tau)
-    with abi.Simulation(pp, f0, prec=prec) as sim:
-        abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, tile)
+    with abi.Simulation(pp, f0, prec=prec, tune=tile < 0) as sim:
+        if tile >= 0:
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, tile)
         sim.step(nsteps)
         torch.cuda.synchronize()
         m = sim.observe(abi.LBCH_OBS_MASS)
-    print(json.dumps({"case": case, "steps": nsteps, "mass": m}))
+        kname = kernel_name(sim.kernel(), prec)
+    print(json.dumps({"case": case, "steps": nsteps, "mass": m, "kernel": kname}))
 
 
 def accuracy(prec, p, phi0, nsteps):
@@ -200,7 +232,7 @@ def main():
                     help="profiling case PREC_N[_TAU] (e.g. f32_4096, f32_4096_0.8): init and --case-steps steps "
                          "of that grid only")
     ap.add_argument("--case-steps", type=int, default=8)
-    ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case")
+    ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case (-1: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -260,6 +292,7 @@ def main():
         t_max = float(t.item())
     info32 = sim32.info()
     tile32 = sim32.tile
+    kern32 = sim32.kernel()
     phi32 = sim32.phi()
     sim32.close()
 
@@ -308,9 +341,9 @@ def main():
             dt = e0.elapsed_time(e1) / 1e3 / nst
             inf = sim.info()
             gbs = inf["bytes_per_lu"] * n * n / dt / 1e9
-            sweep[f"{prec}_{n}" + ("" if tau == 1.0 else f"_tau{tau}")] = {"MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6, "tile": sim.tile,
-                                   "bytes_per_lu": inf["bytes_per_lu"], "achieved_gbs": gbs,
-                                   "frac": gbs / hbm_peak}
+            sweep[f"{prec}_{n}" + ("" if tau == 1.0 else f"_tau{tau}")] = {
+                "MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6, "kernel": kernel_name(sim.kernel(), prec),
+                "bytes_per_lu": inf["bytes_per_lu"], "achieved_gbs": gbs, "frac": gbs / hbm_peak}
             sim.close()
 
 
@@ -333,7 +366,8 @@ def main():
             dt = e0.elapsed_time(e1) / 1e3 / nst
             inf = sim.info()
             gbs = inf["bytes_per_lu"] * enodes / dt / 1e9
-            ensemble[prec] = {"instances": len(eparams), "nodes": enodes, "MLUPS": enodes / dt / 1e6, "tile": sim.tile,
+            ensemble[prec] = {"instances": len(eparams), "nodes": enodes, "MLUPS": enodes / dt / 1e6,
+                              "kernel": kernel_name(sim.kernel(), prec),
                               "us_per_launch": dt * 1e6, "bytes_per_lu": inf["bytes_per_lu"],
                               "achieved_gbs": gbs, "frac": gbs / hbm_peak}
             sim.close()
@@ -347,6 +381,12 @@ def main():
         cpu = {"value": v, "unit": "MLUPS", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{sample} lattice steps of the 256x256 Zalesak workload ({dt:.1f} s)"}
 
+    clocks = clk.summary()
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_tflops = FLOPS_PER_LU_TAU1 * nodes / launch32 / 1e12
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["hash"] == kernel_hash() else None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -358,16 +398,19 @@ def main():
             "fp64": {"MLUPS": world * lu_per_rev / t64 / 1e6, "ms_per_step": 1e3 * t64,
                      "achieved_gbs": achieved64, "frac": achieved64 / hbm_peak},
             "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved32 / hbm_peak, "traffic": None,
-                         "kernel": f"ch_step_kernel<float,float,float,{tile32[0]},{tile32[1]},256>",
-                         "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6},
+                         "frac": achieved32 / hbm_peak, "traffic": traffic, "traffic_profile": TRAFFIC["profile"],
+                         "kernel": kernel_name(kern32, "f32"), "bytes_per_lu": info32["bytes_per_lu"],
+                         "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6,
+                         "alu": {"flops_per_lu": FLOPS_PER_LU_TAU1, "achieved": alu_tflops, "peak": peak_tflops,
+                                 "unit": "TFLOP/s", "frac": alu_tflops / peak_tflops,
+                                 "peak_from": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}},
             "sweep_4096": sweep,
             "ensemble_shear_256": ensemble,
             "accuracy_one_revolution": acc,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
                     "d2h_bytes_per_step": phi0.nbytes},
             "gpu_launches": args.steps * rev,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -19,7 +19,7 @@ PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
 
 # Exported symbols, as declared in include/lbch.h.
 SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free",
-           "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_stream", "lb_ch_test_hook",
+           "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_kernel_info", "lb_ch_stream", "lb_ch_test_hook",
            "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
            "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune")
 LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL = 1, 2, 3, 4, 5
@@ -71,6 +71,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_last_error.argtypes = []
     lib.lb_ch_last_error.restype = ctypes.c_char_p
     lib.lb_ch_info.argtypes = [vp, dp]
+    lib.lb_ch_kernel_info.argtypes = [vp, P(ctypes.c_int)]
     lib.lb_ch_stream.argtypes = [vp]
     lib.lb_ch_stream.restype = vp
     lib.lb_ch_test_hook.argtypes = [vp, ctypes.c_int, ctypes.c_long]
@@ -84,6 +85,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_adjoint_end.argtypes = [vp, vp, dp]
     lib.lb_ch_tune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]
     for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
+                 "lb_ch_kernel_info",
                  "lb_ch_test_hook", "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save",
                  "lb_ch_state_load", "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step",
                  "lb_ch_adjoint_end", "lb_ch_tune"):
@@ -153,6 +155,17 @@ def lb_ch_observe_all(h, what: int, n_inst: int) -> np.ndarray:
 def lb_ch_free(h):
     if h:
         _check(load().lb_ch_free(h), "lb_ch_free")
+
+
+KERNEL_FORMS = {0: "tile", 1: "sweep_tau1", 2: "sweep", 3: "coupled"}
+
+
+def lb_ch_kernel_info(h) -> dict:
+    """The step kernel in use: its form, shape index, tile, rows per warp and threads per block."""
+    out = (ctypes.c_int * 6)()
+    _check(load().lb_ch_kernel_info(h, out), "lb_ch_kernel_info")
+    return {"form": KERNEL_FORMS[out[0]], "shape": out[1], "tile": (out[2], out[3]), "rows_per_warp": out[4],
+            "threads": out[5]}
 
 
 def lb_ch_info(h) -> dict:
@@ -253,6 +266,9 @@ class Simulation:
 
     def info(self) -> dict:
         return lb_ch_info(self.h)
+
+    def kernel(self) -> dict:
+        return lb_ch_kernel_info(self.h)
 
     def close(self):
         if self.h:

@@ -989,6 +989,20 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     return LBCH_OK;
 }
 
+lbch_status lb_ch_kernel_info(lbch_handle* h, int* out)
+{
+    if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
+    const Shape sh = active_tile(h);
+    const bool sw = use_sweep(h);
+    out[0] = h->coupled ? 3 : (!sw ? 0 : (sweep_gen(h) ? 2 : 1));
+    out[1] = h->shape;
+    out[2] = sh.tx;
+    out[3] = sh.ty;
+    out[4] = sw ? kSweep[h->shape].ty : 0;
+    out[5] = h->coupled ? 256 : (sw ? 32 * kSweep[h->shape].nw : NT);
+    return LBCH_OK;
+}
+
 void* lb_ch_stream(lbch_handle* h) { return h ? (void*)h->stream : nullptr; }
 
 lbch_status lb_ch_state_bytes(lbch_handle* h, long long* bytes)

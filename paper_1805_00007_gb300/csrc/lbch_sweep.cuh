@@ -602,19 +602,32 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         using F = std::false_type;
         using Tr = std::true_type;
         SwRow<C> r0 = {}, r1 = {}, r2 = {};
-        // the pipeline fills: rows wy0 - 3 .. wy0 + 2 enter; mu from the third, collisions from the fifth
+        // the pipeline fills: rows wy0 - 3 .. wy0 + 2 enter; mu from the third, collisions from the fifth,
+        // outputs from the seventh
         row_step(F(), F(), F(), 0, r0, r1, r2);
         row_step(F(), F(), F(), 1, r2, r0, r1);
         row_step(Tr(), F(), F(), 2, r1, r2, r0);
         row_step(Tr(), F(), F(), 3, r0, r1, r2);
         row_step(Tr(), Tr(), F(), 4, r2, r0, r1);
         row_step(Tr(), Tr(), F(), 5, r1, r2, r0);
-        // steady state: one output row per row entering
+        if constexpr (GEN) {
+            // steady state, one row per iteration with the slots rotated by register moves: the body with
+            // the populations is large enough that three copies of it (the unrolled rotation below) cost
+            // more in instruction fetch than the moves do (measured: 54 against 49 GLUPS at 4096^2, FP32)
 #pragma unroll 1
-        for (int j = 6; j < TY + 6; j += 3) {
-            row_step(Tr(), Tr(), Tr(), j, r0, r1, r2);
-            row_step(Tr(), Tr(), Tr(), j + 1, r2, r0, r1);
-            row_step(Tr(), Tr(), Tr(), j + 2, r1, r2, r0);
+            for (int j = 6; j < TY + 6; j++) {
+                row_step(Tr(), Tr(), Tr(), j, r0, r1, r2);
+                SwRow<C> t_ = r0; r0 = r2; r2 = r1; r1 = t_;
+            }
+        } else {
+            // steady state: one output row per row entering, three rows per iteration so that the slots
+            // rotate by renaming (measured faster than one row with moves for this smaller body)
+#pragma unroll 1
+            for (int j = 6; j < TY + 6; j += 3) {
+                row_step(Tr(), Tr(), Tr(), j, r0, r1, r2);
+                row_step(Tr(), Tr(), Tr(), j + 1, r2, r0, r1);
+                row_step(Tr(), Tr(), Tr(), j + 2, r1, r2, r0);
+            }
         }
     };
 
