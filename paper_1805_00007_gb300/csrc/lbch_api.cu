@@ -106,6 +106,8 @@ cudaError_t launch_step_v(lbch_handle* h, int parity)
     a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
     a.lo_out = h->lo[parity ^ 1];
     a.ctl = h->ctl;
+    a.t_off = h->t_off;
+    a.t_adv = h->t_adv;
     // a programmatic dependent of the previous launch in the stream (the kernel waits on it before it
     // touches memory that launch writes), so its launch and prologue overlap the previous step's tail
     cudaLaunchConfig_t cfg = {};
@@ -835,7 +837,14 @@ lbch_status lb_ch_step(lbch_handle* h, long nsteps)
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
                 cudaError_t e = cudaSuccess;
-                for (int s = 0; s < kGraphChunk && e == cudaSuccess; s++) e = launch_step(h, parity ^ (s & 1));
+                // step k of the graph is the counter + k; only the last launch advances the counter
+                for (int s = 0; s < kGraphChunk && e == cudaSuccess; s++) {
+                    h->t_off = s;
+                    h->t_adv = s == kGraphChunk - 1 ? kGraphChunk : 0;
+                    e = launch_step(h, parity ^ (s & 1));
+                }
+                h->t_off = 0;
+                h->t_adv = 1;
                 cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
                 if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "step launch during capture"); }
                 if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
@@ -976,7 +985,7 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     // algorithmic HBM bytes per lattice update: read + write of the stored populations and of phi
     double bytes = 2.0 * (h->nq * (double)h->g_elem + (double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
-    if (h->tau1 && !h->force_general)  // only phi is read and written
+    if (use_sweep(h) && !sweep_gen(h))  // only phi is read and written
         bytes = 2.0 * ((double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
     if (h->coupled) {  // f and g read and written, phi read and written, u and p written and read
         const double e = h->prec == LBCH_F64 ? 8.0 : 4.0;
@@ -1115,7 +1124,17 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds)
 lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
 {
     if (!h || steps < 1) return fail(LBCH_EINVAL, "NULL handle or steps < 1");
-    const int ns = n_active(h);
+    // Candidates: every row-sweep configuration and every tile kernel shape.  The two forms give the same
+    // bits except on the half-storage path at tau_g = 1, where the tile kernel streams populations rounded
+    // to half and the sweep keeps only phi; there the sweep alone is a candidate.
+    struct Cand { bool tile; int shape; };
+    std::vector<Cand> cands;
+    if (!h->coupled) {
+        for (int k = 0; k < kSweepShapes; k++) cands.push_back({false, k});
+        if (!(h->prec == LBCH_F16S && h->tau1 && !h->force_general))
+            for (int k = 0; k < n_shapes(h->prec); k++) cands.push_back({true, k});
+    }
+    const int ns = (int)cands.size();
     if (ns > 1) {
         long long bytes = 0;
         lb_ch_state_bytes(h, &bytes);
@@ -1124,10 +1143,11 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
         lbch_status s = lb_ch_state_save(h, backup);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         float best_ms = 0.0f;
-        int best = h->shape;
+        Cand best = {h->force_tile, h->shape};
         if (s == LBCH_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
             for (int k = 0; k < ns && s == LBCH_OK; k++) {
-                h->shape = k;
+                h->force_tile = cands[k].tile;
+                h->shape = cands[k].shape;
                 cudaError_t e = cudaSuccess;
                 for (int w = 0; w < 2 && e == cudaSuccess; w++) { e = launch_step(h, (int)(h->n & 1)); h->n++; }
                 e = e == cudaSuccess ? cudaEventRecord(e0, h->stream) : e;
@@ -1137,7 +1157,7 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
                 float ms = 0.0f;
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                 if (e != cudaSuccess) s = cuda_fail(e, "timing a tile shape");
-                else if (k == 0 || ms < best_ms) { best_ms = ms; best = k; }
+                else if (k == 0 || ms < best_ms) { best_ms = ms; best = cands[k]; }
                 lbch_status r = lb_ch_state_load(h, backup);  // every candidate starts from the same state
                 if (s == LBCH_OK) s = r;
             }
@@ -1145,8 +1165,9 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         cudaFree(backup);
+        h->force_tile = best.tile;
+        h->shape = best.shape;
         if (s != LBCH_OK) return s;
-        h->shape = best;
         for (int k = 0; k < 2; k++)  // graphs captured earlier launch the previous shape's kernel
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
     }

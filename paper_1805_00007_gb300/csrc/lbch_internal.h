@@ -12,8 +12,8 @@ struct Shape { int tx, ty; };
 
 // Configurations of the row-sweep kernel (tau_g = 1): TY output rows per warp, NW warps per CTA; a tile
 // is 56 columns by NW TY rows.  lb_ch_tune picks among them as among the tile shapes.
-struct SweepCfg { int ty, nw; };
-constexpr SweepCfg kSweep[4] = {{12, 4}, {6, 4}, {6, 2}, {3, 4}};
+struct SweepCfg { int ty, nw; bool compact; };
+constexpr SweepCfg kSweep[4] = {{12, 4, false}, {6, 4, false}, {6, 2, true}, {3, 4, true}};
 constexpr int kSweepShapes = 4;
 constexpr int kSweepW = 56;
 inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw}; }
@@ -57,6 +57,7 @@ struct lbch_handle {
     double* result = nullptr;   // n_inst * RED_NV doubles
     int chunks = 0;
     long long n = 0;            // host mirror of the step index
+    int t_off = 0, t_adv = 1;   // the next launch's step offset and counter advance (see Ctl)
     int debug_skip = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     double* h_stage = nullptr;  // pinned host staging

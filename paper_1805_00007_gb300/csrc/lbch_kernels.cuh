@@ -65,7 +65,8 @@ template <typename C> __device__ __forceinline__ const Consts<C>& consts(const I
 template <> __device__ __forceinline__ const Consts<double>& consts<double>(const InstDev& I) { return I.cd; }
 template <> __device__ __forceinline__ const Consts<float>& consts<float>(const InstDev& I) { return I.cf; }
 
-// Step counter shared by the launches of one handle: the last CTA of each step advances `time`.
+// Step counter shared by the launches of one handle.  A launch's step is time + its offset; the launch
+// that ends a batch (a captured graph of steps, or a single step) advances `time` from its last CTA.
 struct Ctl {
     long long time;
     unsigned int done;
@@ -338,6 +339,8 @@ struct StepArgs {
     P* phi_out;
     float* lo_out;       // low part of phi on the float path
     Ctl* ctl;
+    int t_off;           // this launch's step is ctl->time + t_off
+    int t_adv;           // when nonzero, the launch's last CTA advances ctl->time by t_adv
 };
 
 template <typename C, typename S, typename P, int TX, int TY>
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
     grid_launch_dependents();
     if (tid == 0) s_time = a.ctl->time;
     __syncthreads();
-    const long long n = s_time;
+    const long long n = s_time + a.t_off;
 
     // producer: thread 0 issues the boxes of tile t into stage s
     auto issue = [&](int t, int s) {
@@ -657,14 +660,14 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         }
     }
 
-    // the last CTA of the launch advances the step counter read by the next launch.  No fence: the
-    // counter orders no other data, every CTA read the time before its increment, and the next launch
-    // reads it only after this grid has completed (kernel boundary or the dependency wait).
-    if (tid == 0) {
+    // the last CTA of a batch's last launch advances the step counter read by the next launch.  No
+    // fence: the counter orders no other data, every CTA read the time before its increment, and the next
+    // launch reads it only after this grid has completed (kernel boundary or the dependency wait).
+    if (a.t_adv && tid == 0) {
         unsigned int prev = atomicAdd(&a.ctl->done, 1u);
         if (prev == gridDim.x - 1) {
             a.ctl->done = 0u;
-            a.ctl->time = n + 1;
+            a.ctl->time = n - a.t_off + a.t_adv;
         }
     }
 }

@@ -47,6 +47,8 @@ struct SweepArgs {
     P* phi_out;
     float* lo_out;          // low part of phi on the float-float path
     Ctl* ctl;
+    int t_off;              // this launch's step is ctl->time + t_off
+    int t_adv;              // when nonzero, the launch's last CTA advances ctl->time by t_adv
     S* g_out;               // populations (GEN): g[(row * nq + plane) * pitch + column]
     int rows;               // stored rows of the population arrays
 };
@@ -93,6 +95,11 @@ template <typename S, typename C> __device__ __forceinline__ typename Pair<S>::T
 }
 template <> __device__ __forceinline__ __half2 mkpair<__half, float>(float x, float y) { return __floats2half2_rn(x, y); }
 
+
+// A stage flag known at compile time (it converts to a constant bool on the device).
+template <bool V> struct Flag {
+    __host__ __device__ constexpr operator bool() const { return V; }
+};
 
 template <typename C> __device__ __forceinline__ C from_left(C v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 template <typename C> __device__ __forceinline__ C from_right(C v) { return __shfl_down_sync(0xffffffffu, v, 1); }
@@ -156,13 +163,13 @@ __device__ __forceinline__ void store_g_images(S* g_out, long long row0, int pit
     }
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT>
 __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     ch_sweep_kernel(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lo,
                     const __grid_constant__ CUtensorMap tm_grow, const __grid_constant__ CUtensorMap tm_lorow,
                     SweepArgs<C, S, P> a)
 {
-    static_assert(TY % 3 == 0, "the sweep advances three rows per unrolled step");
+    static_assert(COMPACT || TY % 3 == 0, "the sweep advances three rows per unrolled step");
     static_assert(TY + 6 <= 32, "the Y tables of a warp's rows are held one row per lane");
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
     using P2 = typename Pair<P>::T;
@@ -221,16 +228,6 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         }
     }
     if ((int)blockIdx.x < a.total_tiles) locate(blockIdx.x);
-    // Launched as a programmatic dependent of the previous step: nothing that step writes (phi, the step
-    // counter) is read before this wait.
-    grid_dependency_wait();
-    grid_launch_dependents();
-    if (tid == 0) {
-        s_time = a.ctl->time;
-        if (s_tile_inst >= 0) s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time);
-    }
-    __syncthreads();
-    const long long n = s_time;
 
     // producer: thread 0 issues the boxes of tile t into stage s
     auto issue = [&](int t, int s) {
@@ -246,12 +243,21 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         if (FF && !GEN) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, bx, I.row0 + by, &mbar[s]);
     };
 
+    // Launched as a programmatic dependent of the previous step: nothing that step writes (phi, the step
+    // counter) is read before this wait.  The first boxes are issued before the counter is read, so the
+    // two latencies overlap.
+    grid_dependency_wait();
+    grid_launch_dependents();
     if (tid == 0) {
         for (int j = 0; j < 2; j++) {
             const int t = blockIdx.x + j * stride;
             if (t < a.total_tiles && !(a.debug_skip && blockIdx.x == 0 && j == 0)) issue(t, j);
         }
+        s_time = a.ctl->time;
+        if (s_tile_inst >= 0) s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
     }
+    __syncthreads();
+    const long long n = s_time + a.t_off;
 
     // GEN: this warp's ring.  Fill n goes to slot n % RING and completes phase n / RING of the slot's
     // mbarrier; the fills and their uses run in the same row order, tile after tile.
@@ -311,7 +317,9 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         // of row yf - 1; COL: collide row yf - 2; OUT: complete phi(t+1) of row yf - 3.  The three flags
         // are false only while the pipeline fills.
         auto row_step = [&](auto mu_t, auto col_t, auto out_t, const int j, SwRow<C>& A, SwRow<C>& B, SwRow<C>& Cs) {
-            constexpr bool MU = decltype(mu_t)::value, COL = decltype(col_t)::value, OUT = decltype(out_t)::value;
+            // the flags are compile-time constants (Flag<true> / Flag<false>) in the peeled and unrolled
+            // forms and warp-uniform runtime values in the compact form
+            const bool MU = mu_t, COL = col_t, OUT = out_t;
             const int yf = wy0 - 3 + j;
             {
                 const P2 v = *reinterpret_cast<const P2*>(box + j * BW);
@@ -322,7 +330,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                 A.y1 = __shfl_sync(0xffffffffu, ly1, j);
                 A.y2 = __shfl_sync(0xffffffffu, ly2, j);
             }
-            if constexpr (MU) {
+            if (MU) {
                 B.ma = node_mu(B.pa, B.pb, B.pL, A.pa, Cs.pa, A.pb, A.pL, Cs.pb, Cs.pL, beta, kappa, phiA, phiB);
                 B.mb = node_mu(B.pb, B.pR, B.pa, A.pb, Cs.pb, A.pR, A.pa, Cs.pR, Cs.pa, beta, kappa, phiA, phiB);
                 B.mL = from_left(B.mb);
@@ -338,7 +346,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             }
             const int yc = yf - 2;
             C p8a = C(0), p8b = C(0), p7a = C(0), p7b = C(0), p4a = C(0), p4b = C(0);
-            if constexpr (COL) {
+            if (COL) {
                 // GEN: the populations g(t) of row yc (collision row k = j - 4 of the warp)
                 C ga[9], gb[9];
                 if constexpr (GEN) {
@@ -462,7 +470,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                     }
                 }
             }
-            if constexpr (OUT && GEN) {
+            if (GEN && OUT) {
                 // g(t+1) and phi(t+1) of row yo = yf - 3 (slot A): every population has arrived
                 const int yo = yf - 3;
                 const C suma = stream_sum(A.n1a, A.n2a, A.n3a, A.n4a, A.n5a, A.n6a, A.n7a, A.n8a);
@@ -527,13 +535,13 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                     }
                 }
             }
-            if constexpr (COL && GEN) {
+            if (GEN && COL) {
                 // the slot of collision row j - 5 (read by the collision before and the output just done)
                 // takes row j - 1 = k + 3
                 __syncwarp();
                 g_fetch(j - 1);
             }
-            if constexpr (OUT && !GEN) {
+            if (!GEN && OUT) {
                 // phi(t+1) of row yo = yf - 3 (slot A), with g*_4, g*_7, g*_8 of row yo + 1 just computed
                 const int yo = yf - 3;
                 C Ra, Rb, Ca, Cb, La, Lb;
@@ -599,9 +607,19 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             }
         };
 
-        using F = std::false_type;
-        using Tr = std::true_type;
+        using F = Flag<false>;
+        using Tr = Flag<true>;
         SwRow<C> r0 = {}, r1 = {}, r2 = {};
+        if constexpr (COMPACT) {
+            // One loop body for the whole sweep, the pipeline's stages switched on by row: the least code,
+            // for grids too small to fill the GPU, where every launch fetches its instructions afresh.
+#pragma unroll 1
+            for (int j = 0; j < TY + 6; j++) {
+                row_step(j >= 2, j >= 4, j >= 6, j, r0, r1, r2);
+                SwRow<C> t_ = r0; r0 = r2; r2 = r1; r1 = t_;
+            }
+            return;
+        }
         // the pipeline fills: rows wy0 - 3 .. wy0 + 2 enter; mu from the third, collisions from the fifth,
         // outputs from the seventh
         row_step(F(), F(), F(), 0, r0, r1, r2);
@@ -671,13 +689,13 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         }
     }
 
-    // the last CTA of the launch advances the step counter read by the next launch (no fence: the
-    // counter orders no other data, and the next launch reads it only after this grid has completed)
-    if (tid == 0) {
+    // the last CTA of a batch's last launch advances the step counter read by the next launch (no fence:
+    // the counter orders no other data, and the next launch reads it only after this grid has completed)
+    if (a.t_adv && tid == 0) {
         const unsigned int prev = atomicAdd(&a.ctl->done, 1u);
         if (prev == gridDim.x - 1) {
             a.ctl->done = 0u;
-            a.ctl->time = n + 1;
+            a.ctl->time = n - a.t_off + a.t_adv;
         }
     }
 }

@@ -6,7 +6,7 @@
 
 namespace lbch {
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT>
 cudaError_t launch_sweep_v(lbch_handle* h, int parity)
 {
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
@@ -22,6 +22,8 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
     a.lo_out = h->lo[parity ^ 1];
     a.ctl = h->ctl;
+    a.t_off = h->t_off;
+    a.t_adv = h->t_adv;
     a.g_out = static_cast<S*>(h->g[parity ^ 1]);
     a.rows = h->rows;
     cudaLaunchConfig_t cfg = {};
@@ -34,34 +36,34 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>, ps.tm_phi[parity], ps.tm_lo[parity],
+    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT>, ps.tm_phi[parity], ps.tm_lo[parity],
                               h->tm_grow[parity], h->tm_lorow[parity], a);
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool COMPACT>
 cudaError_t launch_sweep_g(lbch_handle* h, int parity)
 {
-    return sweep_gen(h) ? launch_sweep_v<C, S, P, FF, TY, NW, true>(h, parity)
-                        : launch_sweep_v<C, S, P, FF, TY, NW, false>(h, parity);
+    return sweep_gen(h) ? launch_sweep_v<C, S, P, FF, TY, NW, true, COMPACT>(h, parity)
+                        : launch_sweep_v<C, S, P, FF, TY, NW, false, COMPACT>(h, parity);
 }
 
 template <typename C, typename S, typename P, bool FF>
 cudaError_t launch_sweep_t(lbch_handle* h, int parity)
 {
     switch (h->shape) {
-    case 0: return launch_sweep_g<C, S, P, FF, 12, 4>(h, parity);
-    case 1: return launch_sweep_g<C, S, P, FF, 6, 4>(h, parity);
-    case 2: return launch_sweep_g<C, S, P, FF, 6, 2>(h, parity);
-    default: return launch_sweep_g<C, S, P, FF, 3, 4>(h, parity);
+    case 0: return launch_sweep_g<C, S, P, FF, 12, 4, false>(h, parity);
+    case 1: return launch_sweep_g<C, S, P, FF, 6, 4, false>(h, parity);
+    case 2: return launch_sweep_g<C, S, P, FF, 6, 2, true>(h, parity);
+    default: return launch_sweep_g<C, S, P, FF, 3, 4, true>(h, parity);
     }
 }
 
 // Dynamic shared memory of one sweep kernel and the persistent grid that fits the device.
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT>
 cudaError_t prepare_sweep_v(lbch_handle* h, int k)
 {
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
-    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN>;
+    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -74,20 +76,20 @@ cudaError_t prepare_sweep_v(lbch_handle* h, int k)
     return cudaSuccess;
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool COMPACT>
 cudaError_t prepare_sweep_g(lbch_handle* h, int k)
 {
-    cudaError_t e = prepare_sweep_v<C, S, P, FF, TY, NW, true>(h, k);
-    if (e == cudaSuccess && h->tau1) e = prepare_sweep_v<C, S, P, FF, TY, NW, false>(h, k);
+    cudaError_t e = prepare_sweep_v<C, S, P, FF, TY, NW, true, COMPACT>(h, k);
+    if (e == cudaSuccess && h->tau1) e = prepare_sweep_v<C, S, P, FF, TY, NW, false, COMPACT>(h, k);
     return e;
 }
 
 template <typename C, typename S, typename P, bool FF>
 cudaError_t prepare_sweep_t(lbch_handle* h, int k)
 {
-    return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4>(h, k)
-         : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4>(h, k)
-         : k == 2 ? prepare_sweep_g<C, S, P, FF, 6, 2>(h, k) : prepare_sweep_g<C, S, P, FF, 3, 4>(h, k);
+    return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4, false>(h, k)
+         : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4, false>(h, k)
+         : k == 2 ? prepare_sweep_g<C, S, P, FF, 6, 2, true>(h, k) : prepare_sweep_g<C, S, P, FF, 3, 4, true>(h, k);
 }
 
 }  // namespace lbch

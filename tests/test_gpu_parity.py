@@ -202,10 +202,15 @@ def test_every_tile_shape_gives_the_same_bits(prec, nshapes, tile, general):
             assert np.array_equal(a, b)
 
 
-def test_tune_keeps_the_state():
-    p, phi0, _ = wl.zalesak(n=128)
-    with abi.Simulation(p, phi0, prec="f32") as a, abi.Simulation(p, phi0, prec="f32", tune=True) as b:
-        assert b.tile in ((56, 48), (56, 24), (56, 12))  # the row-sweep configurations (tau_g = 1)
+@pytest.mark.parametrize("prec,tau", [("f32", 1.0), ("f64", 1.0), ("f16s", 1.0), ("f32", 0.8), ("f16s", 0.8)])
+def test_tune_keeps_the_state(prec, tau):
+    """The autotuner chooses among kernel forms and shapes that give the same bits, and leaves the state
+    where it found it."""
+    p, phi0, _ = wl.zalesak(n=128, tau=tau)
+    with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(p, phi0, prec=prec, tune=True) as b:
+        assert b.tile in ((56, 48), (56, 24), (56, 12), (32, 16), (32, 8), (16, 8))  # sweep or tile kernel
+        if prec == "f16s" and tau == 1.0:
+            assert b.kernel()["form"] == "sweep_tau1"
         assert b.observe(abi.LBCH_OBS_STEP) == 0
         a.step(100)
         b.step(100)
