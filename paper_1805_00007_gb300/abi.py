@@ -239,7 +239,10 @@ class Simulation:
         self.params = [params] if isinstance(params, dict) else list(params)
         self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         self.h = lb_ch_init(self.params, [phi0] if isinstance(params, dict) else list(phi0), self.prec, stream)
-        self.tile = lb_ch_tune(self.h) if tune else None
+        # enough timed steps per candidate that small grids (a few microseconds per step) are not decided
+        # by timer noise: about 2e7 lattice updates, between 20 and 400 steps
+        nodes = sum(int(p["nx"]) * int(p["ny"]) for p in self.params)
+        self.tile = lb_ch_tune(self.h, max(20, min(400, 20_000_000 // max(nodes, 1)))) if tune else None
 
     def step(self, nsteps: int):
         lb_ch_step(self.h, nsteps)
