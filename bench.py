@@ -58,7 +58,7 @@ def kernel_name(k: dict, prec: str) -> str:
     if k["form"] in ("sweep", "sweep_tau1"):
         nw = k["threads"] // 32
         return f"ch_sweep_kernel<{types},TY={k['rows_per_warp']},NW={nw},GEN={int(k['form'] == 'sweep')}>"
-    return f"ch_step_kernel<{types},tile={k['tile'][0]}x{k['tile'][1]}>"
+    return f"ch_step_kernel<{types},tile={k['tile'][0]}x{k['tile'][1]},TAU1={int(k['form'] == 'tile_tau1')}>"
 
 
 def peaks():

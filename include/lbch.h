@@ -155,7 +155,8 @@ lbch_status lb_ch_info(lbch_handle* h, double* out);
 
 /* Which step kernel advances the handle, for a caller who reports on it: out[0] = its form (0 = tile
  * kernel, 1 = row sweep without the populations -- every instance has tau_g = 1 --, 2 = row sweep with
- * the populations, 3 = the coupled Navier-Stokes kernels), out[1] = the shape index in use (see
+ * the populations, 3 = the coupled Navier-Stokes kernels, 4 = tile kernel without the populations),
+ * out[1] = the shape index in use (see
  * lb_ch_tune), out[2] x out[3] = output nodes of one tile, out[4] = output rows per warp of the row
  * sweep (0 otherwise), out[5] = threads per thread block.  out must hold 6 ints. */
 lbch_status lb_ch_kernel_info(lbch_handle* h, int* out);

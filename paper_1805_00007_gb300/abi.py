@@ -157,7 +157,7 @@ def lb_ch_free(h):
         _check(load().lb_ch_free(h), "lb_ch_free")
 
 
-KERNEL_FORMS = {0: "tile", 1: "sweep_tau1", 2: "sweep", 3: "coupled"}
+KERNEL_FORMS = {0: "tile", 1: "sweep_tau1", 2: "sweep", 3: "coupled", 4: "tile_tau1"}
 
 
 def lb_ch_kernel_info(h) -> dict:

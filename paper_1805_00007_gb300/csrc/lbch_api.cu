@@ -127,7 +127,9 @@ cudaError_t launch_step_v(lbch_handle* h, int parity)
 template <typename C, typename S, typename P, int TX, int TY>
 cudaError_t launch_step_t(lbch_handle* h, int parity)
 {
-    return launch_step_v<C, S, P, TX, TY, false>(h, parity);
+    // at tau_g = 1 the tile kernel drops the populations too (exact, as in the row sweep)
+    return (h->tau1 && !h->force_general) ? launch_step_v<C, S, P, TX, TY, true>(h, parity)
+                                          : launch_step_v<C, S, P, TX, TY, false>(h, parity);
 }
 
 // The row-sweep kernel steps the handle (its shape index then names a sweep configuration), without the
@@ -169,6 +171,9 @@ cudaError_t prepare_step_t(lbch_handle* h, int k)
     using L = StepShape<C, S, P, TX, TY>;
     auto kern = ch_step_kernel<C, S, P, TX, TY, NT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ch_step_kernel<C, S, P, TX, TY, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);
@@ -985,7 +990,7 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     // algorithmic HBM bytes per lattice update: read + write of the stored populations and of phi
     double bytes = 2.0 * (h->nq * (double)h->g_elem + (double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
-    if (use_sweep(h) && !sweep_gen(h))  // only phi is read and written
+    if (h->tau1 && !h->force_general)  // only phi is read and written (either kernel form)
         bytes = 2.0 * ((double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
     if (h->coupled) {  // f and g read and written, phi read and written, u and p written and read
         const double e = h->prec == LBCH_F64 ? 8.0 : 4.0;
@@ -1003,7 +1008,7 @@ lbch_status lb_ch_kernel_info(lbch_handle* h, int* out)
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     const Shape sh = active_tile(h);
     const bool sw = use_sweep(h);
-    out[0] = h->coupled ? 3 : (!sw ? 0 : (sweep_gen(h) ? 2 : 1));
+    out[0] = h->coupled ? 3 : (!sw ? (sweep_gen(h) ? 0 : 4) : (sweep_gen(h) ? 2 : 1));
     out[1] = h->shape;
     out[2] = sh.tx;
     out[3] = sh.ty;

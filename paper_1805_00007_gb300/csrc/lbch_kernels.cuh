@@ -400,20 +400,18 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
     __shared__ InstDev s_I;  // the current tile's instance, copied when the instance changes
 
     const int tid = threadIdx.x;
+    const int stride = gridDim.x;
     if (tid == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         fence_mbar_init();
         s_tile_inst = -1;
+        if ((int)blockIdx.x < a.total_tiles) {  // instance data are constant: read before the dependency wait
+            const int k = find_inst(a.tile_begin, a.n_inst, blockIdx.x);
+            s_I = a.inst[k];
+            s_tile_inst = k;
+        }
     }
-    // Launched as a programmatic dependent of the previous step: everything above overlaps its tail;
-    // nothing it writes (phi, g, the step counter) is touched before this wait.  The next step may then
-    // start its own prologue (it waits in turn before reading what this step writes).
-    grid_dependency_wait();
-    grid_launch_dependents();
-    if (tid == 0) s_time = a.ctl->time;
-    __syncthreads();
-    const long long n = s_time + a.t_off;
 
     // producer: thread 0 issues the boxes of tile t into stage s
     auto issue = [&](int t, int s) {
@@ -438,13 +436,21 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         bulk_load(tb + 2 * L::XT_BYTES + L::YT_BYTES, tY1 + I.ylen + y0, L::YT_BYTES, &mbar[s]);
     };
 
-    const int stride = gridDim.x;
+    // Launched as a programmatic dependent of the previous step: everything above overlaps its tail;
+    // nothing it writes (phi, g, the step counter) is touched before this wait.  The first boxes are
+    // issued before the counter is read, so the two latencies overlap.
+    grid_dependency_wait();
+    grid_launch_dependents();
     if (tid == 0) {
         for (int j = 0; j < 2; j++) {
             int t = blockIdx.x + j * stride;
             if (t < a.total_tiles && !(a.debug_skip && blockIdx.x == 0 && j == 0)) issue(t, j);
         }
+        s_time = a.ctl->time;
+        if (s_tile_inst >= 0) s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
     }
+    __syncthreads();
+    const long long n = s_time + a.t_off;
 
     for (int it = 0;; it++) {
         const int t = blockIdx.x + it * stride;

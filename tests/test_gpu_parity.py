@@ -264,6 +264,15 @@ def test_tau1_kernel_equals_general_kernel_bitwise(prec):
     if prec != "f16s":
         for x, y in zip(res[0], res[1]):
             assert np.array_equal(x, y)
+        # the tile kernel drops the populations at tau_g = 1 too: the same bits again
+        with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(list(params), list(fields), prec=prec) as b:
+            for h in (a.h, b.h):
+                abi.lb_ch_test_hook(h, abi.LBCH_HOOK_TILE_KERNEL, 1)
+            assert a.kernel()["form"] == "tile_tau1"
+            a.step(90)
+            b.step(90)
+            for x, y in zip([a.phi()] + [b.phi(k) for k in range(3)], res[0]):
+                assert np.array_equal(x, y)
     else:
         ref, _ = oracle.simulate(p, phi0, 90)
         assert _maxdiff(res[0][0], ref) <= _maxdiff(res[1][0], ref) + 1e-6
