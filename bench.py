@@ -58,7 +58,8 @@ def kernel_name(k: dict, prec: str) -> str:
     if k["form"] in ("sweep", "sweep_tau1"):
         nw = k["threads"] // 32
         return f"ch_sweep_kernel<{types},TY={k['rows_per_warp']},NW={nw},GEN={int(k['form'] == 'sweep')}>"
-    return f"ch_step_kernel<{types},tile={k['tile'][0]}x{k['tile'][1]},TAU1={int(k['form'] == 'tile_tau1')}>"
+    return (f"ch_step_kernel<{types},tile={k['tile'][0]}x{k['tile'][1]},NT={k['threads']},"
+            f"TAU1={int(k['form'] == 'tile_tau1')}>")
 
 
 def peaks():
@@ -178,7 +179,7 @@ def sweep_params(n, tau=1.0):
     return pp, wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
 
 
-def run_case(case, nsteps, tile=0):
+def run_case(case, nsteps, tile=0, form="sweep"):
     """One grid, no timing: the command ncu profiles."""
     import torch
     from paper_1805_00007_gb300 import abi
@@ -188,6 +189,7 @@ def run_case(case, nsteps, tile=0):
     pp, f0 = sweep_params(n, tau)
     with abi.Simulation(pp, f0, prec=prec, tune=tile < 0) as sim:
         if tile >= 0:
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, int(form == "tile"))
             abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, tile)
         sim.step(nsteps)
         torch.cuda.synchronize()
@@ -233,11 +235,12 @@ def main():
                          "of that grid only")
     ap.add_argument("--case-steps", type=int, default=8)
     ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case (-1: autotune)")
+    ap.add_argument("--case-form", default="sweep", choices=["sweep", "tile"], help="kernel form for --case")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
-        return run_case(args.case, args.case_steps, args.case_tile)
+        return run_case(args.case, args.case_steps, args.case_tile, args.case_form)
 
     import torch
     import torch.distributed as dist

@@ -53,9 +53,9 @@ constexpr int kGraphChunk = 64;  // steps per captured graph (even, so the ping-
 // times them on the handle's own problem and keeps the fastest; the first one is the default.  Every
 // TX divides 32 and every TY divides 16, so one storage layout serves all shapes.
 constexpr int NT = 256;
-constexpr Shape kShapes64[2] = {{32, 8}, {16, 8}};
-constexpr Shape kShapesF[3] = {{32, 16}, {32, 8}, {16, 8}};
-inline int n_shapes(int prec) { return prec == LBCH_F64 ? 2 : 3; }
+constexpr Shape kShapes64[3] = {{32, 8, 256}, {16, 8, 256}, {32, 8, 512}};
+constexpr Shape kShapesF[4] = {{32, 16, 256}, {32, 8, 256}, {16, 8, 256}, {32, 16, 512}};
+inline int n_shapes(int prec) { return prec == LBCH_F64 ? 3 : 4; }
 inline Shape shape_of(int prec, int k) { return prec == LBCH_F64 ? kShapes64[k] : kShapesF[k]; }
 
 
@@ -89,7 +89,7 @@ __attribute__((visibility("hidden"))) void lbch_set_last_error(const char* msg)
 namespace {
 
 
-template <typename C, typename S, typename P, int TX, int TY, bool TAU1>
+template <typename C, typename S, typename P, int TX, int TY, int NTT, bool TAU1>
 cudaError_t launch_step_v(lbch_handle* h, int parity)
 {
     using L = StepShape<C, S, P, TX, TY>;
@@ -112,7 +112,7 @@ cudaError_t launch_step_v(lbch_handle* h, int parity)
     // touches memory that launch writes), so its launch and prologue overlap the previous step's tail
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ps.grid);
-    cfg.blockDim = dim3(NT);
+    cfg.blockDim = dim3(NTT);
     cfg.dynamicSmemBytes = L::BYTES;
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
@@ -120,16 +120,16 @@ cudaError_t launch_step_v(lbch_handle* h, int parity)
     attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ch_step_kernel<C, S, P, TX, TY, NT, TAU1>, ps.tm_g[parity], ps.tm_phi[parity],
+    return cudaLaunchKernelEx(&cfg, ch_step_kernel<C, S, P, TX, TY, NTT, TAU1>, ps.tm_g[parity], ps.tm_phi[parity],
                               ps.tm_lo[parity], a);
 }
 
-template <typename C, typename S, typename P, int TX, int TY>
+template <typename C, typename S, typename P, int TX, int TY, int NTT = NT>
 cudaError_t launch_step_t(lbch_handle* h, int parity)
 {
     // at tau_g = 1 the tile kernel drops the populations too (exact, as in the row sweep)
-    return (h->tau1 && !h->force_general) ? launch_step_v<C, S, P, TX, TY, true>(h, parity)
-                                          : launch_step_v<C, S, P, TX, TY, false>(h, parity);
+    return (h->tau1 && !h->force_general) ? launch_step_v<C, S, P, TX, TY, NTT, true>(h, parity)
+                                          : launch_step_v<C, S, P, TX, TY, NTT, false>(h, parity);
 }
 
 // The row-sweep kernel steps the handle (its shape index then names a sweep configuration), without the
@@ -165,18 +165,18 @@ cudaError_t prepare_sweep(lbch_handle* h, int k)
 }
 
 // Dynamic shared memory of the step kernel, and the persistent grid that fits the device, for shape k.
-template <typename C, typename S, typename P, int TX, int TY>
+template <typename C, typename S, typename P, int TX, int TY, int NTT = NT>
 cudaError_t prepare_step_t(lbch_handle* h, int k)
 {
     using L = StepShape<C, S, P, TX, TY>;
-    auto kern = ch_step_kernel<C, S, P, TX, TY, NT, false>;
+    auto kern = ch_step_kernel<C, S, P, TX, TY, NTT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ch_step_kernel<C, S, P, TX, TY, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(ch_step_kernel<C, S, P, TX, TY, NTT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTT, L::BYTES);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
@@ -189,13 +189,16 @@ cudaError_t prepare_step(lbch_handle* h, int k)
 {
     switch (h->prec) {
     case LBCH_F64:
-        return k == 0 ? prepare_step_t<double, double, double, 32, 8>(h, k) : prepare_step_t<double, double, double, 16, 8>(h, k);
+        return k == 0 ? prepare_step_t<double, double, double, 32, 8>(h, k)
+             : k == 1 ? prepare_step_t<double, double, double, 16, 8>(h, k) : prepare_step_t<double, double, double, 32, 8, 512>(h, k);
     case LBCH_F32:
         return k == 0 ? prepare_step_t<float, float, float, 32, 16>(h, k)
-             : k == 1 ? prepare_step_t<float, float, float, 32, 8>(h, k) : prepare_step_t<float, float, float, 16, 8>(h, k);
+             : k == 1 ? prepare_step_t<float, float, float, 32, 8>(h, k)
+             : k == 2 ? prepare_step_t<float, float, float, 16, 8>(h, k) : prepare_step_t<float, float, float, 32, 16, 512>(h, k);
     default:
         return k == 0 ? prepare_step_t<float, __half, float, 32, 16>(h, k)
-             : k == 1 ? prepare_step_t<float, __half, float, 32, 8>(h, k) : prepare_step_t<float, __half, float, 16, 8>(h, k);
+             : k == 1 ? prepare_step_t<float, __half, float, 32, 8>(h, k)
+             : k == 2 ? prepare_step_t<float, __half, float, 16, 8>(h, k) : prepare_step_t<float, __half, float, 32, 16, 512>(h, k);
     }
 }
 
@@ -260,13 +263,16 @@ cudaError_t launch_step(lbch_handle* h, int parity)
     const int k = h->shape;
     switch (h->prec) {
     case LBCH_F64:
-        return k == 0 ? launch_step_t<double, double, double, 32, 8>(h, parity) : launch_step_t<double, double, double, 16, 8>(h, parity);
+        return k == 0 ? launch_step_t<double, double, double, 32, 8>(h, parity)
+             : k == 1 ? launch_step_t<double, double, double, 16, 8>(h, parity) : launch_step_t<double, double, double, 32, 8, 512>(h, parity);
     case LBCH_F32:
         return k == 0 ? launch_step_t<float, float, float, 32, 16>(h, parity)
-             : k == 1 ? launch_step_t<float, float, float, 32, 8>(h, parity) : launch_step_t<float, float, float, 16, 8>(h, parity);
+             : k == 1 ? launch_step_t<float, float, float, 32, 8>(h, parity)
+             : k == 2 ? launch_step_t<float, float, float, 16, 8>(h, parity) : launch_step_t<float, float, float, 32, 16, 512>(h, parity);
     default:
         return k == 0 ? launch_step_t<float, __half, float, 32, 16>(h, parity)
-             : k == 1 ? launch_step_t<float, __half, float, 32, 8>(h, parity) : launch_step_t<float, __half, float, 16, 8>(h, parity);
+             : k == 1 ? launch_step_t<float, __half, float, 32, 8>(h, parity)
+             : k == 2 ? launch_step_t<float, __half, float, 16, 8>(h, parity) : launch_step_t<float, __half, float, 32, 16, 512>(h, parity);
     }
 }
 
@@ -1013,7 +1019,7 @@ lbch_status lb_ch_kernel_info(lbch_handle* h, int* out)
     out[2] = sh.tx;
     out[3] = sh.ty;
     out[4] = sw ? kSweep[h->shape].ty : 0;
-    out[5] = h->coupled ? 256 : (sw ? 32 * kSweep[h->shape].nw : NT);
+    out[5] = h->coupled ? 256 : sh.nt;
     return LBCH_OK;
 }
 

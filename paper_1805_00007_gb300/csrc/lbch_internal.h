@@ -7,8 +7,8 @@
 #include "lbch_kernels.cuh"
 #include "lbch_ns.cuh"
 
-constexpr int kMaxShapes = 3;
-struct Shape { int tx, ty; };
+constexpr int kMaxShapes = 4;
+struct Shape { int tx, ty, nt; };  // output nodes of a tile, threads per block
 
 // Configurations of the row-sweep kernel (tau_g = 1): TY output rows per warp, NW warps per CTA; a tile
 // is 56 columns by NW TY rows.  lb_ch_tune picks among them as among the tile shapes.
@@ -16,7 +16,7 @@ struct SweepCfg { int ty, nw; bool compact; };
 constexpr SweepCfg kSweep[4] = {{12, 4, false}, {6, 4, false}, {6, 2, true}, {3, 4, true}};
 constexpr int kSweepShapes = 4;
 constexpr int kSweepW = 56;
-inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw}; }
+inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw, 32 * kSweep[k].nw}; }
 
 struct lbch_handle {
     int device = 0;

@@ -373,7 +373,7 @@ struct StepShape {
 // populations are multiplied by 1 - 1/tau = 0, so they are neither loaded nor stored -- the state is phi
 // alone, and the result is bit for bit the general kernel's (which multiplies them by exactly zero).
 template <typename C, typename S, typename P, int TX, int TY, int NT, bool TAU1 = false>
-__global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(const __grid_constant__ CUtensorMap tm_g,
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(const __grid_constant__ CUtensorMap tm_g,
                                                      const __grid_constant__ CUtensorMap tm_phi,
                                                      const __grid_constant__ CUtensorMap tm_lo,
                                                      StepArgs<C, S, P> a)
@@ -396,6 +396,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
 
     __shared__ long long s_time;
     __shared__ int s_tile_inst;
+    __shared__ int3 s_info[2];  // (instance, x0, y0) of the tile in each stage, written when it is issued
     __shared__ C s_T;
     __shared__ InstDev s_I;  // the current tile's instance, copied when the instance changes
 
@@ -420,6 +421,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
         int local = t - a.tile_begin[k];
         int tiles_x = (I.nx + TX - 1) / TX;
         int x0 = (local % tiles_x) * TX, y0 = (local / tiles_x) * TY;
+        s_info[s] = make_int3(k, x0, y0);
         fence_proxy_async();
         mbar_expect_tx(&mbar[s], (TAU1 ? 0u : L::GBOX_BYTES) + L::PBOX_BYTES + L::LBOX_BYTES + L::TAB_BYTES);
         // box column origin: domain x0 - 4 is stored column x0 - 4 + GC = x0
@@ -451,6 +453,7 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
     }
     __syncthreads();
     const long long n = s_time + a.t_off;
+    int cur_inst = s_tile_inst;  // the instance in s_I (a register copy, so that no thread races thread 0)
 
     for (int it = 0;; it++) {
         const int t = blockIdx.x + it * stride;
@@ -467,21 +470,19 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
             }
             break;  // skip the remaining tiles; the step counter below is still kept consistent
         }
-        if (tid == 0) {
-            int k = find_inst(a.tile_begin, a.n_inst, t);
-            if (k != s_tile_inst) {
-                s_I = a.inst[k];
-                s_tile_inst = k;
+        if (s_info[s].x != cur_inst) {  // uniform: a tile of another instance (never the first tile)
+            cur_inst = s_info[s].x;
+            if (tid == 0) {
+                s_I = a.inst[cur_inst];
+                s_tile_inst = cur_inst;
                 s_T = (C)vel_t(s_I.vel, s_I.Tper, n);  // time factor of the flow, once per instance
             }
+            __syncthreads();
         }
-        __syncthreads();
         const InstDev& I = s_I;
         const Consts<C>& K0 = consts<C>(I);
         const int nx = I.nx, ny = I.ny, walls = I.walls, model = I.model;
-        const int local = t - a.tile_begin[s_tile_inst];
-        const int tiles_x = (nx + TX - 1) / TX;
-        const int x0 = (local % tiles_x) * TX, y0 = (local / tiles_x) * TY;
+        const int x0 = s_info[s].y, y0 = s_info[s].z;
         const C T = s_T;
         S* gb = reinterpret_cast<S*>(stage(s));
         const P* pb = reinterpret_cast<const P*>(stage(s) + L::OFF_P);  // phi on tile + 3 at box column c + 1
@@ -658,11 +659,12 @@ __global__ void __launch_bounds__(NT, (sizeof(C) == 8 ? 2 : 3)) ch_step_kernel(c
                 }
             }
         }
-        __syncthreads();  // the stage and the work arrays are free again
-
-        if (tid == 0) {
-            int t2 = t + 2 * stride;
-            if (t2 < a.total_tiles) issue(t2, s);
+        // the stage takes the tile after next once every thread is done with it (the next iteration's
+        // wait is a barrier too, so without a tile to issue nothing needs to wait here)
+        const int t2 = t + 2 * stride;
+        if (t2 < a.total_tiles) {
+            __syncthreads();
+            if (tid == 0) issue(t2, s);
         }
     }
 

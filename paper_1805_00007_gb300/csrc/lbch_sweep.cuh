@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     }
     __syncthreads();
     const long long n = s_time + a.t_off;
+    int cur_inst = s_tile_inst;  // the instance in s_I (a register copy, so that no thread races thread 0)
 
     // GEN: this warp's ring.  Fill n goes to slot n % RING and completes phase n / RING of the slot's
     // mbarrier; the fills and their uses run in the same row order, tile after tile.
@@ -664,20 +665,24 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             }
             break;
         }
-        if (tid == 0 && k_t != s_tile_inst) {
-            s_I = a.inst[k_t];
-            s_tile_inst = k_t;
-            s_T = (C)vel_t(s_I.vel, s_I.Tper, n);
+        if (k_t != cur_inst) {  // uniform: a tile of another instance (never the first tile)
+            cur_inst = k_t;
+            if (tid == 0) {
+                s_I = a.inst[k_t];
+                s_tile_inst = k_t;
+                s_T = (C)vel_t(s_I.vel, s_I.Tper, n);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (s_I.walls) sweep(std::true_type(), s);
         else sweep(std::false_type(), s);
         if (GEN && !ring_ok && lane == 0) atomicOr(&a.ctl->err, 1u);
-        __syncthreads();  // the stage is free again
-
-        if (tid == 0) {
-            const int t2 = t + 2 * stride;
-            if (t2 < a.total_tiles) issue(t2, s);
+        // the stage takes the tile after next once every thread is done with it (the next iteration's
+        // wait is a barrier too, so without a tile to issue nothing needs to wait here)
+        const int t2 = t + 2 * stride;
+        if (t2 < a.total_tiles) {
+            __syncthreads();
+            if (tid == 0) issue(t2, s);
         }
     }
 

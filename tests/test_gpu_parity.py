@@ -176,7 +176,7 @@ def test_nonfinite_is_reported():
         assert ei.value.status == abi.LBCH_ENONFINITE
 
 
-@pytest.mark.parametrize("prec,nshapes,tile,general", [("f64", 2, 1, 1), ("f32", 3, 1, 1), ("f16s", 3, 1, 1),
+@pytest.mark.parametrize("prec,nshapes,tile,general", [("f64", 3, 1, 1), ("f32", 4, 1, 1), ("f16s", 4, 1, 1),
                                                       ("f64", 4, 0, 1), ("f32", 4, 0, 1), ("f16s", 4, 0, 1),
                                                       ("f64", 4, 0, 0), ("f32", 4, 0, 0), ("f16s", 4, 0, 0)])
 def test_every_tile_shape_gives_the_same_bits(prec, nshapes, tile, general):
@@ -209,6 +209,7 @@ def test_tune_keeps_the_state(prec, tau):
     p, phi0, _ = wl.zalesak(n=128, tau=tau)
     with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(p, phi0, prec=prec, tune=True) as b:
         assert b.tile in ((56, 48), (56, 24), (56, 12), (32, 16), (32, 8), (16, 8))  # sweep or tile kernel
+        assert b.kernel()["threads"] in (64, 128, 256, 512)
         if prec == "f16s" and tau == 1.0:
             assert b.kernel()["form"] == "sweep_tau1"
         assert b.observe(abi.LBCH_OBS_STEP) == 0
