@@ -167,7 +167,7 @@ void* lb_ch_stream(lbch_handle* h);
 /* Kernel and tile-shape autotuner.  The step has two kernel forms, each built for several shapes: the
  * row sweep (warps sweeping 56-column strips; tiles of 56 x 48, 56 x 24 and twice 56 x 12 output nodes)
  * and the tile kernel (each tile's stencil fields staged in shared memory; 32x16, 32x8 and 16x8 with 256
- * threads and 32x16 with 512 on the float paths; 32x8 and 16x8 with 256 and 32x8 with 512 for LBCH_F64).  lb_ch_tune times `steps` steps of every candidate on the
+ * threads and 32x16 with 768 on the float paths; 32x8 and 16x8 with 256 and 32x8 with 512 for LBCH_F64).  lb_ch_tune times `steps` steps of every candidate on the
  * handle's own problem, restores the state after each, keeps the fastest, and reports its tile size in
  * *tile_x, *tile_y (either may be NULL).  The result of the simulation does not depend on the choice (on
  * the half-storage path with every tau_g = 1 only the row sweep is a candidate, as the tile kernel would

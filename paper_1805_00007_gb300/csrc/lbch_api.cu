@@ -54,7 +54,7 @@ constexpr int kGraphChunk = 64;  // steps per captured graph (even, so the ping-
 // TX divides 32 and every TY divides 16, so one storage layout serves all shapes.
 constexpr int NT = 256;
 constexpr Shape kShapes64[3] = {{32, 8, 256}, {16, 8, 256}, {32, 8, 512}};
-constexpr Shape kShapesF[4] = {{32, 16, 256}, {32, 8, 256}, {16, 8, 256}, {32, 16, 512}};
+constexpr Shape kShapesF[4] = {{32, 16, 256}, {32, 8, 256}, {16, 8, 256}, {32, 16, 768}};
 inline int n_shapes(int prec) { return prec == LBCH_F64 ? 3 : 4; }
 inline Shape shape_of(int prec, int k) { return prec == LBCH_F64 ? kShapes64[k] : kShapesF[k]; }
 
@@ -194,11 +194,11 @@ cudaError_t prepare_step(lbch_handle* h, int k)
     case LBCH_F32:
         return k == 0 ? prepare_step_t<float, float, float, 32, 16>(h, k)
              : k == 1 ? prepare_step_t<float, float, float, 32, 8>(h, k)
-             : k == 2 ? prepare_step_t<float, float, float, 16, 8>(h, k) : prepare_step_t<float, float, float, 32, 16, 512>(h, k);
+             : k == 2 ? prepare_step_t<float, float, float, 16, 8>(h, k) : prepare_step_t<float, float, float, 32, 16, 768>(h, k);
     default:
         return k == 0 ? prepare_step_t<float, __half, float, 32, 16>(h, k)
              : k == 1 ? prepare_step_t<float, __half, float, 32, 8>(h, k)
-             : k == 2 ? prepare_step_t<float, __half, float, 16, 8>(h, k) : prepare_step_t<float, __half, float, 32, 16, 512>(h, k);
+             : k == 2 ? prepare_step_t<float, __half, float, 16, 8>(h, k) : prepare_step_t<float, __half, float, 32, 16, 768>(h, k);
     }
 }
 
@@ -268,11 +268,11 @@ cudaError_t launch_step(lbch_handle* h, int parity)
     case LBCH_F32:
         return k == 0 ? launch_step_t<float, float, float, 32, 16>(h, parity)
              : k == 1 ? launch_step_t<float, float, float, 32, 8>(h, parity)
-             : k == 2 ? launch_step_t<float, float, float, 16, 8>(h, parity) : launch_step_t<float, float, float, 32, 16, 512>(h, parity);
+             : k == 2 ? launch_step_t<float, float, float, 16, 8>(h, parity) : launch_step_t<float, float, float, 32, 16, 768>(h, parity);
     default:
         return k == 0 ? launch_step_t<float, __half, float, 32, 16>(h, parity)
              : k == 1 ? launch_step_t<float, __half, float, 32, 8>(h, parity)
-             : k == 2 ? launch_step_t<float, __half, float, 16, 8>(h, parity) : launch_step_t<float, __half, float, 32, 16, 512>(h, parity);
+             : k == 2 ? launch_step_t<float, __half, float, 16, 8>(h, parity) : launch_step_t<float, __half, float, 32, 16, 768>(h, parity);
     }
 }
 
