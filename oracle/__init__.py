@@ -100,6 +100,9 @@ def lib() -> ctypes.CDLL:
         _lib.ora_step.argtypes = [P(_Params), dp, dp, ctypes.c_long]
         _lib.ora_run.argtypes = [P(_Params), dp, ctypes.c_long, ctypes.c_long]
         _lib.ora_run.restype = ctypes.c_int
+        _lib.ora_step_full.argtypes = [P(_Params), dp, dp, dp, ctypes.c_int, ctypes.c_long]
+        _lib.ora_run_full.argtypes = [P(_Params), dp, dp, ctypes.c_long, ctypes.c_long]
+        _lib.ora_run_full.restype = ctypes.c_int
         _lib.ora_observe.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
         _lib.ora_d2fdphi2.argtypes = [ctypes.c_double] * 4
         _lib.ora_d2fdphi2.restype = ctypes.c_double
@@ -247,6 +250,27 @@ def run(cfg, g, nsteps: int, n0: int = 0) -> np.ndarray:
     return g
 
 
+def run_full(cfg, g, H, nsteps: int, n0: int = 0):
+    """Model III (model = 3): advance copies of g and of H (the stored part of the time-derivative terms of
+    Eq. F2-1, 2 N values) by nsteps steps from step index n0; H is ignored when n0 = 0."""
+    p = params(cfg)
+    g = _f64(g).copy()
+    H = np.zeros(2 * p.nx * p.ny) if H is None else _f64(H).copy()
+    rc = lib().ora_run_full(ctypes.byref(p), _ptr(g), _ptr(H), n0, nsteps)
+    if rc != 0:
+        raise MemoryError("oracle run failed to allocate")
+    return g, H
+
+
+def step_full(cfg, g, H, n: int):
+    """One Model III step n -> n+1; returns (g', H') (H is ignored at n = 0)."""
+    p = params(cfg)
+    out = np.empty_like(_f64(g))
+    H = np.zeros(2 * p.nx * p.ny) if H is None else _f64(H).copy()
+    lib().ora_step_full(ctypes.byref(p), _ptr(_f64(g)), _ptr(out), _ptr(H), int(n == 0), n)
+    return out, H
+
+
 def observe(phi, phi0) -> dict:
     phi, phi0 = _f64(phi), _f64(phi0)
     ny, nx = phi.shape
@@ -258,6 +282,11 @@ def observe(phi, phi0) -> dict:
 
 def simulate(cfg, phi0, nsteps: int, n0: int = 0):
     """phi after nsteps steps from the initial field phi0 (initial g from the equilibria)."""
+    if int(cfg.get("model", 2)) == 3:
+        if n0 != 0:
+            raise ValueError("a Model III run from phi0 starts at step 0")
+        g, _ = run_full(cfg, init(cfg, phi0), None, nsteps)
+        return phi_of(g), g
     g = run(cfg, init(cfg, phi0), nsteps, n0)
     return phi_of(g), g
 

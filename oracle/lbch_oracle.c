@@ -25,6 +25,10 @@
  *       distributions with the moving-wall term 2 w_i phi (c_i . u_w)/c_s^2, and every stencil operand
  *       (phi, mu, phi*u, div(phi u)) takes at a ghost row the value of that operand at the mirror row
  *   R8  the order of a step is phi -> mu -> grad mu -> u -> F -> g_eq, S -> collide -> stream
+ *   R15 Model III (model = 3) is Model II with the complete diffusive-scale force of Eq. F2-1: the time
+ *       derivatives on the convective scale are replaced by the whole time derivative (as Remarks I and
+ *       II allow), taken as the backward difference over one step; at the first step (no previous step)
+ *       they are zero
  */
 #include <math.h>
 #include <stdlib.h>
@@ -49,7 +53,7 @@ enum { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_SHEAR = 3, VEL_REV
 typedef struct {
     int nx, ny;
     int walls;          /* 0: periodic in x and y; 1: periodic in x, walls at y = -1/2 and y = ny - 1/2 */
-    int model;          /* 1: Model I (F = F1); 2: Model II (F = F1 + F2 of Eq. mark3) */
+    int model;          /* 1: Model I (F = F1); 2: Model II (F = F1 + F2 of Eq. mark3); 3: F2 of Eq. F2-1 */
     int vel;            /* velocity field, VEL_* */
     int nvort;          /* vortex count n of the deformation field (Eq. deformation) */
     double phiA, phiB;  /* bulk values of the order parameter */
@@ -385,6 +389,116 @@ int ora_run(const ora_params* p, double* g, long n0, long nsteps)
     if (!tmp) return -1;
     for (long s = 0; s < nsteps; s++) {
         ora_step(p, g, tmp, n0 + s);
+        memcpy(g, tmp, sizeof(double) * Q * N);
+    }
+    free(tmp);
+    return 0;
+}
+
+/* ---------------------------------------------------------------- Model III: the complete F2 of Eq. F2-1 */
+
+/* F = F1 + F2 with the complete diffusive-scale force of Eq. F2-1 (reading R15):
+ *   F2 = (2 tau - 1 + 3K) d_t F1 + 3 c_s^2 eta K d_t grad mu + 3 c_s^2 K grad(div(phi u)).
+ * The two time derivatives share one backward difference: with
+ *   H(t) = (2 tau - 1 + 3K) F1(t) + 3 c_s^2 eta K grad mu(t),
+ * F2 = H(t) - H(t - 1) + 3 c_s^2 K grad(div(phi u)).  Hprev (two arrays of N) holds H(t - 1), or is NULL at the
+ * first step (the derivatives are then zero); Hout receives H(t). */
+void ora_force_full(const ora_params* p, const ora_consts* c, const double* phi, const double* mu, const double* ux,
+                    const double* uy, const double* Hprevx, const double* Hprevy, double* Fx, double* Fy,
+                    double* Houtx, double* Houty)
+{
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double* gmx = (double*)malloc(sizeof(double) * N);
+    double* gmy = (double*)malloc(sizeof(double) * N);
+    double* jx = (double*)malloc(sizeof(double) * N);
+    double* jy = (double*)malloc(sizeof(double) * N);
+    double* D = (double*)malloc(sizeof(double) * N);
+    double* gDx = (double*)malloc(sizeof(double) * N);
+    double* gDy = (double*)malloc(sizeof(double) * N);
+    ora_grad(nx, ny, p->walls, mu, gmx, gmy);
+    for (long n = 0; n < N; n++) {
+        jx[n] = phi[n] * ux[n];
+        jy[n] = phi[n] * uy[n];
+    }
+    ora_div(nx, ny, p->walls, jx, jy, D);
+    ora_grad(nx, ny, p->walls, D, gDx, gDy);
+    double cF1 = 2.0 * p->tau - 1.0 + 3.0 * c->K;  /* coefficient of d_t F1 */
+    double cmu = 3.0 * CS2 * c->eta * c->K;       /* coefficient of d_t grad mu */
+    for (long n = 0; n < N; n++) {
+        double rho = c->a * phi[n] + c->b;                       /* Eq. rho */
+        double F1x = phi[n] / rho * (-phi[n] * gmx[n]);          /* Eq. t0-phiu with grad p = 0 (R1) */
+        double F1y = phi[n] / rho * (-phi[n] * gmy[n]);
+        double Hx = cF1 * F1x + cmu * gmx[n];
+        double Hy = cF1 * F1y + cmu * gmy[n];
+        double dHx = Hprevx ? Hx - Hprevx[n] : 0.0;              /* backward difference over one step */
+        double dHy = Hprevy ? Hy - Hprevy[n] : 0.0;
+        Fx[n] = F1x + dHx + 3.0 * CS2 * c->K * gDx[n];
+        Fy[n] = F1y + dHy + 3.0 * CS2 * c->K * gDy[n];
+        Houtx[n] = Hx;
+        Houty[n] = Hy;
+    }
+    free(gmx); free(gmy); free(jx); free(jy); free(D); free(gDx); free(gDy);
+}
+
+/* One step of Model III: as ora_step, with F from ora_force_full.  H holds 2 N values (x components, then
+ * y): H(t - 1) on entry (ignored when first != 0) and H(t) on return. */
+void ora_step_full(const ora_params* p, const double* gin, double* gout, double* H, int first, long n)
+{
+    ora_consts c;
+    ora_derive(p, &c);
+    int nx = p->nx, ny = p->ny;
+    long N = (long)nx * ny;
+    double* phi = (double*)malloc(sizeof(double) * N);
+    double* mu = (double*)malloc(sizeof(double) * N);
+    double* ux = (double*)malloc(sizeof(double) * N);
+    double* uy = (double*)malloc(sizeof(double) * N);
+    double* Fx = (double*)malloc(sizeof(double) * N);
+    double* Fy = (double*)malloc(sizeof(double) * N);
+    double* Hn = (double*)malloc(sizeof(double) * 2 * N);
+
+    ora_phi(nx, ny, gin, phi);                 /* Eq. macroscopicg */
+    ora_mu(p, &c, phi, mu);                    /* Eq. mu */
+    ora_velocity_field(p, n, ux, uy);          /* prescribed u at t = n (R6) */
+    ora_force_full(p, &c, phi, mu, ux, uy, first ? NULL : H, first ? NULL : H + N, Fx, Fy, Hn, Hn + N);
+    memcpy(H, Hn, sizeof(double) * 2 * N);
+
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long x = (long)j * nx + i;
+            double geq[Q], S[Q];
+            ora_geq(phi[x], mu[x], ux[x], uy[x], c.eta, geq);  /* Eq. geq */
+            ora_source(Fx[x], Fy[x], S);                       /* Eq. liangFi */
+            for (int q = 0; q < Q; q++) {
+                double post = gin[q * N + x] - (gin[q * N + x] - geq[q]) / p->tau
+                            + (1.0 - 1.0 / (2.0 * p->tau)) * S[q];
+                int ii = ((i + CX[q]) % nx + nx) % nx;
+                int jj = j + CY[q];
+                if (!p->walls) {
+                    jj = ((jj % ny) + ny) % ny;
+                } else if (jj < 0 || jj >= ny) {
+                    double uwx, uwy;
+                    ora_velocity(p, (double)i, jj < 0 ? -0.5 : (double)ny - 0.5, n, &uwx, &uwy);
+                    int o = OPP[q];
+                    gout[o * N + x] = post + 2.0 * WQ[o] * phi[x] * (CX[o] * uwx + CY[o] * uwy) / CS2;
+                    continue;
+                }
+                gout[q * N + (long)jj * nx + ii] = post;
+            }
+        }
+    free(phi); free(mu); free(ux); free(uy); free(Fx); free(Fy); free(Hn);
+}
+
+/* nsteps steps of Model III from step index n0; g and H (2 N) hold the state on entry and on return (H is
+ * ignored on entry when n0 = 0). */
+int ora_run_full(const ora_params* p, double* g, double* H, long n0, long nsteps)
+{
+    long N = (long)p->nx * p->ny;
+    double* tmp = (double*)malloc(sizeof(double) * Q * N);
+    if (!tmp) return -1;
+    for (long s = 0; s < nsteps; s++) {
+        ora_step_full(p, g, tmp, H, n0 + s == 0, n0 + s);
         memcpy(g, tmp, sizeof(double) * Q * N);
     }
     free(tmp);

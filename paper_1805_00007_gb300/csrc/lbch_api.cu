@@ -106,6 +106,9 @@ cudaError_t launch_step_v(lbch_handle* h, int parity)
     a.phi_out = static_cast<P*>(h->phi[parity ^ 1]);
     a.lo_out = h->lo[parity ^ 1];
     a.ctl = h->ctl;
+    a.H_in = static_cast<const C*>(h->H[parity]);
+    a.H_out = static_cast<C*>(h->H[parity ^ 1]);
+    a.H_plane = (long long)h->rows * h->pitch;
     a.t_off = h->t_off;
     a.t_adv = h->t_adv;
     // a programmatic dependent of the previous launch in the stream (the kernel waits on it before it
@@ -134,7 +137,7 @@ cudaError_t launch_step_t(lbch_handle* h, int parity)
 
 // The row-sweep kernel steps the handle (its shape index then names a sweep configuration), without the
 // populations when every instance has tau_g = 1; the tile kernel only when a test asks for it.
-inline bool use_sweep(const lbch_handle* h) { return !h->force_tile && !h->coupled; }
+inline bool use_sweep(const lbch_handle* h) { return !h->force_tile && !h->coupled && !h->model3; }
 inline int n_active(const lbch_handle* h) { return h->coupled ? 1 : (use_sweep(h) ? kSweepShapes : n_shapes(h->prec)); }
 inline const lbch_handle::PerShape& active_ps(const lbch_handle* h) { return use_sweep(h) ? h->sw[h->shape] : h->ps[h->shape]; }
 inline int active_grid(const lbch_handle* h)
@@ -281,7 +284,9 @@ lbch_status check_params(const lbch_params& p, int k)
     if (p.nx < 4 || p.ny < 4 || p.nx > (1 << 20) || p.ny > (1 << 20))
         return fail(LBCH_EINVAL, "instance %d: nx, ny must be in [4, 2^20] (got %d x %d)", k, p.nx, p.ny);
     if (!(p.tau > 0.5)) return fail(LBCH_EINVAL, "instance %d: tau must exceed 1/2", k);
-    if (p.model != 1 && p.model != 2) return fail(LBCH_EINVAL, "instance %d: model must be 1 or 2", k);
+    if (p.model < 1 || p.model > 3) return fail(LBCH_EINVAL, "instance %d: model must be 1, 2 or 3", k);
+    if (p.model == 3 && p.vel == LBCH_VEL_COUPLED)
+        return fail(LBCH_EINVAL, "instance %d: the coupled flow takes Model I or II", k);
     if (p.vel < 0 || p.vel > 6) return fail(LBCH_EINVAL, "instance %d: unknown velocity field %d", k, p.vel);
     if (p.vel == LBCH_VEL_COUPLED && !(p.nu > 0.0)) return fail(LBCH_EINVAL, "instance %d: coupled flow needs nu > 0", k);
     if (p.walls != 0 && p.walls != 1) return fail(LBCH_EINVAL, "instance %d: walls must be 0 or 1", k);
@@ -313,10 +318,13 @@ void derive(const lbch_params& p, InstDev& d)
     c.omt = 1.0 - 1.0 / p.tau;
     c.src = 1.0 - 1.0 / (2.0 * p.tau);
     c.phiA = p.phiA; c.phiB = p.phiB;
+    c.cF1 = 2.0 * p.tau - 1.0 + 3.0 * c.K;                               // Eq. F2-1: coefficient of d_t F1
+    c.cmu = 3.0 * cs2 * c.eta * c.K;                                     // and of d_t grad mu
     Consts<float>& f = d.cf;
     f.beta = (float)c.beta; f.kappa = (float)c.kappa; f.eta = (float)c.eta; f.a = (float)c.a; f.b = (float)c.b;
     f.K = (float)c.K; f.phiA = (float)c.phiA; f.phiB = (float)c.phiB;
     f.itau = (float)c.itau; f.omt = (float)c.omt; f.src = (float)c.src;
+    f.cF1 = (float)c.cF1; f.cmu = (float)c.cmu;
     d.Tper = p.Tper;
     d.walls = p.walls; d.model = p.model; d.vel = p.vel;
 }
@@ -380,6 +388,7 @@ void release(lbch_handle* h)
         if (h->g[k]) cudaFree(h->g[k]);
         if (h->phi[k]) cudaFree(h->phi[k]);
         if (h->lo[k]) cudaFree(h->lo[k]);
+        if (h->H[k]) cudaFree(h->H[k]);
     }
     if (h->d_inst) cudaFree(h->d_inst);
     if (h->d_tabs_f) cudaFree(h->d_tabs_f);
@@ -544,6 +553,7 @@ size_t state_bytes(const lbch_handle* h)
     b += (cells * h->nq * h->g_elem + 255) / 256 * 256;
     b += (cells * h->phi_elem + 255) / 256 * 256;
     if (h->lo[0]) b += (cells * 4 + 255) / 256 * 256;
+    if (h->model3) b += (2 * cells * h->c_elem() + 255) / 256 * 256;
     return b;
 }
 
@@ -658,6 +668,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     h->tau1 = !coupled;
     for (int k = 0; k < n_inst; k++) h->tau1 = h->tau1 && params[k].tau == 1.0;
     h->n_inst = n_inst;
+    for (int k = 0; k < n_inst; k++) h->model3 = h->model3 || params[k].model == 3;
     h->g_elem = prec == LBCH_F64 ? 8 : (prec == LBCH_F32 ? 4 : 2);
     h->phi_elem = prec == LBCH_F64 ? 8 : 4;  // the float path adds a float low part
     h->nq = prec == LBCH_F16S ? 8 : 9;
@@ -746,6 +757,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         CKI(cudaMalloc(&h->g[k], gbytes));
         CKI(cudaMalloc(&h->phi[k], pbytes));
         if (prec == LBCH_F32) CKI(cudaMalloc(&h->lo[k], cells * sizeof(float)));
+        if (h->model3) CKI(cudaMalloc(&h->H[k], 2 * cells * h->c_elem()));
     }
     CKI(cudaMalloc(&h->phi0, cells * sizeof(double)));
     CKI(cudaMalloc(&h->d_inst, sizeof(InstDev) * n_inst));
@@ -998,6 +1010,7 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     double bytes = 2.0 * (h->nq * (double)h->g_elem + (double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
     if (h->tau1 && !h->force_general)  // only phi is read and written (either kernel form)
         bytes = 2.0 * ((double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
+    if (h->model3) bytes += 2.0 * 2.0 * (double)h->c_elem();  // H of Model III, read and written
     if (h->coupled) {  // f and g read and written, phi read and written, u and p written and read
         const double e = h->prec == LBCH_F64 ? 8.0 : 4.0;
         bytes = 2.0 * (18.0 * e + e) + 2.0 * 3.0 * e;
@@ -1048,6 +1061,8 @@ lbch_status lb_ch_state_save(lbch_handle* h, void* dst)
     CK(cudaMemcpyAsync(p, h->phi[par], pb, cudaMemcpyDeviceToDevice, h->stream));
     p += (pb + 255) / 256 * 256;
     if (h->lo[par]) CK(cudaMemcpyAsync(p, h->lo[par], cells * 4, cudaMemcpyDeviceToDevice, h->stream));
+    if (h->lo[par]) p += (cells * 4 + 255) / 256 * 256;
+    if (h->model3) CK(cudaMemcpyAsync(p, h->H[par], 2 * cells * h->c_elem(), cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));  // the step index was copied from a host variable
     return LBCH_OK;
 }
@@ -1070,6 +1085,8 @@ lbch_status lb_ch_state_load(lbch_handle* h, const void* src)
     CK(cudaMemcpyAsync(h->phi[par], p, pb, cudaMemcpyDeviceToDevice, h->stream));
     p += (pb + 255) / 256 * 256;
     if (h->lo[par]) CK(cudaMemcpyAsync(h->lo[par], p, cells * 4, cudaMemcpyDeviceToDevice, h->stream));
+    if (h->lo[par]) p += (cells * 4 + 255) / 256 * 256;
+    if (h->model3) CK(cudaMemcpyAsync(h->H[par], p, 2 * cells * h->c_elem(), cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemcpyAsync(&h->ctl->time, &n, sizeof n, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->n = n;
@@ -1099,6 +1116,7 @@ lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
     if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
     if (h->inst[0].walls) return fail(LBCH_EINVAL, "the adjoint supports periodic domains only");
     if (h->coupled) return fail(LBCH_EINVAL, "the adjoint supports prescribed flows only");
+    if (h->model3) return fail(LBCH_EINVAL, "the adjoint supports Models I and II");
     h->adj_elem = 8;  // the adjoint is carried in double for every storage precision
     if (!h->adj) CK(cudaMalloc(&h->adj, adj_bytes(h)));
     AdjView v = adj_view(h);
@@ -1141,7 +1159,7 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
     struct Cand { bool tile; int shape; };
     std::vector<Cand> cands;
     if (!h->coupled) {
-        for (int k = 0; k < kSweepShapes; k++) cands.push_back({false, k});
+        for (int k = 0; k < kSweepShapes && !h->model3; k++) cands.push_back({false, k});
         if (!(h->prec == LBCH_F16S && h->tau1 && !h->force_general))
             for (int k = 0; k < n_shapes(h->prec); k++) cands.push_back({true, k});
     }

@@ -39,6 +39,9 @@ struct lbch_handle {
     bool tau1 = false;          // every instance has tau_g = 1: the populations drop out of the step
     bool force_general = false; // test hook: keep the populations even when tau1 holds
     bool force_tile = false;    // test hook: step with the tile kernel instead of the row sweep
+    bool model3 = false;        // an instance uses Model III (the tile kernel then steps the handle)
+    void* H[2] = {nullptr, nullptr};  // Model III: H of Eq. F2-1's time derivatives, 2 planes, arithmetic type
+    size_t c_elem() const { return prec == LBCH_F64 ? 8 : 4; }
     bool no_pdl = false;        // test hook: plain stream-ordered step launches
     struct PerShape {           // what depends on the tile shape
         int total_tiles = 0;

@@ -47,6 +47,7 @@ template <typename C>
 struct Consts {
     C beta, kappa, eta, a, b, K, phiA, phiB;
     C itau, omt, src;  // 1/tau, 1 - 1/tau, 1 - 1/(2 tau)
+    C cF1, cmu;        // Model III: 2 tau - 1 + 3K and 3 c_s^2 eta K, the coefficients of d_t F1 and d_t grad mu
 };
 
 // Per-instance parameters, derived constants and layout, resident in device memory.
@@ -201,6 +202,22 @@ __device__ __forceinline__ void node_force(C ph, C gmx, C gmy, C gDx, C gDy, boo
     }
 }
 
+// Model III: the complete diffusive-scale force of Eq. F2-1, with the time derivatives on the convective
+// scale replaced by backward differences over one step (Remarks I, II).  H = cF1 F1 + cmu grad mu is the
+// part under the time derivative; F = F1 + (H - Hprev) + 3 c_s^2 K grad D.  Hprev = H at the first step.
+template <typename C>
+__device__ __forceinline__ void node_force_full(C ph, C gmx, C gmy, C gDx, C gDy, C Hpx, C Hpy, bool first, C ra, C rb,
+                                                C K, C cF1, C cmu, C& Fx, C& Fy, C& Hx, C& Hy)
+{
+    C F1x, F1y;
+    node_force(ph, gmx, gmy, C(0), C(0), false, ra, rb, K, F1x, F1y);
+    Hx = op_fma(cF1, F1x, op_mul(cmu, gmx));
+    Hy = op_fma(cF1, F1y, op_mul(cmu, gmy));
+    const C dHx = first ? C(0) : Hx - Hpx, dHy = first ? C(0) : Hy - Hpy;
+    Fx = op_fma(K, gDx, F1x + dHx);
+    Fy = op_fma(K, gDy, F1y + dHy);
+}
+
 // The prescribed velocity X(x) Y(y) T at a node.
 template <typename C> __device__ __forceinline__ C node_u(C X, C Y, C T) { return op_mul(op_mul(X, Y), T); }
 
@@ -322,6 +339,26 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
         : "memory");
 }
 
+// Model III: H(t) of domain node (x, y) and its ghost images one deep (periodic in x; in y unless walls).
+template <typename C>
+__device__ __forceinline__ void store_h(C* H, long long plane, int row0, int pitch, int nx, int ny, int walls, int x,
+                                        int y, C hx, C hy)
+{
+    const int xa = x == 0 ? nx : (x == nx - 1 ? -1 : x);
+    const int ya = walls ? y : (y == 0 ? ny : (y == ny - 1 ? -1 : y));
+    for (int iy = 0; iy < 2; iy++) {
+        const int yy = iy == 0 ? y : ya;
+        if (iy == 1 && yy == y) continue;
+        for (int ix = 0; ix < 2; ix++) {
+            const int xx = ix == 0 ? x : xa;
+            if (ix == 1 && xx == x) continue;
+            const long long k = (long long)(row0 + yy) * pitch + GC + xx;
+            H[k] = hx;
+            H[plane + k] = hy;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------ step
 // Storage types: S populations, P phi (the high part on the float path), C arithmetic.  The float path
 // (C = S = float) keeps phi as an unevaluated sum of two floats, phi = hi + lo: hi feeds the stencils,
@@ -339,6 +376,9 @@ struct StepArgs {
     P* phi_out;
     float* lo_out;       // low part of phi on the float path
     Ctl* ctl;
+    const C* H_in;       // Model III: H(t - 1), two planes (x, y) of rows x pitch values; nullptr otherwise
+    C* H_out;            // H(t), written for the tile's own nodes and their ghost images
+    long long H_plane;   // values per plane of H
     int t_off;           // this launch's step is ctl->time + t_off
     int t_adv;           // when nonzero, the launch's last CTA advances ctl->time by t_adv
 };
@@ -509,7 +549,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) 
             C pE = cvt<C>(q[1]), pW = cvt<C>(q[-1]), pN = cvt<C>(q[BW]), pS = cvt<C>(q[-BW]);
             C pNE = cvt<C>(q[BW + 1]), pNW = cvt<C>(q[BW - 1]), pSE = cvt<C>(q[-BW + 1]), pSW = cvt<C>(q[-BW - 1]);
             s_mu[e] = node_mu(ce, pE, pW, pN, pS, pNE, pNW, pSE, pSW, beta, kappa, phiA, phiB);
-            if (model == 2)  // the tables at box columns c+1..c+3 and box rows r..r+2
+            if (model >= 2)  // the tables at box columns c+1..c+3 and box rows r..r+2
                 s_D[e] = node_div(pE, pW, pN, pS, pNE, pNW, pSE, pSW, sX1[c + 1], sX1[c + 3], sX2[c + 1], sX2[c + 2],
                                   sX2[c + 3], sY1[r], sY1[r + 1], sY1[r + 2], sY2[r], sY2[r + 2], T);
         }
@@ -525,7 +565,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) 
                 if (r >= 0 && r < MH && rm >= 0 && rm < MH) {
                     C vmu = s_mu[rm * MW + c], vD = s_D[rm * MW + c];
                     s_mu[r * MW + c] = vmu;
-                    if (model == 2) s_D[r * MW + c] = vD;
+                    if (model >= 2) s_D[r * MW + c] = vD;
                 }
             }
         }
@@ -541,13 +581,26 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) 
             C gmx, gmy, gDx = C(0), gDy = C(0);
             grad9(s_mu[m + 1], s_mu[m - 1], s_mu[m + MW], s_mu[m - MW], s_mu[m + MW + 1], s_mu[m + MW - 1],
                   s_mu[m - MW + 1], s_mu[m - MW - 1], gmx, gmy);
-            if (model == 2)
+            if (model >= 2)
                 grad9(s_D[m + 1], s_D[m - 1], s_D[m + MW], s_D[m - MW], s_D[m + MW + 1], s_D[m + MW - 1],
                       s_D[m - MW + 1], s_D[m - MW - 1], gDx, gDy);
             C ph = cvt<C>(pb[(r + 2) * BW + c + 3]);
             C mu = s_mu[m];
             C Fx, Fy;
-            node_force(ph, gmx, gmy, gDx, gDy, model == 2, ra, rb, K, Fx, Fy);
+            if (model == 3) {
+                // H(t - 1) at this node (halo nodes included: its images are stored one deep); H(t) is
+                // stored for the tile's own nodes only
+                const int gx = x0 - 1 + c;
+                const long long hn = (long long)(I.row0 + gy) * a.pitch + GC + gx;
+                const bool first = n == 0;
+                const C Hpx = first ? C(0) : a.H_in[hn], Hpy = first ? C(0) : a.H_in[a.H_plane + hn];
+                C Hx, Hy;
+                node_force_full(ph, gmx, gmy, gDx, gDy, Hpx, Hpy, first, ra, rb, K, K0.cF1, K0.cmu, Fx, Fy, Hx, Hy);
+                if (r >= 1 && r <= TY && c >= 1 && c <= TX && gx < nx && gy < ny)
+                    store_h(a.H_out, a.H_plane, I.row0, a.pitch, nx, ny, walls, gx, gy, Hx, Hy);
+            } else {
+                node_force(ph, gmx, gmy, gDx, gDy, model == 2, ra, rb, K, Fx, Fy);
+            }
             const C ux = node_u(sX1[c + 3], sY1[r + 2], T), uy = node_u(sX2[c + 3], sY2[r + 2], T);  // box row r+2, col c+3
             // the node's populations in the box: row r, plane q - QOFF, column c + 3
             S* gp = gb + (r * NQ) * BW + c + 3;

@@ -61,7 +61,8 @@ def test_invalid_arguments_rejected_without_gpu():
     st = lib.lb_ch_init(arr, 1, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, None, ctypes.byref(h))
     assert st == abi.LBCH_EINVAL and not h.value
     assert b"nx" in lib.lb_ch_last_error()
-    for kw in (dict(tau=0.5), dict(model=3), dict(vel=9), dict(M=0.0, Pe=0.0)):
+    for kw in (dict(tau=0.5), dict(model=4), dict(model=0), dict(vel=9), dict(M=0.0, Pe=0.0),
+               dict(model=3, vel=wl.VEL_COUPLED, nu=0.01)):
         arr = (abi.lbch_params * 1)(abi.make_params(dict(p, **kw)))
         flat = np.ascontiguousarray(phi0.ravel())
         st = lib.lb_ch_init(arr, 1, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, None, ctypes.byref(h))

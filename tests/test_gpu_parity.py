@@ -1,11 +1,12 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
 
 Tolerances (max |phi_gpu - phi_oracle| over every node):
-  FP64 path: 1e-12  (the same arithmetic in a different order, with FMA contraction on the GPU)
+  FP64 path: 1e-12  (the same arithmetic in a different order, with explicit fused multiply-adds)
   FP32 path: 1e-5   (single-precision state and arithmetic; the velocity tables are built in double)
   F16S path: 2e-3 after 50 steps (half-precision populations; rounding of 2^-11 relative per step on
              populations of size up to ~0.15, random-walk accumulated) -- see test_f16s_parity
-Sizes span several tiles (32 x 8 for FP64, 32 x 16 for FP32) with ragged tails in both directions.
+Sizes span several tiles of every kernel form (row-sweep strips of 56 columns, tiles of 32 x 16 and
+32 x 8) with ragged tails in both directions.
 """
 import math
 
@@ -298,3 +299,47 @@ def test_dependent_launch_gives_the_same_bits(prec):
                 assert sim.observe(abi.LBCH_OBS_STEP) == 198
                 out.append(sim.phi())
         assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5), ("f16s", 2e-3)])
+def test_model3_matches_oracle(prec, tol):
+    """Model III (the complete force of Eq. F2-1, time derivatives as one-step backward differences) on a
+    periodic time-dependent flow at tau_g = 0.8 and 1.3 and on a ragged ensemble with walls that mixes
+    Models II and III; graph replays and single launches (the stored H crosses both)."""
+    nsteps = 131 if prec != "f16s" else 50
+    for tau in (0.8, 1.3):
+        p = wl.make_params(nx=45, ny=37, vel=wl.VEL_VORTEX, U0=0.05, Tper=60.0, M=0.02, sigma=0.03, W=3.0,
+                           rhoB=0.4, tau=tau, model=3)
+        phi0 = np.clip(wl.random_smooth_phi(45, 37, seed=5) + 0.6 * wl.circle_phi(45, 37, 20.0, 18.0, 9.0, 3.0) - 0.3,
+                       0, 1)
+        ref, _ = oracle.simulate(p, phi0, nsteps)
+        with abi.Simulation(p, phi0, prec=prec) as sim:
+            assert sim.kernel()["form"] == "tile"
+            sim.step(nsteps)
+            assert _maxdiff(sim.phi(), ref) <= tol
+    ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=6, tau=0.9)
+    ens = [(dict(q, shear=q["shear"] * 30.0, Ustar=q["Ustar"] * 30.0, model=3 if k != 1 else 2), f)
+           for k, (q, f) in enumerate(ens)]
+    params, fields = zip(*ens)
+    with abi.Simulation(list(params), list(fields), prec=prec) as sim:
+        sim.step(nsteps)
+        for k, (q, f) in enumerate(ens):
+            ref, _ = oracle.simulate(q, f, nsteps)
+            assert _maxdiff(sim.phi(k), ref) <= tol
+
+
+def test_model3_state_save_load_round_trip():
+    """The checkpoint of a Model III handle carries H, so a reloaded state continues bit for bit."""
+    torch = pytest.importorskip("torch")
+    p = wl.make_params(nx=40, ny=36, vel=wl.VEL_VORTEX, U0=0.05, Tper=50.0, M=0.02, tau=0.8, model=3)
+    phi0 = wl.circle_phi(40, 36, 20.0, 18.0, 9.0, 3.0)
+    for prec in ("f64", "f32"):
+        with abi.Simulation(p, phi0, prec=prec) as sim:
+            sim.step(13)
+            buf = torch.empty(abi.lb_ch_state_bytes(sim.h), dtype=torch.uint8, device="cuda")
+            abi.lb_ch_state_save(sim.h, buf.data_ptr())
+            sim.step(70)
+            a = sim.phi()
+            abi.lb_ch_state_load(sim.h, buf.data_ptr())
+            sim.step(70)
+            assert np.array_equal(a, sim.phi())

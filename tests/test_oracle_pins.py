@@ -345,3 +345,87 @@ def test_paper_printed_extrema_model2():
     assert np.array_equal(phi1, phi2)
     ob = oracle.observe(phi2, phi0)
     assert 1.0 < ob["max"] < ref["model2_max"] and ref["model2_min"] < ob["min"] < -1.0
+    # Model III (the complete Eq. F2-1, here (2 tau - 1) d_t F1 of Remark I) stays below the printed
+    # overshoot as well (recorded: 1.0198 / -1.0124 after 4T)
+    p3, _, _ = wl.paper_translation(model=3)
+    phi3, _ = oracle.simulate(p3, phi0, 4 * T)
+    ob3 = oracle.observe(phi3, phi0)
+    assert 1.0 < ob3["max"] < ref["model2_max"] and ref["model2_min"] < ob3["min"] < -1.0
+
+
+# ----------------------------------------------------------------------------- Model III, linearised
+
+def _amplification_full(p, c, phibar, kx, ky):
+    """11x11 matrix advancing a Fourier mode of (g', H'(t-1)) by one step of Model III, linearised about the
+    uniform state.  Eq. F2-1: F2 = (2 tau - 1 + 3K) d_t F1 + 3 c_s^2 eta K d_t grad mu + 3 c_s^2 K grad div(phi u),
+    the time derivatives as one-step backward differences of H = (2 tau - 1 + 3K) F1 + 3 c_s^2 eta K grad mu.
+    Assembled here: H'(t) = h phi', F' = F1' + K grad div(phi' u) + H'(t) - H'(t-1); the collision and
+    streaming as in _amplification; the second block row stores H'(t) for the next step."""
+    ux, uy = p["ux0"], p["uy0"]
+    sgx, sgy, slap = _symbols(kx, ky)
+    f = c.beta * np.poly1d([1.0, -p["phiA"]]) ** 2 * np.poly1d([1.0, -p["phiB"]]) ** 2
+    mu_per_phi = f.deriv(2)(phibar) - c.kappa * slap
+    rho = c.a * phibar + c.b
+    tau = p["tau"]
+    cF1, cmu = 2 * tau - 1 + 3 * c.K, c.eta * c.K          # 3 c_s^2 = 1
+    gmu = 1j * np.array([sgx, sgy]) * mu_per_phi           # grad mu' per unit phi'
+    F1 = -(phibar ** 2 / rho) * gmu
+    h = cF1 * F1 + cmu * gmu
+    divu = 1j * (sgx * ux + sgy * uy)
+    F = F1 + c.K * 1j * np.array([sgx, sgy]) * divu + h   # per unit phi', without the -H'(t-1) part
+    dphi = oracle.geq(1.0, 0.0, ux, uy, c.eta)
+    dmu = oracle.geq(0.0, 1.0, ux, uy, c.eta)
+    Sx, Sy = oracle.source(1.0, 0.0), oracle.source(0.0, 1.0)
+    ones = np.ones(9)
+    src = 1 - 1 / (2 * tau)
+    post_g = np.eye(9) - (np.eye(9) - np.outer(dphi + dmu * mu_per_phi, ones)) / tau \
+        + src * np.outer(Sx * F[0] + Sy * F[1], ones)
+    post_h = -src * np.stack([Sx, Sy], axis=1)             # -H'(t-1) enters the force
+    shift = np.diag(np.exp(-1j * (C[:, 0] * kx + C[:, 1] * ky)))
+    A = np.zeros((11, 11), dtype=complex)
+    A[:9, :9] = shift @ post_g
+    A[:9, 9:] = shift @ post_h
+    A[9:, :9] = np.outer(h, ones)
+    return A, h
+
+
+@pytest.mark.parametrize("tau,rhoB,phibar", [(0.8, 0.5, 0.6), (1.0, 0.5, 0.35), (0.5 + math.sqrt(3) / 6, 1.0, 0.2),
+                                             (1.3, 0.25, 0.8)])
+def test_model3_step_matches_linear_amplification(tau, rhoB, phibar):
+    """Model III (Eq. F2-1 in full) against its linearisation assembled independently in Fourier space,
+    including the one-step memory of the time derivatives and the first step, where they vanish."""
+    nx, ny, nsteps = 16, 12, 6
+    p = wl.make_params(nx=nx, ny=ny, model=3, tau=tau, rhoA=1.0, rhoB=rhoB, sigma=0.05, W=3.0,
+                       M=0.02, vel=wl.VEL_UNIFORM, ux0=0.04, uy0=-0.03)
+    c = oracle.derive(p)
+    kx, ky = 2 * np.pi * 3 / nx, 2 * np.pi * 2 / ny
+    A, h = _amplification_full(p, c, phibar, kx, ky)
+    r = np.random.default_rng(11)
+    v = r.normal(size=9) + 1j * r.normal(size=9)
+    gbar = oracle.geq(phibar, oracle.dfdphi(phibar, c.beta, 1.0, 0.0), 0.04, -0.03, c.eta)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    wave = np.exp(1j * (kx * x + ky * y))
+    pert = np.real(v[:, None, None] * wave[None])
+    eps = 1e-5
+    gp, _ = oracle.run_full(p, gbar[:, None, None] + eps * pert, None, nsteps)
+    gm, _ = oracle.run_full(p, gbar[:, None, None] - eps * pert, None, nsteps)
+    got = (gp - gm) / (2 * eps)
+    # at the first step H(t - 1) = H(t): the memory starts as h phi'(0)
+    v11 = np.concatenate([v, h * v.sum()])
+    want = np.real((np.linalg.matrix_power(A, nsteps) @ v11)[:9, None, None] * wave[None])
+    assert np.max(np.abs(got - want)) < 1e-8 * np.max(np.abs(want))
+    # and the memory term matters: Model II (mark3 only) is a different map at this tau
+    g2 = oracle.run(dict(p, model=2), gbar[:, None, None] + eps * pert, nsteps)
+    assert np.max(np.abs(g2 - gp)) > 1e-6 * eps * np.max(np.abs(want))
+
+
+def test_model3_first_step_is_model2_and_mass_is_conserved():
+    """At the first step the time derivatives of Eq. F2-1 vanish (reading R15), so Model III's first step is
+    Model II's bit for bit; the source term has no zeroth moment, so sum phi is constant."""
+    p, phi0, _ = wl.single_vortex(n=32, T=40, tau=0.8, model=3)
+    g0 = oracle.init(p, phi0)
+    g3, H = oracle.step_full(p, g0, None, 0)
+    g2 = oracle.step(dict(p, model=2), g0, 0)
+    assert np.array_equal(g3, g2)
+    g, H = oracle.run_full(p, g3, H, 25, n0=1)
+    assert abs(oracle.phi_of(g).sum() - phi0.sum()) < 1e-11 * phi0.sum()
