@@ -375,6 +375,17 @@ def main():
                               "achieved_gbs": gbs, "frac": gbs / hbm_peak}
             sim.close()
 
+    # --- the paper's relaxation-time study (Sec. III.A) at its own size, every point one ensemble instance
+    tau_sweep = {}
+    if not args.no_sweep and rank == 0:
+        from paper_1805_00007_gb300 import sweeps
+        taus = (0.6, 0.7, sweeps.TAU_STAR, 0.9, 1.0, 1.3)
+        t0 = time.perf_counter()
+        res = sweeps.translation_tau_sweep(taus, models=(1, 2, 3), L0=200, prec="f64", stream=stream.cuda_stream)
+        tau_sweep = {"workload": "diagonal translation, L0 = 200, Pe = 200, W = 2, rhoA/rhoB = 2, one period, FP64",
+                     "err_l2": {f"tau={t:.4f}": {f"model{m}": res[t, m] for m in (1, 2, 3)} for t in taus},
+                     "seconds": time.perf_counter() - t0}
+
     acc = {prec: accuracy(prec, p, phi0, rev) for prec in ("f32", "f64", "f16s")} if rank == 0 else {}
 
     cpu = None
@@ -409,6 +420,7 @@ def main():
                                  "peak_from": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}},
             "sweep_4096": sweep,
             "ensemble_shear_256": ensemble,
+            "paper_tau_sweep": tau_sweep,
             "accuracy_one_revolution": acc,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
                     "d2h_bytes_per_step": phi0.nbytes},

@@ -155,6 +155,29 @@ def paper_translation(L0=200, U0=0.02, Pe=200.0, W=2.0, sigma=0.01, tau=0.5 + ma
     return p, phi0, int(round(L0 / U0))
 
 
+def paper_shear_reversal(L0=200, U0=0.025, W=2.0, Pe=1000.0, tau=1.0, model=2):
+    """The paper's circular interface in a reversing shear flow (Sec. III.C, Eq. shear): R = L0/5 at
+    (L0/2, 0.3 L0), phiA = -phiB = 1, rhoA = 1, rhoB = 0.5, sigma = 0.01; the flow reverses at t = T with
+    T = L0/U0 (the convective period of the other tests; the text does not state it), so the interface
+    returns at t = 2T, the returned step count."""
+    T = int(round(L0 / U0))
+    p = make_params(nx=L0, ny=L0, vel=VEL_REV_SHEAR, U0=U0, Tper=float(T), W=W, Pe=Pe, Ustar=U0, tau=tau,
+                    phiA=1.0, phiB=-1.0, rhoA=1.0, rhoB=0.5, sigma=0.01, model=model)
+    phi0 = circle_phi(L0, L0, 0.5 * L0, 0.3 * L0, L0 / 5, W, 1.0, -1.0)
+    return p, phi0, 2 * T
+
+
+def paper_deformation(L0=500, U0=0.025, W=2.0, Pe=1000.0, nvort=4, tau=1.0, model=2):
+    """The paper's deformation field (Sec. III.D, Eq. deformation): a circle R = L0/5 at the centre in n = 4
+    vortices whose velocity carries the factor cos(pi t/T0), T0 = 5T/4 with T = L0/U0; the flow runs
+    backwards after T0/2, so the interface returns at t = T0, the returned step count."""
+    T0 = int(round(1.25 * L0 / U0))
+    p = make_params(nx=L0, ny=L0, vel=VEL_DEFORM, nvort=nvort, U0=U0, Tper=float(T0), W=W, Pe=Pe, Ustar=U0,
+                    tau=tau, phiA=1.0, phiB=-1.0, rhoA=1.0, rhoB=0.5, sigma=0.01, model=model)
+    phi0 = circle_phi(L0, L0, 0.5 * L0, 0.5 * L0, L0 / 5, W, 1.0, -1.0)
+    return p, phi0, T0
+
+
 def rayleigh_taylor(nx=256, ny=1024, atwood=0.5, Re=3000.0, Pe=1000.0, W=5.0, sqrt_g_lambda=0.04,
                     amp=0.1, sigma=5e-5, tau=1.0, model=2):
     """Rayleigh-Taylor instability (Sec. III.E shape): heavy phase A (phi = 1) above y = ny/2 + amp nx

@@ -343,3 +343,15 @@ def test_model3_state_save_load_round_trip():
             abi.lb_ch_state_load(sim.h, buf.data_ptr())
             sim.step(70)
             assert np.array_equal(a, sim.phi())
+
+
+@pytest.mark.parametrize("setup,L0", [("paper_shear_reversal", 64), ("paper_deformation", 80)])
+def test_paper_reversing_flows_match_oracle(setup, L0):
+    """The paper's reversing shear (Sec. III.C) and deformation (Sec. III.D) workloads at reduced size, over
+    their whole return time, every precision against the oracle's final field."""
+    p, phi0, N = getattr(wl, setup)(L0=L0)
+    ref, _ = oracle.simulate(p, phi0, N)
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-5)):
+        with abi.Simulation(p, phi0, prec=prec) as sim:
+            sim.step(N)
+            assert _maxdiff(sim.phi(), ref) <= tol, prec

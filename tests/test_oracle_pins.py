@@ -429,3 +429,39 @@ def test_model3_first_step_is_model2_and_mass_is_conserved():
     assert np.array_equal(g3, g2)
     g, H = oracle.run_full(p, g3, H, 25, n0=1)
     assert abs(oracle.phi_of(g).sum() - phi0.sum()) < 1e-11 * phi0.sum()
+
+
+# ----------------------------------------------------------------------------- the paper's reversing flows
+
+@pytest.mark.parametrize("setup,L0", [("paper_shear_reversal", 64), ("paper_deformation", 80)])
+def test_paper_reversing_flows_return(setup, L0):
+    """Secs. III.C and III.D: the shear flow reverses at t = T and the deformation field runs backwards
+    after T0/2, so the interface is strongly deformed half-way and returns at the end (up to the
+    interface's own diffusion on these small grids).  A time factor of the wrong sign, or a flow that does
+    not reverse, leaves it far from the start."""
+    p, phi0, N = getattr(wl, setup)(L0=L0)
+    half, _ = oracle.simulate(p, phi0, N // 2)
+    full, _ = oracle.simulate(p, phi0, N)
+    e_half = oracle.observe(half, phi0)["err_l2"]
+    e_full = oracle.observe(full, phi0)["err_l2"]
+    assert e_half > 0.4
+    assert e_full < 0.3 * e_half
+    assert abs(full.sum() - phi0.sum()) < 1e-10 * np.abs(phi0).sum()
+
+
+def test_paper_tau_sweep_claims():
+    """Sec. III.A, the relaxation-time study of the diagonal translation: Model I's error is smallest at
+    tau_g = 0.5 + sqrt(3)/6 among the values tried, and away from it Model II's diffusive-scale force cuts
+    the error markedly (here to about half); at that tau K = 0 and the two models coincide.  L0 = 50
+    keeps it quick; the same holds at the paper's L0 = 200 (bench.py records it)."""
+    taus = (0.6, 0.5 + math.sqrt(3) / 6, 1.0, 1.3)
+    err = {}
+    for tau in taus:
+        for model in (1, 2):
+            p, phi0, T = wl.paper_translation(L0=50, tau=tau, rho_ratio=2.0, model=model)
+            phi, _ = oracle.simulate(p, phi0, T)
+            err[tau, model] = oracle.observe(phi, phi0)["err_l2"]
+    star = taus[1]
+    assert all(err[star, 1] < err[t, 1] for t in taus if t != star)
+    assert err[star, 2] == err[star, 1]
+    assert all(err[t, 2] < 0.7 * err[t, 1] for t in taus if t != star)
