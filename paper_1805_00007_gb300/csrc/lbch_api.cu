@@ -111,6 +111,7 @@ cudaError_t launch_step_v(lbch_handle* h, int parity)
     a.H_plane = (long long)h->rows * h->pitch;
     a.t_off = h->t_off;
     a.t_adv = h->t_adv;
+    a.need_time = h->need_time;
     // a programmatic dependent of the previous launch in the stream (the kernel waits on it before it
     // touches memory that launch writes), so its launch and prologue overlap the previous step's tail
     cudaLaunchConfig_t cfg = {};
@@ -669,6 +670,9 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     for (int k = 0; k < n_inst; k++) h->tau1 = h->tau1 && params[k].tau == 1.0;
     h->n_inst = n_inst;
     for (int k = 0; k < n_inst; k++) h->model3 = h->model3 || params[k].model == 3;
+    for (int k = 0; k < n_inst; k++)  // the flows with a time factor (vel_t), and Model III's first step
+        h->need_time = h->need_time || params[k].model == 3 || params[k].vel == LBCH_VEL_VORTEX ||
+                       params[k].vel == LBCH_VEL_DEFORM || params[k].vel == LBCH_VEL_REV_SHEAR;
     h->g_elem = prec == LBCH_F64 ? 8 : (prec == LBCH_F32 ? 4 : 2);
     h->phi_elem = prec == LBCH_F64 ? 8 : 4;  // the float path adds a float low part
     h->nq = prec == LBCH_F16S ? 8 : 9;

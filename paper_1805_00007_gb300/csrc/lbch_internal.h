@@ -40,6 +40,7 @@ struct lbch_handle {
     bool force_general = false; // test hook: keep the populations even when tau1 holds
     bool force_tile = false;    // test hook: step with the tile kernel instead of the row sweep
     bool model3 = false;        // an instance uses Model III (the tile kernel then steps the handle)
+    bool need_time = false;     // an instance's step depends on the step index (time factor, Model III)
     void* H[2] = {nullptr, nullptr};  // Model III: H of Eq. F2-1's time derivatives, 2 planes, arithmetic type
     size_t c_elem() const { return prec == LBCH_F64 ? 8 : 4; }
     bool no_pdl = false;        // test hook: plain stream-ordered step launches

@@ -381,6 +381,7 @@ struct StepArgs {
     long long H_plane;   // values per plane of H
     int t_off;           // this launch's step is ctl->time + t_off
     int t_adv;           // when nonzero, the launch's last CTA advances ctl->time by t_adv
+    int need_time;       // some instance needs the step index (a time-dependent flow or Model III)
 };
 
 template <typename C, typename S, typename P, int TX, int TY>
@@ -488,7 +489,9 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) 
             int t = blockIdx.x + j * stride;
             if (t < a.total_tiles && !(a.debug_skip && blockIdx.x == 0 && j == 0)) issue(t, j);
         }
-        s_time = a.ctl->time;
+        // the counter is read only when a flow depends on time (or Model III needs the step index);
+        // otherwise nothing waits on that load
+        s_time = a.need_time ? a.ctl->time : 0;
         if (s_tile_inst >= 0) s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
     }
     __syncthreads();
@@ -728,7 +731,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) 
         unsigned int prev = atomicAdd(&a.ctl->done, 1u);
         if (prev == gridDim.x - 1) {
             a.ctl->done = 0u;
-            a.ctl->time = n - a.t_off + a.t_adv;
+            a.ctl->time = (a.need_time ? n - a.t_off : a.ctl->time) + a.t_adv;
         }
     }
 }

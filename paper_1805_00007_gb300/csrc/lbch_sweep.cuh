@@ -49,6 +49,7 @@ struct SweepArgs {
     Ctl* ctl;
     int t_off;              // this launch's step is ctl->time + t_off
     int t_adv;              // when nonzero, the launch's last CTA advances ctl->time by t_adv
+    int need_time;          // some instance needs the step index (a time-dependent flow)
     S* g_out;               // populations (GEN): g[(row * nq + plane) * pitch + column]
     int rows;               // stored rows of the population arrays
 };
@@ -253,7 +254,8 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             const int t = blockIdx.x + j * stride;
             if (t < a.total_tiles && !(a.debug_skip && blockIdx.x == 0 && j == 0)) issue(t, j);
         }
-        s_time = a.ctl->time;
+        // the counter is read only when a flow depends on time; otherwise nothing waits on that load
+        s_time = a.need_time ? a.ctl->time : 0;
         if (s_tile_inst >= 0) s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
     }
     __syncthreads();
@@ -695,7 +697,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         const unsigned int prev = atomicAdd(&a.ctl->done, 1u);
         if (prev == gridDim.x - 1) {
             a.ctl->done = 0u;
-            a.ctl->time = s_time + a.t_adv;
+            a.ctl->time = (a.need_time ? s_time : a.ctl->time) + a.t_adv;
         }
     }
 }

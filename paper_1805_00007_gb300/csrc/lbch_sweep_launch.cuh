@@ -24,6 +24,7 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     a.ctl = h->ctl;
     a.t_off = h->t_off;
     a.t_adv = h->t_adv;
+    a.need_time = h->need_time;
     a.g_out = static_cast<S*>(h->g[parity ^ 1]);
     a.rows = h->rows;
     cudaLaunchConfig_t cfg = {};
