@@ -40,8 +40,10 @@ FLOPS_PER_LU_TAU1 = 169
 SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes (read + write) per launch of the headline kernel, from the ncu capture summarised in
-# profiles/ (kernel source hash, bytes); reported only while the kernel sources still hash the same.
-TRAFFIC = {"hash": None, "bytes_per_launch": None, "profile": None}
+# profiles/; reported only while the kernel sources still hash the same and the autotuner chose that kernel.
+TRAFFIC = {"hash": "f23f65d43c690449", "bytes_per_launch": 588800,
+           "kernel": "ch_step_kernel<float,float,float,FF=1,tile=32x16,NT=768,TAU1=1>",
+           "profile": "profiles/ch_step_f32_256_tile_headline.md"}
 KERNEL_SOURCES = ("lbch_kernels.cuh", "lbch_sweep.cuh", "lbch_sweep_launch.cuh")
 
 
@@ -406,7 +408,8 @@ def main():
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     alu_tflops = FLOPS_PER_LU_TAU1 * nodes / launch32 / 1e12
-    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["hash"] == kernel_hash() else None
+    traffic = (TRAFFIC["bytes_per_launch"]
+               if TRAFFIC["hash"] == kernel_hash() and TRAFFIC["kernel"] == kernel_name(kern32, "f32") else None)
 
     if rank == 0:
         line = {
