@@ -44,7 +44,7 @@ SMS, FP32_LANES_PER_SM = 152, 128
 TRAFFIC = {"hash": "f23f65d43c690449", "bytes_per_launch": 588800,
            "kernel": "ch_step_kernel<float,float,float,FF=1,tile=32x16,NT=768,TAU1=1>",
            "profile": "profiles/ch_step_f32_256_tile_headline.md"}
-KERNEL_SOURCES = ("lbch_kernels.cuh", "lbch_sweep.cuh", "lbch_sweep_launch.cuh")
+KERNEL_SOURCES = ("lbch_kernels.cuh", "lbch_sweep.cuh", "lbch_sweep_launch.cuh", "lbch_pair.cuh")
 
 
 def kernel_hash() -> str:
@@ -60,6 +60,9 @@ def kernel_name(k: dict, prec: str) -> str:
     if k["form"] in ("sweep", "sweep_tau1"):
         nw = k["threads"] // 32
         return f"ch_sweep_kernel<{types},TY={k['rows_per_warp']},NW={nw},GEN={int(k['form'] == 'sweep')}>"
+    if k["form"] == "pair_tau1":
+        pt = {"f32": "float,float", "f64": "double,double"}[prec]
+        return f"ch_pair_kernel<{pt},tile={k['tile'][0]}x{k['tile'][1]},NT={k['threads']}>"
     return (f"ch_step_kernel<{types},tile={k['tile'][0]}x{k['tile'][1]},NT={k['threads']},"
             f"TAU1={int(k['form'] == 'tile_tau1')}>")
 
@@ -181,6 +184,11 @@ def sweep_params(n, tau=1.0):
     return pp, wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
 
 
+def steps_per_launch(k: dict) -> int:
+    """Lattice steps one launch of the kernel takes (the two-step kernel takes two)."""
+    return 2 if k["form"] == "pair_tau1" else 1
+
+
 def run_case(case, nsteps, tile=0, form="sweep"):
     """One grid, no timing: the command ncu profiles."""
     import torch
@@ -192,6 +200,7 @@ def run_case(case, nsteps, tile=0, form="sweep"):
     with abi.Simulation(pp, f0, prec=prec, tune=tile < 0) as sim:
         if tile >= 0:
             abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, int(form == "tile"))
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TWO_STEP, int(form == "pair"))
             abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, tile)
         sim.step(nsteps)
         torch.cuda.synchronize()
@@ -237,7 +246,10 @@ def main():
                          "of that grid only")
     ap.add_argument("--case-steps", type=int, default=8)
     ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case (-1: autotune)")
-    ap.add_argument("--case-form", default="sweep", choices=["sweep", "tile"], help="kernel form for --case")
+    ap.add_argument("--case-form", default="sweep", choices=["sweep", "tile", "pair"], help="kernel form for --case")
+    ap.add_argument("--kernel", default=None,
+                    help="FORM:SHAPE (sweep|tile|pair and a shape index): pin the FP32 headline kernel instead of "
+                         "autotuning it -- for a profiler run, under which the tuner's timings are distorted")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -266,9 +278,14 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def timed_revolutions(prec, k, w):
+    def timed_revolutions(prec, k, w, pin=None):
         """Run w warm-up and k timed revolutions; returns (seconds per revolution, the simulation)."""
-        sim = abi.Simulation(p, phi0, prec=prec, stream=stream.cuda_stream, tune=True)
+        sim = abi.Simulation(p, phi0, prec=prec, stream=stream.cuda_stream, tune=pin is None)
+        if pin is not None:
+            form, shape = pin.split(":")
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, int(form == "tile"))
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TWO_STEP, int(form == "pair"))
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, int(shape))
         for _ in range(w):
             with torch.cuda.stream(stream):
                 flush_l2(flush)
@@ -289,7 +306,7 @@ def main():
 
     # --- FP32 path: the headline value
     with Clocks(local) as clk:
-        t32, sim32 = timed_revolutions("f32", args.steps, args.warmup)
+        t32, sim32 = timed_revolutions("f32", args.steps, args.warmup, args.kernel)
     t_max = t32
     if world > 1:
         t = torch.tensor([t32], device=dev, dtype=torch.float64)
@@ -310,8 +327,9 @@ def main():
 
     lu_per_rev = nodes * rev
     value = world * lu_per_rev / t_max / 1e6
-    launch32 = t32 / rev
-    achieved32 = info32["bytes_per_lu"] * nodes / launch32 / 1e9
+    spl32 = steps_per_launch(kern32)
+    launch32 = t32 / rev * spl32  # one launch of the headline kernel
+    achieved32 = info32["bytes_per_lu"] * nodes * spl32 / launch32 / 1e9
     achieved64 = info64["bytes_per_lu"] * nodes / (t64 / rev) / 1e9
 
     # --- end to end through the C ABI with host buffers: init (H2D of phi0), one revolution, read phi (D2H)
@@ -347,7 +365,8 @@ def main():
             inf = sim.info()
             gbs = inf["bytes_per_lu"] * n * n / dt / 1e9
             sweep[f"{prec}_{n}" + ("" if tau == 1.0 else f"_tau{tau}")] = {
-                "MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6, "kernel": kernel_name(sim.kernel(), prec),
+                "MLUPS": n * n / dt / 1e6, "us_per_launch": dt * 1e6 * steps_per_launch(sim.kernel()),
+                "kernel": kernel_name(sim.kernel(), prec),
                 "bytes_per_lu": inf["bytes_per_lu"], "achieved_gbs": gbs, "frac": gbs / hbm_peak}
             sim.close()
 
@@ -380,7 +399,8 @@ def main():
             ensemble[prec] = {"instances": len(ens), "nodes": enodes, "MLUPS": enodes / dt / 1e6,
                               "ranks": world, "sharding": "instances across ranks, no exchange",
                               "kernel": kernel_name(sim.kernel(), prec),
-                              "us_per_launch": dt * 1e6, "bytes_per_lu": inf["bytes_per_lu"],
+                              "us_per_launch": dt * 1e6 * steps_per_launch(sim.kernel()),
+                              "bytes_per_lu": inf["bytes_per_lu"],
                               "achieved_gbs": gbs, "frac": gbs / hbm_peak}
             sim.close()
 
@@ -407,7 +427,7 @@ def main():
     clocks = clk.summary()
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    alu_tflops = FLOPS_PER_LU_TAU1 * nodes / launch32 / 1e12
+    alu_tflops = FLOPS_PER_LU_TAU1 * nodes * spl32 / launch32 / 1e12
     traffic = (TRAFFIC["bytes_per_launch"]
                if TRAFFIC["hash"] == kernel_hash() and TRAFFIC["kernel"] == kernel_name(kern32, "f32") else None)
 
@@ -434,7 +454,7 @@ def main():
             "accuracy_one_revolution": acc,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
                     "d2h_bytes_per_step": phi0.nbytes},
-            "gpu_launches": args.steps * rev,
+            "gpu_launches": args.steps * rev // spl32,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

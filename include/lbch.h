@@ -153,12 +153,15 @@ const char* lb_ch_last_error(void);
 
 /* Sizes for a caller who times the step kernel itself: out[0] = total lattice nodes, out[1] = algorithmic
  * HBM bytes per lattice update of the step kernel (one read and one write of the stored populations and
- * of phi), out[2] = persistent thread blocks of one step launch, out[3] = current step index. */
+ * of phi; of phi alone when every tau_g = 1; half that with the two-step kernel, which reads and writes
+ * phi once per two updates), out[2] = persistent thread blocks of one step launch, out[3] = current step
+ * index. */
 lbch_status lb_ch_info(lbch_handle* h, double* out);
 
 /* Which step kernel advances the handle, for a caller who reports on it: out[0] = its form (0 = tile
  * kernel, 1 = row sweep without the populations -- every instance has tau_g = 1 --, 2 = row sweep with
- * the populations, 3 = the coupled Navier-Stokes kernels, 4 = tile kernel without the populations),
+ * the populations, 3 = the coupled Navier-Stokes kernels, 4 = tile kernel without the populations, 5 = the
+ * two-step kernel: two steps per launch, periodic instances with tau_g = 1),
  * out[1] = the shape index in use (see
  * lb_ch_tune), out[2] x out[3] = output nodes of one tile, out[4] = output rows per warp of the row
  * sweep (0 otherwise), out[5] = threads per thread block.  out must hold 6 ints. */
@@ -167,10 +170,14 @@ lbch_status lb_ch_kernel_info(lbch_handle* h, int* out);
 /* The CUDA stream the handle enqueues on (a cudaStream_t). */
 void* lb_ch_stream(lbch_handle* h);
 
-/* Kernel and tile-shape autotuner.  The step has two kernel forms, each built for several shapes: the
- * row sweep (warps sweeping 56-column strips; tiles of 56 x 48, 56 x 24 and twice 56 x 12 output nodes)
- * and the tile kernel (each tile's stencil fields staged in shared memory; 32x16, 32x8 and 16x8 with 256
- * threads and 32x16 with 768 on the float paths; 32x8 and 16x8 with 256 and 32x8 with 512 for LBCH_F64).  lb_ch_tune times `steps` steps of every candidate on the
+/* Kernel and tile-shape autotuner.  The step has three kernel forms, each built for several shapes: the
+ * row sweep (warps sweeping 56-column strips; tiles of 56 x 48, 56 x 24 and twice 56 x 12 output nodes),
+ * the tile kernel (each tile's stencil fields staged in shared memory; 32x16, 32x8 and 16x8 with 256
+ * threads and 32x16 with 768 on the float paths; 32x8 and 16x8 with 256 and 32x8 with 512 for LBCH_F64)
+ * and, for handles whose instances are all periodic with tau_g = 1 in LBCH_F32 or LBCH_F64, the two-step
+ * kernel (two steps per launch from phi on the tile + 6; 32x16 with 768 threads, 32x8 and 16x16 with 512
+ * in LBCH_F32; 32x8 with 512, 16x8 with 256 and 16x16 with 512 in LBCH_F64; an odd last step of
+ * lb_ch_step then runs the fastest one-step candidate).  lb_ch_tune times `steps` steps of every candidate on the
  * handle's own problem, restores the state after each, keeps the fastest, and reports its tile size in
  * *tile_x, *tile_y (either may be NULL).  The result of the simulation does not depend on the choice (on
  * the half-storage path with every tau_g = 1 only the row sweep is a candidate, as the tile kernel would
@@ -215,7 +222,10 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
  * lb_ch_step); the two give the same bits.  With hook LBCH_HOOK_TILE_KERNEL and value != 0, the steps
  * run the tile kernel (each tile's stencil fields staged in shared memory) instead of the row sweep, with
  * the populations; the tile shape hook then indexes its own list of shapes, and the results are the same
- * bits again.  With hook LBCH_HOOK_NO_PDL and value != 0,
+ * bits again.  With hook LBCH_HOOK_TWO_STEP and value != 0 (periodic instances with tau_g = 1 in
+ * LBCH_F32 or LBCH_F64, else LBCH_EINVAL), lb_ch_step takes the steps two at a time with the two-step
+ * kernel (the tile shape hook then indexes its list), the same bits once more; value 0 returns to the
+ * one-step kernel.  With hook LBCH_HOOK_NO_PDL and value != 0,
  * step launches are ordinary stream-ordered launches instead of programmatic dependents of the previous
  * step (whose launch and prologue overlap that step's tail); the results are the same bits.  Not for
  * production use. */
@@ -224,7 +234,8 @@ enum {
     LBCH_HOOK_TILE_SHAPE = 2,
     LBCH_HOOK_GENERAL_PATH = 3,
     LBCH_HOOK_NO_PDL = 4,
-    LBCH_HOOK_TILE_KERNEL = 5
+    LBCH_HOOK_TILE_KERNEL = 5,
+    LBCH_HOOK_TWO_STEP = 6
 };
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
 

@@ -22,7 +22,8 @@ SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb
            "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_kernel_info", "lb_ch_stream", "lb_ch_test_hook",
            "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
            "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune")
-LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL = 1, 2, 3, 4, 5
+(LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL,
+ LBCH_HOOK_TWO_STEP) = 1, 2, 3, 4, 5, 6
 
 
 class lbch_params(ctypes.Structure):
@@ -157,7 +158,7 @@ def lb_ch_free(h):
         _check(load().lb_ch_free(h), "lb_ch_free")
 
 
-KERNEL_FORMS = {0: "tile", 1: "sweep_tau1", 2: "sweep", 3: "coupled", 4: "tile_tau1"}
+KERNEL_FORMS = {0: "tile", 1: "sweep_tau1", 2: "sweep", 3: "coupled", 4: "tile_tau1", 5: "pair_tau1"}
 
 
 def lb_ch_kernel_info(h) -> dict:

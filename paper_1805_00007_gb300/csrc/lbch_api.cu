@@ -48,6 +48,7 @@ lbch_status cuda_fail(cudaError_t e, const char* what)
     } while (0)
 
 constexpr int kGraphChunk = 64;  // steps per captured graph (even, so the ping-pong parity is preserved)
+static_assert(kGraphChunk % 4 == 0, "a graph of two-step launches must hold an even number of launches");
 
 // Tile shapes the step kernel is built for (output nodes per tile; 256 threads per CTA).  lb_ch_tune
 // times them on the handle's own problem and keeps the fastest; the first one is the default.  Every
@@ -137,17 +138,32 @@ cudaError_t launch_step_t(lbch_handle* h, int parity)
 }
 
 // The row-sweep kernel steps the handle (its shape index then names a sweep configuration), without the
-// populations when every instance has tau_g = 1; the tile kernel only when a test asks for it.
+// populations when every instance has tau_g = 1; the tile kernel only when a test asks for it.  When the
+// two-step kernel is selected (and applies), it takes the steps two at a time and the one-step kernel
+// takes an odd last step.
+inline bool use_pair(const lbch_handle* h) { return h->pair && pair_ok(h); }
 inline bool use_sweep(const lbch_handle* h) { return !h->force_tile && !h->coupled && !h->model3; }
-inline int n_active(const lbch_handle* h) { return h->coupled ? 1 : (use_sweep(h) ? kSweepShapes : n_shapes(h->prec)); }
-inline const lbch_handle::PerShape& active_ps(const lbch_handle* h) { return use_sweep(h) ? h->sw[h->shape] : h->ps[h->shape]; }
+inline int n_active(const lbch_handle* h)
+{
+    return h->coupled ? 1 : (use_pair(h) ? kPairShapes : (use_sweep(h) ? kSweepShapes : n_shapes(h->prec)));
+}
+inline const lbch_handle::PerShape& active_ps(const lbch_handle* h)
+{
+    return use_pair(h) ? h->pr[h->pshape] : (use_sweep(h) ? h->sw[h->shape] : h->ps[h->shape]);
+}
 inline int active_grid(const lbch_handle* h)
 {
-    return use_sweep(h) && sweep_gen(h) ? h->sw[h->shape].grid_gen : active_ps(h).grid;
+    return !use_pair(h) && use_sweep(h) && sweep_gen(h) ? h->sw[h->shape].grid_gen : active_ps(h).grid;
 }
 inline Shape active_tile(const lbch_handle* h)
 {
-    return h->coupled ? Shape{0, 0} : (use_sweep(h) ? sweep_tile(h->shape) : shape_of(h->prec, h->shape));
+    return h->coupled ? Shape{0, 0}
+         : use_pair(h) ? pair_shape(h->prec, h->pshape) : (use_sweep(h) ? sweep_tile(h->shape) : shape_of(h->prec, h->shape));
+}
+inline void drop_graphs(lbch_handle* h)  // graphs captured earlier launch another kernel or shape
+{
+    for (int k = 0; k < 2; k++)
+        if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
 }
 
 cudaError_t launch_sweep(lbch_handle* h, int parity)
@@ -280,6 +296,20 @@ cudaError_t launch_step(lbch_handle* h, int parity)
     }
 }
 
+// Two steps by one launch of the two-step kernel, outside a graph (the launch advances the counter by
+// two); phi(n + 2) lands in the other buffer, so the buffer of the current step flips.
+cudaError_t launch_pair_now(lbch_handle* h)
+{
+    h->t_adv = 2;
+    cudaError_t e = lbch_launch_pair(h, cur_buf(h));
+    h->t_adv = 1;
+    if (e == cudaSuccess) {
+        h->n += 2;
+        h->flip ^= 1;
+    }
+    return e;
+}
+
 lbch_status check_params(const lbch_params& p, int k)
 {
     if (p.nx < 4 || p.ny < 4 || p.nx > (1 << 20) || p.ny > (1 << 20))
@@ -397,6 +427,8 @@ void release(lbch_handle* h)
         if (h->ps[k].d_tile_begin) cudaFree(h->ps[k].d_tile_begin);
     for (int k = 0; k < kSweepShapes; k++)
         if (h->sw[k].d_tile_begin) cudaFree(h->sw[k].d_tile_begin);
+    for (int k = 0; k < kPairShapes; k++)
+        if (h->pr[k].d_tile_begin) cudaFree(h->pr[k].d_tile_begin);
     if (h->d_node_begin) cudaFree(h->d_node_begin);
     if (h->d_tabs) cudaFree(h->d_tabs);
     if (h->phi0) cudaFree(h->phi0);
@@ -531,7 +563,7 @@ lbch_status check_err(lbch_handle* h)
 
 lbch_status run_reduce(lbch_handle* h)
 {
-    int parity = (int)(h->n & 1);
+    int parity = cur_buf(h);
     dim3 grid(h->chunks, h->n_inst);
     if (h->phi_elem == 8)
         reduce_partials_kernel<double><<<grid, RED_NT, 0, h->stream>>>(h->d_inst, (const double*)h->phi[parity], nullptr, h->phi0,
@@ -670,6 +702,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     for (int k = 0; k < n_inst; k++) h->tau1 = h->tau1 && params[k].tau == 1.0;
     h->n_inst = n_inst;
     for (int k = 0; k < n_inst; k++) h->model3 = h->model3 || params[k].model == 3;
+    for (int k = 0; k < n_inst; k++) h->walls = h->walls || params[k].walls != 0;
     for (int k = 0; k < n_inst; k++)  // the flows with a time factor (vel_t), and Model III's first step
         h->need_time = h->need_time || params[k].model == 3 || params[k].vel == LBCH_VEL_VORTEX ||
                        params[k].vel == LBCH_VEL_DEFORM || params[k].vel == LBCH_VEL_REV_SHEAR;
@@ -721,6 +754,17 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         sweep_begin[sk].push_back(t);
         h->sw[sk].total_tiles = t;
     }
+    std::vector<int> pair_begin[kPairShapes];
+    for (int sk = 0; sk < kPairShapes; sk++) {
+        const Shape sh = pair_shape(prec, sk);
+        int t = 0;
+        for (int k = 0; k < n_inst; k++) {
+            pair_begin[sk].push_back(t);
+            t += ((params[k].nx + sh.tx - 1) / sh.tx) * ((params[k].ny + sh.ty - 1) / sh.ty);
+        }
+        pair_begin[sk].push_back(t);
+        h->pr[sk].total_tiles = t;
+    }
     for (int k = 0; k < n_inst; k++) {
         h->inst[k].tab = (int)tabs.size();
         velocity_tables(params[k], h->pitch, h->inst[k].ylen, tabs);
@@ -745,6 +789,12 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
             CKI(prepare_sweep(h, sk));
             CKI(cudaMalloc(&h->sw[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
             CKI(cudaMemcpy(h->sw[sk].d_tile_begin, sweep_begin[sk].data(), sizeof(int) * (n_inst + 1),
+                           cudaMemcpyHostToDevice));
+        }
+        for (int sk = 0; sk < kPairShapes && prec != LBCH_F16S; sk++) {
+            CKI(lbch_prepare_pair(h, sk));
+            CKI(cudaMalloc(&h->pr[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
+            CKI(cudaMemcpy(h->pr[sk].d_tile_begin, pair_begin[sk].data(), sizeof(int) * (n_inst + 1),
                            cudaMemcpyHostToDevice));
         }
     }
@@ -857,18 +907,22 @@ lbch_status lb_ch_step(lbch_handle* h, long nsteps)
 {
     if (!h || nsteps < 0) return fail(LBCH_EINVAL, "NULL handle or negative step count");
     static const bool no_graph = std::getenv("LBCH_NO_GRAPH") != nullptr;
+    const bool two = use_pair(h);
     while (nsteps > 0) {
-        int parity = (int)(h->n & 1);
+        int parity = cur_buf(h);
         if (!no_graph && !h->debug_skip && nsteps >= kGraphChunk) {
             if (!h->graph[parity]) {
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
                 cudaError_t e = cudaSuccess;
-                // step k of the graph is the counter + k; only the last launch advances the counter
-                for (int s = 0; s < kGraphChunk && e == cudaSuccess; s++) {
-                    h->t_off = s;
-                    h->t_adv = s == kGraphChunk - 1 ? kGraphChunk : 0;
-                    e = launch_step(h, parity ^ (s & 1));
+                // step k of the graph is the counter + k; only the last launch advances the counter.  With
+                // the two-step kernel, launch s takes steps 2s and 2s + 1; the chunk's launch count is even,
+                // so the graph ends in the buffer it starts from, as the one-step graph does.
+                const int per = two ? 2 : 1, launches = kGraphChunk / per;
+                for (int s = 0; s < launches && e == cudaSuccess; s++) {
+                    h->t_off = s * per;
+                    h->t_adv = s == launches - 1 ? kGraphChunk : 0;
+                    e = two ? lbch_launch_pair(h, parity ^ (s & 1)) : launch_step(h, parity ^ (s & 1));
                 }
                 h->t_off = 0;
                 h->t_adv = 1;
@@ -882,6 +936,9 @@ lbch_status lb_ch_step(lbch_handle* h, long nsteps)
             CK(cudaGraphLaunch(h->graph[parity], h->stream));
             h->n += kGraphChunk;
             nsteps -= kGraphChunk;
+        } else if (two && nsteps >= 2) {
+            CK(launch_pair_now(h));
+            nsteps -= 2;
         } else {
             CK(launch_step(h, parity));
             h->n += 1;
@@ -901,7 +958,7 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out)
     }
     if (what == LBCH_OBS_PHI) {
         const InstDev& d = h->inst[inst];
-        int parity = (int)(h->n & 1);
+        int parity = cur_buf(h);
         lbch_status s = stage(h, (size_t)d.nx * d.ny * sizeof(double));
         if (s != LBCH_OK) return s;
         const size_t off = (size_t)d.row0 * h->pitch + GC;
@@ -929,7 +986,7 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out)
     }
     if (what == LBCH_OBS_U || what == LBCH_OBS_P) {
         if (!h->coupled) return fail(LBCH_EINVAL, "velocity and pressure are observable on coupled handles only");
-        const int parity = (int)(h->n & 1);
+        const int parity = cur_buf(h);
         CK(h->prec == LBCH_F64 ? ns_fields_t<double>(h, parity) : ns_fields_t<float>(h, parity));
         const size_t N = (size_t)h->inst[0].nx * h->inst[0].ny, e = h->prec == LBCH_F64 ? 8 : 4;
         lbch_status s = stage(h, 2 * N * sizeof(double));
@@ -1014,6 +1071,7 @@ lbch_status lb_ch_info(lbch_handle* h, double* out)
     double bytes = 2.0 * (h->nq * (double)h->g_elem + (double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
     if (h->tau1 && !h->force_general)  // only phi is read and written (either kernel form)
         bytes = 2.0 * ((double)h->phi_elem + (h->lo[0] ? 4.0 : 0.0));
+    if (use_pair(h)) bytes *= 0.5;     // the two-step kernel reads and writes phi once per two updates
     if (h->model3) bytes += 2.0 * 2.0 * (double)h->c_elem();  // H of Model III, read and written
     if (h->coupled) {  // f and g read and written, phi read and written, u and p written and read
         const double e = h->prec == LBCH_F64 ? 8.0 : 4.0;
@@ -1031,11 +1089,12 @@ lbch_status lb_ch_kernel_info(lbch_handle* h, int* out)
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     const Shape sh = active_tile(h);
     const bool sw = use_sweep(h);
-    out[0] = h->coupled ? 3 : (!sw ? (sweep_gen(h) ? 0 : 4) : (sweep_gen(h) ? 2 : 1));
-    out[1] = h->shape;
+    const bool pr = use_pair(h);
+    out[0] = h->coupled ? 3 : pr ? 5 : (!sw ? (sweep_gen(h) ? 0 : 4) : (sweep_gen(h) ? 2 : 1));
+    out[1] = pr ? h->pshape : h->shape;
     out[2] = sh.tx;
     out[3] = sh.ty;
-    out[4] = sw ? kSweep[h->shape].ty : 0;
+    out[4] = sw && !pr ? kSweep[h->shape].ty : 0;
     out[5] = h->coupled ? 256 : sh.nt;
     return LBCH_OK;
 }
@@ -1053,7 +1112,7 @@ lbch_status lb_ch_state_save(lbch_handle* h, void* dst)
 {
     if (!h || !dst) return fail(LBCH_EINVAL, "NULL handle or buffer");
     if (h->coupled) return fail(LBCH_EINVAL, "checkpoints are for prescribed-flow handles");
-    const int par = (int)(h->n & 1);
+    const int par = cur_buf(h);
     const size_t cells = (size_t)h->rows * h->pitch;
     char* p = static_cast<char*>(dst);
     long long n = h->n;
@@ -1094,6 +1153,7 @@ lbch_status lb_ch_state_load(lbch_handle* h, const void* src)
     CK(cudaMemcpyAsync(&h->ctl->time, &n, sizeof n, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->n = n;
+    h->flip = 0;  // the state was written into the buffers of step n
     return LBCH_OK;
 }
 
@@ -1101,7 +1161,7 @@ lbch_status lb_ch_tape_phi(lbch_handle* h, void* dst)
 {
     if (!h || !dst) return fail(LBCH_EINVAL, "NULL handle or buffer");
     if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
-    const int par = (int)(h->n & 1);
+    const int par = cur_buf(h);
     const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
     const int nb = (int)((N + 255) / 256);
     if (h->prec == LBCH_F64)
@@ -1160,12 +1220,15 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
     // Candidates: every row-sweep configuration and every tile kernel shape.  The two forms give the same
     // bits except on the half-storage path at tau_g = 1, where the tile kernel streams populations rounded
     // to half and the sweep keeps only phi; there the sweep alone is a candidate.
-    struct Cand { bool tile; int shape; };
+    // Where it applies, the two-step kernel is a candidate too (it then takes the steps two at a time; an odd
+    // last step goes to the fastest one-step candidate).
+    struct Cand { bool tile, pair; int shape; };
     std::vector<Cand> cands;
     if (!h->coupled) {
-        for (int k = 0; k < kSweepShapes && !h->model3; k++) cands.push_back({false, k});
+        for (int k = 0; k < kSweepShapes && !h->model3; k++) cands.push_back({false, false, k});
         if (!(h->prec == LBCH_F16S && h->tau1 && !h->force_general))
-            for (int k = 0; k < n_shapes(h->prec); k++) cands.push_back({true, k});
+            for (int k = 0; k < n_shapes(h->prec); k++) cands.push_back({true, false, k});
+        for (int k = 0; k < kPairShapes && pair_ok(h); k++) cands.push_back({false, true, k});
     }
     const int ns = (int)cands.size();
     if (ns > 1) {
@@ -1175,22 +1238,37 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
         CK(cudaMalloc(&backup, (size_t)bytes));
         lbch_status s = lb_ch_state_save(h, backup);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        float best_ms = 0.0f;
-        Cand best = {h->force_tile, h->shape};
+        float best_ms = 0.0f, best1_ms = 0.0f;  // per step: over all candidates; over the one-step ones
+        Cand best = {h->force_tile, use_pair(h), use_pair(h) ? h->pshape : h->shape};
+        Cand best1 = {h->force_tile, false, h->shape};
+        const int steps2 = (steps + 1) / 2;  // launches of a two-step candidate
         if (s == LBCH_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
             for (int k = 0; k < ns && s == LBCH_OK; k++) {
-                h->force_tile = cands[k].tile;
-                h->shape = cands[k].shape;
+                const Cand c = cands[k];
+                h->pair = c.pair;
+                if (c.pair) h->pshape = c.shape;
+                else { h->force_tile = c.tile; h->shape = c.shape; }
                 cudaError_t e = cudaSuccess;
-                for (int w = 0; w < 2 && e == cudaSuccess; w++) { e = launch_step(h, (int)(h->n & 1)); h->n++; }
+                auto one = [&]() {
+                    if (c.pair) return launch_pair_now(h);
+                    cudaError_t r = launch_step(h, cur_buf(h));
+                    h->n++;
+                    return r;
+                };
+                for (int w = 0; w < 2 && e == cudaSuccess; w++) e = one();
                 e = e == cudaSuccess ? cudaEventRecord(e0, h->stream) : e;
-                for (int i = 0; i < steps && e == cudaSuccess; i++) { e = launch_step(h, (int)(h->n & 1)); h->n++; }
+                const int launches = c.pair ? steps2 : steps;
+                for (int i = 0; i < launches && e == cudaSuccess; i++) e = one();
                 e = e == cudaSuccess ? cudaEventRecord(e1, h->stream) : e;
                 e = e == cudaSuccess ? cudaEventSynchronize(e1) : e;
                 float ms = 0.0f;
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                ms /= (float)(c.pair ? 2 * steps2 : steps);
                 if (e != cudaSuccess) s = cuda_fail(e, "timing a tile shape");
-                else if (k == 0 || ms < best_ms) { best_ms = ms; best = cands[k]; }
+                else {
+                    if (k == 0 || ms < best_ms) { best_ms = ms; best = c; }
+                    if (!c.pair && (k == 0 || ms < best1_ms)) { best1_ms = ms; best1 = c; }
+                }
                 lbch_status r = lb_ch_state_load(h, backup);  // every candidate starts from the same state
                 if (s == LBCH_OK) s = r;
             }
@@ -1198,11 +1276,12 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         cudaFree(backup);
-        h->force_tile = best.tile;
-        h->shape = best.shape;
+        h->force_tile = best1.tile;
+        h->shape = best1.shape;
+        h->pair = best.pair;
+        if (best.pair) h->pshape = best.shape;
         if (s != LBCH_OK) return s;
-        for (int k = 0; k < 2; k++)  // graphs captured earlier launch the previous shape's kernel
-            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        drop_graphs(h);  // graphs captured earlier launch the previous shape's kernel
     }
     const Shape sh = active_tile(h);
     if (tile_x) *tile_x = sh.tx;
@@ -1223,6 +1302,14 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
         return LBCH_OK;
     }
+    if (hook == LBCH_HOOK_TWO_STEP) {
+        if (value && !pair_ok(h))
+            return fail(LBCH_EINVAL, "the two-step kernel needs periodic instances with tau_g = 1 in f32 or f64");
+        h->pair = value != 0;
+        h->pshape = 0;
+        drop_graphs(h);
+        return LBCH_OK;
+    }
     if (hook == LBCH_HOOK_TILE_KERNEL) {
         if (h->coupled) return fail(LBCH_EINVAL, "the coupled flow has no tile kernel");
         if (h->force_tile != (value != 0)) h->shape = 0;  // the shape index names the other kernel's list
@@ -1239,7 +1326,7 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
     }
     if (hook == LBCH_HOOK_TILE_SHAPE) {
         if (h->coupled || value < 0 || value >= n_active(h)) return fail(LBCH_EINVAL, "no tile shape %ld", value);
-        h->shape = (int)value;
+        (use_pair(h) ? h->pshape : h->shape) = (int)value;
         for (int k = 0; k < 2; k++)
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
         return LBCH_OK;

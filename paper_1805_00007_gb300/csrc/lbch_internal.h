@@ -18,6 +18,12 @@ constexpr int kSweepShapes = 4;
 constexpr int kSweepW = 56;
 inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw, 32 * kSweep[k].nw}; }
 
+// Tile shapes of the two-step kernel (periodic instances, tau_g = 1; f32 and f64 only).
+constexpr int kPairShapes = 3;
+constexpr Shape kPairF[kPairShapes] = {{32, 16, 768}, {32, 8, 512}, {16, 16, 512}};
+constexpr Shape kPair64[kPairShapes] = {{32, 8, 512}, {16, 8, 256}, {16, 16, 512}};
+inline Shape pair_shape(int prec, int k) { return prec == LBCH_F64 ? kPair64[k] : kPairF[k]; }
+
 struct lbch_handle {
     int device = 0;
     int prec = LBCH_F64;
@@ -39,6 +45,9 @@ struct lbch_handle {
     bool tau1 = false;          // every instance has tau_g = 1: the populations drop out of the step
     bool force_general = false; // test hook: keep the populations even when tau1 holds
     bool force_tile = false;    // test hook: step with the tile kernel instead of the row sweep
+    bool pair = false;          // step two at a time with the two-step kernel (when pair_ok holds); odd
+    int pshape = 0;             // steps take the one-step kernel above; pshape indexes pair_shape()
+    bool walls = false;         // an instance has walls
     bool model3 = false;        // an instance uses Model III (the tile kernel then steps the handle)
     bool need_time = false;     // an instance's step depends on the step index (time factor, Model III)
     void* H[2] = {nullptr, nullptr};  // Model III: H of Eq. F2-1's time derivatives, 2 planes, arithmetic type
@@ -50,7 +59,8 @@ struct lbch_handle {
         int grid_gen = 0;       // row sweep with the populations (the tile kernel uses grid)
         int* d_tile_begin = nullptr;
         CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
-    } ps[kMaxShapes], sw[kSweepShapes];  // tile kernel shapes; row-sweep configurations (tm_g unused)
+    } ps[kMaxShapes], sw[kSweepShapes], pr[kPairShapes];  // tile kernel shapes; row-sweep configurations
+                                                          // (tm_g unused); two-step shapes (no maps)
     CUtensorMap tm_grow[2], tm_lorow[2];  // one row of the populations / of phi's low part (row sweep)
     void* g[2] = {nullptr, nullptr};
     void* phi[2] = {nullptr, nullptr};
@@ -61,6 +71,7 @@ struct lbch_handle {
     double* result = nullptr;   // n_inst * RED_NV doubles
     int chunks = 0;
     long long n = 0;            // host mirror of the step index
+    int flip = 0;               // the state of step n is in buffer (n & 1) ^ flip (two-step launches toggle it)
     int t_off = 0, t_adv = 1;   // the next launch's step offset and counter advance (see Ctl)
     int debug_skip = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -83,8 +94,18 @@ template <typename C> inline const C* tables(lbch_handle* h);
 template <> inline const double* tables<double>(lbch_handle* h) { return h->d_tabs; }
 template <> inline const float* tables<float>(lbch_handle* h) { return h->d_tabs_f; }
 
+// The buffer (0 or 1 of each ping-pong pair) holding the state of the current step.
+inline int cur_buf(const lbch_handle* h) { return (int)(h->n & 1) ^ h->flip; }
+
 // The row sweep keeps the populations unless every instance has tau_g = 1 (and no test asks for them).
 inline bool sweep_gen(const lbch_handle* h) { return !h->tau1 || h->force_general; }
+
+// The two-step kernel serves handles whose instances are all periodic with tau_g = 1, in f32 or f64 (the
+// half-storage path is left to the row sweep).
+inline bool pair_ok(const lbch_handle* h)
+{
+    return h->tau1 && !h->force_general && !h->coupled && !h->model3 && !h->walls && h->prec != LBCH_F16S;
+}
 
 // Row-sweep launches and set-up, one translation unit per precision (lbch_sweep_*.cu).
 #define LBCH_INTERNAL __attribute__((visibility("hidden")))
@@ -94,3 +115,6 @@ LBCH_INTERNAL cudaError_t lbch_launch_sweep_f16s(lbch_handle* h, int parity);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f64(lbch_handle* h, int k);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f32(lbch_handle* h, int k);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f16s(lbch_handle* h, int k);
+// Two-step launches and set-up (lbch_pair.cu); the handle's shape index names a pair_shape().
+LBCH_INTERNAL cudaError_t lbch_launch_pair(lbch_handle* h, int parity);
+LBCH_INTERNAL cudaError_t lbch_prepare_pair(lbch_handle* h, int k);
