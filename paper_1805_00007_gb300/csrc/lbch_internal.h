@@ -19,9 +19,9 @@ constexpr int kSweepW = 56;
 inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw, 32 * kSweep[k].nw}; }
 
 // Tile shapes of the two-step kernel (periodic instances, tau_g = 1; f32 and f64 only).
-constexpr int kPairShapes = 3;
-constexpr Shape kPairF[kPairShapes] = {{32, 16, 768}, {32, 8, 512}, {16, 16, 512}};
-constexpr Shape kPair64[kPairShapes] = {{32, 8, 512}, {16, 8, 256}, {16, 16, 512}};
+constexpr int kPairShapes = 4;
+constexpr Shape kPairF[kPairShapes] = {{32, 16, 768}, {32, 14, 1024}, {32, 16, 1024}, {32, 8, 512}};
+constexpr Shape kPair64[kPairShapes] = {{32, 8, 512}, {16, 8, 256}, {16, 16, 512}, {32, 14, 1024}};
 inline Shape pair_shape(int prec, int k) { return prec == LBCH_F64 ? kPair64[k] : kPairF[k]; }
 
 struct lbch_handle {
@@ -115,6 +115,6 @@ LBCH_INTERNAL cudaError_t lbch_launch_sweep_f16s(lbch_handle* h, int parity);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f64(lbch_handle* h, int k);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f32(lbch_handle* h, int k);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f16s(lbch_handle* h, int k);
-// Two-step launches and set-up (lbch_pair.cu); the handle's shape index names a pair_shape().
+// Two-step launches and set-up (lbch_pair.cu); pshape names a pair_shape().
 LBCH_INTERNAL cudaError_t lbch_launch_pair(lbch_handle* h, int parity);
 LBCH_INTERNAL cudaError_t lbch_prepare_pair(lbch_handle* h, int k);

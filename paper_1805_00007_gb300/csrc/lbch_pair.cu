@@ -47,8 +47,7 @@ cudaError_t prepare_pair_v(lbch_handle* h, int k)
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     h->pr[k].grid = std::max(1, std::min(h->pr[k].total_tiles, per_sm * sms));
@@ -66,9 +65,11 @@ cudaError_t lbch_launch_pair(lbch_handle* h, int parity)
     if (k < 0 || k >= kPairShapes || !h->pr[k].d_tile_begin || h->pr[k].grid < 1) return cudaErrorInvalidValue;
     if (h->prec == LBCH_F64)
         return k == 0 ? launch_pair_v<double, double, 32, 8, 512>(h, parity)
-             : k == 1 ? launch_pair_v<double, double, 16, 8, 256>(h, parity) : launch_pair_v<double, double, 16, 16, 512>(h, parity);
+             : k == 1 ? launch_pair_v<double, double, 16, 8, 256>(h, parity)
+             : k == 2 ? launch_pair_v<double, double, 16, 16, 512>(h, parity) : launch_pair_v<double, double, 32, 14, 1024>(h, parity);
     return k == 0 ? launch_pair_v<float, float, 32, 16, 768>(h, parity)
-         : k == 1 ? launch_pair_v<float, float, 32, 8, 512>(h, parity) : launch_pair_v<float, float, 16, 16, 512>(h, parity);
+         : k == 1 ? launch_pair_v<float, float, 32, 14, 1024>(h, parity)
+         : k == 2 ? launch_pair_v<float, float, 32, 16, 1024>(h, parity) : launch_pair_v<float, float, 32, 8, 512>(h, parity);
 }
 
 cudaError_t lbch_prepare_pair(lbch_handle* h, int k)
@@ -76,7 +77,9 @@ cudaError_t lbch_prepare_pair(lbch_handle* h, int k)
     using namespace lbch;
     if (h->prec == LBCH_F64)
         return k == 0 ? prepare_pair_v<double, double, 32, 8, 512>(h, k)
-             : k == 1 ? prepare_pair_v<double, double, 16, 8, 256>(h, k) : prepare_pair_v<double, double, 16, 16, 512>(h, k);
+             : k == 1 ? prepare_pair_v<double, double, 16, 8, 256>(h, k)
+             : k == 2 ? prepare_pair_v<double, double, 16, 16, 512>(h, k) : prepare_pair_v<double, double, 32, 14, 1024>(h, k);
     return k == 0 ? prepare_pair_v<float, float, 32, 16, 768>(h, k)
-         : k == 1 ? prepare_pair_v<float, float, 32, 8, 512>(h, k) : prepare_pair_v<float, float, 16, 16, 512>(h, k);
+         : k == 1 ? prepare_pair_v<float, float, 32, 14, 1024>(h, k)
+         : k == 2 ? prepare_pair_v<float, float, 32, 16, 1024>(h, k) : prepare_pair_v<float, float, 32, 8, 512>(h, k);
 }

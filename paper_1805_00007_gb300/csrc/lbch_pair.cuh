@@ -150,110 +150,215 @@ __device__ __forceinline__ P pair_phi(P h_in, float lo_in, C v0, C sumq, float& 
     return (P)(v0 + sumq);
 }
 
+// Shared-memory views of one CTA's regions.
+template <typename C, typename P, int TX, int TY>
+struct PairSmem {
+    P* phi0;     // phi(t) on tile + 6
+    float* lo0;  // its low part on tile + 3 (float path)
+    P* hi1;      // phi(t+1) on tile + 3
+    float* lo1;
+    C *mu, *D;   // mu and D of the step in progress
+    C* post;     // post-collision populations of the step in progress, nine planes
+    C *X1, *X2, *Y1, *Y2;  // velocity tables over the columns / rows of tile + 6
+    __device__ explicit PairSmem(unsigned char* raw)
+    {
+        using L = PairShape<C, P, TX, TY>;
+        unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+        phi0 = reinterpret_cast<P*>(base);
+        lo0 = reinterpret_cast<float*>(base + L::OFF_LO0);
+        hi1 = reinterpret_cast<P*>(base + L::OFF_HI1);
+        lo1 = reinterpret_cast<float*>(base + L::OFF_LO1);
+        mu = reinterpret_cast<C*>(base + L::OFF_MU);
+        D = reinterpret_cast<C*>(base + L::OFF_D);
+        post = reinterpret_cast<C*>(base + L::OFF_POST);
+        X1 = reinterpret_cast<C*>(base + L::OFF_TAB);
+        X2 = X1 + L::W6;
+        Y1 = X2 + L::W6;
+        Y2 = Y1 + L::H6;
+    }
+};
+
+// The velocity tables of tile + 6 by wrapped stored column and row (constant after set-up).
 template <typename C, typename P, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(PairArgs<C, P> a)
+__device__ __forceinline__ void pair_tables(const PairSmem<C, P, TX, TY>& S, const InstDev& I, const C* tabs, int pitch,
+                                            int x0, int y0)
+{
+    constexpr int W6 = PairShape<C, P, TX, TY>::W6, H6 = PairShape<C, P, TX, TY>::H6;
+    const C* tX1 = tabs + I.tab;
+    const C* tY1 = tX1 + 2 * pitch;
+    for (int e = threadIdx.x; e < 2 * (W6 + H6); e += NT) {
+        if (e < 2 * W6) {
+            const int j = e >= W6, c = e - j * W6;
+            S.X1[e] = __ldg(tX1 + j * pitch + GC + wrap_near(x0 - 6 + c, I.nx));
+        } else {
+            const int j = (e - 2 * W6) >= H6, r = e - 2 * W6 - j * H6;
+            S.Y1[e - 2 * W6] = __ldg(tY1 + j * I.ylen + GR + wrap_near(y0 - 6 + r, I.ny));
+        }
+    }
+}
+
+// The values one thread loads for a tile: phi on tile + 6 and (float path) its low part on tile + 3, at
+// periodically wrapped domain positions.  The offsets, from the instance's first domain node, are computed
+// once per tile; -1 marks no value.
+template <typename C, typename P, int TX, int TY, int NT>
+struct PairLoad {
+    using L = PairShape<C, P, TX, TY>;
+    static constexpr int IT6 = (L::N6 + NT - 1) / NT, IT3 = (L::N3 + NT - 1) / NT;
+    long long o6[IT6], o3[IT3];
+    __device__ void init(const InstDev& I, int pitch, int x0, int y0)
+    {
+#pragma unroll
+        for (int i = 0; i < IT6; i++) {
+            const int e = threadIdx.x + i * NT, r = e / L::W6, c = e - r * L::W6;
+            o6[i] = e < L::N6 ? (long long)wrap_near(y0 - 6 + r, I.ny) * pitch + wrap_near(x0 - 6 + c, I.nx) : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < IT3; i++) {
+            const int e = threadIdx.x + i * NT, r = e / L::W3, c = e - r * L::W3;
+            o3[i] = e < L::N3 && L::FF ? (long long)wrap_near(y0 - 3 + r, I.ny) * pitch + wrap_near(x0 - 3 + c, I.nx) : -1;
+        }
+    }
+    // every load is in flight before the first store to shared memory; L2 only (another CTA wrote them)
+    __device__ void load(const PairSmem<C, P, TX, TY>& S, const P* phi, const float* lo) const
+    {
+        P v[IT6];
+        float w[IT3];
+#pragma unroll
+        for (int i = 0; i < IT6; i++)
+            if (o6[i] >= 0) v[i] = __ldcg(phi + o6[i]);
+#pragma unroll
+        for (int i = 0; i < IT3; i++)
+            if (o3[i] >= 0) w[i] = __ldcg(lo + o3[i]);
+#pragma unroll
+        for (int i = 0; i < IT6; i++)
+            if (o6[i] >= 0) S.phi0[threadIdx.x + i * NT] = v[i];
+#pragma unroll
+        for (int i = 0; i < IT3; i++)
+            if (o3[i] >= 0) S.lo0[threadIdx.x + i * NT] = w[i];
+    }
+};
+
+// Steps t and t+1 of one tile from phi(t) and the tables in shared memory (loaded and synchronised by the
+// caller): phi(t+2) of the tile's domain nodes and their ghost images into phi_out (rb: the instance's first
+// domain node).  T0, T1: the flow's time factor at the two steps.  Ends without a barrier.
+template <typename C, typename P, int TX, int TY, int NT>
+__device__ __forceinline__ void pair_steps(const PairSmem<C, P, TX, TY>& S, const InstDev& I, C T0, C T1, int x0,
+                                           int y0, int pitch, long long rb, P* phi_out, float* lo_out)
 {
     using L = PairShape<C, P, TX, TY>;
     constexpr bool kFF = L::FF;
     constexpr bool kShift = sizeof(C) == 4;  // float arithmetic carries g_0 - phi
-    constexpr int W6 = L::W6, H6 = L::H6, W3 = L::W3;
+    constexpr int W6 = L::W6, W3 = L::W3;
     constexpr int NONE = -0x40000000;
-    constexpr int IT6 = (L::N6 + NT - 1) / NT, IT3 = (L::N3 + NT - 1) / NT;
+    const int tid = threadIdx.x;
+    const Consts<C>& K0 = consts<C>(I);
+    const bool model2 = I.model == 2;
 
+    // step t: mu, D on tile + 5; collision on tile + 4; streaming to phi(t+1) on tile + 3
+    pair_mu_div<C, P, L::W5, L::H5, W6, NT>(S.phi0, S.X1, S.X2, S.Y1, S.Y2, 0, K0, model2, T0, S.mu, S.D);
+    __syncthreads();
+    pair_collide<C, P, L::W4, L::H4, L::W5, W6, NT, kShift>(S.phi0, S.mu, S.D, S.X1, S.X2, S.Y1, S.Y2, 2, K0, model2, T0,
+                                                           S.post);
+    __syncthreads();
+    for (int e = tid; e < L::N3; e += NT) {
+        const int r = e / W3, c = e - r * W3;
+        C v0;
+        const C sumq = pair_pull<C, W3, L::N4>(S.post, r, c, v0);
+        float lo1;
+        S.hi1[e] = pair_phi<C, P, kFF>(S.phi0[(r + 3) * W6 + c + 3], kFF ? S.lo0[e] : 0.0f, v0, sumq, lo1);
+        if (kFF) S.lo1[e] = lo1;
+    }
+    __syncthreads();
+
+    // step t+1: mu, D on tile + 2; collision on tile + 1; streaming to phi(t+2) on the tile
+    pair_mu_div<C, P, L::W2, L::H2, W3, NT>(S.hi1, S.X1, S.X2, S.Y1, S.Y2, 3, K0, model2, T1, S.mu, S.D);
+    __syncthreads();
+    pair_collide<C, P, L::W1, L::H1, L::W2, W3, NT, kShift>(S.hi1, S.mu, S.D, S.X1, S.X2, S.Y1, S.Y2, 5, K0, model2, T1,
+                                                           S.post);
+    __syncthreads();
+    const int nx = I.nx, ny = I.ny;
+    for (int e = tid; e < TX * TY; e += NT) {
+        const int r = e / TX, c = e - r * TX;
+        const int gx = x0 + c, gy = y0 + r;
+        if (gx >= nx || gy >= ny) continue;
+        C v0;
+        const C sumq = pair_pull<C, TX, L::N1>(S.post, r, c, v0);
+        const int h1 = (r + 3) * W3 + c + 3;
+        float lo;
+        const P hi = pair_phi<C, P, kFF>(S.hi1[h1], kFF ? S.lo1[h1] : 0.0f, v0, sumq, lo);
+        const long long node = rb + (long long)gy * pitch + gx;
+        phi_out[node] = hi;
+        if (kFF) lo_out[node] = lo;
+        if (gx < 3 || gx >= nx - 3 || gy < 3 || gy >= ny - 3) {
+            // the node's periodic images in the ghost frame (three deep), read by one-step launches
+            const int xa = gx < 3 ? gx + nx : NONE, xb = gx >= nx - 3 ? gx - nx : NONE;
+            const int ya = gy < 3 ? gy + ny : NONE, yb = gy >= ny - 3 ? gy - ny : NONE;
+            for (int iy = 0; iy < 3; iy++) {
+                const int yy = iy == 0 ? gy : (iy == 1 ? ya : yb);
+                if (yy == NONE) continue;
+                for (int ix = 0; ix < 3; ix++) {
+                    const int xx = ix == 0 ? gx : (ix == 1 ? xa : xb);
+                    if (xx == NONE || (ix == 0 && iy == 0)) continue;
+                    phi_out[rb + (long long)yy * pitch + xx] = hi;
+                }
+            }
+        }
+    }
+}
+
+// The instance and origin of tile t.
+template <int TX, int TY>
+__device__ __forceinline__ void pair_locate(const int* tile_begin, int n_inst, const InstDev* inst, int t, int& k,
+                                            int& x0, int& y0)
+{
+    k = find_inst(tile_begin, n_inst, t);
+    const int local = t - tile_begin[k];
+    const int tiles_x = (inst[k].nx + TX - 1) / TX;
+    x0 = (local % tiles_x) * TX;
+    y0 = (local / tiles_x) * TY;
+}
+
+// One launch per two steps: a persistent CTA walks its tiles.
+template <typename C, typename P, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(PairArgs<C, P> a)
+{
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    P* s_phi0 = reinterpret_cast<P*>(base);
-    float* s_lo0 = reinterpret_cast<float*>(base + L::OFF_LO0);
-    P* s_hi1 = reinterpret_cast<P*>(base + L::OFF_HI1);
-    float* s_lo1 = reinterpret_cast<float*>(base + L::OFF_LO1);
-    C* s_mu = reinterpret_cast<C*>(base + L::OFF_MU);
-    C* s_D = reinterpret_cast<C*>(base + L::OFF_D);
-    C* s_post = reinterpret_cast<C*>(base + L::OFF_POST);
-    C* sX1 = reinterpret_cast<C*>(base + L::OFF_TAB);  // X1, X2 over the columns of tile + 6
-    C* sX2 = sX1 + W6;
-    C* sY1 = sX2 + W6;                                 // Y1, Y2 over its rows
-    C* sY2 = sY1 + H6;
-
+    const PairSmem<C, P, TX, TY> S(smem_raw);
     __shared__ long long s_time;
     __shared__ int s_k, s_x0, s_y0;
     __shared__ C s_T[2];
     __shared__ InstDev s_I;
-
     const int tid = threadIdx.x;
     const int stride = gridDim.x;
+    PairLoad<C, P, TX, TY, NT> ld;
 
-    // thread 0: the instance and origin of tile t (the instance record is copied when it changes)
+    // thread 0: tile t's instance (copied when it changes) and origin
     auto locate = [&](int t) {
-        const int k = find_inst(a.tile_begin, a.n_inst, t);
-        if (k != s_k) {
-            s_I = a.inst[k];
-            s_k = k;
-        }
-        const int local = t - a.tile_begin[k];
-        const int tiles_x = (s_I.nx + TX - 1) / TX;
-        s_x0 = (local % tiles_x) * TX;
-        s_y0 = (local / tiles_x) * TY;
-    };
-    // the velocity tables of tile + 6, by wrapped stored column and row (constant after set-up)
-    auto load_tables = [&]() {
-        const C* tX1 = a.tabs + s_I.tab;
-        const C* tY1 = tX1 + 2 * a.pitch;
-        for (int e = tid; e < 2 * (W6 + H6); e += NT) {
-            if (e < 2 * W6) {
-                const int j = e >= W6, c = e - j * W6;
-                sX1[e] = __ldg(tX1 + j * a.pitch + GC + wrap_near(s_x0 - 6 + c, s_I.nx));
-            } else {
-                const int j = (e - 2 * W6) >= H6, r = e - 2 * W6 - j * H6;
-                sY1[e - 2 * W6] = __ldg(tY1 + j * s_I.ylen + GR + wrap_near(s_y0 - 6 + r, s_I.ny));
-            }
-        }
-    };
-    // phi(t) on tile + 6 and its low part on tile + 3, all loads in flight before the first store (L2
-    // only: the previous launch wrote them)
-    auto load_phi = [&]() {
-        const int nx = s_I.nx, ny = s_I.ny, x0 = s_x0, y0 = s_y0;
-        const long long rb = (long long)s_I.row0 * a.pitch + GC;
-        P v[IT6];
-        float w[IT3];
-#pragma unroll
-        for (int i = 0; i < IT6; i++) {
-            const int e = tid + i * NT;
-            if (e < L::N6) {
-                const int r = e / W6, c = e - r * W6;
-                v[i] = __ldcg(a.phi_in + rb + (long long)wrap_near(y0 - 6 + r, ny) * a.pitch + wrap_near(x0 - 6 + c, nx));
-            }
-        }
-        if (kFF) {
-#pragma unroll
-            for (int i = 0; i < IT3; i++) {
-                const int e = tid + i * NT;
-                if (e < L::N3) {
-                    const int r = e / W3, c = e - r * W3;
-                    w[i] = __ldcg(a.lo_in + rb + (long long)wrap_near(y0 - 3 + r, ny) * a.pitch + wrap_near(x0 - 3 + c, nx));
-                }
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < IT6; i++)
-            if (tid + i * NT < L::N6) s_phi0[tid + i * NT] = v[i];
-        if (kFF) {
-#pragma unroll
-            for (int i = 0; i < IT3; i++)
-                if (tid + i * NT < L::N3) s_lo0[tid + i * NT] = w[i];
-        }
+        int k, x0, y0;
+        pair_locate<TX, TY>(a.tile_begin, a.n_inst, a.inst, t, k, x0, y0);
+        const bool changed = k != s_k;
+        if (changed) s_I = a.inst[k];
+        s_k = k;
+        s_x0 = x0;
+        s_y0 = y0;
+        return changed;
     };
 
-    // the first tile's instance and tables are constant data: read before the dependency wait, so they
-    // overlap the previous launch's tail
+    // the first tile's instance, tables and load offsets are constant data: before the dependency wait, so
+    // that they overlap the previous launch's tail
     if (tid == 0) {
         s_k = -1;
         if ((int)blockIdx.x < a.total_tiles) locate(blockIdx.x);
     }
     __syncthreads();
-    if ((int)blockIdx.x < a.total_tiles) load_tables();
+    if ((int)blockIdx.x < a.total_tiles) {
+        pair_tables<C, P, TX, TY, NT>(S, s_I, a.tabs, a.pitch, s_x0, s_y0);
+        ld.init(s_I, a.pitch, s_x0, s_y0);
+    }
     grid_dependency_wait();
     grid_launch_dependents();
-    if ((int)blockIdx.x < a.total_tiles) load_phi();
+    long long rb = (long long)s_I.row0 * a.pitch + GC;
+    if ((int)blockIdx.x < a.total_tiles) ld.load(S, a.phi_in + rb, a.lo_in + rb);
     if (tid == 0) {
         s_time = a.need_time ? a.ctl->time : 0;
         if (s_k >= 0) {
@@ -267,73 +372,18 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(PairArgs
     for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
         if (t != (int)blockIdx.x) {
             __syncthreads();  // the previous tile's shared data are read no more
-            if (tid == 0) {
-                const int k0 = s_k;
-                locate(t);
-                if (s_k != k0) {
-                    s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, n);
-                    s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, n + 1);
-                }
+            if (tid == 0 && locate(t)) {
+                s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, n);
+                s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, n + 1);
             }
             __syncthreads();
-            load_tables();
-            load_phi();
+            pair_tables<C, P, TX, TY, NT>(S, s_I, a.tabs, a.pitch, s_x0, s_y0);
+            ld.init(s_I, a.pitch, s_x0, s_y0);
+            rb = (long long)s_I.row0 * a.pitch + GC;
+            ld.load(S, a.phi_in + rb, a.lo_in + rb);
             __syncthreads();
         }
-        const Consts<C>& K0 = consts<C>(s_I);
-        const bool model2 = s_I.model == 2;
-
-        // step t: mu, D on tile + 5; collision on tile + 4; streaming to phi(t+1) on tile + 3
-        pair_mu_div<C, P, L::W5, L::H5, W6, NT>(s_phi0, sX1, sX2, sY1, sY2, 0, K0, model2, s_T[0], s_mu, s_D);
-        __syncthreads();
-        pair_collide<C, P, L::W4, L::H4, L::W5, W6, NT, kShift>(s_phi0, s_mu, s_D, sX1, sX2, sY1, sY2, 2, K0, model2,
-                                                               s_T[0], s_post);
-        __syncthreads();
-        for (int e = tid; e < L::N3; e += NT) {
-            const int r = e / W3, c = e - r * W3;
-            C v0;
-            const C sumq = pair_pull<C, W3, L::N4>(s_post, r, c, v0);
-            float lo1;
-            s_hi1[e] = pair_phi<C, P, kFF>(s_phi0[(r + 3) * W6 + c + 3], kFF ? s_lo0[e] : 0.0f, v0, sumq, lo1);
-            if (kFF) s_lo1[e] = lo1;
-        }
-        __syncthreads();
-
-        // step t+1: mu, D on tile + 2; collision on tile + 1; streaming to phi(t+2) on the tile
-        pair_mu_div<C, P, L::W2, L::H2, W3, NT>(s_hi1, sX1, sX2, sY1, sY2, 3, K0, model2, s_T[1], s_mu, s_D);
-        __syncthreads();
-        pair_collide<C, P, L::W1, L::H1, L::W2, W3, NT, kShift>(s_hi1, s_mu, s_D, sX1, sX2, sY1, sY2, 5, K0, model2,
-                                                               s_T[1], s_post);
-        __syncthreads();
-        const int nx = s_I.nx, ny = s_I.ny, x0 = s_x0, y0 = s_y0, pitch = a.pitch;
-        const long long rb = (long long)s_I.row0 * pitch + GC;
-        for (int e = tid; e < TX * TY; e += NT) {
-            const int r = e / TX, c = e - r * TX;
-            const int gx = x0 + c, gy = y0 + r;
-            if (gx >= nx || gy >= ny) continue;
-            C v0;
-            const C sumq = pair_pull<C, TX, L::N1>(s_post, r, c, v0);
-            const int h1 = (r + 3) * W3 + c + 3;
-            float lo;
-            const P hi = pair_phi<C, P, kFF>(s_hi1[h1], kFF ? s_lo1[h1] : 0.0f, v0, sumq, lo);
-            const long long node = rb + (long long)gy * pitch + gx;
-            a.phi_out[node] = hi;
-            if (kFF) a.lo_out[node] = lo;
-            if (gx < 3 || gx >= nx - 3 || gy < 3 || gy >= ny - 3) {
-                // the node's periodic images in the ghost frame (three deep), read by one-step launches
-                const int xa = gx < 3 ? gx + nx : NONE, xb = gx >= nx - 3 ? gx - nx : NONE;
-                const int ya = gy < 3 ? gy + ny : NONE, yb = gy >= ny - 3 ? gy - ny : NONE;
-                for (int iy = 0; iy < 3; iy++) {
-                    const int yy = iy == 0 ? gy : (iy == 1 ? ya : yb);
-                    if (yy == NONE) continue;
-                    for (int ix = 0; ix < 3; ix++) {
-                        const int xx = ix == 0 ? gx : (ix == 1 ? xa : xb);
-                        if (xx == NONE || (ix == 0 && iy == 0)) continue;
-                        a.phi_out[rb + (long long)yy * pitch + xx] = hi;
-                    }
-                }
-            }
-        }
+        pair_steps<C, P, TX, TY, NT>(S, s_I, s_T[0], s_T[1], s_x0, s_y0, a.pitch, rb, a.phi_out, a.lo_out);
     }
 
     // the last CTA of a batch's last launch advances the step counter (as in the one-step kernels)

@@ -57,7 +57,7 @@ def _run(params, fields, prec, pair, shape=0, schedule=SCHEDULE):
 def test_two_step_kernel_gives_the_same_bits(prec):
     params, fields = zip(*_ensemble())
     ref = _run(params, fields, prec, pair=False)
-    for shape in range(3):
+    for shape in range(4):
         got = _run(params, fields, prec, pair=True, shape=shape)
         for a_call, b_call in zip(got, ref):
             for a, b in zip(a_call, b_call):

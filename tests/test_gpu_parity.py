@@ -210,8 +210,8 @@ def test_tune_keeps_the_state(prec, tau):
     p, phi0, _ = wl.zalesak(n=128, tau=tau)
     with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(p, phi0, prec=prec, tune=True) as b:
         # row sweep, tile kernel or (periodic, tau_g = 1, not half storage) the two-step kernel
-        assert b.tile in ((56, 48), (56, 24), (56, 12), (32, 16), (32, 8), (16, 8), (16, 16))
-        assert b.kernel()["threads"] in (64, 128, 256, 512, 768)
+        assert b.tile in ((56, 48), (56, 24), (56, 12), (32, 16), (32, 8), (16, 8), (16, 16), (32, 14))
+        assert b.kernel()["threads"] in (64, 128, 256, 512, 768, 1024)
         if prec == "f16s" and tau == 1.0:
             assert b.kernel()["form"] == "sweep_tau1"
         if tau != 1.0:
