@@ -11,6 +11,7 @@ cudaError_t launch_pair_v(lbch_handle* h, int parity)
     using L = PairShape<C, P, TX, TY>;
     const lbch_handle::PerShape& ps = h->pr[h->pshape];
     PairArgs<C, P> a;
+    a.inst0 = h->inst[0];
     a.inst = h->d_inst;
     a.tile_begin = ps.d_tile_begin;
     a.tabs = tables<C>(h);

@@ -21,6 +21,7 @@ namespace lbch {
 
 template <typename C, typename P>
 struct PairArgs {
+    InstDev inst0;          // the record of instance 0, for single-instance handles (read from the parameters)
     const InstDev* inst;
     const int* tile_begin;  // first tile of each instance for this launch's tile shape
     const C* tabs;          // velocity tables of all instances (constant after set-up)
@@ -179,20 +180,21 @@ struct PairSmem {
 };
 
 // The velocity tables of tile + 6 by wrapped stored column and row (constant after set-up).
+// (nx, ny, tab, ylen: the instance's sizes and table layout)
 template <typename C, typename P, int TX, int TY, int NT>
-__device__ __forceinline__ void pair_tables(const PairSmem<C, P, TX, TY>& S, const InstDev& I, const C* tabs, int pitch,
-                                            int x0, int y0)
+__device__ __forceinline__ void pair_tables(const PairSmem<C, P, TX, TY>& S, int nx, int ny, int tab, int ylen,
+                                            const C* tabs, int pitch, int x0, int y0)
 {
     constexpr int W6 = PairShape<C, P, TX, TY>::W6, H6 = PairShape<C, P, TX, TY>::H6;
-    const C* tX1 = tabs + I.tab;
+    const C* tX1 = tabs + tab;
     const C* tY1 = tX1 + 2 * pitch;
     for (int e = threadIdx.x; e < 2 * (W6 + H6); e += NT) {
         if (e < 2 * W6) {
             const int j = e >= W6, c = e - j * W6;
-            S.X1[e] = __ldg(tX1 + j * pitch + GC + wrap_near(x0 - 6 + c, I.nx));
+            S.X1[e] = __ldg(tX1 + j * pitch + GC + wrap_near(x0 - 6 + c, nx));
         } else {
             const int j = (e - 2 * W6) >= H6, r = e - 2 * W6 - j * H6;
-            S.Y1[e - 2 * W6] = __ldg(tY1 + j * I.ylen + GR + wrap_near(y0 - 6 + r, I.ny));
+            S.Y1[e - 2 * W6] = __ldg(tY1 + j * ylen + GR + wrap_near(y0 - 6 + r, ny));
         }
     }
 }
@@ -205,17 +207,17 @@ struct PairLoad {
     using L = PairShape<C, P, TX, TY>;
     static constexpr int IT6 = (L::N6 + NT - 1) / NT, IT3 = (L::N3 + NT - 1) / NT;
     long long o6[IT6], o3[IT3];
-    __device__ void init(const InstDev& I, int pitch, int x0, int y0)
+    __device__ void init(int nx, int ny, int pitch, int x0, int y0)
     {
 #pragma unroll
         for (int i = 0; i < IT6; i++) {
             const int e = threadIdx.x + i * NT, r = e / L::W6, c = e - r * L::W6;
-            o6[i] = e < L::N6 ? (long long)wrap_near(y0 - 6 + r, I.ny) * pitch + wrap_near(x0 - 6 + c, I.nx) : -1;
+            o6[i] = e < L::N6 ? (long long)wrap_near(y0 - 6 + r, ny) * pitch + wrap_near(x0 - 6 + c, nx) : -1;
         }
 #pragma unroll
         for (int i = 0; i < IT3; i++) {
             const int e = threadIdx.x + i * NT, r = e / L::W3, c = e - r * L::W3;
-            o3[i] = e < L::N3 && L::FF ? (long long)wrap_near(y0 - 3 + r, I.ny) * pitch + wrap_near(x0 - 3 + c, I.nx) : -1;
+            o3[i] = e < L::N3 && L::FF ? (long long)wrap_near(y0 - 3 + r, ny) * pitch + wrap_near(x0 - 3 + c, nx) : -1;
         }
     }
     // every load is in flight before the first store to shared memory; L2 only (another CTA wrote them)
@@ -318,9 +320,11 @@ __device__ __forceinline__ void pair_locate(const int* tile_begin, int n_inst, c
     y0 = (local / tiles_x) * TY;
 }
 
-// One launch per two steps: a persistent CTA walks its tiles.
+// One launch per two steps: a persistent CTA walks its tiles.  With one instance, its record comes with the
+// launch parameters, so the first tile's origin, tables and load offsets need no memory round trip: the
+// table loads start at once and the phi loads right after the dependency wait.
 template <typename C, typename P, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(PairArgs<C, P> a)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __grid_constant__ PairArgs<C, P> a)
 {
     extern __shared__ unsigned char smem_raw[];
     const PairSmem<C, P, TX, TY> S(smem_raw);
@@ -330,35 +334,58 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(PairArgs
     __shared__ InstDev s_I;
     const int tid = threadIdx.x;
     const int stride = gridDim.x;
+    const bool single = a.n_inst == 1;
+    const bool any = (int)blockIdx.x < a.total_tiles;
     PairLoad<C, P, TX, TY, NT> ld;
 
     // thread 0: tile t's instance (copied when it changes) and origin
     auto locate = [&](int t) {
         int k, x0, y0;
-        pair_locate<TX, TY>(a.tile_begin, a.n_inst, a.inst, t, k, x0, y0);
+        if (single) {
+            const int tiles_x = (a.inst0.nx + TX - 1) / TX;
+            k = 0;
+            x0 = (t % tiles_x) * TX;
+            y0 = (t / tiles_x) * TY;
+        } else {
+            pair_locate<TX, TY>(a.tile_begin, a.n_inst, a.inst, t, k, x0, y0);
+        }
         const bool changed = k != s_k;
-        if (changed) s_I = a.inst[k];
+        if (changed) s_I = single ? a.inst0 : a.inst[k];
         s_k = k;
         s_x0 = x0;
         s_y0 = y0;
         return changed;
     };
 
-    // the first tile's instance, tables and load offsets are constant data: before the dependency wait, so
-    // that they overlap the previous launch's tail
-    if (tid == 0) {
-        s_k = -1;
-        if ((int)blockIdx.x < a.total_tiles) locate(blockIdx.x);
-    }
-    __syncthreads();
-    if ((int)blockIdx.x < a.total_tiles) {
-        pair_tables<C, P, TX, TY, NT>(S, s_I, a.tabs, a.pitch, s_x0, s_y0);
-        ld.init(s_I, a.pitch, s_x0, s_y0);
+    // the first tile: instance, tables and load offsets are constant data, set up before the dependency wait
+    long long rb = 0;
+    if (single) {
+        const int tiles_x = (a.inst0.nx + TX - 1) / TX;
+        const int x0 = ((int)blockIdx.x % tiles_x) * TX, y0 = ((int)blockIdx.x / tiles_x) * TY;
+        if (tid == 0) {
+            s_k = -1;
+            if (any) locate(blockIdx.x);
+        }
+        if (any) {
+            pair_tables<C, P, TX, TY, NT>(S, a.inst0.nx, a.inst0.ny, a.inst0.tab, a.inst0.ylen, a.tabs, a.pitch, x0, y0);
+            ld.init(a.inst0.nx, a.inst0.ny, a.pitch, x0, y0);
+        }
+        rb = (long long)a.inst0.row0 * a.pitch + GC;
+    } else {
+        if (tid == 0) {
+            s_k = -1;
+            if (any) locate(blockIdx.x);
+        }
+        __syncthreads();
+        if (any) {
+            pair_tables<C, P, TX, TY, NT>(S, s_I.nx, s_I.ny, s_I.tab, s_I.ylen, a.tabs, a.pitch, s_x0, s_y0);
+            ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
+        }
+        rb = (long long)s_I.row0 * a.pitch + GC;
     }
     grid_dependency_wait();
     grid_launch_dependents();
-    long long rb = (long long)s_I.row0 * a.pitch + GC;
-    if ((int)blockIdx.x < a.total_tiles) ld.load(S, a.phi_in + rb, a.lo_in + rb);
+    if (any) ld.load(S, a.phi_in + rb, a.lo_in + rb);
     if (tid == 0) {
         s_time = a.need_time ? a.ctl->time : 0;
         if (s_k >= 0) {
@@ -377,8 +404,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(PairArgs
                 s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, n + 1);
             }
             __syncthreads();
-            pair_tables<C, P, TX, TY, NT>(S, s_I, a.tabs, a.pitch, s_x0, s_y0);
-            ld.init(s_I, a.pitch, s_x0, s_y0);
+            pair_tables<C, P, TX, TY, NT>(S, s_I.nx, s_I.ny, s_I.tab, s_I.ylen, a.tabs, a.pitch, s_x0, s_y0);
+            ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
             rb = (long long)s_I.row0 * a.pitch + GC;
             ld.load(S, a.phi_in + rb, a.lo_in + rb);
             __syncthreads();
