@@ -41,9 +41,9 @@ SMS, FP32_LANES_PER_SM = 152, 128
 
 # DRAM bytes (read + write) per launch of the headline kernel, from the ncu capture summarised in
 # profiles/; reported only while the kernel sources still hash the same and the autotuner chose that kernel.
-TRAFFIC = {"hash": "f23f65d43c690449", "bytes_per_launch": 588800,
-           "kernel": "ch_step_kernel<float,float,float,FF=1,tile=32x16,NT=768,TAU1=1>",
-           "profile": "profiles/ch_step_f32_256_tile_headline.md"}
+TRAFFIC = {"hash": "49c4986ea5e9a314", "bytes_per_launch": 602880,
+           "kernel": "ch_pair_kernel<float,float,tile=32x14,NT=1024>",
+           "profile": "profiles/ch_pair_f32_256_headline.md"}
 KERNEL_SOURCES = ("lbch_kernels.cuh", "lbch_sweep.cuh", "lbch_sweep_launch.cuh", "lbch_pair.cuh")
 
 

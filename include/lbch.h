@@ -177,9 +177,11 @@ void* lb_ch_stream(lbch_handle* h);
  * and, for handles whose instances are all periodic with tau_g = 1 in LBCH_F32 or LBCH_F64, the two-step
  * kernel (two steps per launch from phi on the tile + 6; 32x16 with 768 threads, 32x14 and 32x16 with
  * 1024 and 32x8 with 512 in LBCH_F32; 32x8 with 512, 16x8 with 256, 16x16 with 512 and 32x14 with 1024
- * in LBCH_F64; an odd last step of
- * lb_ch_step then runs the fastest one-step candidate).  lb_ch_tune times `steps` steps of every candidate on the
- * handle's own problem, restores the state after each, keeps the fastest, and reports its tile size in
+ * in LBCH_F64; an odd last step of lb_ch_step then runs the fastest one-step candidate).  lb_ch_tune
+ * times every candidate on the handle's own problem through lb_ch_step (as a run steps: CUDA graphs of 64
+ * steps) -- one graph of warm-up, then the faster of two runs of `steps` steps rounded up to whole graphs
+ * (below 64 steps: two steps of warm-up and two runs of `steps` steps) --, restores the state after each,
+ * keeps the fastest, and reports its tile size in
  * *tile_x, *tile_y (either may be NULL).  The result of the simulation does not depend on the choice (on
  * the half-storage path with every tau_g = 1 only the row sweep is a candidate, as the tile kernel would
  * round the streamed populations to half).  Allocates a temporary state copy; synchronises. */

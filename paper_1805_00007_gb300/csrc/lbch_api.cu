@@ -1241,35 +1241,38 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
         float best_ms = 0.0f, best1_ms = 0.0f;  // per step: over all candidates; over the one-step ones
         Cand best = {h->force_tile, use_pair(h), use_pair(h) ? h->pshape : h->shape};
         Cand best1 = {h->force_tile, false, h->shape};
-        const int steps2 = (steps + 1) / 2;  // launches of a two-step candidate
+        // every candidate steps through lb_ch_step, as a caller's run does (CUDA graphs of kGraphChunk steps):
+        // one graph of warm-up, which captures it, then the faster of two timed runs of `steps` steps rounded
+        // up to whole graphs.  Fewer than kGraphChunk steps (large grids, where launches cost little) are
+        // timed as they are, after two steps of warm-up.
+        const long timed = steps < kGraphChunk ? steps : (long)((steps + kGraphChunk - 1) / kGraphChunk) * kGraphChunk;
+        const long warm = steps < kGraphChunk ? 2 : kGraphChunk;
         if (s == LBCH_OK && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
             for (int k = 0; k < ns && s == LBCH_OK; k++) {
                 const Cand c = cands[k];
                 h->pair = c.pair;
                 if (c.pair) h->pshape = c.shape;
                 else { h->force_tile = c.tile; h->shape = c.shape; }
-                cudaError_t e = cudaSuccess;
-                auto one = [&]() {
-                    if (c.pair) return launch_pair_now(h);
-                    cudaError_t r = launch_step(h, cur_buf(h));
-                    h->n++;
-                    return r;
-                };
-                for (int w = 0; w < 2 && e == cudaSuccess; w++) e = one();
-                e = e == cudaSuccess ? cudaEventRecord(e0, h->stream) : e;
-                const int launches = c.pair ? steps2 : steps;
-                for (int i = 0; i < launches && e == cudaSuccess; i++) e = one();
-                e = e == cudaSuccess ? cudaEventRecord(e1, h->stream) : e;
-                e = e == cudaSuccess ? cudaEventSynchronize(e1) : e;
-                float ms = 0.0f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                ms /= (float)(c.pair ? 2 * steps2 : steps);
-                if (e != cudaSuccess) s = cuda_fail(e, "timing a tile shape");
+                drop_graphs(h);
+                lbch_status r = lb_ch_step(h, warm);
+                float ms = -1.0f;
+                for (int rep = 0; rep < 2 && r == LBCH_OK; rep++) {
+                    cudaError_t e = cudaEventRecord(e0, h->stream);
+                    if (e == cudaSuccess) r = lb_ch_step(h, timed);
+                    if (e == cudaSuccess && r == LBCH_OK) e = cudaEventRecord(e1, h->stream);
+                    if (e == cudaSuccess && r == LBCH_OK) e = cudaEventSynchronize(e1);
+                    float t = 0.0f;
+                    if (e == cudaSuccess && r == LBCH_OK) e = cudaEventElapsedTime(&t, e0, e1);
+                    if (e != cudaSuccess) r = cuda_fail(e, "timing a kernel candidate");
+                    else if (r == LBCH_OK && (ms < 0.0f || t < ms)) ms = t;
+                }
+                if (r != LBCH_OK) s = r;
                 else {
+                    ms /= (float)timed;
                     if (k == 0 || ms < best_ms) { best_ms = ms; best = c; }
                     if (!c.pair && (k == 0 || ms < best1_ms)) { best1_ms = ms; best1 = c; }
                 }
-                lbch_status r = lb_ch_state_load(h, backup);  // every candidate starts from the same state
+                r = lb_ch_state_load(h, backup);  // every candidate starts from the same state
                 if (s == LBCH_OK) s = r;
             }
         }
