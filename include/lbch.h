@@ -134,7 +134,10 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
  * is enqueued (in CUDA graphs of 64 steps when possible) and the call returns.  When every instance has
  * tau_g = 1 (the paper's default), Eq. LB reduces to g* = g_eq + S/2 and the populations drop out of the
  * step: the library then reads and writes phi only (the stored populations are left unchanged and are
- * not part of the state), with the same results bit for bit. */
+ * not part of the state), with the same results bit for bit.  Until lb_ch_tune chooses otherwise, a
+ * handle whose instances are all periodic with tau_g = 1 (LBCH_F32 or LBCH_F64) and whose grid fits the
+ * device in one wave of two-step tiles (up to about 68 K nodes in LBCH_F32) steps two steps per launch
+ * with the two-step kernel; every other handle steps with the row sweep. */
 lbch_status lb_ch_step(lbch_handle* h, long nsteps);
 
 /* Read an observable of instance inst into out (host, sized as lbch_obs states).  Synchronises the
@@ -225,7 +228,7 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
  * lb_ch_step); the two give the same bits.  With hook LBCH_HOOK_TILE_KERNEL and value != 0, the steps
  * run the tile kernel (each tile's stencil fields staged in shared memory) instead of the row sweep, with
  * the populations; the tile shape hook then indexes its own list of shapes, and the results are the same
- * bits again.  With hook LBCH_HOOK_TWO_STEP and value != 0 (periodic instances with tau_g = 1 in
+ * bits again; with value 0, the row sweep (either value turns the two-step kernel off).  With hook LBCH_HOOK_TWO_STEP and value != 0 (periodic instances with tau_g = 1 in
  * LBCH_F32 or LBCH_F64, else LBCH_EINVAL), lb_ch_step takes the steps two at a time with the two-step
  * kernel (the tile shape hook then indexes its list), the same bits once more; value 0 returns to the
  * one-step kernel.  With hook LBCH_HOOK_NO_PDL and value != 0,

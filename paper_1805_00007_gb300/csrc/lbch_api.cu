@@ -899,6 +899,14 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     }
     CKI(cudaStreamSynchronize(h->stream));  // the pinned staging buffer and the tables are reused after this
 #undef CKI
+    // Kernel before any tuning: the two-step kernel where it applies and its tiles fit the device in one
+    // wave (a step of such a grid is bound by latency, and one launch per two steps halves the launches);
+    // otherwise the row sweep.  lb_ch_tune measures instead.
+    const int k2 = prec == LBCH_F64 ? 0 : 1;
+    if (pair_ok(h) && h->pr[k2].d_tile_begin && h->pr[k2].grid == h->pr[k2].total_tiles) {
+        h->pair = true;
+        h->pshape = k2;
+    }
     *out = h;
     return LBCH_OK;
 }
@@ -1317,6 +1325,7 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
         if (h->coupled) return fail(LBCH_EINVAL, "the coupled flow has no tile kernel");
         if (h->force_tile != (value != 0)) h->shape = 0;  // the shape index names the other kernel's list
         h->force_tile = value != 0;
+        h->pair = false;  // either way a one-step kernel takes every step
         for (int k = 0; k < 2; k++)
             if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
         return LBCH_OK;

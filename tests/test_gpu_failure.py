@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 def test_bounded_wait_runs_out_and_reports_etimeout(prec):
     p, phi0, _ = wl.zalesak(n=64)
     with abi.Simulation(p, phi0, prec=prec) as sim:
+        abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, 0)  # the row sweep: its copies have bounded waits
         abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_SKIP_FIRST_LOAD, 1)
         sim.step(1)
         with pytest.raises(abi.LbchError) as ei:

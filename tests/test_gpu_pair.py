@@ -40,6 +40,7 @@ def _ensemble():
 
 def _run(params, fields, prec, pair, shape=0, schedule=SCHEDULE):
     with abi.Simulation(list(params), list(fields), prec=prec) as sim:
+        abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, 0)  # the row sweep, one step per launch
         if pair:
             abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TWO_STEP, 1)
             abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, shape)
@@ -112,6 +113,21 @@ def test_two_step_kernel_counts_half_the_bytes():
     """The two-step kernel reads and writes phi once per two lattice updates."""
     p, phi0 = _ensemble()[0]
     with abi.Simulation(p, phi0, prec="f32") as sim:
+        abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, 0)
         one = sim.info()["bytes_per_lu"]
         abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TWO_STEP, 1)
         assert sim.info()["bytes_per_lu"] == one / 2 == 8.0
+
+
+def test_small_periodic_tau1_grids_default_to_two_steps():
+    """Before tuning, a grid that fits the device in one wave of two-step tiles steps with the two-step
+    kernel; a larger one, or one with walls, with the row sweep."""
+    p, phi0 = _ensemble()[1]
+    with abi.Simulation(p, phi0, prec="f32") as sim:
+        assert sim.kernel()["form"] == "pair_tau1"
+    big = wl.make_params(nx=512, ny=512, vel=wl.VEL_UNIFORM, ux0=0.02, uy0=0.01, M=0.02)
+    with abi.Simulation(big, wl.circle_phi(512, 512, 256.0, 256.0, 64.0, 3.0), prec="f32") as sim:
+        assert sim.kernel()["form"] == "sweep_tau1"
+    walls = wl.make_params(nx=64, ny=64, vel=wl.VEL_SHEAR, walls=1, shear=1e-3, M=0.02)
+    with abi.Simulation(walls, wl.circle_phi(64, 64, 32.0, 32.0, 12.0, 3.0), prec="f32") as sim:
+        assert sim.kernel()["form"] == "sweep_tau1"

@@ -258,6 +258,7 @@ def test_tau1_kernel_equals_general_kernel_bitwise(prec):
     res = []
     for general in (0, 1):
         with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(list(params), list(fields), prec=prec) as b:
+            abi.lb_ch_test_hook(a.h, abi.LBCH_HOOK_TILE_KERNEL, 0)  # the row sweep
             abi.lb_ch_test_hook(a.h, abi.LBCH_HOOK_GENERAL_PATH, general)
             abi.lb_ch_test_hook(b.h, abi.LBCH_HOOK_GENERAL_PATH, general)
             a.step(90)
