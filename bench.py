@@ -37,7 +37,9 @@ METRIC = "MLUPS and % HBM roofline (FP32 vs FP64 step) at stated phi error vs FP
 # operations of the per-node helpers (a fused multiply-add counts 2): mu 23, D = div(phi u) 34, grad mu and
 # grad D 28, force 11, velocity 4, equilibrium + source + collision 55, streaming sum and TwoSum 14.
 FLOPS_PER_LU_TAU1 = 169
-SMS, FP32_LANES_PER_SM = 152, 128
+# The FP64 step does the same operations without the TwoSum (6 fewer) and with a reciprocal refined by two
+# Newton steps (6 more): 169 as well.
+SMS, FP32_LANES_PER_SM, FP64_LANES_PER_SM = 152, 128, 2
 
 # DRAM bytes (read + write) per launch of the headline kernel, from the ncu capture summarised in
 # profiles/; reported only while the kernel sources still hash the same and the autotuner chose that kernel.
@@ -189,6 +191,42 @@ def steps_per_launch(k: dict) -> int:
     return 2 if k["form"] == "pair_tau1" else 1
 
 
+def size_sweep(sizes, precs):
+    """The step on square periodic grids from 1024^2 up: the diagonal translation workload of Sec. III.A
+    (circle of radius n/4, W = 4, u = (0.04, 0.04), M = 0.01, tau_g = 0.8, Model II), each grid autotuned
+    and timed over enough steps for about 50 ms.  One JSON line; not part of the default run."""
+    import torch
+    from paper_1805_00007_gb300 import abi
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.Stream()
+    out = {}
+    for prec in precs:
+        for n in sizes:
+            pp = wl.make_params(nx=n, ny=n, vel=wl.VEL_UNIFORM, ux0=0.04, uy0=0.04, W=4.0, M=0.01, tau=0.8)
+            f0 = wl.circle_phi(n, n, n / 2, n / 2, n / 4, 4.0)
+            with abi.Simulation(pp, f0, prec=prec, stream=stream.cuda_stream, tune=True) as sim:
+                sim.step(4)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(4)
+                e1.record(stream)
+                e1.synchronize()
+                nst = max(8, min(256, int(0.05 / (e0.elapsed_time(e1) / 1e3 / 4))))
+                e0.record(stream)
+                sim.step(nst)
+                e1.record(stream)
+                e1.synchronize()
+                dt = e0.elapsed_time(e1) / 1e3 / nst
+                inf = sim.info()
+                gbs = inf["bytes_per_lu"] * n * n / dt / 1e9
+                out[f"{prec}_{n}"] = {"MLUPS": n * n / dt / 1e6, "us_per_step": dt * 1e6, "steps_timed": nst,
+                                      "kernel": kernel_name(sim.kernel(), prec), "bytes_per_lu": inf["bytes_per_lu"],
+                                      "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+    print(json.dumps({"size_sweep": out, "workload": "diagonal translation, tau_g = 0.8, Model II",
+                      "peak_gbs": hbm_peak, "peak_kind": peak_kind}))
+
+
 def run_case(case, nsteps, tile=0, form="sweep"):
     """One grid, no timing: the command ncu profiles."""
     import torch
@@ -241,6 +279,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--size-sweep", action="store_true",
+                    help="time the step on 1024^2 .. 16384^2 grids (tau_g = 0.8) instead of the benchmark")
     ap.add_argument("--case", default=None,
                     help="profiling case PREC_N[_TAU] (e.g. f32_4096, f32_4096_0.8): init and --case-steps steps "
                          "of that grid only")
@@ -255,6 +295,8 @@ def main():
         return run_reference(args)
     if args.case:
         return run_case(args.case, args.case_steps, args.case_tile, args.case_form)
+    if args.size_sweep:
+        return size_sweep((1024, 2048, 4096, 8192, 16384), ("f32", "f64", "f16s"))
 
     import torch
     import torch.distributed as dist
@@ -320,6 +362,7 @@ def main():
 
     # --- FP64 path, same revolution
     t64, sim64 = timed_revolutions("f64", max(1, args.steps // 2), 1)
+    kern64 = sim64.kernel()
     info64 = sim64.info()
     n_rev64 = args.steps // 2 + 1 + max(1, args.steps // 2)
     phi64 = sim64.phi()
@@ -403,6 +446,27 @@ def main():
                               "bytes_per_lu": inf["bytes_per_lu"],
                               "achieved_gbs": gbs, "frac": gbs / hbm_peak}
             sim.close()
+            if prec == "f32":
+                # the same instances as separate single-instance handles, stepped one after another on the
+                # same stream (each with the untuned default kernel): what the batched launch saves
+                sims = [abi.Simulation(q, f, prec=prec, stream=stream.cuda_stream) for q, f in zip(eparams, efields)]
+                for s in sims:
+                    s.step(64)
+                barrier()
+                e0.record(stream)
+                for s in sims:
+                    s.step(nst)
+                e1.record(stream)
+                e1.synchronize()
+                dt_loop = e0.elapsed_time(e1) / 1e3 / nst
+                if world > 1:
+                    t = torch.tensor([dt_loop], device=dev, dtype=torch.float64)
+                    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                    dt_loop = float(t.item())
+                for s in sims:
+                    s.close()
+                ensemble[prec]["looped_single_instance_MLUPS"] = enodes / dt_loop / 1e6
+                ensemble[prec]["batched_speedup"] = dt_loop / dt
 
     # --- the paper's relaxation-time study (Sec. III.A) at its own size, every point one ensemble instance
     tau_sweep = {}
@@ -427,7 +491,12 @@ def main():
     clocks = clk.summary()
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    peak64_tflops = SMS * FP64_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     alu_tflops = FLOPS_PER_LU_TAU1 * nodes * spl32 / launch32 / 1e12
+    alu64_tflops = FLOPS_PER_LU_TAU1 * nodes / (t64 / rev) / 1e12
+    # the FMA throughput the device sustains (lb_ch_alu_peak), beside the unit-count peaks
+    fma32 = abi.lb_ch_alu_peak(abi.LBCH_F32, stream.cuda_stream) / 1e12
+    fma64 = abi.lb_ch_alu_peak(abi.LBCH_F64, stream.cuda_stream) / 1e12
     traffic = (TRAFFIC["bytes_per_launch"]
                if TRAFFIC["hash"] == kernel_hash() and TRAFFIC["kernel"] == kernel_name(kern32, "f32") else None)
 
@@ -440,14 +509,19 @@ def main():
                        "lattice_steps_per_step": rev, "model": "II", "l2": "flushed before each step",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "fp64": {"MLUPS": world * lu_per_rev / t64 / 1e6, "ms_per_step": 1e3 * t64,
-                     "achieved_gbs": achieved64, "frac": achieved64 / hbm_peak},
+                     "achieved_gbs": achieved64, "frac": achieved64 / hbm_peak, "kernel": kernel_name(kern64, "f64"),
+                     "alu": {"flops_per_lu": FLOPS_PER_LU_TAU1, "achieved": alu64_tflops, "peak": peak64_tflops,
+                             "unit": "TFLOP/s", "frac": alu64_tflops / peak64_tflops,
+                             "peak_from": "152 SMs x 2 FP64 lanes x 2 flop x median SM clock under load",
+                             "peak_measured": fma64, "frac_of_measured": alu64_tflops / fma64}},
             "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved32 / hbm_peak, "traffic": traffic, "traffic_profile": TRAFFIC["profile"],
                          "kernel": kernel_name(kern32, "f32"), "bytes_per_lu": info32["bytes_per_lu"],
                          "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6,
                          "alu": {"flops_per_lu": FLOPS_PER_LU_TAU1, "achieved": alu_tflops, "peak": peak_tflops,
                                  "unit": "TFLOP/s", "frac": alu_tflops / peak_tflops,
-                                 "peak_from": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}},
+                                 "peak_from": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+                                 "peak_measured": fma32, "frac_of_measured": alu_tflops / fma32}},
             "sweep_4096": sweep,
             "ensemble_shear_256": ensemble,
             "paper_tau_sweep": tau_sweep,

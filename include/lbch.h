@@ -267,6 +267,13 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
 lbch_status lb_ch_field_stats_noalloc(const double* phi, const double* phi0, int nx, int ny, int pitch,
                                       double* out, void* stream);
 
+/* Fused multiply-add throughput of the current device in prec (LBCH_F32 or LBCH_F64, else LBCH_EINVAL), for
+ * the arithmetic rooflines reported beside the step (the paper has no counterpart).  One kernel fills every
+ * SM with threads that each run eight independent chains of FMAs; a short run sizes the measured one to
+ * about 20 ms and the fastest of three counts (2 flop per FMA).  *flop_per_s receives flop/s (host).
+ * Allocates one element of device memory; synchronises `stream` (a cudaStream_t, NULL = legacy default). */
+lbch_status lb_ch_alu_peak(int prec, void* stream, double* flop_per_s);
+
 #ifdef __cplusplus
 }
 #endif

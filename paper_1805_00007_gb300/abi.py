@@ -21,7 +21,8 @@ PRECISIONS = {"f64": LBCH_F64, "f32": LBCH_F32, "f16s": LBCH_F16S}
 SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free",
            "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_kernel_info", "lb_ch_stream", "lb_ch_test_hook",
            "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
-           "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune")
+           "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune",
+           "lb_ch_alu_peak")
 (LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL,
  LBCH_HOOK_TWO_STEP) = 1, 2, 3, 4, 5, 6
 
@@ -85,11 +86,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_adjoint_step.argtypes = [vp, vp, ctypes.c_long]
     lib.lb_ch_adjoint_end.argtypes = [vp, vp, dp]
     lib.lb_ch_tune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]
+    lib.lb_ch_alu_peak.argtypes = [ctypes.c_int, vp, dp]
     for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
                  "lb_ch_kernel_info",
                  "lb_ch_test_hook", "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save",
                  "lb_ch_state_load", "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step",
-                 "lb_ch_adjoint_end", "lb_ch_tune"):
+                 "lb_ch_adjoint_end", "lb_ch_tune", "lb_ch_alu_peak"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -177,6 +179,13 @@ def lb_ch_info(h) -> dict:
 
 def lb_ch_test_hook(h, hook: int, value: int):
     _check(load().lb_ch_test_hook(h, int(hook), int(value)), "lb_ch_test_hook")
+
+
+def lb_ch_alu_peak(prec: int, stream: int | None = None) -> float:
+    """Fused multiply-add throughput of the current device in prec (LBCH_F32 or LBCH_F64), flop/s."""
+    out = ctypes.c_double(0.0)
+    _check(load().lb_ch_alu_peak(int(prec), ctypes.c_void_p(stream or 0), ctypes.byref(out)), "lb_ch_alu_peak")
+    return out.value
 
 
 def lb_ch_field_stats_noalloc(phi_ptr: int, phi0_ptr: int, nx: int, ny: int, pitch: int, out_ptr: int,
