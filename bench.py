@@ -274,7 +274,7 @@ def accuracy(prec, p, phi0, nsteps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
@@ -321,7 +321,8 @@ def main():
             dist.barrier()
 
     def timed_revolutions(prec, k, w, pin=None):
-        """Run w warm-up and k timed revolutions; returns (seconds per revolution, the simulation)."""
+        """Run w warm-up and k timed revolutions; returns (mean seconds per revolution, the simulation, the
+        time of each revolution)."""
         sim = abi.Simulation(p, phi0, prec=prec, stream=stream.cuda_stream, tune=pin is None)
         if pin is not None:
             form, shape = pin.split(":")
@@ -333,7 +334,7 @@ def main():
                 flush_l2(flush)
             sim.step(rev)
         barrier()
-        total = 0.0
+        times = []
         for _ in range(k):
             with torch.cuda.stream(stream):
                 flush_l2(flush)
@@ -342,13 +343,13 @@ def main():
             sim.step(rev)
             e1.record(stream)
             e1.synchronize()
-            total += e0.elapsed_time(e1) / 1e3
+            times.append(e0.elapsed_time(e1) / 1e3)
         barrier()
-        return total / k, sim
+        return sum(times) / k, sim, times
 
     # --- FP32 path: the headline value
     with Clocks(local) as clk:
-        t32, sim32 = timed_revolutions("f32", args.steps, args.warmup, args.kernel)
+        t32, sim32, times32 = timed_revolutions("f32", args.steps, args.warmup, args.kernel)
     t_max = t32
     if world > 1:
         t = torch.tensor([t32], device=dev, dtype=torch.float64)
@@ -361,7 +362,7 @@ def main():
     sim32.close()
 
     # --- FP64 path, same revolution
-    t64, sim64 = timed_revolutions("f64", max(1, args.steps // 2), 1)
+    t64, sim64, times64 = timed_revolutions("f64", max(1, args.steps // 2), 1)
     kern64 = sim64.kernel()
     info64 = sim64.info()
     n_rev64 = args.steps // 2 + 1 + max(1, args.steps // 2)
@@ -508,7 +509,12 @@ def main():
             "config": {"workload": "zalesak_256x256_one_revolution", "nx": REV_N, "ny": REV_N,
                        "lattice_steps_per_step": rev, "model": "II", "l2": "flushed before each step",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "revolution_ms": {"mean": 1e3 * t32, "best": 1e3 * min(times32),
+                              "median": 1e3 * statistics.median(times32), "n": len(times32)},
+            "fp32_over_fp64": t64 / t32,
             "fp64": {"MLUPS": world * lu_per_rev / t64 / 1e6, "ms_per_step": 1e3 * t64,
+                     "revolution_ms": {"best": 1e3 * min(times64), "median": 1e3 * statistics.median(times64),
+                                       "n": len(times64)},
                      "achieved_gbs": achieved64, "frac": achieved64 / hbm_peak, "kernel": kernel_name(kern64, "f64"),
                      "alu": {"flops_per_lu": FLOPS_PER_LU_TAU1, "achieved": alu64_tflops, "peak": peak64_tflops,
                              "unit": "TFLOP/s", "frac": alu64_tflops / peak64_tflops,

@@ -36,15 +36,19 @@ cudaError_t launch_pair_v(lbch_handle* h, int parity)
     attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ch_pair_kernel<C, P, TX, TY, NT>, a);
+    return h->n_inst == 1 ? cudaLaunchKernelEx(&cfg, ch_pair_kernel<C, P, TX, TY, NT, true>, a)
+                          : cudaLaunchKernelEx(&cfg, ch_pair_kernel<C, P, TX, TY, NT, false>, a);
 }
 
 template <typename C, typename P, int TX, int TY, int NT>
 cudaError_t prepare_pair_v(lbch_handle* h, int k)
 {
     using L = PairShape<C, P, TX, TY>;
-    auto kern = ch_pair_kernel<C, P, TX, TY, NT>;
+    auto kern = ch_pair_kernel<C, P, TX, TY, NT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ch_pair_kernel<C, P, TX, TY, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);

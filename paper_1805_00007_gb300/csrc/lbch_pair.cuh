@@ -320,10 +320,11 @@ __device__ __forceinline__ void pair_locate(const int* tile_begin, int n_inst, c
     y0 = (local / tiles_x) * TY;
 }
 
-// One launch per two steps: a persistent CTA walks its tiles.  With one instance, its record comes with the
-// launch parameters, so the first tile's origin, tables and load offsets need no memory round trip: the
-// table loads start at once and the phi loads right after the dependency wait.
-template <typename C, typename P, int TX, int TY, int NT>
+// One launch per two steps: a persistent CTA walks its tiles.  SINGLE (a handle of one instance): the
+// instance record stays in the launch parameters, so the tile's origin, tables and load offsets need no
+// memory round trip (the table loads start at once, the phi loads right after the dependency wait), and the
+// per-node helpers take the instance's constants as constant-bank operands instead of loading them.
+template <typename C, typename P, int TX, int TY, int NT, bool SINGLE>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __grid_constant__ PairArgs<C, P> a)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -334,44 +335,54 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
     __shared__ InstDev s_I;
     const int tid = threadIdx.x;
     const int stride = gridDim.x;
-    const bool single = a.n_inst == 1;
     const bool any = (int)blockIdx.x < a.total_tiles;
     PairLoad<C, P, TX, TY, NT> ld;
+    long long n = 0;
 
-    // thread 0: tile t's instance (copied when it changes) and origin
-    auto locate = [&](int t) {
-        int k, x0, y0;
-        if (single) {
-            const int tiles_x = (a.inst0.nx + TX - 1) / TX;
-            k = 0;
-            x0 = (t % tiles_x) * TX;
-            y0 = (t / tiles_x) * TY;
-        } else {
-            pair_locate<TX, TY>(a.tile_begin, a.n_inst, a.inst, t, k, x0, y0);
+    if constexpr (SINGLE) {
+        const InstDev& I = a.inst0;
+        const int tiles_x = (I.nx + TX - 1) / TX;
+        const long long rb = (long long)I.row0 * a.pitch + GC;
+        int x0 = ((int)blockIdx.x % tiles_x) * TX, y0 = ((int)blockIdx.x / tiles_x) * TY;
+        if (any) {  // constant data: before the dependency wait
+            pair_tables<C, P, TX, TY, NT>(S, I.nx, I.ny, I.tab, I.ylen, a.tabs, a.pitch, x0, y0);
+            ld.init(I.nx, I.ny, a.pitch, x0, y0);
         }
-        const bool changed = k != s_k;
-        if (changed) s_I = single ? a.inst0 : a.inst[k];
-        s_k = k;
-        s_x0 = x0;
-        s_y0 = y0;
-        return changed;
-    };
-
-    // the first tile: instance, tables and load offsets are constant data, set up before the dependency wait
-    long long rb = 0;
-    if (single) {
-        const int tiles_x = (a.inst0.nx + TX - 1) / TX;
-        const int x0 = ((int)blockIdx.x % tiles_x) * TX, y0 = ((int)blockIdx.x / tiles_x) * TY;
+        grid_dependency_wait();
+        grid_launch_dependents();
+        if (any) ld.load(S, a.phi_in + rb, a.lo_in + rb);
         if (tid == 0) {
-            s_k = -1;
-            if (any) locate(blockIdx.x);
+            s_time = a.need_time ? a.ctl->time : 0;
+            s_T[0] = (C)vel_t(I.vel, I.Tper, s_time + a.t_off);
+            s_T[1] = (C)vel_t(I.vel, I.Tper, s_time + a.t_off + 1);
         }
-        if (any) {
-            pair_tables<C, P, TX, TY, NT>(S, a.inst0.nx, a.inst0.ny, a.inst0.tab, a.inst0.ylen, a.tabs, a.pitch, x0, y0);
-            ld.init(a.inst0.nx, a.inst0.ny, a.pitch, x0, y0);
+        __syncthreads();
+        n = s_time + a.t_off;
+        for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
+            if (t != (int)blockIdx.x) {
+                __syncthreads();  // the previous tile's shared data are read no more
+                x0 = (t % tiles_x) * TX;
+                y0 = (t / tiles_x) * TY;
+                pair_tables<C, P, TX, TY, NT>(S, I.nx, I.ny, I.tab, I.ylen, a.tabs, a.pitch, x0, y0);
+                ld.init(I.nx, I.ny, a.pitch, x0, y0);
+                ld.load(S, a.phi_in + rb, a.lo_in + rb);
+                __syncthreads();
+            }
+            pair_steps<C, P, TX, TY, NT>(S, I, s_T[0], s_T[1], x0, y0, a.pitch, rb, a.phi_out, a.lo_out);
         }
-        rb = (long long)a.inst0.row0 * a.pitch + GC;
     } else {
+        // thread 0: tile t's instance (copied when it changes) and origin
+        auto locate = [&](int t) {
+            int k, x0, y0;
+            pair_locate<TX, TY>(a.tile_begin, a.n_inst, a.inst, t, k, x0, y0);
+            const bool changed = k != s_k;
+            if (changed) s_I = a.inst[k];
+            s_k = k;
+            s_x0 = x0;
+            s_y0 = y0;
+            return changed;
+        };
+        // the first tile: instance, tables and load offsets are constant data, set up before the wait
         if (tid == 0) {
             s_k = -1;
             if (any) locate(blockIdx.x);
@@ -381,36 +392,35 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
             pair_tables<C, P, TX, TY, NT>(S, s_I.nx, s_I.ny, s_I.tab, s_I.ylen, a.tabs, a.pitch, s_x0, s_y0);
             ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
         }
-        rb = (long long)s_I.row0 * a.pitch + GC;
-    }
-    grid_dependency_wait();
-    grid_launch_dependents();
-    if (any) ld.load(S, a.phi_in + rb, a.lo_in + rb);
-    if (tid == 0) {
-        s_time = a.need_time ? a.ctl->time : 0;
-        if (s_k >= 0) {
-            s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
-            s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off + 1);
-        }
-    }
-    __syncthreads();
-    const long long n = s_time + a.t_off;
-
-    for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
-        if (t != (int)blockIdx.x) {
-            __syncthreads();  // the previous tile's shared data are read no more
-            if (tid == 0 && locate(t)) {
-                s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, n);
-                s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, n + 1);
+        long long rb = (long long)s_I.row0 * a.pitch + GC;
+        grid_dependency_wait();
+        grid_launch_dependents();
+        if (any) ld.load(S, a.phi_in + rb, a.lo_in + rb);
+        if (tid == 0) {
+            s_time = a.need_time ? a.ctl->time : 0;
+            if (s_k >= 0) {
+                s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
+                s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off + 1);
             }
-            __syncthreads();
-            pair_tables<C, P, TX, TY, NT>(S, s_I.nx, s_I.ny, s_I.tab, s_I.ylen, a.tabs, a.pitch, s_x0, s_y0);
-            ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
-            rb = (long long)s_I.row0 * a.pitch + GC;
-            ld.load(S, a.phi_in + rb, a.lo_in + rb);
-            __syncthreads();
         }
-        pair_steps<C, P, TX, TY, NT>(S, s_I, s_T[0], s_T[1], s_x0, s_y0, a.pitch, rb, a.phi_out, a.lo_out);
+        __syncthreads();
+        n = s_time + a.t_off;
+        for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
+            if (t != (int)blockIdx.x) {
+                __syncthreads();  // the previous tile's shared data are read no more
+                if (tid == 0 && locate(t)) {
+                    s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, n);
+                    s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, n + 1);
+                }
+                __syncthreads();
+                pair_tables<C, P, TX, TY, NT>(S, s_I.nx, s_I.ny, s_I.tab, s_I.ylen, a.tabs, a.pitch, s_x0, s_y0);
+                ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
+                rb = (long long)s_I.row0 * a.pitch + GC;
+                ld.load(S, a.phi_in + rb, a.lo_in + rb);
+                __syncthreads();
+            }
+            pair_steps<C, P, TX, TY, NT>(S, s_I, s_T[0], s_T[1], s_x0, s_y0, a.pitch, rb, a.phi_out, a.lo_out);
+        }
     }
 
     // the last CTA of a batch's last launch advances the step counter (as in the one-step kernels)

@@ -37,6 +37,7 @@ namespace lbch {
 
 template <typename C, typename S, typename P>
 struct SweepArgs {
+    InstDev inst0;          // the record of instance 0, for single-instance handles (read from the parameters)
     const InstDev* inst;
     const int* tile_begin;  // first tile of each instance (n_inst + 1 entries)
     const C* tabs;          // velocity tables in the arithmetic type
@@ -164,11 +165,21 @@ __device__ __forceinline__ void store_g_images(S* g_out, long long row0, int pit
     }
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT>
+// The instance record a kernel reads: with SINGLE (a handle of one instance) the one in the launch
+// parameters, whose fields the arithmetic then takes as constant-bank operands; otherwise the copy in
+// shared memory of the tile's instance.
+template <bool SINGLE>
+__device__ __forceinline__ const InstDev& pick_inst(const InstDev& param, const InstDev& shared)
+{
+    if constexpr (SINGLE) return param;
+    else return shared;
+}
+
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT, bool SINGLE>
 __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     ch_sweep_kernel(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lo,
                     const __grid_constant__ CUtensorMap tm_grow, const __grid_constant__ CUtensorMap tm_lorow,
-                    SweepArgs<C, S, P> a)
+                    const __grid_constant__ SweepArgs<C, S, P> a)
 {
     static_assert(COMPACT || TY % 3 == 0, "the sweep advances three rows per unrolled step");
     static_assert(TY + 6 <= 32, "the Y tables of a warp's rows are held one row per lane");
@@ -199,20 +210,21 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     int k_t = 0, x0 = 0, y0 = 0;
     C X1m, X1a, X1b, X1p, X2m, X2a, X2b, X2p, ly1, ly2;
     auto locate = [&](int t) {
-        k_t = find_inst(a.tile_begin, a.n_inst, t);
-        const InstDev* I = a.inst + k_t;
-        const int local = t - a.tile_begin[k_t];
-        const int tiles_x = (I->nx + L::W - 1) / L::W;
+        k_t = SINGLE ? 0 : find_inst(a.tile_begin, a.n_inst, t);
+        const int local = SINGLE ? t : t - a.tile_begin[k_t];
+        const int nx_t = SINGLE ? a.inst0.nx : a.inst[k_t].nx;
+        const int tab_t = SINGLE ? a.inst0.tab : a.inst[k_t].tab;
+        const int ylen = SINGLE ? a.inst0.ylen : a.inst[k_t].ylen;
+        const int tiles_x = (nx_t + L::W - 1) / L::W;
         x0 = (local % tiles_x) * L::W;
         y0 = (local / tiles_x) * TH;
-        const C* tX1 = a.tabs + I->tab;
+        const C* tX1 = a.tabs + tab_t;
         const C* tX2 = tX1 + a.pitch;
         const C* tY1 = tX2 + a.pitch;
         const int sa = x0 + 2 * lane;
         const int cm = max(sa - 1, 0), ca = min(sa, a.pitch - 1), cb = min(sa + 1, a.pitch - 1), cp = min(sa + 2, a.pitch - 1);
         X1m = tX1[cm]; X1a = tX1[ca]; X1b = tX1[cb]; X1p = tX1[cp];
         X2m = tX2[cm]; X2a = tX2[ca]; X2b = tX2[cb]; X2p = tX2[cp];
-        const int ylen = I->ylen;
         const int yk = min(max(y0 + warp * TY - 3 + lane + GR, 0), ylen - 1);
         ly1 = tY1[yk];
         ly2 = tY1[ylen + yk];
@@ -223,8 +235,8 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         fence_mbar_init();
         s_tile_inst = -1;
         if ((int)blockIdx.x < a.total_tiles) {  // instance data are constant: read before the dependency wait
-            const int k = find_inst(a.tile_begin, a.n_inst, blockIdx.x);
-            s_I = a.inst[k];
+            const int k = SINGLE ? 0 : find_inst(a.tile_begin, a.n_inst, blockIdx.x);
+            s_I = SINGLE ? a.inst0 : a.inst[k];
             s_tile_inst = k;
         }
     }
@@ -232,9 +244,9 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
 
     // producer: thread 0 issues the boxes of tile t into stage s
     auto issue = [&](int t, int s) {
-        const int k = find_inst(a.tile_begin, a.n_inst, t);
-        const InstDev& I = a.inst[k];
-        const int local = t - a.tile_begin[k];
+        const int k = SINGLE ? 0 : find_inst(a.tile_begin, a.n_inst, t);
+        const InstDev& I = pick_inst<SINGLE>(a.inst0, a.inst[k]);
+        const int local = SINGLE ? t : t - a.tile_begin[k];
         const int tiles_x = (I.nx + L::W - 1) / L::W;
         const int bx = (local % tiles_x) * L::W, by = (local / tiles_x) * TH;
         fence_proxy_async();
@@ -273,7 +285,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     // of that code.
     auto sweep = [&](auto walls_t, int s) {
         constexpr bool WALLS = decltype(walls_t)::value;
-        const InstDev& I = s_I;
+        const InstDev& I = pick_inst<SINGLE>(a.inst0, s_I);
         const int nx = I.nx, ny = I.ny;
         const int wy0 = y0 + warp * TY;  // the warp's first output row
         if (wy0 >= ny) return;
@@ -675,7 +687,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
             s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
         }
         __syncthreads();
-        if (s_I.walls) sweep(std::true_type(), s);
+        if (pick_inst<SINGLE>(a.inst0, s_I).walls) sweep(std::true_type(), s);
         else sweep(std::false_type(), s);
         if (GEN && !ring_ok && lane == 0) atomicOr(&a.ctl->err, 1u);
         __syncthreads();  // the stage is free again

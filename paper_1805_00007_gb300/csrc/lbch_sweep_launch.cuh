@@ -12,6 +12,7 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
     const lbch_handle::PerShape& ps = h->sw[h->shape];
     SweepArgs<C, S, P> a;
+    a.inst0 = h->inst[0];
     a.inst = h->d_inst;
     a.tile_begin = ps.d_tile_begin;
     a.tabs = tables<C>(h);
@@ -37,8 +38,12 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     attr[0].val.programmaticStreamSerializationAllowed = h->no_pdl ? 0 : 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT>, ps.tm_phi[parity], ps.tm_lo[parity],
-                              h->tm_grow[parity], h->tm_lorow[parity], a);
+    // a single instance's record is read from the launch parameters (ch_sweep_kernel's SINGLE form)
+    if (h->n_inst == 1)
+        return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true>, ps.tm_phi[parity],
+                                  ps.tm_lo[parity], h->tm_grow[parity], h->tm_lorow[parity], a);
+    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false>, ps.tm_phi[parity],
+                              ps.tm_lo[parity], h->tm_grow[parity], h->tm_lorow[parity], a);
 }
 
 template <typename C, typename S, typename P, bool FF, int TY, int NW, bool COMPACT>
@@ -64,8 +69,11 @@ template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN,
 cudaError_t prepare_sweep_v(lbch_handle* h, int k)
 {
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
-    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT>;
+    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, L::BYTES);
