@@ -427,8 +427,10 @@ void release(lbch_handle* h)
         if (h->ps[k].d_tile_begin) cudaFree(h->ps[k].d_tile_begin);
     for (int k = 0; k < kSweepShapes; k++)
         if (h->sw[k].d_tile_begin) cudaFree(h->sw[k].d_tile_begin);
-    for (int k = 0; k < kPairShapes; k++)
+    for (int k = 0; k < kPairShapes; k++) {
         if (h->pr[k].d_tile_begin) cudaFree(h->pr[k].d_tile_begin);
+        if (h->pr[k].d_ttabs) cudaFree(h->pr[k].d_ttabs);
+    }
     if (h->d_node_begin) cudaFree(h->d_node_begin);
     if (h->d_tabs) cudaFree(h->d_tabs);
     if (h->phi0) cudaFree(h->phi0);
@@ -796,6 +798,43 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
             CKI(cudaMalloc(&h->pr[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
             CKI(cudaMemcpy(h->pr[sk].d_tile_begin, pair_begin[sk].data(), sizeof(int) * (n_inst + 1),
                            cudaMemcpyHostToDevice));
+            // each tile's velocity tables over the tile + 6 (periodically wrapped), contiguous per tile so that
+            // one bulk copy brings them (the layout of PairShape: X1, X2 by column, Y1, Y2 by row, 16-byte
+            // padded)
+            const Shape sh = pair_shape(prec, sk);
+            const int W6 = sh.tx + 12, H6 = sh.ty + 12;
+            const size_t esz = prec == LBCH_F64 ? 8 : 4;
+            const size_t stride = ((size_t)(2 * (W6 + H6)) * esz + 15) / 16 * 16 / esz;
+            std::vector<double> tt((size_t)h->pr[sk].total_tiles * stride, 0.0);
+            for (int k = 0; k < n_inst; k++) {
+                const InstDev& d = h->inst[k];
+                const double* X1 = &tabs[d.tab];
+                const double* X2 = X1 + h->pitch;
+                const double* Y1 = X2 + h->pitch;
+                const double* Y2 = Y1 + d.ylen;
+                const int tiles_x = (d.nx + sh.tx - 1) / sh.tx, tiles_y = (d.ny + sh.ty - 1) / sh.ty;
+                for (int l = 0; l < tiles_x * tiles_y; l++) {
+                    const int x0 = (l % tiles_x) * sh.tx, y0 = (l / tiles_x) * sh.ty;
+                    double* o = &tt[(size_t)(pair_begin[sk][k] + l) * stride];
+                    for (int c = 0; c < W6; c++) {
+                        const int x = ((x0 - 6 + c) % d.nx + d.nx) % d.nx;
+                        o[c] = X1[GC + x];
+                        o[W6 + c] = X2[GC + x];
+                    }
+                    for (int r = 0; r < H6; r++) {
+                        const int y = ((y0 - 6 + r) % d.ny + d.ny) % d.ny;
+                        o[2 * W6 + r] = Y1[GR + y];
+                        o[2 * W6 + H6 + r] = Y2[GR + y];
+                    }
+                }
+            }
+            CKI(cudaMalloc(&h->pr[sk].d_ttabs, tt.size() * esz));
+            if (prec == LBCH_F64) {
+                CKI(cudaMemcpy(h->pr[sk].d_ttabs, tt.data(), tt.size() * esz, cudaMemcpyHostToDevice));
+            } else {
+                std::vector<float> tf(tt.begin(), tt.end());  // rounded as the float tables are
+                CKI(cudaMemcpy(h->pr[sk].d_ttabs, tf.data(), tf.size() * esz, cudaMemcpyHostToDevice));
+            }
         }
     }
     if (stream) {

@@ -14,7 +14,8 @@ cudaError_t launch_pair_v(lbch_handle* h, int parity)
     a.inst0 = h->inst[0];
     a.inst = h->d_inst;
     a.tile_begin = ps.d_tile_begin;
-    a.tabs = tables<C>(h);
+    a.ttabs = static_cast<const C*>(ps.d_ttabs);
+    static_assert(L::TAB_STRIDE * sizeof(C) == L::TAB_BYTES, "the host lays the tables out with this stride");
     a.n_inst = h->n_inst;
     a.total_tiles = ps.total_tiles;
     a.pitch = h->pitch;

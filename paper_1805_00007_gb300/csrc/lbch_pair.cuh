@@ -24,7 +24,7 @@ struct PairArgs {
     InstDev inst0;          // the record of instance 0, for single-instance handles (read from the parameters)
     const InstDev* inst;
     const int* tile_begin;  // first tile of each instance for this launch's tile shape
-    const C* tabs;          // velocity tables of all instances (constant after set-up)
+    const C* ttabs;         // each tile's velocity tables over tile + 6, PairShape::TAB_STRIDE values per tile
     int n_inst;
     int total_tiles;
     int pitch;
@@ -56,7 +56,11 @@ struct PairShape {
     static constexpr size_t OFF_D = OFF_MU + a128(N5 * sizeof(C));
     static constexpr size_t OFF_POST = OFF_D + a128(N5 * sizeof(C));
     static constexpr size_t OFF_TAB = OFF_POST + a128(9 * N4 * sizeof(C));
-    static constexpr size_t BYTES = OFF_TAB + a128((2 * W6 + 2 * H6) * sizeof(C)) + 128;  // + alignment slack
+    // a tile's velocity tables: X1, X2 over the W6 columns, Y1, Y2 over the H6 rows, padded to 16 bytes
+    static constexpr int TAB_N = 2 * W6 + 2 * H6;
+    static constexpr unsigned TAB_BYTES = (TAB_N * sizeof(C) + 15) / 16 * 16;
+    static constexpr int TAB_STRIDE = TAB_BYTES / sizeof(C);
+    static constexpr size_t BYTES = OFF_TAB + a128(TAB_BYTES) + 128;  // + alignment slack
 };
 
 // i reduced into [0, n); i lies within a few periods of the domain
@@ -179,24 +183,17 @@ struct PairSmem {
     }
 };
 
-// The velocity tables of tile + 6 by wrapped stored column and row (constant after set-up).
-// (nx, ny, tab, ylen: the instance's sizes and table layout)
-template <typename C, typename P, int TX, int TY, int NT>
-__device__ __forceinline__ void pair_tables(const PairSmem<C, P, TX, TY>& S, int nx, int ny, int tab, int ylen,
-                                            const C* tabs, int pitch, int x0, int y0)
+// A tile's velocity tables (columns and rows of tile + 6, periodically wrapped; laid out per tile at
+// set-up) arrive by one bulk copy on an mbarrier, issued by thread 0 first thing, so that the copy's
+// latency overlaps the dependency wait and the phi loads.  Thread 0 waits for it (bounded: a copy that never
+// lands is reported through ctl->err) before the barrier that precedes the first phase.
+template <typename C, typename P, int TX, int TY>
+__device__ __forceinline__ void pair_fetch_tables(const PairSmem<C, P, TX, TY>& S, const C* ttabs, int t, uint64_t* bar)
 {
-    constexpr int W6 = PairShape<C, P, TX, TY>::W6, H6 = PairShape<C, P, TX, TY>::H6;
-    const C* tX1 = tabs + tab;
-    const C* tY1 = tX1 + 2 * pitch;
-    for (int e = threadIdx.x; e < 2 * (W6 + H6); e += NT) {
-        if (e < 2 * W6) {
-            const int j = e >= W6, c = e - j * W6;
-            S.X1[e] = __ldg(tX1 + j * pitch + GC + wrap_near(x0 - 6 + c, nx));
-        } else {
-            const int j = (e - 2 * W6) >= H6, r = e - 2 * W6 - j * H6;
-            S.Y1[e - 2 * W6] = __ldg(tY1 + j * ylen + GR + wrap_near(y0 - 6 + r, ny));
-        }
-    }
+    using L = PairShape<C, P, TX, TY>;
+    fence_proxy_async();  // the table region was last read through the generic proxy
+    mbar_expect_tx(bar, L::TAB_BYTES);
+    bulk_load(S.X1, ttabs + (size_t)t * L::TAB_STRIDE, L::TAB_BYTES, bar);
 }
 
 // The values one thread loads for a tile: phi on tile + 6 and (float path) its low part on tile + 3, at
@@ -333,25 +330,34 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
     __shared__ int s_k, s_x0, s_y0;
     __shared__ C s_T[2];
     __shared__ InstDev s_I;
+    __shared__ __align__(8) uint64_t s_tbar;  // completion of the table copy
     const int tid = threadIdx.x;
     const int stride = gridDim.x;
     const bool any = (int)blockIdx.x < a.total_tiles;
     PairLoad<C, P, TX, TY, NT> ld;
     long long n = 0;
+    int tuse = 0;  // table copies waited for so far (the mbarrier's phase)
+    auto wait_tables = [&]() {  // thread 0
+        if (!mbar_wait_bounded(&s_tbar, (unsigned)(tuse & 1), 1u << 22)) atomicOr(&a.ctl->err, 1u);
+        tuse++;
+    };
+    if (tid == 0 && any) {
+        mbar_init(&s_tbar, 1);
+        fence_mbar_init();
+        pair_fetch_tables<C, P, TX, TY>(S, a.ttabs, blockIdx.x, &s_tbar);
+    }
 
     if constexpr (SINGLE) {
         const InstDev& I = a.inst0;
         const int tiles_x = (I.nx + TX - 1) / TX;
         const long long rb = (long long)I.row0 * a.pitch + GC;
         int x0 = ((int)blockIdx.x % tiles_x) * TX, y0 = ((int)blockIdx.x / tiles_x) * TY;
-        if (any) {  // constant data: before the dependency wait
-            pair_tables<C, P, TX, TY, NT>(S, I.nx, I.ny, I.tab, I.ylen, a.tabs, a.pitch, x0, y0);
-            ld.init(I.nx, I.ny, a.pitch, x0, y0);
-        }
+        if (any) ld.init(I.nx, I.ny, a.pitch, x0, y0);  // constant data: before the dependency wait
         grid_dependency_wait();
         grid_launch_dependents();
         if (any) ld.load(S, a.phi_in + rb, a.lo_in + rb);
         if (tid == 0) {
+            if (any) wait_tables();
             s_time = a.need_time ? a.ctl->time : 0;
             s_T[0] = (C)vel_t(I.vel, I.Tper, s_time + a.t_off);
             s_T[1] = (C)vel_t(I.vel, I.Tper, s_time + a.t_off + 1);
@@ -361,11 +367,12 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
         for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
             if (t != (int)blockIdx.x) {
                 __syncthreads();  // the previous tile's shared data are read no more
+                if (tid == 0) pair_fetch_tables<C, P, TX, TY>(S, a.ttabs, t, &s_tbar);
                 x0 = (t % tiles_x) * TX;
                 y0 = (t / tiles_x) * TY;
-                pair_tables<C, P, TX, TY, NT>(S, I.nx, I.ny, I.tab, I.ylen, a.tabs, a.pitch, x0, y0);
                 ld.init(I.nx, I.ny, a.pitch, x0, y0);
                 ld.load(S, a.phi_in + rb, a.lo_in + rb);
+                if (tid == 0) wait_tables();
                 __syncthreads();
             }
             pair_steps<C, P, TX, TY, NT>(S, I, s_T[0], s_T[1], x0, y0, a.pitch, rb, a.phi_out, a.lo_out);
@@ -388,15 +395,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
             if (any) locate(blockIdx.x);
         }
         __syncthreads();
-        if (any) {
-            pair_tables<C, P, TX, TY, NT>(S, s_I.nx, s_I.ny, s_I.tab, s_I.ylen, a.tabs, a.pitch, s_x0, s_y0);
-            ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
-        }
+        if (any) ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
         long long rb = (long long)s_I.row0 * a.pitch + GC;
         grid_dependency_wait();
         grid_launch_dependents();
         if (any) ld.load(S, a.phi_in + rb, a.lo_in + rb);
         if (tid == 0) {
+            if (any) wait_tables();
             s_time = a.need_time ? a.ctl->time : 0;
             if (s_k >= 0) {
                 s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
@@ -408,15 +413,18 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
         for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
             if (t != (int)blockIdx.x) {
                 __syncthreads();  // the previous tile's shared data are read no more
-                if (tid == 0 && locate(t)) {
-                    s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, n);
-                    s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, n + 1);
+                if (tid == 0) {
+                    pair_fetch_tables<C, P, TX, TY>(S, a.ttabs, t, &s_tbar);
+                    if (locate(t)) {
+                        s_T[0] = (C)vel_t(s_I.vel, s_I.Tper, n);
+                        s_T[1] = (C)vel_t(s_I.vel, s_I.Tper, n + 1);
+                    }
                 }
                 __syncthreads();
-                pair_tables<C, P, TX, TY, NT>(S, s_I.nx, s_I.ny, s_I.tab, s_I.ylen, a.tabs, a.pitch, s_x0, s_y0);
                 ld.init(s_I.nx, s_I.ny, a.pitch, s_x0, s_y0);
                 rb = (long long)s_I.row0 * a.pitch + GC;
                 ld.load(S, a.phi_in + rb, a.lo_in + rb);
+                if (tid == 0) wait_tables();
                 __syncthreads();
             }
             pair_steps<C, P, TX, TY, NT>(S, s_I, s_T[0], s_T[1], s_x0, s_y0, a.pitch, rb, a.phi_out, a.lo_out);
