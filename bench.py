@@ -469,6 +469,49 @@ def main():
                 ensemble[prec]["looped_single_instance_MLUPS"] = enodes / dt_loop / 1e6
                 ensemble[prec]["batched_speedup"] = dt_loop / dt
 
+    # --- the coupled Rayleigh-Taylor workload (256 x 1024, Navier-Stokes + Cahn-Hilliard, walls in y) and the
+    #     adjoint step of the 512^2 single-vortex workload: the step rates of the other two kernel families
+    coupled, adjoint = {}, {}
+    if not args.no_sweep and rank == 0:
+        prt, frt = wl.rayleigh_taylor()
+        nrt = prt["nx"] * prt["ny"]
+        for prec in ("f32", "f64"):
+            with abi.Simulation(prt, frt, prec=prec, stream=stream.cuda_stream) as sim:
+                sim.step(64)
+                torch.cuda.synchronize()
+                nst = 256 if prec == "f32" else 64
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(nst)
+                e1.record(stream)
+                e1.synchronize()
+                dt = e0.elapsed_time(e1) / 1e3 / nst
+                inf = sim.info()
+                gbs = inf["bytes_per_lu"] * nrt / dt / 1e9
+                coupled[prec] = {"MLUPS": nrt / dt / 1e6, "us_per_step": dt * 1e6, "bytes_per_lu": inf["bytes_per_lu"],
+                                 "achieved_gbs": gbs, "frac": gbs / hbm_peak, "kernels_per_step": 5}
+        pv, fv, _ = wl.single_vortex(n=512)
+        nv = pv["nx"] * pv["ny"]
+        with abi.Simulation(pv, fv, prec="f32", stream=stream.cuda_stream) as sim:
+            sim.step(4)
+            tape = torch.empty((pv["ny"], pv["nx"]), dtype=torch.float32, device=dev)
+            abi.lb_ch_tape_phi(sim.h, tape.data_ptr())
+            seed = torch.zeros((pv["ny"], pv["nx"]), dtype=torch.float64, device=dev)
+            abi.lb_ch_adjoint_begin(sim.h, seed.data_ptr())
+            for k in range(8):
+                abi.lb_ch_adjoint_step(sim.h, tape.data_ptr(), 100 - k)
+            torch.cuda.synchronize()
+            nst = 64
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(nst):
+                abi.lb_ch_adjoint_step(sim.h, tape.data_ptr(), 90 - k)
+            e1.record(stream)
+            e1.synchronize()
+            dta = e0.elapsed_time(e1) / 1e3 / nst
+            adjoint = {"workload": "512^2 single vortex, FP32 forward tape, adjoint carried in FP64",
+                       "MLUPS": nv / dta / 1e6, "us_per_step": dta * 1e6}
+
     # --- the paper's relaxation-time study (Sec. III.A) at its own size, every point one ensemble instance
     tau_sweep = {}
     if not args.no_sweep and rank == 0:
@@ -531,6 +574,8 @@ def main():
             "sweep_4096": sweep,
             "ensemble_shear_256": ensemble,
             "paper_tau_sweep": tau_sweep,
+            "coupled_rt_256x1024": coupled,
+            "adjoint_vortex_512": adjoint,
             "accuracy_one_revolution": acc,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
                     "d2h_bytes_per_step": phi0.nbytes},

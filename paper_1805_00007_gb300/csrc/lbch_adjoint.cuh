@@ -103,7 +103,7 @@ __global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const TP* phi, C* 
     const Consts<C>& K0 = consts<C>(I);
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)a.nx * a.ny) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
     C c = (C)phi[k], s = C(0);
 #pragma unroll
     for (int q = 1; q < 9; q++) {
@@ -123,7 +123,7 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
     const long long N = (long long)a.nx * a.ny;
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
     C ph = (C)phi[k];
     C ux, uy;
     vel_at(I, tabs, a, x, y, T, ux, uy);
@@ -176,7 +176,7 @@ __global__ void transpose1_kernel(const InstDev* inst, AdjArgs a, const C* gmb, 
     const long long N = (long long)a.nx * a.ny;
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
     mub[k] += gradT(gmb, a.nx, a.ny, x, y, 0) + gradT(gmb + N, a.nx, a.ny, x, y, 1);
     Db[k] = (a.model == 2) ? K0.K * (gradT(Fb, a.nx, a.ny, x, y, 0) + gradT(Fb + N, a.nx, a.ny, x, y, 1)) : C(0);
 }
@@ -191,7 +191,7 @@ __global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjAr
     const long long N = (long long)a.nx * a.ny;
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
     C ph = (C)phi[k];
     C ux, uy;
     vel_at(I, tabs, a, x, y, T, ux, uy);
@@ -203,7 +203,8 @@ __global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjAr
         bx += ph * jbx;
         by += ph * jby;
     }
-    ds[k] = (double)bx * (double)ux + (double)by * (double)uy;  // u = s u_ref: du/ds = u
+    // u = s u_ref: du/ds = u.  Accumulated per node over the adjoint steps and summed once at the end.
+    ds[k] += (double)bx * (double)ux + (double)by * (double)uy;
 #pragma unroll
     for (int q = 0; q < 9; q++) lam[q * N + k] += pb;           // phi = sum_q g_q
 }
@@ -218,7 +219,7 @@ __global__ void init_local_kernel(const InstDev* inst, const double* tabs, AdjAr
     const long long N = (long long)a.nx * a.ny;
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
     C ph = (C)phi0[(long long)(I.row0 + y) * pitch0 + GC + x];
     C ux, uy;
     vel_at(I, tabs, a, x, y, T, ux, uy);
@@ -235,7 +236,7 @@ __global__ void init_local_kernel(const InstDev* inst, const double* tabs, AdjAr
     }
     dphi0[k] = pl;
     mub[k] = ml;
-    ds[k] = (double)bx * (double)ux + (double)by * (double)uy;
+    ds[k] += (double)bx * (double)ux + (double)by * (double)uy;
 }
 
 template <typename C>
@@ -246,12 +247,13 @@ __global__ void init_transpose_kernel(const InstDev* inst, AdjArgs a, const doub
     const Consts<C>& K0 = consts<C>(I);
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)a.nx * a.ny) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
     C ph = (C)phi0[(long long)(I.row0 + y) * pitch0 + GC + x];
     dphi0[k] += d2f(ph, K0.beta, K0.phiA, K0.phiB) * mub[k] - K0.kappa * lapT(mub, a.nx, a.ny, x, y);
 }
 
-// deterministic sum of ds[0..N) into *acc (one block, fixed order), executed once per adjoint step
+// deterministic sum of ds[0..N) into *acc (one block, fixed order), executed once, at the end of the adjoint
+// sweep (ds holds each node's contributions from every step)
 __global__ void __launch_bounds__(256) sum_into_kernel(const double* ds, long long N, double* acc)
 {
     __shared__ double sh[256];
@@ -273,7 +275,7 @@ __global__ void tape_kernel(const InstDev* inst, int pitch, const P* phi, const 
     const InstDev& I = inst[0];
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)I.nx * I.ny) return;
-    int y = (int)(k / I.nx), x = (int)(k - (long long)y * I.nx);
+    int y = (int)k / I.nx, x = (int)k - y * I.nx;  // fewer than 2^31 nodes (lb_ch_tape_phi checks)
     long long gi = (long long)(I.row0 + y) * pitch + GC + x;
     out[k] = (C)((double)phi[gi] + (lo ? (double)lo[gi] : 0.0));
 }

@@ -656,7 +656,6 @@ cudaError_t adjoint_step_t(lbch_handle* h, const TP* phi_n, long long n)
                                                          (C*)v.Db);
     adj::transpose2_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib,
                                                          (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam, v.ds);
-    adj::sum_into_kernel<<<1, 256, 0, h->stream>>>(v.ds, N, v.dLds);
     h->adj_par ^= 1;
     return cudaGetLastError();
 }
@@ -696,6 +695,8 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     for (int k = 0; k < n_inst; k++) coupled = coupled || params[k].vel == LBCH_VEL_COUPLED;
     if (coupled && (n_inst != 1 || prec == LBCH_F16S))
         return fail(LBCH_EINVAL, "the coupled flow needs a single instance in LBCH_F64 or LBCH_F32");
+    if (coupled && (long long)params[0].nx * params[0].ny >= (1LL << 31))
+        return fail(LBCH_EINVAL, "the coupled flow supports grids of fewer than 2^31 nodes");
     lbch_handle* h = new (std::nothrow) lbch_handle();
     if (!h) return fail(LBCH_ENOMEM, "host allocation failed");
     h->prec = prec;
@@ -923,6 +924,8 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         h->nsd.gx = p.gx; h->nsd.gy = p.gy; h->nsd.M = M; h->nsd.rbar = 0.5 * (p.rhoA + p.rhoB);
         h->nsf.tauf = (float)h->nsd.tauf; h->nsf.gx = (float)p.gx; h->nsf.gy = (float)p.gy;
         h->nsf.M = (float)M; h->nsf.rbar = (float)h->nsd.rbar;
+        h->nsd.itauf = 1.0 / h->nsd.tauf; h->nsd.srcf = 1.0 - 0.5 / h->nsd.tauf;
+        h->nsf.itauf = (float)h->nsd.itauf; h->nsf.srcf = (float)h->nsd.srcf;
         const size_t N = (size_t)d.nx * d.ny, esz = prec == LBCH_F64 ? 8 : 4;
         CKI(cudaMalloc(&h->ns, 47 * N * esz));
         CKI(cudaMemsetAsync(h->ns, 0, 47 * N * esz, h->stream));
@@ -1210,6 +1213,7 @@ lbch_status lb_ch_tape_phi(lbch_handle* h, void* dst)
     if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
     const int par = cur_buf(h);
     const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
+    if (N >= (1LL << 31)) return fail(LBCH_EINVAL, "the adjoint supports grids of fewer than 2^31 nodes");
     const int nb = (int)((N + 255) / 256);
     if (h->prec == LBCH_F64)
         adj::tape_kernel<double, double><<<nb, 256, 0, h->stream>>>(h->d_inst, h->pitch, (const double*)h->phi[par],
@@ -1228,6 +1232,8 @@ lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
     if (h->inst[0].walls) return fail(LBCH_EINVAL, "the adjoint supports periodic domains only");
     if (h->coupled) return fail(LBCH_EINVAL, "the adjoint supports prescribed flows only");
     if (h->model3) return fail(LBCH_EINVAL, "the adjoint supports Models I and II");
+    if ((long long)h->inst[0].nx * h->inst[0].ny >= (1LL << 31))
+        return fail(LBCH_EINVAL, "the adjoint supports grids of fewer than 2^31 nodes");
     h->adj_elem = 8;  // the adjoint is carried in double for every storage precision
     if (!h->adj) CK(cudaMalloc(&h->adj, adj_bytes(h)));
     AdjView v = adj_view(h);
@@ -1237,6 +1243,7 @@ lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
     adj::adj_begin_kernel<double><<<nb, 256, 0, h->stream>>>(N, (const double*)dL_dphiT, (double*)v.lam[0]);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(v.dLds, 0, sizeof(double), h->stream));
+    CK(cudaMemsetAsync(v.ds, 0, (size_t)N * sizeof(double), h->stream));  // per-node dL/ds, summed at the end
     return LBCH_OK;
 }
 

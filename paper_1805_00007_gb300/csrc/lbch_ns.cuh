@@ -25,6 +25,7 @@ namespace ns {
 template <typename C>
 struct NsConsts {
     C tauf, gx, gy, M, rbar;
+    C itauf, srcf;  // 1/tau_f and 1 - 1/(2 tau_f), formed once on the host (no divisions in the kernels)
 };
 
 template <typename C>
@@ -37,31 +38,52 @@ struct NsArgs {
     C *mu, *ux, *uy, *pr, *Fx, *Fy, *grx, *gry, *gmx, *gmy, *D;  // [N]
 };
 
-// neighbour (x + dx, y + dy): periodic in x; periodic in y or mirrored at walls
-__device__ __forceinline__ long long nb(int nx, int ny, int walls, int x, int y, int dx, int dy)
+// The coordinates of neighbour (x + dx, y + dy): periodic in x; periodic in y or mirrored at walls.
+__device__ __forceinline__ int2 nbxy(int nx, int ny, int walls, int x, int y, int dx, int dy)
 {
     int xx = x + dx, yy = y + dy;
     xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
     if (walls) yy = yy < 0 ? -1 - yy : (yy >= ny ? 2 * ny - 1 - yy : yy);
     else yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-    return (long long)yy * nx + xx;
+    return make_int2(xx, yy);
+}
+// its index in the [node] arrays
+__device__ __forceinline__ int nb(int nx, int ny, int walls, int x, int y, int dx, int dy)
+{
+    const int2 v = nbxy(nx, ny, walls, x, y, dx, dy);
+    return v.y * nx + v.x;
 }
 
-template <typename C> __device__ __forceinline__ C phi_at(const NsArgs<C>& a, long long k)
+// phi at node (x, y) in the handle's padded array
+template <typename C> __device__ __forceinline__ C phi_xy(const NsArgs<C>& a, int x, int y)
 {
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
     return a.phi_in[(long long)(a.row0 + y) * a.pitch + GC + x];
+}
+template <typename C> __device__ __forceinline__ C phi_nb(const NsArgs<C>& a, int x, int y, int dx, int dy)
+{
+    const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, dx, dy);
+    return phi_xy(a, v.x, v.y);
+}
+
+// The node of this thread: index k, coordinates (x, y) (a coupled handle has fewer than 2^31 nodes, which
+// lb_ch_init checks; the coordinates take one 32-bit division).
+__device__ __forceinline__ bool node_of(int nx, int ny, int& k, int& x, int& y)
+{
+    k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nx * ny) return false;
+    y = k / nx;
+    x = k - y * nx;
+    return true;
 }
 
 template <typename C>
 __global__ void mu_kernel(NsArgs<C> a)
 {
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long long)a.nx * a.ny) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
-    C c = phi_at(a, k), s = C(0);
+    int k, x, y;
+    if (!node_of(a.nx, a.ny, k, x, y)) return;
+    C c = phi_xy(a, x, y), s = C(0);
 #pragma unroll
-    for (int q = 1; q < 9; q++) s += C(2) * wq<C>(q) * (phi_at(a, nb(a.nx, a.ny, a.walls, x, y, cx(q), cy(q))) - c);
+    for (int q = 1; q < 9; q++) s += C(2) * wq<C>(q) * (phi_nb(a, x, y, cx(q), cy(q)) - c);
     a.mu[k] = dfdphi(c, a.k.beta, a.k.phiA, a.k.phiB) - a.k.kappa * C(3) * s;
 }
 
@@ -69,16 +91,15 @@ __global__ void mu_kernel(NsArgs<C> a)
 template <typename C>
 __global__ void fields_kernel(NsArgs<C> a)
 {
-    const long long N = (long long)a.nx * a.ny;
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
+    int k, x, y;
+    if (!node_of(a.nx, a.ny, k, x, y)) return;
     C gmx = C(0), gmy = C(0), gpx = C(0), gpy = C(0), lap = C(0);
     C m0 = a.mu[k];
 #pragma unroll
     for (int q = 1; q < 9; q++) {
-        long long j = nb(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
-        C m = a.mu[j], ph = phi_at(a, j);
+        const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
+        C m = a.mu[v.y * a.nx + v.x], ph = phi_xy(a, v.x, v.y);
         gmx += wq<C>(q) * (C)cx(q) * m;
         gmy += wq<C>(q) * (C)cy(q) * m;
         gpx += wq<C>(q) * (C)cx(q) * ph;
@@ -86,7 +107,7 @@ __global__ void fields_kernel(NsArgs<C> a)
         lap += C(2) * wq<C>(q) * (m - m0);
     }
     gmx *= C(3); gmy *= C(3); lap *= C(3);
-    C phi = phi_at(a, k), rho = a.k.a * phi + a.k.b;
+    C phi = phi_xy(a, x, y), rho = a.k.a * phi + a.k.b;
     C grx = a.k.a * C(3) * gpx, gry = a.k.a * C(3) * gpy;   // grad rho = a grad phi
     C F0x = -phi * gmx - (rho - a.n.rbar) * a.n.gx;
     C F0y = -phi * gmy - (rho - a.n.rbar) * a.n.gy;
@@ -113,14 +134,14 @@ __global__ void fields_kernel(NsArgs<C> a)
 template <typename C>
 __global__ void div_kernel(NsArgs<C> a)
 {
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long long)a.nx * a.ny) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    int k, x, y;
+    if (!node_of(a.nx, a.ny, k, x, y)) return;
     C s = C(0);
 #pragma unroll
     for (int q = 1; q < 9; q++) {
-        long long j = nb(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
-        C ph = phi_at(a, j);
+        const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
+        const int j = v.y * a.nx + v.x;
+        C ph = phi_xy(a, v.x, v.y);
         s += wq<C>(q) * ((C)cx(q) * ph * a.ux[j] + (C)cy(q) * ph * a.uy[j]);
     }
     a.D[k] = C(3) * s;
@@ -130,14 +151,13 @@ __global__ void div_kernel(NsArgs<C> a)
 template <typename C>
 __global__ void collide_kernel(NsArgs<C> a)
 {
-    const long long N = (long long)a.nx * a.ny;
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
+    int k, x, y;
+    if (!node_of(a.nx, a.ny, k, x, y)) return;
     C gpx = C(0), gpy = C(0), gdx = C(0), gdy = C(0);
 #pragma unroll
     for (int q = 1; q < 9; q++) {
-        long long j = nb(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
+        const int j = nb(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
         gpx += wq<C>(q) * (C)cx(q) * a.pr[j];
         gpy += wq<C>(q) * (C)cy(q) * a.pr[j];
         if (a.model == 2) {
@@ -146,14 +166,15 @@ __global__ void collide_kernel(NsArgs<C> a)
         }
     }
     gpx *= C(3); gpy *= C(3); gdx *= C(3); gdy *= C(3);
-    C phi = phi_at(a, k), rho = a.k.a * phi + a.k.b;
+    C phi = phi_xy(a, x, y), rho = a.k.a * phi + a.k.b;
     C ux = a.ux[k], uy = a.uy[k], mu = a.mu[k];
     // Cahn-Hilliard force with the flow's pressure (Eq. t0-phiu) and Eq. mark3
     C Fx = phi / rho * (-phi * a.gmx[k] - gpx) + a.k.K * gdx;
     C Fy = phi / rho * (-phi * a.gmy[k] - gpy) + a.k.K * gdy;
-    C FFx = a.Fx[k], FFy = a.Fy[k], grx = a.grx[k], gry = a.gry[k], pr = a.pr[k];
+    C FFx = a.Fx[k], FFy = a.Fy[k], pr = a.pr[k];
+    const C grx3 = a.grx[k] / C(3), gry3 = a.gry[k] / C(3);  // c_s^2 grad rho
     C uu = ux * ux + uy * uy;
-    const C tauf = a.n.tauf;
+    const C itauf = a.n.itauf, srcf = a.n.srcf;
 #pragma unroll
     for (int q = 0; q < 9; q++) {
         C cu = (C)cx(q) * ux + (C)cy(q) * uy;
@@ -167,15 +188,15 @@ __global__ void collide_kernel(NsArgs<C> a)
         // flow lattice
         C feq = (q == 0 ? (wq<C>(0) - C(1)) : wq<C>(q)) * C(3) * pr + rho * s;
         C Gam = wq<C>(q) + s;
-        C G = C(3) * (((C)cx(q) - ux) * (Gam * FFx + s * grx / C(3)) + ((C)cy(q) - uy) * (Gam * FFy + s * gry / C(3)));
+        C G = C(3) * (((C)cx(q) - ux) * (Gam * FFx + s * grx3) + ((C)cy(q) - uy) * (Gam * FFy + s * gry3));
         C fq = a.f_in[q * N + k];
-        C pf = fq - (fq - feq) / tauf + (C(1) - C(1) / (C(2) * tauf)) * G;
+        C pf = fq - (fq - feq) * itauf + srcf * G;
         int yy = y + cy(q);
         if (a.walls && (yy < 0 || yy >= a.ny)) {
             a.g_out[opp(q) * N + k] = pg;  // halfway bounce-back at a wall at rest
             a.f_out[opp(q) * N + k] = pf;
         } else {
-            long long j = nb(a.nx, a.ny, 0, x, y, cx(q), cy(q));
+            const int j = nb(a.nx, a.ny, 0, x, y, cx(q), cy(q));
             a.g_out[q * N + j] = pg;
             a.f_out[q * N + j] = pf;
         }
@@ -186,10 +207,9 @@ __global__ void collide_kernel(NsArgs<C> a)
 template <typename C>
 __global__ void phi_kernel(NsArgs<C> a)
 {
-    const long long N = (long long)a.nx * a.ny;
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
+    int k, x, y;
+    if (!node_of(a.nx, a.ny, k, x, y)) return;
     C s = C(0);
 #pragma unroll
     for (int q = 0; q < 9; q++) s += a.g_out[q * N + k];
@@ -200,14 +220,12 @@ __global__ void phi_kernel(NsArgs<C> a)
 template <typename C>
 __global__ void init_kernel(NsArgs<C> a, const double* phi0)
 {
-    const long long N = (long long)a.nx * a.ny;
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+    const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
+    int k, x, y;
+    if (!node_of(a.nx, a.ny, k, x, y)) return;
     auto at = [&](int dx, int dy) -> double {
-        long long j = nb(a.nx, a.ny, a.walls, x, y, dx, dy);
-        int yj = (int)(j / a.nx), xj = (int)(j - (long long)yj * a.nx);
-        return phi0[(long long)(a.row0 + yj) * a.pitch + GC + xj];
+        const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, dx, dy);
+        return phi0[(long long)(a.row0 + v.y) * a.pitch + GC + v.x];
     };
     double c0 = at(0, 0), s = 0.0;
     for (int q = 1; q < 9; q++) s += 2.0 * wq<double>(q) * (at(cx(q), cy(q)) - c0);
