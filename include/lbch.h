@@ -136,7 +136,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
  * step: the library then reads and writes phi only (the stored populations are left unchanged and are
  * not part of the state), with the same results bit for bit.  Until lb_ch_tune chooses otherwise, a
  * handle whose instances are all periodic with tau_g = 1 (LBCH_F32 or LBCH_F64) and whose grid fits the
- * device in one wave of two-step tiles (up to about 68 K nodes in LBCH_F32) steps two steps per launch
+ * device in one wave of two-step tiles (up to about 68 K nodes) steps two steps per launch
  * with the two-step kernel; every other handle steps with the row sweep. */
 lbch_status lb_ch_step(lbch_handle* h, long nsteps);
 

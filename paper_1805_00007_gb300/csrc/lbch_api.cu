@@ -356,6 +356,20 @@ void derive(const lbch_params& p, InstDev& d)
     f.K = (float)c.K; f.phiA = (float)c.phiA; f.phiB = (float)c.phiB;
     f.itau = (float)c.itau; f.omt = (float)c.omt; f.src = (float)c.src;
     f.cF1 = (float)c.cF1; f.cmu = (float)c.cmu;
+    // the collision's per-class coefficients, each one product rounded in the kernel's arithmetic type
+    // (the same rounding as forming them at a node would give)
+    auto coll = [](auto& k) {
+        using T = decltype(k.itau);
+        const T w1 = T(1) / T(9), w5 = T(1) / T(36);
+        k.k1a = w1 * k.itau;
+        k.k1d = w5 * k.itau;
+        k.k2a = T(3) * k.k1a;
+        k.k2d = T(3) * k.k1d;
+        k.k3a = (T(3) * w1) * k.src;
+        k.k3d = (T(3) * w5) * k.src;
+    };
+    coll(c);
+    coll(f);
     d.Tper = p.Tper;
     d.walls = p.walls; d.model = p.model; d.vel = p.vel;
 }
@@ -944,7 +958,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     // Kernel before any tuning: the two-step kernel where it applies and its tiles fit the device in one
     // wave (a step of such a grid is bound by latency, and one launch per two steps halves the launches);
     // otherwise the row sweep.  lb_ch_tune measures instead.
-    const int k2 = prec == LBCH_F64 ? 0 : 1;
+    const int k2 = prec == LBCH_F64 ? 3 : 1;  // 32 x 14 tiles in either precision
     if (pair_ok(h) && h->pr[k2].d_tile_begin && h->pr[k2].grid == h->pr[k2].total_tiles) {
         h->pair = true;
         h->pshape = k2;

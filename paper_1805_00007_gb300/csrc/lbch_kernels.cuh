@@ -48,6 +48,9 @@ struct Consts {
     C beta, kappa, eta, a, b, K, phiA, phiB;
     C itau, omt, src;  // 1/tau, 1 - 1/tau, 1 - 1/(2 tau)
     C cF1, cmu;        // Model III: 2 tau - 1 + 3K and 3 c_s^2 eta K, the coefficients of d_t F1 and d_t grad mu
+    // the collision's coefficients per direction class (axis a, diagonal d), each one rounded product:
+    // w/tau, 3 (w/tau), (3 w)(1 - 1/(2 tau)), formed once at set-up rather than at every node
+    C k1a, k1d, k2a, k2d, k3a, k3d;
 };
 
 // Per-instance parameters, derived constants and layout, resident in device memory.
@@ -223,15 +226,17 @@ template <typename C> __device__ __forceinline__ C node_u(C X, C Y, C T) { retur
 
 // Eq. LB as g* = (1 - 1/tau) g + g_eq / tau + (1 - 1/(2 tau)) S, with Eq. geq and the source
 // S_i = w_i c_i . F / c_s^2 (Eq. liangFi), split into the parts even and odd in c_i.  With kShift the
-// rest population is carried as g_0 - phi.  With TAU1 (tau = 1) the populations g are not read.
-template <typename C, bool TAU1, bool kShift>
+// rest population is carried as g_0 - phi.  With TAU1 (tau = 1) the populations g are not read.  PRE:
+// take the per-class coefficients precomputed in K0, else form them here (the same rounded products, so
+// the same bits; which is faster depends on the kernel's register budget).
+template <typename C, bool TAU1, bool kShift, bool PRE = true>
 __device__ __forceinline__ void collide9(C ph, C mu, C Fx, C Fy, C ux, C uy, const C* g, const Consts<C>& K0, C* post)
 {
-    const C itau = K0.itau, omt = K0.omt, src = K0.src;
+    const C itau = K0.itau, omt = K0.omt;
     // per direction class (axis, diagonal): w/tau, 3 w/tau, 3 w (1 - 1/(2 tau))
-    const C k1a = op_mul(wq<C>(1), itau), k1d = op_mul(wq<C>(5), itau);
-    const C k2a = op_mul(C(3), k1a), k2d = op_mul(C(3), k1d);
-    const C k3a = op_mul(C(3) * wq<C>(1), src), k3d = op_mul(C(3) * wq<C>(5), src);
+    const C k1a = PRE ? K0.k1a : op_mul(wq<C>(1), itau), k1d = PRE ? K0.k1d : op_mul(wq<C>(5), itau);
+    const C k2a = PRE ? K0.k2a : op_mul(C(3), k1a), k2d = PRE ? K0.k2d : op_mul(C(3), k1d);
+    const C k3a = PRE ? K0.k3a : op_mul(C(3) * wq<C>(1), K0.src), k3d = PRE ? K0.k3d : op_mul(C(3) * wq<C>(5), K0.src);
     const C emu = op_mul(K0.eta, mu);
     const C phuu = op_mul(ph, op_fma(ux, ux, op_mul(uy, uy)));
     const C even = op_fma(C(-1.5), phuu, emu);

@@ -406,9 +406,9 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                     node_force(Cs.pa, gmxa, gmya, gDxa, gDya, model2, ra, rb, K, Fxa, Fya);
                     node_force(Cs.pb, gmxb, gmyb, gDxb, gDyb, model2, ra, rb, K, Fxb, Fyb);
                     C pa_[9], pb_[9];
-                    collide9<C, !GEN, kShift>(Cs.pa, Cs.ma, Fxa, Fya, node_u(X1a, Cs.y1, T), node_u(X2a, Cs.y2, T), ga,
+                    collide9<C, !GEN, kShift, !GEN>(Cs.pa, Cs.ma, Fxa, Fya, node_u(X1a, Cs.y1, T), node_u(X2a, Cs.y2, T), ga,
                                               K0, pa_);
-                    collide9<C, !GEN, kShift>(Cs.pb, Cs.mb, Fxb, Fyb, node_u(X1b, Cs.y1, T), node_u(X2b, Cs.y2, T), gb,
+                    collide9<C, !GEN, kShift, !GEN>(Cs.pb, Cs.mb, Fxb, Fyb, node_u(X1b, Cs.y1, T), node_u(X2b, Cs.y2, T), gb,
                                               K0, pb_);
                     if constexpr (GEN && kHalf) {
                         // the streamed populations are stored in half: they travel rounded (g*_0 stays at the
