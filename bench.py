@@ -86,12 +86,15 @@ def dist_env():
 
 
 class Clocks:
-    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs (the samples go to
+    $LBCH_CLOCKS_DIR, else the system's temporary directory)."""
 
     def __init__(self, index: int):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        out = os.environ.get("LBCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_rank{index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

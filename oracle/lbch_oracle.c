@@ -3,7 +3,7 @@
  * model for the Cahn-Hilliard equation with the high-order source term of Zhang, Guo & Liang,
  * "A high-order lattice Boltzmann model for the Cahn-Hilliard equation" (arXiv:1805.00007).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the checker the CUDA path is compared against.  It shares no
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA path is compared against.  It shares no
  * code, header, table or helper with the product library; only tests, the smoke check and the CPU
  * baseline leg of the benchmark may load it.  It is written for a reader who checks it against the
  * paper by eye: one loop per field, in the order the paper introduces the quantities, double precision

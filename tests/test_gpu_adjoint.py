@@ -2,8 +2,8 @@
 finite differences of the GPU forward map.
 
 Tolerances: FP64 adjoint vs the oracle adjoint 1e-10 relative (the same linear algebra in another
-order); FP32 adjoint vs the oracle adjoint and vs finite differences 1e-4 relative (the north-star
-figure for the adjoint).  The loss is L = 1/2 sum (phi(T) - phi_ref)^2 with phi_ref = phi0 detached.
+order); FP32 adjoint vs the oracle adjoint and vs finite differences 1e-4 relative (the tolerance the
+single-vortex workload states for its gradient).  The loss is L = 1/2 sum (phi(T) - phi_ref)^2 with phi_ref = phi0 detached.
 """
 import numpy as np
 import pytest
