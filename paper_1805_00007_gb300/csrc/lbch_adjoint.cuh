@@ -59,13 +59,15 @@ __device__ __forceinline__ void geq_partials(C phi, C ux, C uy, C eta, C* dphi, 
     dmu[0] = (wq<C>(0) - C(1)) * eta;
     dux[0] = -wq<C>(0) * phi * C(3) * ux;
     duy[0] = -wq<C>(0) * phi * C(3) * uy;
+    // (the loops are unrolled, so the lattice components are constants: terms with a zero component are
+    // left out rather than multiplied by zero, which the compiler may not fold away)
 #pragma unroll
     for (int q = 1; q < 9; q++) {
-        C cu = (C)cx(q) * ux + (C)cy(q) * uy;
+        const C cu = cx(q) == 0 ? (C)cy(q) * uy : (cy(q) == 0 ? (C)cx(q) * ux : (C)cx(q) * ux + (C)cy(q) * uy);
         dphi[q] = wq<C>(q) * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
         dmu[q] = wq<C>(q) * eta;
-        dux[q] = wq<C>(q) * phi * (C(3) * (C)cx(q) + C(9) * cu * (C)cx(q) - C(3) * ux);
-        duy[q] = wq<C>(q) * phi * (C(3) * (C)cy(q) + C(9) * cu * (C)cy(q) - C(3) * uy);
+        dux[q] = wq<C>(q) * phi * (cx(q) == 0 ? -(C(3) * ux) : C(3) * (C)cx(q) + C(9) * cu * (C)cx(q) - C(3) * ux);
+        duy[q] = wq<C>(q) * phi * (cy(q) == 0 ? -(C(3) * uy) : C(3) * (C)cy(q) + C(9) * cu * (C)cy(q) - C(3) * uy);
     }
 }
 
@@ -76,8 +78,10 @@ __device__ __forceinline__ C gradT(const C* v, int nx, int ny, int x, int y, int
     C s = C(0);
 #pragma unroll
     for (int k = 1; k < 9; k++) {
+        const int ck = comp == 0 ? cx(k) : cy(k);
+        if (ck == 0) continue;  // a zero component contributes nothing
         int xs = wp(x - cx(k), nx), ys = wp(y - cy(k), ny);
-        s += wq<C>(k) * (C)(comp == 0 ? cx(k) : cy(k)) * v[(long long)ys * nx + xs];
+        s += wq<C>(k) * (C)ck * v[(long long)ys * nx + xs];
     }
     return C(3) * s;
 }
@@ -132,8 +136,8 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
 #pragma unroll
     for (int q = 1; q < 9; q++) {
         C m = mu[(long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
-        gx += wq<C>(q) * (C)cx(q) * m;
-        gy += wq<C>(q) * (C)cy(q) * m;
+        if (cx(q) != 0) gx += wq<C>(q) * (C)cx(q) * m;
+        if (cy(q) != 0) gy += wq<C>(q) * (C)cy(q) * m;
     }
     gx *= C(3);
     gy *= C(3);
@@ -147,8 +151,8 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
         lam[q * N + k] = K0.omt * pb;
         C geqb = pb * K0.itau;
         C Sb = K0.src * pb;
-        fbx += Sb * C(3) * wq<C>(q) * (C)cx(q);  // S_q = w_q c_q . F / c_s^2
-        fby += Sb * C(3) * wq<C>(q) * (C)cy(q);
+        if (cx(q) != 0) fbx += Sb * C(3) * wq<C>(q) * (C)cx(q);  // S_q = w_q c_q . F / c_s^2
+        if (cy(q) != 0) fby += Sb * C(3) * wq<C>(q) * (C)cy(q);
         pl += geqb * dphi[q];
         ml += geqb * dmu[q];
         bx += geqb * dux[q];

@@ -100,10 +100,15 @@ __global__ void fields_kernel(NsArgs<C> a)
     for (int q = 1; q < 9; q++) {
         const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
         C m = a.mu[v.y * a.nx + v.x], ph = phi_xy(a, v.x, v.y);
-        gmx += wq<C>(q) * (C)cx(q) * m;
-        gmy += wq<C>(q) * (C)cy(q) * m;
-        gpx += wq<C>(q) * (C)cx(q) * ph;
-        gpy += wq<C>(q) * (C)cy(q) * ph;
+        // (unrolled: terms with a zero lattice component are left out, not multiplied by zero)
+        if (cx(q) != 0) {
+            gmx += wq<C>(q) * (C)cx(q) * m;
+            gpx += wq<C>(q) * (C)cx(q) * ph;
+        }
+        if (cy(q) != 0) {
+            gmy += wq<C>(q) * (C)cy(q) * m;
+            gpy += wq<C>(q) * (C)cy(q) * ph;
+        }
         lap += C(2) * wq<C>(q) * (m - m0);
     }
     gmx *= C(3); gmy *= C(3); lap *= C(3);
@@ -115,8 +120,8 @@ __global__ void fields_kernel(NsArgs<C> a)
 #pragma unroll
     for (int q = 0; q < 9; q++) {
         C fq = a.f_in[q * N + k];
-        mx += (C)cx(q) * fq;
-        my += (C)cy(q) * fq;
+        if (cx(q) != 0) mx += (C)cx(q) * fq;
+        if (cy(q) != 0) my += (C)cy(q) * fq;
         if (q > 0) s1 += fq;
     }
     C den = rho - C(0.5) * a.k.a * a.n.M * lap;   // rho u = m + F/2 with F = F0 + a M lap(mu) u
@@ -142,7 +147,9 @@ __global__ void div_kernel(NsArgs<C> a)
         const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
         const int j = v.y * a.nx + v.x;
         C ph = phi_xy(a, v.x, v.y);
-        s += wq<C>(q) * ((C)cx(q) * ph * a.ux[j] + (C)cy(q) * ph * a.uy[j]);
+        const C t = cx(q) == 0 ? (C)cy(q) * ph * a.uy[j]
+                  : (cy(q) == 0 ? (C)cx(q) * ph * a.ux[j] : (C)cx(q) * ph * a.ux[j] + (C)cy(q) * ph * a.uy[j]);
+        s += wq<C>(q) * t;
     }
     a.D[k] = C(3) * s;
 }
@@ -158,11 +165,11 @@ __global__ void collide_kernel(NsArgs<C> a)
 #pragma unroll
     for (int q = 1; q < 9; q++) {
         const int j = nb(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
-        gpx += wq<C>(q) * (C)cx(q) * a.pr[j];
-        gpy += wq<C>(q) * (C)cy(q) * a.pr[j];
+        if (cx(q) != 0) gpx += wq<C>(q) * (C)cx(q) * a.pr[j];
+        if (cy(q) != 0) gpy += wq<C>(q) * (C)cy(q) * a.pr[j];
         if (a.model == 2) {
-            gdx += wq<C>(q) * (C)cx(q) * a.D[j];
-            gdy += wq<C>(q) * (C)cy(q) * a.D[j];
+            if (cx(q) != 0) gdx += wq<C>(q) * (C)cx(q) * a.D[j];
+            if (cy(q) != 0) gdy += wq<C>(q) * (C)cy(q) * a.D[j];
         }
     }
     gpx *= C(3); gpy *= C(3); gdx *= C(3); gdy *= C(3);
@@ -177,12 +184,13 @@ __global__ void collide_kernel(NsArgs<C> a)
     const C itauf = a.n.itauf, srcf = a.n.srcf;
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        C cu = (C)cx(q) * ux + (C)cy(q) * uy;
+        const C cu = cx(q) == 0 ? (C)cy(q) * uy : (cy(q) == 0 ? (C)cx(q) * ux : (C)cx(q) * ux + (C)cy(q) * uy);
         C s = wq<C>(q) * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
         // Cahn-Hilliard lattice: Eq. geq, Eq. liangFi, Eq. LB
         C geq = (q == 0) ? phi + (wq<C>(0) - C(1)) * a.k.eta * mu - wq<C>(0) * C(1.5) * phi * uu
                          : wq<C>(q) * a.k.eta * mu + phi * s;
-        C Sq = C(3) * wq<C>(q) * ((C)cx(q) * Fx + (C)cy(q) * Fy);
+        const C cF = cx(q) == 0 ? (C)cy(q) * Fy : (cy(q) == 0 ? (C)cx(q) * Fx : (C)cx(q) * Fx + (C)cy(q) * Fy);
+        C Sq = C(3) * wq<C>(q) * cF;
         C gq = a.g_in[q * N + k];
         C pg = gq - (gq - geq) * a.k.itau + a.k.src * Sq;
         // flow lattice
