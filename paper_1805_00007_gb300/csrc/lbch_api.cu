@@ -244,35 +244,31 @@ ns::NsArgs<C> ns_args(lbch_handle* h, int parity)
     a.f_in = f[parity]; a.f_out = f[parity ^ 1];
     a.g_in = g[parity]; a.g_out = g[parity ^ 1];
     C* w = p + 36 * N;
-    a.mu = w; a.ux = w + N; a.uy = w + 2 * N; a.pr = w + 3 * N; a.Fx = w + 4 * N; a.Fy = w + 5 * N;
-    a.grx = w + 6 * N; a.gry = w + 7 * N; a.gmx = w + 8 * N; a.gmy = w + 9 * N; a.D = w + 10 * N;
+    a.ux = w; a.uy = w + N; a.pr = w + 2 * N; a.mu = w + 3 * N;
     a.phi_in = static_cast<C*>(h->phi[parity]);
     a.phi_out = static_cast<C*>(h->phi[parity ^ 1]);
     return a;
 }
 
-// One coupled step: mu, the flow's moments and forces, div(phi u), collide-and-stream, phi(t+1).
+// One coupled step: the flow's u and p; both collisions with push streaming; phi(t+1).
 template <typename C>
 cudaError_t launch_ns_t(lbch_handle* h, int parity)
 {
     ns::NsArgs<C> a = ns_args<C>(h, parity);
+    const int tiles = ns::tiles_of(a.nx, a.ny);
     const int nb = (int)(((long long)a.nx * a.ny + 255) / 256);
-    ns::mu_kernel<C><<<nb, 256, 0, h->stream>>>(a);
-    ns::fields_kernel<C><<<nb, 256, 0, h->stream>>>(a);
-    if (a.model == 2) ns::div_kernel<C><<<nb, 256, 0, h->stream>>>(a);
-    ns::collide_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    ns::fields_kernel<C><<<tiles, ns::NT, 0, h->stream>>>(a);
+    ns::collide_kernel<C><<<tiles, ns::NT, 0, h->stream>>>(a);
     ns::phi_kernel<C><<<nb, 256, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
 
-// The flow's u and p of the current state (for observation): mu and fields kernels on it.
+// The flow's u and p of the current state (for observation).
 template <typename C>
 cudaError_t ns_fields_t(lbch_handle* h, int parity)
 {
     ns::NsArgs<C> a = ns_args<C>(h, parity);
-    const int nb = (int)(((long long)a.nx * a.ny + 255) / 256);
-    ns::mu_kernel<C><<<nb, 256, 0, h->stream>>>(a);
-    ns::fields_kernel<C><<<nb, 256, 0, h->stream>>>(a);
+    ns::fields_kernel<C><<<ns::tiles_of(a.nx, a.ny), ns::NT, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -938,11 +934,11 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         h->nsd.gx = p.gx; h->nsd.gy = p.gy; h->nsd.M = M; h->nsd.rbar = 0.5 * (p.rhoA + p.rhoB);
         h->nsf.tauf = (float)h->nsd.tauf; h->nsf.gx = (float)p.gx; h->nsf.gy = (float)p.gy;
         h->nsf.M = (float)M; h->nsf.rbar = (float)h->nsd.rbar;
-        h->nsd.itauf = 1.0 / h->nsd.tauf; h->nsd.srcf = 1.0 - 0.5 / h->nsd.tauf;
-        h->nsf.itauf = (float)h->nsd.itauf; h->nsf.srcf = (float)h->nsd.srcf;
+        h->nsd.itauf = 1.0 / h->nsd.tauf; h->nsd.omtf = 1.0 - h->nsd.itauf; h->nsd.srcf = 1.0 - 0.5 / h->nsd.tauf;
+        h->nsf.itauf = (float)h->nsd.itauf; h->nsf.omtf = (float)h->nsd.omtf; h->nsf.srcf = (float)h->nsd.srcf;
         const size_t N = (size_t)d.nx * d.ny, esz = prec == LBCH_F64 ? 8 : 4;
-        CKI(cudaMalloc(&h->ns, 47 * N * esz));
-        CKI(cudaMemsetAsync(h->ns, 0, 47 * N * esz, h->stream));
+        CKI(cudaMalloc(&h->ns, 40 * N * esz));  // f, g (two buffers each), u, p, mu
+        CKI(cudaMemsetAsync(h->ns, 0, 40 * N * esz, h->stream));
         const int nbn = (int)((N + 255) / 256);
         if (prec == LBCH_F64) {
             ns::NsArgs<double> a = ns_args<double>(h, 1);  // writes the parity-0 buffers
@@ -1055,9 +1051,9 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out)
         const size_t N = (size_t)h->inst[0].nx * h->inst[0].ny, e = h->prec == LBCH_F64 ? 8 : 4;
         lbch_status s = stage(h, 2 * N * sizeof(double));
         if (s != LBCH_OK) return s;
-        const char* w = static_cast<const char*>(h->ns) + 36 * N * e;  // mu, ux, uy, pr, ...
-        if (what == LBCH_OBS_U) CK(cudaMemcpyAsync(h->h_stage, w + N * e, 2 * N * e, cudaMemcpyDeviceToHost, h->stream));
-        else CK(cudaMemcpyAsync(h->h_stage, w + 3 * N * e, N * e, cudaMemcpyDeviceToHost, h->stream));
+        const char* w = static_cast<const char*>(h->ns) + 36 * N * e;  // ux, uy, pr, mu
+        if (what == LBCH_OBS_U) CK(cudaMemcpyAsync(h->h_stage, w, 2 * N * e, cudaMemcpyDeviceToHost, h->stream));
+        else CK(cudaMemcpyAsync(h->h_stage, w + 2 * N * e, N * e, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         const size_t cnt = what == LBCH_OBS_U ? 2 * N : N;
         if (e == 8) std::memcpy(out, h->h_stage, cnt * 8);

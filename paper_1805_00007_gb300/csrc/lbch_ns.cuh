@@ -13,9 +13,14 @@
 // (Eq. t0-phiu) plus the Eq. mark3 term.  Walls: halfway bounce-back for both lattices at rest; stencil
 // operands at ghost rows take the mirror values.
 //
-// One step is five one-thread-per-node kernels over plain [q][node] population arrays: mu from phi;
-// the flow's moments (u, p) and forces; D = div(phi u); the coupled collide-and-push-stream of both
-// lattices; phi(t+1) = sum_q g_q into the handle's padded phi array (which observations read).
+// One step is three kernels.  The first two work on 32 x 8 tiles of nodes, one node per thread, with the
+// stencil operands staged in shared memory.  fields_kernel stages phi on tile + 2, forms mu on tile + 1
+// and gives mu, u and p at the tile's nodes.  collide_kernel stages phi (and phi u) on tile + 2 and mu and
+// p on tile + 1, forms D = div(phi u) on tile + 1 for Model II (kept there rather than stored), collides
+// both lattices and pushes them to the neighbours (bounce-back at walls).  phi_kernel sums
+// phi(t+1) = sum_q g_q into the handle's padded phi array (which observations read).  A stencil operand
+// at a ghost row beyond a wall takes the value of the mirror node: a staged operand is read at that node,
+// and a derived one is formed at the mirror row of the tile's region.
 #pragma once
 #include "lbch_kernels.cuh"
 
@@ -25,7 +30,7 @@ namespace ns {
 template <typename C>
 struct NsConsts {
     C tauf, gx, gy, M, rbar;
-    C itauf, srcf;  // 1/tau_f and 1 - 1/(2 tau_f), formed once on the host (no divisions in the kernels)
+    C itauf, omtf, srcf;  // 1/tau_f, 1 - 1/tau_f and 1 - 1/(2 tau_f), formed once on the host
 };
 
 template <typename C>
@@ -35,23 +40,48 @@ struct NsArgs {
     NsConsts<C> n;    // the flow's constants
     C* f_in; C* f_out; C* g_in; C* g_out;   // [9][N]
     C* phi_in; C* phi_out;                  // padded phi of the handle
-    C *mu, *ux, *uy, *pr, *Fx, *Fy, *grx, *gry, *gmx, *gmy, *D;  // [N]
+    C *ux, *uy, *pr, *mu;                   // [N], written by fields_kernel
 };
 
-// The coordinates of neighbour (x + dx, y + dy): periodic in x; periodic in y or mirrored at walls.
-__device__ __forceinline__ int2 nbxy(int nx, int ny, int walls, int x, int y, int dx, int dy)
+// tiles and the regions staged around them
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int W2 = TX + 4, H2 = TY + 4, N2 = W2 * H2;  // tile + 2
+constexpr int W1 = TX + 2, H1 = TY + 2, N1 = W1 * H1;  // tile + 1
+
+__host__ __device__ inline int tiles_of(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
+
+__device__ __forceinline__ int wrap_any(int v, int n)
 {
-    int xx = x + dx, yy = y + dy;
-    xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-    if (walls) yy = yy < 0 ? -1 - yy : (yy >= ny ? 2 * ny - 1 - yy : yy);
-    else yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-    return make_int2(xx, yy);
+    if (v < 0 || v >= n) {
+        v %= n;
+        if (v < 0) v += n;
+    }
+    return v;
 }
-// its index in the [node] arrays
-__device__ __forceinline__ int nb(int nx, int ny, int walls, int x, int y, int dx, int dy)
+
+// The node whose value a stencil operand at coordinate (x, y) takes: periodic in x; periodic in y or
+// mirrored at walls.  (Coordinates more than one row beyond a wall occur only in the region of a ragged
+// tile, where no node reads them; they are clamped into the domain.)
+__device__ __forceinline__ int2 node_at(int nx, int ny, int walls, int x, int y)
 {
-    const int2 v = nbxy(nx, ny, walls, x, y, dx, dy);
-    return v.y * nx + v.x;
+    x = wrap_any(x, nx);
+    if (walls) {
+        y = y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y);
+        y = min(max(y, 0), ny - 1);
+    } else {
+        y = wrap_any(y, ny);
+    }
+    return make_int2(x, y);
+}
+
+// The row of region tile + 1 (origin row y0 - 1) at which a derived field is formed for its row j: j
+// itself, or the mirror row of a ghost row beyond a wall.
+__device__ __forceinline__ int r1_row(int walls, int ny, int y0, int j)
+{
+    if (!walls) return j;
+    const int y = y0 - 1 + j;
+    const int m = (y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y)) - (y0 - 1);
+    return (m >= 0 && m < H1) ? m : j;
 }
 
 // phi at node (x, y) in the handle's padded array
@@ -59,165 +89,223 @@ template <typename C> __device__ __forceinline__ C phi_xy(const NsArgs<C>& a, in
 {
     return a.phi_in[(long long)(a.row0 + y) * a.pitch + GC + x];
 }
-template <typename C> __device__ __forceinline__ C phi_nb(const NsArgs<C>& a, int x, int y, int dx, int dy)
+
+// The isotropic stencils on a staged region of row width W around flat index c (x to the east, y to the
+// north): grad psi = sum_k w_k c_k psi(x + c_k) / c_s^2 and lap psi = sum_k 2 w_k (psi(x + c_k) - psi) / c_s^2.
+template <typename C, int W> __device__ __forceinline__ C sgx(const C* s, int c)
 {
-    const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, dx, dy);
-    return phi_xy(a, v.x, v.y);
+    return op_fma(C(1) / C(3), s[c + 1] - s[c - 1],
+                  op_mul(C(1) / C(12), (s[c + W + 1] - s[c + W - 1]) + (s[c - W + 1] - s[c - W - 1])));
+}
+template <typename C, int W> __device__ __forceinline__ C sgy(const C* s, int c)
+{
+    return op_fma(C(1) / C(3), s[c + W] - s[c - W],
+                  op_mul(C(1) / C(12), (s[c + W + 1] + s[c + W - 1]) - (s[c - W + 1] + s[c - W - 1])));
+}
+template <typename C, int W> __device__ __forceinline__ C slap(const C* s, int c)
+{
+    const C ce = s[c];
+    const C ax = (s[c + 1] + s[c - 1]) + (s[c + W] + s[c - W]);
+    const C dg = (s[c + W + 1] + s[c + W - 1]) + (s[c - W + 1] + s[c - W - 1]);
+    return op_fma(C(2) / C(3), op_fma(C(-4), ce, ax), op_mul(C(1) / C(6), op_fma(C(-4), ce, dg)));
 }
 
-// The node of this thread: index k, coordinates (x, y) (a coupled handle has fewer than 2^31 nodes, which
-// lb_ch_init checks; the coordinates take one 32-bit division).
-__device__ __forceinline__ bool node_of(int nx, int ny, int& k, int& x, int& y)
+// The tile of this block: origin (x0, y0)
+__device__ __forceinline__ void tile_origin(int nx, int& x0, int& y0)
 {
-    k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nx * ny) return false;
-    y = k / nx;
-    x = k - y * nx;
-    return true;
+    const int tiles_x = (nx + TX - 1) / TX;
+    x0 = ((int)blockIdx.x % tiles_x) * TX;
+    y0 = ((int)blockIdx.x / tiles_x) * TY;
 }
 
+// phi on tile + 2 into s2 (and, with jx, the components of phi u there)
 template <typename C>
-__global__ void mu_kernel(NsArgs<C> a)
+__device__ __forceinline__ void stage_phi(const NsArgs<C>& a, int x0, int y0, C* s2, C* jx, C* jy)
 {
-    int k, x, y;
-    if (!node_of(a.nx, a.ny, k, x, y)) return;
-    C c = phi_xy(a, x, y), s = C(0);
-#pragma unroll
-    for (int q = 1; q < 9; q++) s += C(2) * wq<C>(q) * (phi_nb(a, x, y, cx(q), cy(q)) - c);
-    a.mu[k] = dfdphi(c, a.k.beta, a.k.phiA, a.k.phiB) - a.k.kappa * C(3) * s;
+    for (int e = threadIdx.x; e < N2; e += NT) {
+        const int j = e / W2, i = e - j * W2;
+        const int2 v = node_at(a.nx, a.ny, a.walls, x0 - 2 + i, y0 - 2 + j);
+        const C ph = phi_xy(a, v.x, v.y);
+        s2[e] = ph;
+        if (jx) {
+            const int k = v.y * a.nx + v.x;
+            jx[e] = ph * a.ux[k];
+            jy[e] = ph * a.uy[k];
+        }
+    }
 }
 
-// the flow's moments and forces at every node
+// mu (Eq. mu) on tile + 1 from phi on tile + 2
 template <typename C>
-__global__ void fields_kernel(NsArgs<C> a)
+__device__ __forceinline__ void form_mu(const NsArgs<C>& a, int y0, const C* s2, C* mu1)
 {
+    for (int e = threadIdx.x; e < N1; e += NT) {
+        const int j = e / W1, i = e - j * W1;
+        const int c = (r1_row(a.walls, a.ny, y0, j) + 1) * W2 + i + 1;
+        mu1[e] = op_fma(-a.k.kappa, slap<C, W2>(s2, c), node_dfdphi(s2[c], a.k.beta, a.k.phiA, a.k.phiB));
+    }
+}
+
+// mu and the flow's velocity and pressure at every node
+template <typename C>
+__global__ void __launch_bounds__(NT) fields_kernel(NsArgs<C> a)
+{
+    __shared__ C s2[N2], mu1[N1];
+    int x0, y0;
+    tile_origin(a.nx, x0, y0);
+    stage_phi<C>(a, x0, y0, s2, nullptr, nullptr);
+    __syncthreads();
+    form_mu(a, y0, s2, mu1);
+    __syncthreads();
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, x = x0 + tx, y = y0 + ty;
+    if (x >= a.nx || y >= a.ny) return;
+    const int c1 = (ty + 1) * W1 + tx + 1, c2 = (ty + 2) * W2 + tx + 2;
     const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
-    int k, x, y;
-    if (!node_of(a.nx, a.ny, k, x, y)) return;
-    C gmx = C(0), gmy = C(0), gpx = C(0), gpy = C(0), lap = C(0);
-    C m0 = a.mu[k];
+    const int k = y * a.nx + x;
+    const C gmx = sgx<C, W1>(mu1, c1), gmy = sgy<C, W1>(mu1, c1), lap = slap<C, W1>(mu1, c1);
+    const C phi = s2[c2], rho = op_fma(a.k.a, phi, a.k.b);
+    const C grx = op_mul(a.k.a, sgx<C, W2>(s2, c2)), gry = op_mul(a.k.a, sgy<C, W2>(s2, c2));  // grad rho
+    const C db = rho - a.n.rbar;
+    const C F0x = -op_fma(phi, gmx, op_mul(db, a.n.gx)), F0y = -op_fma(phi, gmy, op_mul(db, a.n.gy));
+    C f[9];
 #pragma unroll
-    for (int q = 1; q < 9; q++) {
-        const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
-        C m = a.mu[v.y * a.nx + v.x], ph = phi_xy(a, v.x, v.y);
-        // (unrolled: terms with a zero lattice component are left out, not multiplied by zero)
-        if (cx(q) != 0) {
-            gmx += wq<C>(q) * (C)cx(q) * m;
-            gpx += wq<C>(q) * (C)cx(q) * ph;
-        }
-        if (cy(q) != 0) {
-            gmy += wq<C>(q) * (C)cy(q) * m;
-            gpy += wq<C>(q) * (C)cy(q) * ph;
-        }
-        lap += C(2) * wq<C>(q) * (m - m0);
-    }
-    gmx *= C(3); gmy *= C(3); lap *= C(3);
-    C phi = phi_xy(a, x, y), rho = a.k.a * phi + a.k.b;
-    C grx = a.k.a * C(3) * gpx, gry = a.k.a * C(3) * gpy;   // grad rho = a grad phi
-    C F0x = -phi * gmx - (rho - a.n.rbar) * a.n.gx;
-    C F0y = -phi * gmy - (rho - a.n.rbar) * a.n.gy;
-    C mx = C(0), my = C(0), s1 = C(0);
-#pragma unroll
-    for (int q = 0; q < 9; q++) {
-        C fq = a.f_in[q * N + k];
-        if (cx(q) != 0) mx += (C)cx(q) * fq;
-        if (cy(q) != 0) my += (C)cy(q) * fq;
-        if (q > 0) s1 += fq;
-    }
-    C den = rho - C(0.5) * a.k.a * a.n.M * lap;   // rho u = m + F/2 with F = F0 + a M lap(mu) u
-    C ux = (mx + C(0.5) * F0x) / den, uy = (my + C(0.5) * F0y) / den;
-    C uu = ux * ux + uy * uy;
-    C s0 = -wq<C>(0) * C(1.5) * uu;
-    a.ux[k] = ux; a.uy[k] = uy;
-    a.Fx[k] = F0x + a.k.a * a.n.M * lap * ux;
-    a.Fy[k] = F0y + a.k.a * a.n.M * lap * uy;
-    a.pr[k] = (C(1) / C(3)) / (C(1) - wq<C>(0)) * (s1 + C(0.5) * (ux * grx + uy * gry) + rho * s0);
-    a.grx[k] = grx; a.gry[k] = gry; a.gmx[k] = gmx; a.gmy[k] = gmy;
-}
-
-// D = div(phi u) (Model II)
-template <typename C>
-__global__ void div_kernel(NsArgs<C> a)
-{
-    int k, x, y;
-    if (!node_of(a.nx, a.ny, k, x, y)) return;
-    C s = C(0);
-#pragma unroll
-    for (int q = 1; q < 9; q++) {
-        const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
-        const int j = v.y * a.nx + v.x;
-        C ph = phi_xy(a, v.x, v.y);
-        const C t = cx(q) == 0 ? (C)cy(q) * ph * a.uy[j]
-                  : (cy(q) == 0 ? (C)cx(q) * ph * a.ux[j] : (C)cx(q) * ph * a.ux[j] + (C)cy(q) * ph * a.uy[j]);
-        s += wq<C>(q) * t;
-    }
-    a.D[k] = C(3) * s;
+    for (int q = 0; q < 9; q++) f[q] = a.f_in[q * N + k];
+    const C mx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
+    const C my = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+    const C s1 = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+    // rho u = m + F/2 with F = F0 + a M lap(mu) u, solved for u
+    const C r = rcp<C>(op_fma(C(-0.5) * a.k.a, op_mul(a.n.M, lap), rho));
+    const C ux = op_mul(op_fma(C(0.5), F0x, mx), r), uy = op_mul(op_fma(C(0.5), F0y, my), r);
+    const C uu = op_fma(ux, ux, op_mul(uy, uy));
+    // p = c_s^2/(1 - w_0) [sum_{q>0} f_q + u.grad rho / 2 + rho s_0(u)],  s_0 = -(3/2) w_0 u^2
+    const C t = op_fma(C(0.5), op_fma(ux, grx, op_mul(uy, gry)), s1);
+    a.ux[k] = ux;
+    a.uy[k] = uy;
+    a.mu[k] = mu1[c1];
+    a.pr[k] = op_mul(C(3) / C(5), op_fma(-C(1.5) * wq<C>(0), op_mul(rho, uu), t));
 }
 
 // both lattices: collide at x, push to x + c_q (bounce-back at walls)
 template <typename C>
-__global__ void collide_kernel(NsArgs<C> a)
+__global__ void __launch_bounds__(NT) collide_kernel(NsArgs<C> a)
 {
-    const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
-    int k, x, y;
-    if (!node_of(a.nx, a.ny, k, x, y)) return;
-    C gpx = C(0), gpy = C(0), gdx = C(0), gdy = C(0);
-#pragma unroll
-    for (int q = 1; q < 9; q++) {
-        const int j = nb(a.nx, a.ny, a.walls, x, y, cx(q), cy(q));
-        if (cx(q) != 0) gpx += wq<C>(q) * (C)cx(q) * a.pr[j];
-        if (cy(q) != 0) gpy += wq<C>(q) * (C)cy(q) * a.pr[j];
-        if (a.model == 2) {
-            if (cx(q) != 0) gdx += wq<C>(q) * (C)cx(q) * a.D[j];
-            if (cy(q) != 0) gdy += wq<C>(q) * (C)cy(q) * a.D[j];
+    __shared__ C s2[N2], jx2[N2], jy2[N2], mu1[N1], p1[N1], D1[N1];
+    int x0, y0;
+    tile_origin(a.nx, x0, y0);
+    const bool model2 = a.model == 2;
+    stage_phi<C>(a, x0, y0, s2, model2 ? jx2 : nullptr, jy2);
+    for (int e = threadIdx.x; e < N1; e += NT) {  // p on tile + 1
+        const int j = e / W1, i = e - j * W1;
+        const int2 v = node_at(a.nx, a.ny, a.walls, x0 - 1 + i, y0 - 1 + j);
+        p1[e] = a.pr[v.y * a.nx + v.x];
+        mu1[e] = a.mu[v.y * a.nx + v.x];
+    }
+    __syncthreads();
+    if (model2) {  // D = div(phi u) on tile + 1
+        for (int e = threadIdx.x; e < N1; e += NT) {
+            const int j = e / W1, i = e - j * W1;
+            const int c = (r1_row(a.walls, a.ny, y0, j) + 1) * W2 + i + 1;
+            D1[e] = sgx<C, W2>(jx2, c) + sgy<C, W2>(jy2, c);
         }
     }
-    gpx *= C(3); gpy *= C(3); gdx *= C(3); gdy *= C(3);
-    C phi = phi_xy(a, x, y), rho = a.k.a * phi + a.k.b;
-    C ux = a.ux[k], uy = a.uy[k], mu = a.mu[k];
-    // Cahn-Hilliard force with the flow's pressure (Eq. t0-phiu) and Eq. mark3
-    C Fx = phi / rho * (-phi * a.gmx[k] - gpx) + a.k.K * gdx;
-    C Fy = phi / rho * (-phi * a.gmy[k] - gpy) + a.k.K * gdy;
-    C FFx = a.Fx[k], FFy = a.Fy[k], pr = a.pr[k];
-    const C grx3 = a.grx[k] / C(3), gry3 = a.gry[k] / C(3);  // c_s^2 grad rho
-    C uu = ux * ux + uy * uy;
-    const C itauf = a.n.itauf, srcf = a.n.srcf;
+    __syncthreads();
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, x = x0 + tx, y = y0 + ty;
+    if (x >= a.nx || y >= a.ny) return;
+    const int c1 = (ty + 1) * W1 + tx + 1, c2 = (ty + 2) * W2 + tx + 2;
+    const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
+    const int k = y * a.nx + x;
+
+    // the node's fields
+    const C phi = s2[c2], mu = mu1[c1], pr = p1[c1], ux = a.ux[k], uy = a.uy[k];
+    const C rho = op_fma(a.k.a, phi, a.k.b);
+    const C gmx = sgx<C, W1>(mu1, c1), gmy = sgy<C, W1>(mu1, c1), lap = slap<C, W1>(mu1, c1);
+    const C gpx = sgx<C, W1>(p1, c1), gpy = sgy<C, W1>(p1, c1);
+    const C gr3x = op_mul(a.k.a * (C(1) / C(3)), sgx<C, W2>(s2, c2));  // c_s^2 grad rho
+    const C gr3y = op_mul(a.k.a * (C(1) / C(3)), sgy<C, W2>(s2, c2));
+    // Cahn-Hilliard force with the flow's pressure (Eq. t0-phiu), plus Eq. mark3 for Model II
+    const C por = op_mul(phi, rcp<C>(rho));
+    C Fx = op_mul(por, -op_fma(phi, gmx, gpx)), Fy = op_mul(por, -op_fma(phi, gmy, gpy));
+    if (model2) {
+        Fx = op_fma(a.k.K, sgx<C, W1>(D1, c1), Fx);
+        Fy = op_fma(a.k.K, sgy<C, W1>(D1, c1), Fy);
+    }
+    // the flow's force F = -phi grad mu - (rho - rbar) g + a M lap(mu) u
+    const C db = rho - a.n.rbar, aml = op_mul(a.k.a, op_mul(a.n.M, lap));
+    const C FFx = op_fma(aml, ux, -op_fma(phi, gmx, op_mul(db, a.n.gx)));
+    const C FFy = op_fma(aml, uy, -op_fma(phi, gmy, op_mul(db, a.n.gy)));
+
+    // The collision (Eq. LB for g with Eq. geq and the source of Eq. liangFi; the flow's lattice with
+    // f_eq and G as above) in pairs of opposite directions: with cu = c.u, s_q = e + o and
+    // s_opp = e - o, e = w (9/2 cu^2 - 3/2 u^2), o = 3 w cu; and G = 3 (c - u).(A + o B) for q and
+    // 3 (-c - u).(A - o B) for opp, A = (w + e) F + e c_s^2 grad rho, B = F + c_s^2 grad rho.
+    const C itau = a.k.itau, omt = a.k.omt, itauf = a.n.itauf, omtf = a.n.omtf;
+    const C src3 = C(3) * a.k.src, srcf3 = C(3) * a.n.srcf;
+    const C uu = op_fma(ux, ux, op_mul(uy, uy));
+    const C P1 = op_mul(itau, phi), Pf = op_mul(itauf, rho);
+    const C ietamu = op_mul(itau, op_mul(a.k.eta, mu)), itfp3 = op_mul(C(3) * itauf, pr);
+    const C Bx = FFx + gr3x, By = FFy + gr3y;
+    const C uB = op_fma(ux, Bx, op_mul(uy, By));
+    const C uF = op_fma(ux, FFx, op_mul(uy, FFy)), ug = op_fma(ux, gr3x, op_mul(uy, gr3y));
+
+    C pg[9], pf[9];
+    {   // q = 0: s_0 = -(3/2) w_0 u^2, S_0 = 0, G_0 = -3 (Gamma_0 u.F + s_0 u.c_s^2 grad rho)
+        const C s0 = op_mul(C(-1.5) * wq<C>(0), uu);
+        const C geq = op_fma(phi, s0, op_fma(wq<C>(0) - C(1), op_mul(a.k.eta, mu), phi));
+        pg[0] = op_fma(omt, a.g_in[k], op_mul(itau, geq));
+        const C feq = op_fma(rho, s0, op_mul(C(3) * (wq<C>(0) - C(1)), pr));
+        const C G = op_mul(C(-3), op_fma(wq<C>(0) + s0, uF, op_mul(s0, ug)));
+        pf[0] = op_fma(omtf, a.f_in[k], op_fma(itauf, feq, op_mul(a.n.srcf, G)));
+    }
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        // pairs (q, opp q): (1, 3) c = (1, 0); (2, 4) c = (0, 1); (5, 7) c = (1, 1); (6, 8) c = (-1, 1)
+        const int q = (m == 0) ? 1 : (m == 1) ? 2 : (m == 2) ? 5 : 6, o_ = opp(q);
+        const C w = wq<C>(q);
+        const C cu = (m == 0) ? ux : (m == 1) ? uy : (m == 2) ? ux + uy : uy - ux;
+        const C cF = (m == 0) ? Fx : (m == 1) ? Fy : (m == 2) ? Fx + Fy : Fy - Fx;
+        const C cB = (m == 0) ? Bx : (m == 1) ? By : (m == 2) ? Bx + By : By - Bx;
+        const C e = op_fma(op_mul(C(4.5) * w, cu), cu, op_mul(C(-1.5) * w, uu));
+        const C o = op_mul(C(3) * w, cu);
+        // Cahn-Hilliard lattice: post = (1 - 1/tau) g + g_eq/tau + (1 - 1/(2 tau)) S
+        const C Ge = op_fma(P1, e, op_mul(w, ietamu));
+        const C Go = op_fma(P1, o, op_mul(w * src3, cF));
+        pg[q] = op_fma(omt, a.g_in[q * N + k], Ge + Go);
+        pg[o_] = op_fma(omt, a.g_in[o_ * N + k], Ge - Go);
+        // the flow's lattice
+        const C we = w + e;
+        const C Ax = op_fma(we, FFx, op_mul(e, gr3x)), Ay = op_fma(we, FFy, op_mul(e, gr3y));
+        const C cA = (m == 0) ? Ax : (m == 1) ? Ay : (m == 2) ? Ax + Ay : Ay - Ax;
+        const C uA = op_fma(ux, Ax, op_mul(uy, Ay));
+        const C Fe = op_fma(srcf3, op_fma(o, cB, -uA), op_fma(Pf, e, op_mul(w, itfp3)));
+        const C Fo = op_fma(Pf, o, op_mul(srcf3, op_fma(-o, uB, cA)));
+        pf[q] = op_fma(omtf, a.f_in[q * N + k], Fe + Fo);
+        pf[o_] = op_fma(omtf, a.f_in[o_ * N + k], Fe - Fo);
+    }
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        const C cu = cx(q) == 0 ? (C)cy(q) * uy : (cy(q) == 0 ? (C)cx(q) * ux : (C)cx(q) * ux + (C)cy(q) * uy);
-        C s = wq<C>(q) * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
-        // Cahn-Hilliard lattice: Eq. geq, Eq. liangFi, Eq. LB
-        C geq = (q == 0) ? phi + (wq<C>(0) - C(1)) * a.k.eta * mu - wq<C>(0) * C(1.5) * phi * uu
-                         : wq<C>(q) * a.k.eta * mu + phi * s;
-        const C cF = cx(q) == 0 ? (C)cy(q) * Fy : (cy(q) == 0 ? (C)cx(q) * Fx : (C)cx(q) * Fx + (C)cy(q) * Fy);
-        C Sq = C(3) * wq<C>(q) * cF;
-        C gq = a.g_in[q * N + k];
-        C pg = gq - (gq - geq) * a.k.itau + a.k.src * Sq;
-        // flow lattice
-        C feq = (q == 0 ? (wq<C>(0) - C(1)) : wq<C>(q)) * C(3) * pr + rho * s;
-        C Gam = wq<C>(q) + s;
-        C G = C(3) * (((C)cx(q) - ux) * (Gam * FFx + s * grx3) + ((C)cy(q) - uy) * (Gam * FFy + s * gry3));
-        C fq = a.f_in[q * N + k];
-        C pf = fq - (fq - feq) * itauf + srcf * G;
-        int yy = y + cy(q);
+        const int yy = y + cy(q);
         if (a.walls && (yy < 0 || yy >= a.ny)) {
-            a.g_out[opp(q) * N + k] = pg;  // halfway bounce-back at a wall at rest
-            a.f_out[opp(q) * N + k] = pf;
+            a.g_out[opp(q) * N + k] = pg[q];  // halfway bounce-back at a wall at rest
+            a.f_out[opp(q) * N + k] = pf[q];
         } else {
-            const int j = nb(a.nx, a.ny, 0, x, y, cx(q), cy(q));
-            a.g_out[q * N + j] = pg;
-            a.f_out[q * N + j] = pf;
+            int xx = x + cx(q);
+            xx = xx < 0 ? xx + a.nx : (xx >= a.nx ? xx - a.nx : xx);
+            const int y2 = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
+            const int j = y2 * a.nx + xx;
+            a.g_out[q * N + j] = pg[q];
+            a.f_out[q * N + j] = pf[q];
         }
     }
 }
 
-// phi(t+1) = sum_q g_q into the padded phi array
+// phi(t+1) = sum_q g_q into the padded phi array; one thread per node
 template <typename C>
 __global__ void phi_kernel(NsArgs<C> a)
 {
     const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
-    int k, x, y;
-    if (!node_of(a.nx, a.ny, k, x, y)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int y = k / a.nx, x = k - y * a.nx;
     C s = C(0);
 #pragma unroll
     for (int q = 0; q < 9; q++) s += a.g_out[q * N + k];
@@ -229,10 +317,11 @@ template <typename C>
 __global__ void init_kernel(NsArgs<C> a, const double* phi0)
 {
     const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
-    int k, x, y;
-    if (!node_of(a.nx, a.ny, k, x, y)) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int y = k / a.nx, x = k - y * a.nx;
     auto at = [&](int dx, int dy) -> double {
-        const int2 v = nbxy(a.nx, a.ny, a.walls, x, y, dx, dy);
+        const int2 v = node_at(a.nx, a.ny, a.walls, x + dx, y + dy);
         return phi0[(long long)(a.row0 + v.y) * a.pitch + GC + v.x];
     };
     double c0 = at(0, 0), s = 0.0;
