@@ -13,9 +13,10 @@
 // Layout: plain arrays over the instance, node index y*nx + x; lambda is [9][N].  The adjoint is carried
 // in double for every storage precision (at tau = 1 all nine lambda_q are equal and dL/du is formed from
 // differences of neighbouring lambda, which float storage would round away); the tape keeps the
-// forward phi in the precision of the forward path, so the gradient is that of the path actually run.  Five one-thread-per-node
-// kernels per adjoint step (forward mu; local adjoints; mu_bar and D_bar; phi_bar and the new lambda;
-// the dL/ds reduction), written for clarity first.
+// forward phi in the precision of the forward path, so the gradient is that of the path actually run.
+// Four one-thread-per-node kernels per adjoint step (forward mu; local adjoints; mu_bar and D_bar; phi_bar
+// and the new lambda), and one deterministic sum of dL/ds at the end of the sweep.
+
 #pragma once
 #include "lbch_kernels.cuh"
 
@@ -50,25 +51,32 @@ template <typename C> __device__ __forceinline__ C d2f(C phi, C beta, C phiA, C 
                           + C(2) * (phi - phiA) * (phi - phiB));
 }
 
-// Partial derivatives of Eq. geq with respect to phi, mu and u at one node.
+// The contractions sum_q l_q d g_eq_q / d(phi, mu, u) at one node (Eq. geq), for the adjoint l of the
+// equilibria.  g_eq_q is quadratic in c_q . u, so they depend on l only through l_0 and its moments
+// m0 = sum_q w_q l_q, m1 = sum_q w_q l_q c_q and m2 = sum_q w_q l_q c_q c_q, formed from the sums and
+// differences of opposite directions.  m1 is returned too (the source term S_q is linear in c_q).
 template <typename C>
-__device__ __forceinline__ void geq_partials(C phi, C ux, C uy, C eta, C* dphi, C* dmu, C* dux, C* duy)
+__device__ __forceinline__ void geq_contract(const C* l, C phi, C ux, C uy, C eta, C& pl, C& ml, C& bx, C& by,
+                                             C& m1x, C& m1y)
 {
-    C uu = ux * ux + uy * uy;
-    dphi[0] = C(1) - wq<C>(0) * C(1.5) * uu;
-    dmu[0] = (wq<C>(0) - C(1)) * eta;
-    dux[0] = -wq<C>(0) * phi * C(3) * ux;
-    duy[0] = -wq<C>(0) * phi * C(3) * uy;
-    // (the loops are unrolled, so the lattice components are constants: terms with a zero component are
-    // left out rather than multiplied by zero, which the compiler may not fold away)
-#pragma unroll
-    for (int q = 1; q < 9; q++) {
-        const C cu = cx(q) == 0 ? (C)cy(q) * uy : (cy(q) == 0 ? (C)cx(q) * ux : (C)cx(q) * ux + (C)cy(q) * uy);
-        dphi[q] = wq<C>(q) * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
-        dmu[q] = wq<C>(q) * eta;
-        dux[q] = wq<C>(q) * phi * (cx(q) == 0 ? -(C(3) * ux) : C(3) * (C)cx(q) + C(9) * cu * (C)cx(q) - C(3) * ux);
-        duy[q] = wq<C>(q) * phi * (cy(q) == 0 ? -(C(3) * uy) : C(3) * (C)cy(q) + C(9) * cu * (C)cy(q) - C(3) * uy);
-    }
+    // opposite pairs (1, 3) c = (1, 0); (2, 4) c = (0, 1); (5, 7) c = (1, 1); (6, 8) c = (-1, 1)
+    const C E1 = l[1] + l[3], O1 = l[1] - l[3], E2 = l[2] + l[4], O2 = l[2] - l[4];
+    const C E5 = l[5] + l[7], O5 = l[5] - l[7], E6 = l[6] + l[8], O6 = l[6] - l[8];
+    const C wa = wq<C>(1), wd = wq<C>(5);
+    const C Ed = wd * (E5 + E6);
+    const C m2xx = wa * E1 + Ed, m2yy = wa * E2 + Ed, m2xy = wd * (E5 - E6);
+    const C m0 = wq<C>(0) * l[0] + (wa * (E1 + E2) + Ed);
+    m1x = wa * O1 + wd * (O5 - O6);
+    m1y = wa * O2 + wd * (O5 + O6);
+    const C vx = ux * m2xx + uy * m2xy, vy = ux * m2xy + uy * m2yy;  // sum_q w_q l_q (c_q . u) c_q
+    const C uu = ux * ux + uy * uy;
+    // d g_eq_0/d phi = 1 - (3/2) w_0 u^2;  d g_eq_q/d phi = w_q (3 c_q.u + (9/2)(c_q.u)^2 - (3/2) u^2)
+    pl = l[0] + C(3) * (ux * m1x + uy * m1y) + C(4.5) * (ux * vx + uy * vy) - C(1.5) * uu * m0;
+    // d g_eq_0/d mu = (w_0 - 1) eta;  d g_eq_q/d mu = w_q eta
+    ml = eta * (m0 - l[0]);
+    // d g_eq_q/d u = w_q phi (3 c_q + 9 (c_q.u) c_q - 3 u), q = 0 included
+    bx = phi * (C(3) * m1x + C(9) * vx - C(3) * ux * m0);
+    by = phi * (C(3) * m1y + C(9) * vy - C(3) * uy * m0);
 }
 
 // (G^T v)(x), component comp, on the periodic lattice.
@@ -117,7 +125,7 @@ __global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const TP* phi, C* 
     mu[k] = dfdphi(c, K0.beta, K0.phiA, K0.phiB) - K0.kappa * C(3) * s;
 }
 
-// local adjoints of streaming, collision, g_eq, S and F1
+// local adjoints of collision, g_eq, S and F1 (lambda itself is written by transpose2_kernel)
 template <typename C, typename TP>
 __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
                              const C* mu, const C* lam_next, C* lam, C* gmb, C* Fb, C* phib, C* mub, C* ub)
@@ -141,26 +149,23 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
     }
     gx *= C(3);
     gy *= C(3);
-    C dphi[9], dmu[9], dux[9], duy[9];
-    geq_partials(ph, ux, uy, K0.eta, dphi, dmu, dux, duy);
-    C fbx = C(0), fby = C(0), pl = C(0), ml = C(0), bx = C(0), by = C(0);
+    C pb[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) {
         // reverse streaming: post_q(x) was sent to x + c_q
-        C pb = lam_next[q * N + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
-        lam[q * N + k] = K0.omt * pb;
-        C geqb = pb * K0.itau;
-        C Sb = K0.src * pb;
-        if (cx(q) != 0) fbx += Sb * C(3) * wq<C>(q) * (C)cx(q);  // S_q = w_q c_q . F / c_s^2
-        if (cy(q) != 0) fby += Sb * C(3) * wq<C>(q) * (C)cy(q);
-        pl += geqb * dphi[q];
-        ml += geqb * dmu[q];
-        bx += geqb * dux[q];
-        by += geqb * duy[q];
+        pb[q] = lam_next[q * N + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
     }
-    C rho = K0.a * ph + K0.b;
-    C coef = ph * ph / rho;                                  // F1 = -coef grad mu
-    C dcoef = ph * (K0.a * ph + C(2) * K0.b) / (rho * rho);
+    // post_q takes g_eq_q / tau and (1 - 1/(2 tau)) S_q, S_q = w_q c_q . F / c_s^2
+    C pl, ml, bx, by, m1x, m1y;
+    geq_contract(pb, ph, ux, uy, K0.eta, pl, ml, bx, by, m1x, m1y);
+    pl *= K0.itau;
+    ml *= K0.itau;
+    bx *= K0.itau;
+    by *= K0.itau;
+    const C fbx = C(3) * K0.src * m1x, fby = C(3) * K0.src * m1y;
+    const C rho = K0.a * ph + K0.b, r = rcp<C>(rho);
+    const C coef = ph * ph * r;                                 // F1 = -coef grad mu
+    const C dcoef = ph * (K0.a * ph + C(2) * K0.b) * (r * r);  // d coef / d phi
     gmb[k] = -coef * fbx;
     gmb[N + k] = -coef * fby;
     Fb[k] = fbx;
@@ -185,10 +190,12 @@ __global__ void transpose1_kernel(const InstDev* inst, AdjArgs a, const C* gmb, 
     Db[k] = (a.model == 2) ? K0.K * (gradT(Fb, a.nx, a.ny, x, y, 0) + gradT(Fb + N, a.nx, a.ny, x, y, 1)) : C(0);
 }
 
-// phi_bar = local + f''(phi) mu_bar - kappa L^T mu_bar + u . G^T D_bar; lambda_q += phi_bar; dL/ds per node
+// phi_bar = local + f''(phi) mu_bar - kappa L^T mu_bar + u . G^T D_bar;
+// lambda_q(x) = (1 - 1/tau) lambda_next_q(x + c_q) + phi_bar(x); dL/ds per node
 template <typename C, typename TP>
 __global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
-                                  const C* phib, const C* mub, const C* Db, const C* ub, C* lam, double* ds)
+                                  const C* phib, const C* mub, const C* Db, const C* ub, const C* lam_next, C* lam,
+                                  double* ds)
 {
     const InstDev& I = inst[0];
     const Consts<C>& K0 = consts<C>(I);
@@ -210,7 +217,8 @@ __global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjAr
     // u = s u_ref: du/ds = u.  Accumulated per node over the adjoint steps and summed once at the end.
     ds[k] += (double)bx * (double)ux + (double)by * (double)uy;
 #pragma unroll
-    for (int q = 0; q < 9; q++) lam[q * N + k] += pb;           // phi = sum_q g_q
+    for (int q = 0; q < 9; q++)  // reverse streaming and collision, plus phi = sum_q g_q
+        lam[q * N + k] = K0.omt * lam_next[q * N + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)] + pb;
 }
 
 // adjoint of the initial equilibria: dL/dphi0 (two kernels: local, then the mu transpose)
@@ -227,17 +235,11 @@ __global__ void init_local_kernel(const InstDev* inst, const double* tabs, AdjAr
     C ph = (C)phi0[(long long)(I.row0 + y) * pitch0 + GC + x];
     C ux, uy;
     vel_at(I, tabs, a, x, y, T, ux, uy);
-    C dphi[9], dmu[9], dux[9], duy[9];
-    geq_partials(ph, ux, uy, K0.eta, dphi, dmu, dux, duy);
-    C pl = C(0), ml = C(0), bx = C(0), by = C(0);
+    C l[9];
 #pragma unroll
-    for (int q = 0; q < 9; q++) {
-        C l = lam[q * N + k];
-        pl += l * dphi[q];
-        ml += l * dmu[q];
-        bx += l * dux[q];
-        by += l * duy[q];
-    }
+    for (int q = 0; q < 9; q++) l[q] = lam[q * N + k];
+    C pl, ml, bx, by, m1x, m1y;
+    geq_contract(l, ph, ux, uy, K0.eta, pl, ml, bx, by, m1x, m1y);
     dphi0[k] = pl;
     mub[k] = ml;
     ds[k] += (double)bx * (double)ux + (double)by * (double)uy;

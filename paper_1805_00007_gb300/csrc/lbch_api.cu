@@ -665,7 +665,7 @@ cudaError_t adjoint_step_t(lbch_handle* h, const TP* phi_n, long long n)
     adj::transpose1_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, (const C*)v.gmb, (const C*)v.Fb, (C*)v.mub,
                                                          (C*)v.Db);
     adj::transpose2_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib,
-                                                         (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam, v.ds);
+                                                         (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam_next, lam, v.ds);
     h->adj_par ^= 1;
     return cudaGetLastError();
 }
