@@ -244,6 +244,22 @@ def run_case(case, nsteps, tile=0, form="sweep"):
             m = sim.observe(abi.LBCH_OBS_MASS)
         print(json.dumps({"case": case, "steps": nsteps, "mass": m, "kernels": "ns::fields, ns::collide, ns::phi"}))
         return
+    if parts[0] == "adj":  # adjoint steps on the n^2 single vortex (FP32 forward tape), e.g. adj_512
+        from paper_1805_00007_gb300 import workloads as wl
+        n = int(parts[1])
+        pv, fv, _ = wl.single_vortex(n=n)
+        with abi.Simulation(pv, fv, prec="f32") as sim:
+            sim.step(4)
+            tape = torch.empty((n, n), dtype=torch.float32, device="cuda")
+            abi.lb_ch_tape_phi(sim.h, tape.data_ptr())
+            seed = torch.ones((n, n), dtype=torch.float64, device="cuda")
+            abi.lb_ch_adjoint_begin(sim.h, seed.data_ptr())
+            for k in range(nsteps):
+                abi.lb_ch_adjoint_step(sim.h, tape.data_ptr(), 4 + nsteps - 1 - k)
+            torch.cuda.synchronize()
+        print(json.dumps({"case": case, "adjoint_steps": nsteps,
+                          "kernels": "adj::fwd_mu, adj::local, adj::transpose1, adj::transpose2"}))
+        return
     prec, n = parts[0], int(parts[1])
     tau = float(parts[2]) if len(parts) > 2 else 1.0
     pp, f0 = sweep_params(n, tau)
@@ -294,8 +310,9 @@ def main():
     ap.add_argument("--size-sweep", action="store_true",
                     help="time the step on 1024^2 .. 16384^2 grids (tau_g = 0.8) instead of the benchmark")
     ap.add_argument("--case", default=None,
-                    help="profiling case PREC_N[_TAU] (e.g. f32_4096, f32_4096_0.8), or rt_PREC (the coupled "
-                         "Rayleigh-Taylor grid): init and --case-steps steps of that grid only")
+                    help="profiling case PREC_N[_TAU] (e.g. f32_4096, f32_4096_0.8), rt_PREC (the coupled "
+                         "Rayleigh-Taylor grid) or adj_N (adjoint steps on the N^2 single vortex): init and "
+                         "--case-steps steps of that case only")
     ap.add_argument("--case-steps", type=int, default=8)
     ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case (-1: autotune)")
     ap.add_argument("--case-form", default="sweep", choices=["sweep", "tile", "pair"], help="kernel form for --case")
