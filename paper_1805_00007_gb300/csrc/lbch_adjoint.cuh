@@ -79,32 +79,42 @@ __device__ __forceinline__ void geq_contract(const C* l, C phi, C ux, C uy, C et
     by = phi * (C(3) * m1y + C(9) * vy - C(3) * uy * m0);
 }
 
-// (G^T v)(x), component comp, on the periodic lattice.
+// The isotropic stencils on the periodic lattice, grouped by axis and diagonal neighbours:
+// (G v)(x) = sum_k w_k c_k v(x + c_k)/c_s^2 and (L v)(x) = sum_k 2 w_k (v(x + c_k) - v(x))/c_s^2.  Their
+// transposes follow by substituting c_k -> -c_k: G^T = -G and L^T = L.
+template <typename C, typename V>
+__device__ __forceinline__ C at_nb(const V* v, int nx, int ny, int x, int y, int dx, int dy)
+{
+    return (C)v[(long long)wp(y + dy, ny) * nx + wp(x + dx, nx)];
+}
+template <typename C, typename V>
+__device__ __forceinline__ C grad_c(const V* v, int nx, int ny, int x, int y, int comp)
+{
+    auto at = [&](int dx, int dy) { return at_nb<C>(v, nx, ny, x, y, dx, dy); };
+    if (comp == 0)
+        return C(1) / C(3) * (at(1, 0) - at(-1, 0)) + C(1) / C(12) * ((at(1, 1) - at(-1, 1)) + (at(1, -1) - at(-1, -1)));
+    return C(1) / C(3) * (at(0, 1) - at(0, -1)) + C(1) / C(12) * ((at(1, 1) + at(-1, 1)) - (at(1, -1) + at(-1, -1)));
+}
+template <typename C, typename V>
+__device__ __forceinline__ C lap_c(const V* v, int nx, int ny, int x, int y)
+{
+    auto at = [&](int dx, int dy) { return at_nb<C>(v, nx, ny, x, y, dx, dy); };
+    const C c = at(0, 0);
+    const C ax = (at(1, 0) + at(-1, 0)) + (at(0, 1) + at(0, -1));
+    const C dg = (at(1, 1) + at(-1, 1)) + (at(1, -1) + at(-1, -1));
+    return C(2) / C(3) * (ax - C(4) * c) + C(1) / C(6) * (dg - C(4) * c);
+}
+// (G^T v)(x), component comp
 template <typename C>
 __device__ __forceinline__ C gradT(const C* v, int nx, int ny, int x, int y, int comp)
 {
-    C s = C(0);
-#pragma unroll
-    for (int k = 1; k < 9; k++) {
-        const int ck = comp == 0 ? cx(k) : cy(k);
-        if (ck == 0) continue;  // a zero component contributes nothing
-        int xs = wp(x - cx(k), nx), ys = wp(y - cy(k), ny);
-        s += wq<C>(k) * (C)ck * v[(long long)ys * nx + xs];
-    }
-    return C(3) * s;
+    return -grad_c<C>(v, nx, ny, x, y, comp);
 }
-
-// (L^T v)(x) on the periodic lattice.
+// (L^T v)(x)
 template <typename C>
 __device__ __forceinline__ C lapT(const C* v, int nx, int ny, int x, int y)
 {
-    C c = v[(long long)y * nx + x], s = C(0);
-#pragma unroll
-    for (int k = 1; k < 9; k++) {
-        int xs = wp(x - cx(k), nx), ys = wp(y - cy(k), ny);
-        s += C(2) * wq<C>(k) * (v[(long long)ys * nx + xs] - c);
-    }
-    return C(3) * s;
+    return lap_c<C>(v, nx, ny, x, y);
 }
 
 // forward mu = f'(phi) - kappa lap phi at step n (phi from the tape, of type TP)
@@ -116,13 +126,7 @@ __global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const TP* phi, C* 
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)a.nx * a.ny) return;
     int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
-    C c = (C)phi[k], s = C(0);
-#pragma unroll
-    for (int q = 1; q < 9; q++) {
-        int xs = wp(x + cx(q), a.nx), ys = wp(y + cy(q), a.ny);
-        s += C(2) * wq<C>(q) * ((C)phi[(long long)ys * a.nx + xs] - c);
-    }
-    mu[k] = dfdphi(c, K0.beta, K0.phiA, K0.phiB) - K0.kappa * C(3) * s;
+    mu[k] = dfdphi((C)phi[k], K0.beta, K0.phiA, K0.phiB) - K0.kappa * lap_c<C>(phi, a.nx, a.ny, x, y);
 }
 
 // local adjoints of collision, g_eq, S and F1 (lambda itself is written by transpose2_kernel)
@@ -139,16 +143,7 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
     C ph = (C)phi[k];
     C ux, uy;
     vel_at(I, tabs, a, x, y, T, ux, uy);
-    // grad mu at x
-    C gx = C(0), gy = C(0);
-#pragma unroll
-    for (int q = 1; q < 9; q++) {
-        C m = mu[(long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
-        if (cx(q) != 0) gx += wq<C>(q) * (C)cx(q) * m;
-        if (cy(q) != 0) gy += wq<C>(q) * (C)cy(q) * m;
-    }
-    gx *= C(3);
-    gy *= C(3);
+    const C gx = grad_c<C>(mu, a.nx, a.ny, x, y, 0), gy = grad_c<C>(mu, a.nx, a.ny, x, y, 1);  // grad mu at x
     C pb[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) {
