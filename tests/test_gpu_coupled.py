@@ -55,6 +55,22 @@ def test_shear_wave_periodic_matches_oracle():
     assert np.max(np.abs(phi - phi_r)) <= 1e-12 and np.max(np.abs(u[0] - ux_r)) <= 1e-12
 
 
+@pytest.mark.parametrize("nx,ny,model,tau", [(20, 37, 2, 0.8), (20, 37, 1, 1.0), (5, 6, 2, 1.0), (33, 9, 2, 1.0)])
+def test_ragged_tiles_with_walls_match_oracle(nx, ny, model, tau):
+    """Domains that do not fill the coupled kernels' 32 x 8 tiles -- narrower than a tile, ragged in x and
+    y, fewer rows than a tile -- between walls (the stencil operands at the ghost rows are the mirror
+    nodes' values), with an asymmetric field, gravity along both axes and tau_g != 1 for the
+    Cahn-Hilliard lattice."""
+    p = wl.make_params(nx=nx, ny=ny, walls=1, vel=wl.VEL_COUPLED, phiA=1.0, phiB=-1.0, rhoA=1.0, rhoB=0.4,
+                       sigma=0.01, W=3.0, M=0.02, tau=tau, model=model, nu=0.05, gx=1e-5, gy=-2e-5)
+    phi0 = np.clip(wl.random_smooth_phi(nx, ny, seed=7 + nx, amp=1.6, mean=0.0), -1, 1)
+    phi_r, ux_r, uy_r, pr_r, _, _ = oracle.ns_simulate(p, phi0, 60)
+    phi, u, pr = _run(p, phi0, 60, "f64")
+    assert np.max(np.abs(phi - phi_r)) <= 1e-12
+    assert np.max(np.abs(u[0] - ux_r)) <= 1e-12 and np.max(np.abs(u[1] - uy_r)) <= 1e-12
+    assert np.max(np.abs(pr - pr_r)) <= 1e-12
+
+
 def test_long_run_invariants():
     p, phi0 = wl.rayleigh_taylor(nx=64, ny=256, Re=1000.0)
     with abi.Simulation(p, phi0, prec="f32") as sim:
