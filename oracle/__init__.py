@@ -98,6 +98,8 @@ def lib() -> ctypes.CDLL:
         _lib.ora_force.argtypes = [P(_Params), P(_Consts), dp, dp, dp, dp, dp, dp]
         _lib.ora_init.argtypes = [P(_Params), dp, dp]
         _lib.ora_step.argtypes = [P(_Params), dp, dp, ctypes.c_long]
+        _lib.ora_set_threads.argtypes = [ctypes.c_int]
+        _lib.ora_set_threads.restype = ctypes.c_int
         _lib.ora_run.argtypes = [P(_Params), dp, ctypes.c_long, ctypes.c_long]
         _lib.ora_run.restype = ctypes.c_int
         _lib.ora_step_full.argtypes = [P(_Params), dp, dp, dp, ctypes.c_int, ctypes.c_long]
@@ -238,6 +240,12 @@ def step(cfg, g, n: int) -> np.ndarray:
     g = _f64(g); out = np.zeros_like(g)
     lib().ora_step(ctypes.byref(p), _ptr(g), _ptr(out), n)
     return out
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops from now on (n > 0; 1 = single-threaded); 0 only queries.
+    Returns the count in effect.  Results do not depend on it."""
+    return int(lib().ora_set_threads(int(n)))
 
 
 def run(cfg, g, nsteps: int, n0: int = 0) -> np.ndarray:

@@ -33,6 +33,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 9
 
@@ -382,6 +385,19 @@ void ora_step(const ora_params* p, const double* gin, double* gout, long n)
 }
 
 /* nsteps steps starting at step index n0; g holds the state on entry and on return. */
+/* Threads of the parallel loops from now on (n > 0; 1 gives the single-threaded oracle); returns the count
+ * in effect.  Results do not depend on it: every parallel loop writes disjoint nodes. */
+int ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int ora_run(const ora_params* p, double* g, long n0, long nsteps)
 {
     long N = (long)p->nx * p->ny;

@@ -465,3 +465,20 @@ def test_paper_tau_sweep_claims():
     assert all(err[star, 1] < err[t, 1] for t in taus if t != star)
     assert err[star, 2] == err[star, 1]
     assert all(err[t, 2] < 0.7 * err[t, 1] for t in taus if t != star)
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    """The oracle's parallel loops write disjoint nodes, so one thread and several give the same bits
+    (the CPU baseline is timed both ways)."""
+    p = wl.make_params(nx=37, ny=29, vel=wl.VEL_VORTEX, U0=0.02, xc=18.5, yc=14.5, half=18.5, W=3.0, M=0.01,
+                       tau=0.8, model=2, Tper=200.0)
+    g0 = oracle.init(p, wl.circle_phi(37, 29, 17.0, 15.0, 8.0, 3.0))
+    prev = oracle.set_threads(0)
+    try:
+        oracle.set_threads(1)
+        a = oracle.run(p, g0, 12)
+        oracle.set_threads(4)
+        b = oracle.run(p, g0, 12)
+    finally:
+        oracle.set_threads(prev)
+    assert np.array_equal(a, b)
