@@ -63,3 +63,51 @@ def test_flat_interface_at_rest_stays_quiet():
     phi, ux, uy, pr, _, _ = oracle.ns_simulate(p, phi0, 400)
     assert np.max(np.hypot(ux, uy)) < 1e-5
     assert np.max(np.abs(phi - phi0)) < 0.02
+
+
+def _shear_flow(nx, ny):
+    """A divergence-free initial flow: ux depends on y only, uy on x only."""
+    x = np.arange(nx)[None, :] * np.ones((ny, 1))
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    return 1e-3 * np.sin(2 * np.pi * y / ny + 0.3), 7e-4 * np.cos(2 * np.pi * x / nx + 1.1)
+
+
+@pytest.mark.parametrize("gravity", [False, True])
+def test_initial_equilibria_invert_to_the_given_flow(gravity):
+    """f = f_eq(p = 0, rho, u0) has sum_q f_q = 0 and sum_q c_q f_q = rho u0 (the moments of f_eq), and the
+    velocity carries half the force (rho u = sum_q c_q f_q + F/2): a single phase at rest in pressure
+    gives back u = u0 + F/(2 rho), and p = 0 when there is no force."""
+    nx, ny = 24, 20
+    g = (2e-6, -3e-6) if gravity else (0.0, 0.0)
+    p = _single_phase(nx, ny, nu=0.05, gx=g[0], gy=g[1])
+    ux0, uy0 = _shear_flow(nx, ny)
+    ux, uy, pr = oracle.ns_fields(p, *oracle.ns_init(p, np.ones((ny, nx)), ux0, uy0))
+    rho, rbar = p["rhoA"], 0.5 * (p["rhoA"] + p["rhoB"])   # phi = phiA everywhere
+    Fx, Fy = -(rho - rbar) * g[0], -(rho - rbar) * g[1]
+    assert np.max(np.abs(ux - (ux0 + Fx / (2 * rho)))) < 1e-16
+    assert np.max(np.abs(uy - (uy0 + Fy / (2 * rho)))) < 1e-16
+    if not gravity:
+        assert np.max(np.abs(pr)) < 1e-17
+
+
+@pytest.mark.parametrize("gravity", [False, True])
+def test_total_momentum_grows_by_the_force(gravity):
+    """On a periodic single phase the collision keeps sum_q c_q f_q and the forcing adds F (its first
+    moment), so the total momentum sum_x rho u after n steps is rho sum u0 + (n + 1/2) N F: conserved to
+    rounding without a force; with gravity to within the weak coupling through phi, whose O(u^2) changes
+    move rho (about 1e-8 of n N F here, against an error of order N F from a wrong forcing moment or a
+    missing half force)."""
+    nx, ny, n = 24, 20, 50
+    g = (2e-6, -3e-6) if gravity else (0.0, 0.0)
+    p = _single_phase(nx, ny, nu=0.05, gx=g[0], gy=g[1])
+    ux0, uy0 = _shear_flow(nx, ny)
+    _, ux, uy, _, _, _ = oracle.ns_simulate(p, np.ones((ny, nx)), n, ux0=ux0, uy0=uy0)
+    rho, rbar = p["rhoA"], 0.5 * (p["rhoA"] + p["rhoB"])
+    N = nx * ny
+    Fx, Fy = -(rho - rbar) * g[0], -(rho - rbar) * g[1]
+    ex = rho * ux.sum() - (rho * ux0.sum() + (n + 0.5) * N * Fx)
+    ey = rho * uy.sum() - (rho * uy0.sum() + (n + 0.5) * N * Fy)
+    if gravity:
+        assert abs(ex) < 1e-6 * abs(n * N * Fx) and abs(ey) < 1e-6 * abs(n * N * Fy)
+    else:
+        assert abs(ex) < 1e-15 and abs(ey) < 1e-15
