@@ -233,15 +233,19 @@ lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
  * kernel (the tile shape hook then indexes its list), the same bits once more; value 0 returns to the
  * one-step kernel.  With hook LBCH_HOOK_NO_PDL and value != 0,
  * step launches are ordinary stream-ordered launches instead of programmatic dependents of the previous
- * step (whose launch and prologue overlap that step's tail); the results are the same bits.  Not for
- * production use. */
+ * step (whose launch and prologue overlap that step's tail); the results are the same bits.  With hook
+ * LBCH_HOOK_POISON (value ignored), every device buffer the next step writes -- phi, its low part, the
+ * populations and Model III's H of the next state, or on coupled handles f, g, u, p and mu -- is filled
+ * with all bits set (NaN in every storage type), stream-ordered before the next step; a step that reads
+ * a cell it did not write first carries NaN into phi.  Not for production use. */
 enum {
     LBCH_HOOK_SKIP_FIRST_LOAD = 1,
     LBCH_HOOK_TILE_SHAPE = 2,
     LBCH_HOOK_GENERAL_PATH = 3,
     LBCH_HOOK_NO_PDL = 4,
     LBCH_HOOK_TILE_KERNEL = 5,
-    LBCH_HOOK_TWO_STEP = 6
+    LBCH_HOOK_TWO_STEP = 6,
+    LBCH_HOOK_POISON = 7
 };
 lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
 

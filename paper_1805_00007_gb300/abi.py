@@ -24,7 +24,7 @@ SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb
            "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune",
            "lb_ch_alu_peak")
 (LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL,
- LBCH_HOOK_TWO_STEP) = 1, 2, 3, 4, 5, 6
+ LBCH_HOOK_TWO_STEP, LBCH_HOOK_POISON) = 1, 2, 3, 4, 5, 6, 7
 
 
 class lbch_params(ctypes.Structure):

@@ -83,7 +83,7 @@ struct lbch_handle {
                                 // mu_bar, D_bar, u_bar (2N) in the adjoint type; then ds (N) and dL/ds, double
     size_t adj_elem = 8;
     int adj_par = 0;            // which lambda holds the current adjoint
-    // coupled Navier-Stokes state (LBCH_VEL_COUPLED): f[2], g[2] ([9][N]) and 11 node fields, one block
+    // coupled Navier-Stokes state (LBCH_VEL_COUPLED): f[2], g[2] ([9][N]) and u, p, mu ([N]), one block
     bool coupled = false;
     void* ns = nullptr;
     lbch::ns::NsConsts<double> nsd;
