@@ -76,3 +76,35 @@ def test_binding_rejects_shape_mismatch():
     p, phi0, _ = wl.translation(nx=8)
     with pytest.raises(ValueError):
         abi.lb_ch_init(p, phi0[:, :4])
+
+
+def test_every_entry_point_rejects_null_arguments_without_gpu():
+    """Each entry point checks its handle and pointers before touching a device: NULL gives LBCH_EINVAL
+    (lb_ch_free(NULL) is a no-op, lb_ch_stream(NULL) is NULL) and sets the last-error message."""
+    lib = abi.load()
+    d = ctypes.c_double()
+    i = ctypes.c_int()
+    ll = ctypes.c_longlong()
+    buf = ctypes.c_void_p(8)  # never dereferenced: the NULL handle is rejected first
+    calls = {
+        "lb_ch_observe": lambda: lib.lb_ch_observe(None, 0, abi.LBCH_OBS_MASS, ctypes.byref(d)),
+        "lb_ch_observe_all": lambda: lib.lb_ch_observe_all(None, abi.LBCH_OBS_MASS, ctypes.byref(d)),
+        "lb_ch_info": lambda: lib.lb_ch_info(None, ctypes.byref(d)),
+        "lb_ch_kernel_info": lambda: lib.lb_ch_kernel_info(None, ctypes.byref(i)),
+        "lb_ch_tune": lambda: lib.lb_ch_tune(None, 8, ctypes.byref(i), ctypes.byref(i)),
+        "lb_ch_state_bytes": lambda: lib.lb_ch_state_bytes(None, ctypes.byref(ll)),
+        "lb_ch_state_save": lambda: lib.lb_ch_state_save(None, buf),
+        "lb_ch_state_load": lambda: lib.lb_ch_state_load(None, buf),
+        "lb_ch_tape_phi": lambda: lib.lb_ch_tape_phi(None, buf),
+        "lb_ch_adjoint_begin": lambda: lib.lb_ch_adjoint_begin(None, buf),
+        "lb_ch_adjoint_step": lambda: lib.lb_ch_adjoint_step(None, buf, 0),
+        "lb_ch_adjoint_end": lambda: lib.lb_ch_adjoint_end(None, buf, ctypes.byref(d)),
+        "lb_ch_test_hook": lambda: lib.lb_ch_test_hook(None, abi.LBCH_HOOK_POISON, 1),
+        "lb_ch_field_stats_noalloc": lambda: lib.lb_ch_field_stats_noalloc(None, None, 4, 4, 4, None, None),
+        "lb_ch_alu_peak (bad precision)": lambda: lib.lb_ch_alu_peak(abi.LBCH_F16S, None, ctypes.byref(d)),
+    }
+    for name, call in calls.items():
+        assert call() == abi.LBCH_EINVAL, name
+        assert lib.lb_ch_last_error(), name
+    assert lib.lb_ch_free(None) == abi.LBCH_OK
+    assert lib.lb_ch_stream(None) is None
