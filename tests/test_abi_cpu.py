@@ -108,3 +108,14 @@ def test_every_entry_point_rejects_null_arguments_without_gpu():
         assert lib.lb_ch_last_error(), name
     assert lib.lb_ch_free(None) == abi.LBCH_OK
     assert lib.lb_ch_stream(None) is None
+
+
+def test_missing_library_fails_loudly():
+    """There is no fallback: a binding whose library is absent raises instead of computing anything."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_1805_00007_gb300 import abi\n"
+            "abi.load('/nonexistent/liblbch.so')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "CUDA library not found" in r.stderr
