@@ -42,9 +42,11 @@ typedef enum {
 
 /* Storage and arithmetic precision of the lattice state.
  *   LBCH_F64  : g and phi stored in double, double arithmetic.
- *   LBCH_F32  : shifted float storage -- g_1..g_8 and g_0 - phi stored in float, phi in double; float
- *               arithmetic on these small quantities, phi(t+1) = phi(t) + (float increment) summed in
- *               double (velocity tables built in double).  88 bytes per lattice update.
+ *   LBCH_F32  : shifted float storage -- g_1..g_8 and g_0 - phi stored in float; phi carried as a pair
+ *               of floats (a high part that feeds the stencils and a low part kept at the node), float
+ *               arithmetic on these small quantities, and phi(t+1) = phi(t) + (float increment) formed
+ *               exactly by a TwoSum of the pair (velocity tables built in double and rounded once to
+ *               float).  88 bytes per lattice update (16 when every tau_g = 1, phi alone).
  *   LBCH_F16S : shifted half storage -- phi kept in float, g_1..g_8 stored in half, g_0 not stored but
  *               recovered as phi - sum_{i>0} g_i, so sum_i g_i = phi holds exactly; float arithmetic.
  *               40 bytes per lattice update. */
@@ -201,7 +203,10 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y);
  *
  * lb_ch_state_bytes / lb_ch_state_save / lb_ch_state_load: the full state (populations, phi, step
  * index) to and from a caller buffer of lb_ch_state_bytes() bytes -- the checkpoints of a segmented
- * (square-root) reverse sweep.  Loading also restores the step index.
+ * reverse sweep.  Loading also restores the step index.  The buffer starts with a 256-byte header that
+ * records the layout it was saved for (sizes, precision, instances, model); lb_ch_state_load reads that
+ * header first and returns LBCH_EINVAL, copying nothing, for a buffer that holds no saved state or was
+ * saved by a handle of another layout, precision or model.
  * lb_ch_tape_phi: phi of the current state into dst (nx*ny values, row-major, tape type).
  * lb_ch_adjoint_begin: lambda = dL/dg_q(T) = dL/dphi(T) for every q (dL_dphiT: nx*ny values).
  * lb_ch_adjoint_step: one step backwards: lambda_n from lambda_{n+1}, given phi_n (the forward phi at
@@ -255,15 +260,15 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value);
  *
  * phi, phi0: device pointers to ny rows of nx doubles, row r starting at element r * pitch.
  * out: device pointer to 6 doubles, written asynchronously on `stream` (a cudaStream_t, NULL = legacy
- * default stream): out[0] = sum phi, out[1] = sum (phi - phi0)^2, out[2] = sum phi0^2 (so that
- * ||E_phi||_2 of Eq. err is sqrt(out[1] / out[2])), out[3] = max phi, out[4] = min phi, out[5] = number
- * of non-finite phi values (left out of the other five).  The values equal those lb_ch_observe reports
+ * default stream): out[0] = sum phi, out[1] = sum (phi - phi0)^2, out[2] = sum phi0^2 (so the relative
+ * L2 difference of phi from phi0 is sqrt(out[1] / out[2])), out[3] = max phi, out[4] = min phi, out[5] =
+ * number of non-finite phi values (left out of the other five).  The values equal those lb_ch_observe reports
  * for the same field up to the order of the floating-point sums.
  *
  * The per-block partial sums go to a file-scope device array of LBCH_NOALLOC_MAX_BLOCKS x 6 doubles
- * (48 KiB), which every GPU that loads this library holds until the process exits.  The first call on a
- * device looks up that array's device address (with the device current) and caches it; make that first
- * call before any stream capture.  Calls share the array: each overwrites what it uses, but calls that
+ * (48 KiB), which every GPU that loads this library holds until the process exits.  The first call in a
+ * CUDA context looks up that array's device address (with the context's device current) and caches it
+ * for that context (thread-safe); make that first call before any stream capture.  Calls share the array: each overwrites what it uses, but calls that
  * overlap on the GPU race.  Fields of more than LBCH_NOALLOC_MAX_NODES nodes are rejected with
  * LBCH_EINVAL; no cudaMalloc, cudaFree or allocating library routine is ever called. */
 #define LBCH_NOALLOC_MAX_BLOCKS 1024

@@ -32,6 +32,10 @@ class _Evolve(torch.autograd.Function):
     def forward(ctx, phi0, scale, params, nsteps, prec, segment):
         dev = torch.device("cuda", torch.cuda.current_device())
         s = float(scale)
+        if s == 0.0 or not math.isfinite(s):
+            # the adjoint differentiates in a multiplier of the configured velocity at 1; with the velocity
+            # scaled to zero it cannot give d/dscale back (that derivative would be divided by zero)
+            raise ValueError(f"evolve: scale must be finite and nonzero (got {s})")
         stream = torch.cuda.current_stream(dev).cuda_stream
         sim = abi.Simulation(scaled_params(params, s), phi0.detach().double().cpu().numpy(), prec=prec,
                              stream=stream)

@@ -604,12 +604,61 @@ lbch_status run_reduce(lbch_handle* h)
 size_t state_bytes(const lbch_handle* h)
 {
     const size_t cells = (size_t)h->rows * h->pitch;
-    size_t b = 256;  // header: the step index
+    size_t b = 256;  // header (StateHeader)
     b += (cells * h->nq * h->g_elem + 255) / 256 * 256;
     b += (cells * h->phi_elem + 255) / 256 * 256;
     if (h->lo[0]) b += (cells * 4 + 255) / 256 * 256;
     if (h->model3) b += (2 * cells * h->c_elem() + 255) / 256 * 256;
     return b;
+}
+
+// The first 256 bytes of a saved state: the step index and what the rest of the buffer was laid out for.
+// lb_ch_state_load compares every field with the loading handle before it copies anything, so a buffer
+// saved by a handle of another size, precision or model (or one that holds no saved state) is refused
+// instead of being read past its end.
+struct StateHeader {
+    long long n;                 // step index of the saved state
+    unsigned long long magic;    // kStateMagic
+    long long bytes;             // state_bytes() of the saving handle
+    int prec, nq, rows, pitch, n_inst, model3, lo;
+    int pad_;
+    unsigned long long layout;   // layout_hash() of the saving handle
+};
+static_assert(sizeof(StateHeader) <= 256, "the header fits the 256 bytes reserved for it");
+constexpr unsigned long long kStateMagic = 0x4c4243485354415aull;  // "LBCHSTAZ"
+
+// FNV-1a over each instance's size, origin row and boundary: equal for handles of the same layout.
+unsigned long long layout_hash(const lbch_handle* h)
+{
+    unsigned long long x = 1469598103934665603ull;
+    auto mix = [&](long long v) {
+        for (int b = 0; b < 8; b++) {
+            x ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+            x *= 1099511628211ull;
+        }
+    };
+    for (const InstDev& d : h->inst) {
+        mix(d.nx); mix(d.ny); mix(d.row0); mix(d.walls); mix(d.model);
+    }
+    return x;
+}
+
+StateHeader state_header(const lbch_handle* h, long long n)
+{
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    hd.n = n;
+    hd.magic = kStateMagic;
+    hd.bytes = (long long)state_bytes(h);
+    hd.prec = h->prec;
+    hd.nq = h->nq;
+    hd.rows = h->rows;
+    hd.pitch = h->pitch;
+    hd.n_inst = h->n_inst;
+    hd.model3 = h->model3 ? 1 : 0;
+    hd.lo = h->lo[0] ? 1 : 0;
+    hd.layout = layout_hash(h);
+    return hd;
 }
 
 struct AdjView {  // pointers into the adjoint workspace
@@ -1188,8 +1237,8 @@ lbch_status lb_ch_state_save(lbch_handle* h, void* dst)
     const int par = cur_buf(h);
     const size_t cells = (size_t)h->rows * h->pitch;
     char* p = static_cast<char*>(dst);
-    long long n = h->n;
-    CK(cudaMemcpyAsync(p, &n, sizeof n, cudaMemcpyHostToDevice, h->stream));
+    const StateHeader hd = state_header(h, h->n);
+    CK(cudaMemcpyAsync(p, &hd, sizeof hd, cudaMemcpyHostToDevice, h->stream));
     p += 256;
     size_t gb = cells * h->nq * h->g_elem, pb = cells * h->phi_elem;
     CK(cudaMemcpyAsync(p, h->g[par], gb, cudaMemcpyDeviceToDevice, h->stream));
@@ -1199,7 +1248,7 @@ lbch_status lb_ch_state_save(lbch_handle* h, void* dst)
     if (h->lo[par]) CK(cudaMemcpyAsync(p, h->lo[par], cells * 4, cudaMemcpyDeviceToDevice, h->stream));
     if (h->lo[par]) p += (cells * 4 + 255) / 256 * 256;
     if (h->model3) CK(cudaMemcpyAsync(p, h->H[par], 2 * cells * h->c_elem(), cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));  // the step index was copied from a host variable
+    CK(cudaStreamSynchronize(h->stream));  // the header was copied from a host variable
     return LBCH_OK;
 }
 
@@ -1208,9 +1257,20 @@ lbch_status lb_ch_state_load(lbch_handle* h, const void* src)
     if (!h || !src) return fail(LBCH_EINVAL, "NULL handle or buffer");
     if (h->coupled) return fail(LBCH_EINVAL, "checkpoints are for prescribed-flow handles");
     const char* p = static_cast<const char*>(src);
-    long long n = 0;
-    CK(cudaMemcpyAsync(&n, p, sizeof n, cudaMemcpyDeviceToHost, h->stream));
+    StateHeader hd;
+    CK(cudaMemcpyAsync(&hd, p, sizeof hd, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (hd.magic != kStateMagic) return fail(LBCH_EINVAL, "buffer does not hold a saved state");
+    const StateHeader mine = state_header(h, hd.n);
+    if (hd.bytes != mine.bytes || hd.prec != mine.prec || hd.nq != mine.nq || hd.rows != mine.rows ||
+        hd.pitch != mine.pitch || hd.n_inst != mine.n_inst || hd.model3 != mine.model3 || hd.lo != mine.lo ||
+        hd.layout != mine.layout)
+        return fail(LBCH_EINVAL,
+                    "saved state does not fit this handle (saved: %lld bytes, precision %d, %d instance(s), %d x %d "
+                    "stored cells; this handle: %lld bytes, precision %d, %d instance(s), %d x %d)",
+                    hd.bytes, hd.prec, hd.n_inst, hd.rows, hd.pitch, mine.bytes, mine.prec, mine.n_inst, mine.rows,
+                    mine.pitch);
+    const long long n = hd.n;
     if (n < 0) return fail(LBCH_EINVAL, "buffer does not hold a saved state");
     const int par = (int)(n & 1);
     const size_t cells = (size_t)h->rows * h->pitch;

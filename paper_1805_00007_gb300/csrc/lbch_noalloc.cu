@@ -9,17 +9,20 @@
 //
 // The partial sums are written to a static __device__ array of LBCH_NOALLOC_MAX_BLOCKS x 6 doubles
 // (48 KiB) that every GPU which loads this library holds until the process exits.  Host code never
-// uses the array's name as an address: at the first call on a device, with that device current, the
-// entry point asks the runtime for the array's device address (cudaGetSymbolAddress) and caches it per
-// device.  That first call should therefore happen before any stream capture.  All calls share the
-// array; each call overwrites the slots it uses before reading them, so nothing needs clearing, but
-// calls whose kernels overlap on the GPU (on different streams, say) race on it.
+// uses the array's name as an address: the first call in a CUDA context (with that context's device
+// current) asks the runtime for the array's device address (cudaGetSymbolAddress) and caches it for
+// that context, under a lock, so concurrent first calls from several host threads are safe and a
+// context created later (after cudaDeviceReset, say) gets its own lookup.  That first call should
+// happen before any stream capture.  All calls share the array; each call overwrites the slots it uses
+// before reading them, so nothing needs clearing, but calls whose kernels overlap on the GPU (on
+// different streams, say) race on it.
 #include "lbch.h"
 
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 namespace {
 
@@ -89,9 +92,52 @@ __global__ void __launch_bounds__(NA_NT) na_final_kernel(const double* partials,
         for (int k = 0; k < NA_NV; k++) out[k] = v[k];
 }
 
-// Device address of the partials array, looked up once per device (with that device current).
-constexpr int kMaxDevices = 64;
-double* g_partials_addr[kMaxDevices] = {nullptr};
+// Device address of the partials array in each CUDA context it has been looked up in.  The context (not
+// the device ordinal) is the key: an address belongs to the context it was taken in.
+typedef int (*CtxGetCurrentFn)(void**);  // cuCtxGetCurrent, reached through the runtime's entry-point query
+constexpr int kMaxContexts = 64;
+struct AddrEntry { void* ctx; double* addr; };
+AddrEntry g_addr[kMaxContexts];
+int g_n_addr = 0;
+std::mutex g_addr_mu;
+
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    return fn;
+}
+
+// The partials array's address in the current context (set-up on first use in that context).
+cudaError_t partials_addr(double** out)
+{
+    *out = nullptr;
+    void* ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (!get || get(&ctx) != 0 || !ctx) {
+        // no context to key on: look the address up on every call instead of caching it
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        *out = static_cast<double*>(p);
+        return e;
+    }
+    std::lock_guard<std::mutex> lock(g_addr_mu);
+    for (int i = 0; i < g_n_addr; i++)
+        if (g_addr[i].ctx == ctx) { *out = g_addr[i].addr; return cudaSuccess; }
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    if (g_n_addr < kMaxContexts) g_addr[g_n_addr++] = AddrEntry{ctx, static_cast<double*>(p)};
+    *out = static_cast<double*>(p);
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -124,27 +170,24 @@ lbch_status lb_ch_field_stats_noalloc(const double* phi, const double* phi0, int
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return na_fail(LBCH_ECUDA, "no usable current device");
-    if (!g_partials_addr[dev]) {
-        // set-up on this device: the device address of the static partials array
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess || !p) {
-            snprintf(msg, sizeof msg, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            cudaGetLastError();
-            return na_fail(LBCH_ECUDA, msg);
-        }
-        g_partials_addr[dev] = static_cast<double*>(p);
+    if (e != cudaSuccess) return na_fail(LBCH_ECUDA, "no usable current device");
+    double* partials = nullptr;
+    e = partials_addr(&partials);  // set-up in this context: the device address of the static array
+    if (e != cudaSuccess || !partials) {
+        snprintf(msg, sizeof msg, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        return na_fail(LBCH_ECUDA, msg);
     }
+    cudaGetLastError();  // a launch error reported below is then this call's, not an earlier one left pending
     long long N = (long long)nx * ny;
     int nblocks = (int)((N + NA_NT * 8 - 1) / (NA_NT * 8));
     if (nblocks > LBCH_NOALLOC_MAX_BLOCKS) nblocks = LBCH_NOALLOC_MAX_BLOCKS;
     if (nblocks < 1) nblocks = 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    na_partials_kernel<<<nblocks, NA_NT, 0, s>>>(phi, phi0, nx, ny, pitch, g_partials_addr[dev]);
+    na_partials_kernel<<<nblocks, NA_NT, 0, s>>>(phi, phi0, nx, ny, pitch, partials);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
-        na_final_kernel<<<1, NA_NT, 0, s>>>(g_partials_addr[dev], nblocks, out);
+        na_final_kernel<<<1, NA_NT, 0, s>>>(partials, nblocks, out);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

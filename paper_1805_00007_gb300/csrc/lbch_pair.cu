@@ -27,6 +27,7 @@ cudaError_t launch_pair_v(lbch_handle* h, int parity)
     a.t_off = h->t_off;
     a.t_adv = h->t_adv;
     a.need_time = h->need_time;
+    a.debug_skip = h->debug_skip;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ps.grid);
     cfg.blockDim = dim3(NT);

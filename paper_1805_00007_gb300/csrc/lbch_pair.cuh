@@ -36,6 +36,7 @@ struct PairArgs {
     int t_off;              // the launch's first step is ctl->time + t_off, its second one step later
     int t_adv;              // when nonzero, the launch's last CTA advances ctl->time by t_adv
     int need_time;          // some instance's flow depends on the step index
+    int debug_skip;         // test hook: CTA 0 never issues its first table copy (its bounded wait runs out)
 };
 
 // Shared-memory regions, each centred on the tile: region k spans the tile plus k nodes on every side.
@@ -331,20 +332,29 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
     __shared__ C s_T[2];
     __shared__ InstDev s_I;
     __shared__ __align__(8) uint64_t s_tbar;  // completion of the table copy
+    __shared__ int s_abort;                    // a table wait ran out: the CTA stops after it
     const int tid = threadIdx.x;
     const int stride = gridDim.x;
     const bool any = (int)blockIdx.x < a.total_tiles;
     PairLoad<C, P, TX, TY, NT> ld;
     long long n = 0;
     int tuse = 0;  // table copies waited for so far (the mbarrier's phase)
-    auto wait_tables = [&]() {  // thread 0
-        if (!mbar_wait_bounded(&s_tbar, (unsigned)(tuse & 1), 1u << 22)) atomicOr(&a.ctl->err, 1u);
+    // thread 0: wait (bounded) for the tile's table copy.  When the wait runs out the kernel records the
+    // error, lets the copy land if it was issued (bounded again) so that no copy into this CTA's shared
+    // memory outlives it, and tells the CTA to stop; the step counter is still kept consistent below.
+    auto wait_tables = [&]() {
+        if (!mbar_wait_bounded(&s_tbar, (unsigned)(tuse & 1), 1u << 22)) {
+            atomicOr(&a.ctl->err, 1u);
+            mbar_wait_bounded(&s_tbar, (unsigned)(tuse & 1), 1u << 22);
+            s_abort = 1;
+        }
         tuse++;
     };
+    if (tid == 0) s_abort = 0;
     if (tid == 0 && any) {
         mbar_init(&s_tbar, 1);
         fence_mbar_init();
-        pair_fetch_tables<C, P, TX, TY>(S, a.ttabs, blockIdx.x, &s_tbar);
+        if (!(a.debug_skip && blockIdx.x == 0)) pair_fetch_tables<C, P, TX, TY>(S, a.ttabs, blockIdx.x, &s_tbar);
     }
 
     if constexpr (SINGLE) {
@@ -364,7 +374,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
         }
         __syncthreads();
         n = s_time + a.t_off;
-        for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
+        for (int t = blockIdx.x; t < a.total_tiles && !s_abort; t += stride) {
             if (t != (int)blockIdx.x) {
                 __syncthreads();  // the previous tile's shared data are read no more
                 if (tid == 0) pair_fetch_tables<C, P, TX, TY>(S, a.ttabs, t, &s_tbar);
@@ -374,6 +384,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
                 ld.load(S, a.phi_in + rb, a.lo_in + rb);
                 if (tid == 0) wait_tables();
                 __syncthreads();
+                if (s_abort) break;
             }
             pair_steps<C, P, TX, TY, NT>(S, I, s_T[0], s_T[1], x0, y0, a.pitch, rb, a.phi_out, a.lo_out);
         }
@@ -410,7 +421,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
         }
         __syncthreads();
         n = s_time + a.t_off;
-        for (int t = blockIdx.x; t < a.total_tiles; t += stride) {
+        for (int t = blockIdx.x; t < a.total_tiles && !s_abort; t += stride) {
             if (t != (int)blockIdx.x) {
                 __syncthreads();  // the previous tile's shared data are read no more
                 if (tid == 0) {
@@ -426,6 +437,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 2) ch_pair_kernel(const __
                 ld.load(S, a.phi_in + rb, a.lo_in + rb);
                 if (tid == 0) wait_tables();
                 __syncthreads();
+                if (s_abort) break;
             }
             pair_steps<C, P, TX, TY, NT>(S, s_I, s_T[0], s_T[1], s_x0, s_y0, a.pitch, rb, a.phi_out, a.lo_out);
         }

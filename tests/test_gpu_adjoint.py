@@ -79,6 +79,39 @@ def test_state_save_load_round_trip():
             assert np.array_equal(a, sim.phi())
 
 
+def test_state_load_rejects_a_buffer_of_another_layout():
+    """A saved state carries the layout it was saved for; loading it into a handle of another size,
+    precision or model, or loading a buffer that holds no saved state, is refused before anything is
+    copied, and the handle's own state is left as it was."""
+    dev = torch.device("cuda")
+    p_small, f_small, _ = wl.zalesak(n=32)
+    p_big, f_big, _ = wl.zalesak(n=64)
+    with abi.Simulation(p_small, f_small, prec="f32") as small:
+        small.step(3)
+        buf = torch.empty(abi.lb_ch_state_bytes(small.h), dtype=torch.uint8, device=dev)
+        abi.lb_ch_state_save(small.h, buf.data_ptr())
+    for prec, params, field in (("f32", p_big, f_big), ("f64", p_small, f_small), ("f16s", p_small, f_small)):
+        with abi.Simulation(params, field, prec=prec) as sim:
+            sim.step(5)
+            before = sim.phi()
+            with pytest.raises(abi.LbchError) as ei:
+                abi.lb_ch_state_load(sim.h, buf.data_ptr())
+            assert ei.value.status == abi.LBCH_EINVAL and "does not fit" in str(ei.value)
+            assert sim.observe(abi.LBCH_OBS_STEP) == 5 and np.array_equal(before, sim.phi())
+    q = wl.make_params(nx=32, ny=32, model=1, vel=wl.VEL_UNIFORM, ux0=0.01, uy0=0.0, M=0.02)
+    with abi.Simulation(q, f_small, prec="f32") as sim:  # the same layout but Model I: the hash tells
+        with pytest.raises(abi.LbchError) as ei:
+            abi.lb_ch_state_load(sim.h, buf.data_ptr())
+        assert ei.value.status == abi.LBCH_EINVAL
+    with abi.Simulation(p_small, f_small, prec="f32") as sim:
+        zeros = torch.zeros_like(buf)
+        with pytest.raises(abi.LbchError) as ei:
+            abi.lb_ch_state_load(sim.h, zeros.data_ptr())
+        assert ei.value.status == abi.LBCH_EINVAL and "does not hold a saved state" in str(ei.value)
+        abi.lb_ch_state_load(sim.h, buf.data_ptr())  # the matching handle still takes it
+        assert sim.observe(abi.LBCH_OBS_STEP) == 3
+
+
 def test_single_vortex_adjoint_vs_finite_differences():
     """The 512 x 512 single-vortex workload (R = 76.8 at (256, 384), U0 = 0.04, Pe = 1000) for its full
     reversal period T = 8000 steps: the FP32 adjoint (checkpointed) against central differences of the

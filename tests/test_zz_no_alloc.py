@@ -82,3 +82,27 @@ def test_noalloc_rejects_bad_arguments():
             abi.lb_ch_field_stats_noalloc(*args, out.data_ptr(), 0)
         assert ei.value.status == abi.LBCH_EINVAL
         assert words in str(ei.value)
+
+
+def test_noalloc_counts_non_finite_values_and_leaves_them_out():
+    p, phi0, _ = wl.zalesak(n=64)
+    phi, _ = _reference(p, phi0, 40)
+    bad = phi.copy()
+    rng = np.random.default_rng(7)
+    idx = rng.choice(bad.size, size=13, replace=False)
+    vals = [np.nan, np.inf, -np.inf]
+    for k, i in enumerate(idx):
+        bad.flat[i] = vals[k % 3]
+    o = _noalloc(bad, phi0, pad=8)
+    keep = np.isfinite(bad)
+    assert o[5] == 13.0
+    tol = 1e-12
+    assert abs(o[0] - bad[keep].sum()) <= tol * abs(bad[keep].sum())
+    d = (bad - phi0)[keep]
+    assert abs(o[1] - float((d * d).sum())) <= tol * float((d * d).sum())
+    assert abs(o[2] - float((phi0[keep] ** 2).sum())) <= tol * float((phi0[keep] ** 2).sum())
+    assert o[3] == bad[keep].max() and o[4] == bad[keep].min()
+    # the next call on a clean field is unaffected by the shared scratch of this one
+    _check(_noalloc(phi, phi0), {abi.LBCH_OBS_MASS: float(phi.sum()),
+                                 abi.LBCH_OBS_ERR_L2: float(np.sqrt(((phi - phi0) ** 2).sum() / (phi0 ** 2).sum())),
+                                 abi.LBCH_OBS_MAX: float(phi.max()), abi.LBCH_OBS_MIN: float(phi.min())})
