@@ -5,10 +5,14 @@ package to check and time the CUDA library; the product path never imports it.  
 in ``lbch_oracle.c`` (plain C, double precision, no fast-math, no FMA contraction); this module only
 compiles it with gcc and marshals numpy arrays through ctypes.
 
-Parity status of each oracle function (what pins it is in ``tests/test_oracle_pins.py``):
+Parity status of each oracle function (what pins it is in ``tests/test_oracle_pins.py`` and
+``tests/test_oracle_chapman_enskog.py``):
   geq, source, dfdphi, grad, lap, div, mu, force, init, step, observe -- pinned
   (moment identities, exact stencil symbols, polynomial exactness, a linear-stability amplification
-  matrix built independently, conservation, stationarity, special values of K).
+  matrix built independently, conservation, stationarity, special values of K, the co-moving uniform
+  state between moving walls for the bounce-back term, and the Chapman-Enskog expansion of the update:
+  the dispersion of small waves matches the exact series whose terms are the Cahn-Hilliard equation and
+  the paper's third-order error R1 + R2).
   The long-time benchmark behaviour (paper Sec. III) is pinned only softly (printed max/min of phi);
   the paper's error curves are figures that are not available, so those are "parity unpinned".
 """

@@ -206,3 +206,12 @@ def random_smooth_phi(nx, ny, seed, amp=0.3, mean=0.5, modes=4) -> np.ndarray:
         ph = rng.uniform(0, 2 * np.pi)
         f += amp / modes * np.cos(2 * np.pi * (kx * x / nx + ky * y / ny) + ph)
     return f
+
+
+def moving_wall_case(nx=45, ny=37, shear=2e-3, tau=0.8, model=2, seed=SEED_BASE + 11):
+    """A wall-bounded shear flow at tau_g != 1 with a field that varies along the walls: the walls move at
+    -/+ shear * ny / 2, and the bounced populations carry the moving-wall term into phi one step later.
+    Returns (params, phi0)."""
+    p = make_params(nx=nx, ny=ny, walls=1, vel=VEL_SHEAR, shear=shear, model=model, tau=tau, M=0.02,
+                    sigma=0.02, W=3.0)
+    return p, random_smooth_phi(nx, ny, seed=seed)

@@ -359,3 +359,25 @@ def test_paper_reversing_flows_match_oracle(setup, L0):
         with abi.Simulation(p, phi0, prec=prec) as sim:
             sim.step(N)
             assert _maxdiff(sim.phi(), ref) <= tol, prec
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5), ("f16s", 2e-3)])
+@pytest.mark.parametrize("form", ["sweep", "tile"])
+def test_moving_walls_match_oracle(prec, tol, form):
+    """The moving-wall bounce-back (reading R7, pinned on the oracle by the co-moving uniform state) on the
+    wall-driven shear case at tau_g = 0.8, where the bounced populations reach phi a step later: every
+    kernel form through the C ABI against the oracle.  A wrong sign, factor or a wall at rest moves phi by
+    more than 100 times the FP32 tolerance here (tests/test_oracle_pins.py plants each in the oracle)."""
+    p, phi0 = wl.moving_wall_case()
+    ref, _ = oracle.simulate(p, phi0, 60)
+    with abi.Simulation(p, phi0, prec=prec) as sim:
+        abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, 1 if form == "tile" else 0)
+        assert sim.kernel()["form"] == ("tile" if form == "tile" else "sweep")
+        sim.step(60)
+        assert _maxdiff(sim.phi(), ref) <= tol
+    # the co-moving uniform state stays put on the GPU as well
+    q = wl.make_params(nx=40, ny=21, walls=1, vel=wl.VEL_UNIFORM, ux0=0.05, uy0=0.0, model=2, tau=0.8, M=0.01)
+    with abi.Simulation(q, np.full((21, 40), 0.37), prec=prec) as sim:
+        abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, 1 if form == "tile" else 0)
+        sim.step(70)
+        assert _maxdiff(sim.phi(), np.full((21, 40), 0.37)) <= (1e-14 if prec == "f64" else 1e-6)

@@ -278,6 +278,75 @@ def test_uniform_state_is_fixed_point():
     np.testing.assert_allclose(phi, 0.37, atol=1e-15)
 
 
+# ----------------------------------------------------------------------------- moving walls (reading R7)
+
+CO_MOVING = [(0.06, 0.0), (0.05, 0.03)]
+
+
+def _co_moving(u):
+    p = wl.make_params(nx=7, ny=6, walls=1, vel=wl.VEL_UNIFORM, ux0=u[0], uy0=u[1], model=2, tau=0.8, M=0.01)
+    return p, np.full((6, 7), 0.37)
+
+
+@pytest.mark.parametrize("u", CO_MOVING)
+def test_walls_moving_with_a_uniform_flow_keep_the_uniform_state(u):
+    """Halfway bounce-back with the moving-wall term: a uniform phi in a uniform flow between walls that
+    move with it is an equilibrium of the step -- all nine populations at every node, the rows next to the
+    walls included, come back unchanged.  At a wall row the population leaving along c_q returns along
+    c_o = -c_q with 2 w_o phi (c_o . u_w)/c_s^2 added, and the equilibria of Eq. geq for opposite
+    directions differ by exactly 2 w_o phi (c_o . u)/c_s^2; a wrong sign or factor would break it."""
+    p, phi = _co_moving(u)
+    g0 = oracle.init(p, phi)
+    g1 = oracle.step(p, g0, 0)
+    np.testing.assert_allclose(g1, g0, rtol=0, atol=1e-15)
+    # the moving wall matters here: the bounced populations are far from their values for a wall at rest
+    cxu = 2 * WT[5] * 0.37 * (C[5] @ np.array(u)) / CS2
+    assert abs(cxu) > 1e-3
+
+
+def _mutant_run(tmp_path, new_text):
+    """Compile a copy of the oracle with its moving-wall line of the step changed (a planted mistake) and
+    return a runner for it (the same entry point as oracle.run)."""
+    import ctypes
+    import subprocess
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "lbch_oracle.c")).read()
+    old = "gout[o * N + x] = post + 2.0 * WQ[o]"
+    assert src.count(old) == 2
+    mutated = src.replace(old, new_text, 1)  # the step of Models I and II
+    c, so = tmp_path / "mutant.c", tmp_path / "mutant.so"
+    c.write_text(mutated)
+    subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99", str(c),
+                    "-o", str(so), "-lm"], check=True)
+    lib = ctypes.CDLL(str(so))
+    dp = ctypes.POINTER(ctypes.c_double)
+
+    def run(cfg, g, nsteps):
+        par = oracle.params(cfg)
+        g = np.ascontiguousarray(g, dtype=np.float64).copy()
+        lib.ora_run.argtypes = [ctypes.POINTER(type(par)), dp, ctypes.c_long, ctypes.c_long]
+        assert lib.ora_run(ctypes.byref(par), g.ctypes.data_as(dp), 0, nsteps) == 0
+        return g
+    return run
+
+
+@pytest.mark.parametrize("mistake", ["gout[o * N + x] = post - 2.0 * WQ[o]",   # wrong sign
+                                     "gout[o * N + x] = post + 1.0 * WQ[o]",   # wrong factor
+                                     "gout[o * N + x] = post + 0.0 * WQ[o]"])  # wall at rest
+def test_a_planted_wall_mistake_is_caught(tmp_path, mistake):
+    """The pins above catch a wrong moving-wall term, and so does the walled GPU parity case: with the
+    mistake planted in a copy of the oracle, the co-moving state is no longer kept, and phi of the wall-driven
+    shear case at tau_g = 0.8 (workloads.moving_wall_case) moves by more than 100 times the FP32 tolerance."""
+    run = _mutant_run(tmp_path, mistake)
+    for u in CO_MOVING:
+        p, phi = _co_moving(u)
+        g0 = oracle.init(p, phi)
+        assert np.max(np.abs(run(p, g0, 1) - g0)) > 1e-4
+    p, phi0 = wl.moving_wall_case()
+    ref, _ = oracle.simulate(p, phi0, 60)
+    bad = oracle.phi_of(run(p, oracle.init(p, phi0), 60))
+    assert np.max(np.abs(bad - ref)) > 100 * 1e-5
+
+
 def test_planar_interface_is_nearly_stationary():
     """Eq. analytical is the continuum equilibrium: at rest the discrete profile moves only by O(dx^2/W^2)
     and the chemical potential it carries stays small."""
