@@ -132,6 +132,39 @@ typedef struct lbch_handle lbch_handle;
 lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0, int prec,
                        void* stream, lbch_handle** out);
 
+/* ---- domain decomposition: one periodic grid split into slabs of rows over several handles ----
+ *
+ * Eq. LB is explicit and local: phi(t+1) at a node depends on the state at time t only within three nodes
+ * (mu and D = div(phi u) one node out, their gradients and the collision one further, the pull of the
+ * streaming one more; Eqs. mu, mark3, LB with the isotropic stencils of Sec. III).  A grid that is
+ * periodic in y can therefore be split into slabs of consecutive rows, each stepped by its own handle (on
+ * its own GPU, or several on one), if before every step each slab receives from its two neighbours the
+ * three rows of phi next to it and the one row of populations that streams across the cut.  The result is
+ * the whole-grid result, bit for bit.
+ *
+ * lb_ch_init_slab: a handle for global rows y0 .. y0 + ny_local - 1 of the problem `global` (walls = 0,
+ * a prescribed flow, Model I or II; ny_local >= 4).  phi0_halo (host) holds ny_local + 6 rows of global->nx
+ * doubles: global rows y0 - 3 .. y0 + ny_local + 2, taken periodically, so that the initial equilibria at
+ * the slab's edge rows see their true neighbours.  The velocity field is evaluated at global coordinates.
+ * A slab handle steps with the row sweep or the tile kernel (not the two-step kernel), advances at most one
+ * step per lb_ch_step call (LBCH_EINVAL otherwise), and must receive both halos before every step,
+ * including the first.  Observables are the slab's own (sum them over the slabs for global ones).
+ * lb_ch_halo_bytes: size of one side's halo (the same for every slab of a grid in one precision).
+ * lb_ch_halo_export: the slab's own edge rows into dst (device, lb_ch_halo_bytes bytes): side 0 = its
+ *   lowest rows (for the slab below), side 1 = its highest rows (for the slab above).
+ * lb_ch_halo_import: the neighbour's export into the slab's ghost rows: side 0 = the rows below it (the
+ *   lower neighbour's side-1 export), side 1 = the rows above it (the upper neighbour's side-0 export).
+ * Both are stream-ordered on the handle's stream and apply to the current state; the caller moves the
+ * buffers between slabs (a device-to-device copy, a peer copy or an NCCL send/recv into each GPU's own
+ * memory) and orders the streams.  Halo layout: 3 rows of phi (the high part in LBCH_F32), 3 rows of phi's
+ * low part (LBCH_F32 only), one row of the stored populations; each row is one stored row of the handle,
+ * ghost columns included, so slabs of one grid must share nx and the precision. */
+lbch_status lb_ch_init_slab(const lbch_params* global, int y0, int ny_local, const double* phi0_halo, int prec,
+                            void* stream, lbch_handle** out);
+lbch_status lb_ch_halo_bytes(lbch_handle* h, long long* bytes);
+lbch_status lb_ch_halo_export(lbch_handle* h, int side, void* dst);
+lbch_status lb_ch_halo_import(lbch_handle* h, int side, const void* src);
+
 /* Advance every instance by nsteps >= 0 steps of Eq. LB.  Asynchronous on the handle's stream: the work
  * is enqueued (in CUDA graphs of 64 steps when possible) and the call returns.  When every instance has
  * tau_g = 1 (the paper's default), Eq. LB reduces to g* = g_eq + S/2 and the populations drop out of the

@@ -358,3 +358,24 @@ def ns_simulate(cfg, phi0, nsteps: int, ux0=None, uy0=None):
         f, g = fo, go
     ux, uy, pr = ns_fields(cfg, f, g)
     return phi_of(g), ux, uy, pr, f, g
+
+
+def _simulate_one(args):
+    cfg, phi0, nsteps = args
+    set_threads(1)
+    return simulate(cfg, phi0, nsteps)[0]
+
+
+def simulate_many(cases, nsteps: int, processes: int | None = None) -> list:
+    """phi after nsteps steps for each (cfg, phi0) of `cases` -- the same runs as simulate(), one
+    single-threaded oracle per worker process, the workers started with `spawn` (never forked from a
+    process that may hold a CUDA context).  Largest cases first, results in the order of `cases`."""
+    import multiprocessing as mp
+    order = sorted(range(len(cases)), key=lambda i: -int(cases[i][0]["nx"]) * int(cases[i][0]["ny"]))
+    n = processes or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(processes=min(n, len(cases))) as pool:
+        res = pool.map(_simulate_one, [(cases[i][0], cases[i][1], nsteps) for i in order], chunksize=1)
+    out = [None] * len(cases)
+    for i, r in zip(order, res):
+        out[i] = r
+    return out

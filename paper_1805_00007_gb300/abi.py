@@ -22,7 +22,7 @@ SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb
            "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_kernel_info", "lb_ch_stream", "lb_ch_test_hook",
            "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
            "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune",
-           "lb_ch_alu_peak")
+           "lb_ch_alu_peak", "lb_ch_init_slab", "lb_ch_halo_bytes", "lb_ch_halo_export", "lb_ch_halo_import")
 (LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL,
  LBCH_HOOK_TWO_STEP, LBCH_HOOK_POISON) = 1, 2, 3, 4, 5, 6, 7
 
@@ -87,11 +87,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_adjoint_end.argtypes = [vp, vp, dp]
     lib.lb_ch_tune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]
     lib.lb_ch_alu_peak.argtypes = [ctypes.c_int, vp, dp]
+    lib.lb_ch_init_slab.argtypes = [P(lbch_params), ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, vp, P(vp)]
+    lib.lb_ch_halo_bytes.argtypes = [vp, P(ctypes.c_longlong)]
+    lib.lb_ch_halo_export.argtypes = [vp, ctypes.c_int, vp]
+    lib.lb_ch_halo_import.argtypes = [vp, ctypes.c_int, vp]
     for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
                  "lb_ch_kernel_info",
                  "lb_ch_test_hook", "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save",
                  "lb_ch_state_load", "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step",
-                 "lb_ch_adjoint_end", "lb_ch_tune", "lb_ch_alu_peak"):
+                 "lb_ch_adjoint_end", "lb_ch_tune", "lb_ch_alu_peak", "lb_ch_init_slab", "lb_ch_halo_bytes",
+                 "lb_ch_halo_export", "lb_ch_halo_import"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -132,6 +137,34 @@ def lb_ch_init(params, phi0, prec=LBCH_F64, stream=None):
     _check(lib.lb_ch_init(arr, n, _dptr(flat), int(prec), ctypes.c_void_p(stream or 0), ctypes.byref(h)),
            "lb_ch_init")
     return h
+
+
+def lb_ch_init_slab(params: dict, y0: int, ny_local: int, phi0_halo, prec=LBCH_F64, stream=None):
+    """A handle for global rows y0 .. y0 + ny_local - 1 of the periodic problem `params`; phi0_halo holds
+    ny_local + 6 rows (global rows y0 - 3 .. y0 + ny_local + 2, wrapped) of nx values."""
+    lib = load()
+    f = np.ascontiguousarray(phi0_halo, dtype=np.float64)
+    if f.shape != (int(ny_local) + 6, params["nx"]):
+        raise ValueError(f"phi0_halo of shape {f.shape} is not (ny_local + 6, nx) = ({ny_local + 6}, {params['nx']})")
+    h = ctypes.c_void_p()
+    p = make_params(params)
+    _check(lib.lb_ch_init_slab(ctypes.byref(p), int(y0), int(ny_local), _dptr(f), int(prec),
+                               ctypes.c_void_p(stream or 0), ctypes.byref(h)), "lb_ch_init_slab")
+    return h
+
+
+def lb_ch_halo_bytes(h) -> int:
+    out = ctypes.c_longlong(0)
+    _check(load().lb_ch_halo_bytes(h, ctypes.byref(out)), "lb_ch_halo_bytes")
+    return out.value
+
+
+def lb_ch_halo_export(h, side: int, dst_ptr: int):
+    _check(load().lb_ch_halo_export(h, int(side), ctypes.c_void_p(dst_ptr)), "lb_ch_halo_export")
+
+
+def lb_ch_halo_import(h, side: int, src_ptr: int):
+    _check(load().lb_ch_halo_import(h, int(side), ctypes.c_void_p(src_ptr)), "lb_ch_halo_import")
 
 
 def lb_ch_step(h, nsteps: int):

@@ -384,7 +384,13 @@ void derive(const lbch_params& p, InstDev& d)
 // indexed like the stored arrays: X1, X2 by stored column (domain x = column - GC, periodic images in
 // the ghost columns), Y1, Y2 by row of the instance's stored band (domain y = row - GR; periodic or
 // mirror images in the ghost rows, matching the stored phi), then Y1, Y2 at the walls y = -1/2, ny - 1/2.
-void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<double>& t)
+// A slab of a larger periodic grid (lb_ch_init_slab): the handle holds global rows y0 .. y0 + ny - 1.
+struct SlabSpec {
+    int y0;   // first global row of the slab
+    int ny;   // rows of the slab
+};
+
+void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<double>& t, const SlabSpec* slab = nullptr)
 {
     const double pi = 3.14159265358979323846;
     const double Lx = (double)p.nx, Ly = (double)p.ny;
@@ -422,10 +428,13 @@ void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<doub
         if (x < -GC || x >= p.nx + GC) continue;
         X((double)(((x % p.nx) + p.nx) % p.nx), X1[col], X2[col]);
     }
+    const int ny_rows = slab ? slab->ny : p.ny;  // rows of the stored band (p.ny is the global grid's)
     for (int k = 0; k < ylen; k++) {
         int y = k - GR;
-        if (y < -GR || y >= p.ny + GR) continue;
-        int yy = p.walls ? (y < 0 ? -1 - y : (y >= p.ny ? 2 * p.ny - 1 - y : y)) : ((y % p.ny) + p.ny) % p.ny;
+        if (y < -GR || y >= ny_rows + GR) continue;
+        int yy;
+        if (slab) yy = (((slab->y0 + y) % p.ny) + p.ny) % p.ny;  // the global row a slab's row stands for
+        else yy = p.walls ? (y < 0 ? -1 - y : (y >= p.ny ? 2 * p.ny - 1 - y : y)) : ((y % p.ny) + p.ny) % p.ny;
         Y((double)yy, Y1[k], Y2[k]);
     }
     Y(-0.5, W[0], W[2]);
@@ -661,6 +670,41 @@ StateHeader state_header(const lbch_handle* h, long long n)
     return hd;
 }
 
+// A slab's halo on one side, as lb_ch_halo_export writes it: GR rows of phi (the high part on the float
+// path), GR rows of phi's low part (LBCH_F32), then one row of the stored populations (nq planes), each
+// row `pitch` elements wide with its ghost columns.
+size_t halo_bytes(const lbch_handle* h)
+{
+    size_t b = (size_t)GR * h->pitch * h->phi_elem;
+    if (h->lo[0]) b += (size_t)GR * h->pitch * sizeof(float);
+    b += (size_t)h->nq * h->pitch * h->g_elem;
+    return b;
+}
+
+// Copy a halo between the buffer `buf` and the current state: phi and its low part on the GR stored rows
+// from `phi_row`, the populations of stored row `g_row`; out = true copies state -> buf.  Stream-ordered.
+lbch_status halo_copy(lbch_handle* h, void* buf, int phi_row, int g_row, bool out)
+{
+    const int par = cur_buf(h);
+    char* b = static_cast<char*>(buf);
+    auto cp = [&](void* state, size_t off, size_t n) {
+        char* sp = static_cast<char*>(state) + off;
+        return out ? cudaMemcpyAsync(b, sp, n, cudaMemcpyDeviceToDevice, h->stream)
+                   : cudaMemcpyAsync(sp, b, n, cudaMemcpyDeviceToDevice, h->stream);
+    };
+    const size_t np = (size_t)GR * h->pitch * h->phi_elem;
+    CK(cp(h->phi[par], (size_t)phi_row * h->pitch * h->phi_elem, np));
+    b += np;
+    if (h->lo[par]) {
+        const size_t nl = (size_t)GR * h->pitch * sizeof(float);
+        CK(cp(h->lo[par], (size_t)phi_row * h->pitch * sizeof(float), nl));
+        b += nl;
+    }
+    const size_t ng = (size_t)h->nq * h->pitch * h->g_elem;
+    CK(cp(h->g[par], (size_t)g_row * h->nq * h->pitch * h->g_elem, ng));
+    return LBCH_OK;
+}
+
 struct AdjView {  // pointers into the adjoint workspace
     void* lam[2];
     void *mu, *gmb, *Fb, *phib, *mub, *Db, *ub;
@@ -745,14 +789,12 @@ cudaError_t adjoint_end_t(lbch_handle* h, C* dphi0)
     return cudaGetLastError();
 }
 
-}  // namespace
-
-extern "C" {
-
-lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0, int prec, void* stream,
-                       lbch_handle** out)
+// lb_ch_init and lb_ch_init_slab.  With a slab, params is the one instance of the slab (the global problem
+// with ny = slab->ny), gparams the global problem (for the velocity tables), and phi0 holds slab->ny + 2 GR
+// rows: the slab's rows with GR rows of each neighbour (global rows y0 - GR .. y0 + ny + GR - 1, wrapped).
+lbch_status init_impl(const lbch_params* params, int n_inst, const double* phi0, int prec, void* stream,
+                      lbch_handle** out, const SlabSpec* slab, const lbch_params* gparams)
 {
-    NvtxRange nvtx_("lb_ch_init");
     if (!out) return fail(LBCH_EINVAL, "out is NULL");
     *out = nullptr;
     if (!params || !phi0 || n_inst < 1) return fail(LBCH_EINVAL, "params/phi0 NULL or n_inst < 1");
@@ -770,6 +812,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     lbch_handle* h = new (std::nothrow) lbch_handle();
     if (!h) return fail(LBCH_ENOMEM, "host allocation failed");
     h->prec = prec;
+    h->slab = slab != nullptr;
     h->coupled = coupled;
     h->tau1 = !coupled;
     for (int k = 0; k < n_inst; k++) h->tau1 = h->tau1 && params[k].tau == 1.0;
@@ -795,6 +838,7 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         derive(p, d);
         d.nx = p.nx;
         d.ny = p.ny;
+        d.slab = slab ? 1 : 0;
         d.row0 = row + GR;
         d.ylen = (p.ny + 15) / 16 * 16 + 8;  // the Y slice of a tile spans TY + 8 rows from its first halo row
         row += p.ny + 2 * GR;
@@ -840,7 +884,8 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     }
     for (int k = 0; k < n_inst; k++) {
         h->inst[k].tab = (int)tabs.size();
-        velocity_tables(params[k], h->pitch, h->inst[k].ylen, tabs);
+        if (slab) velocity_tables(*gparams, h->pitch, h->inst[k].ylen, tabs, slab);
+        else velocity_tables(params[k], h->pitch, h->inst[k].ylen, tabs);
     }
     std::vector<float> tabs_f(tabs.begin(), tabs.end());
 
@@ -950,11 +995,17 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
         const InstDev& d = h->inst[k];
         for (int y = -GR; y < d.ny + GR; y++) {
             int yy;
-            if (d.walls) yy = y < 0 ? -1 - y : (y >= d.ny ? 2 * d.ny - 1 - y : y);
-            else yy = ((y % d.ny) + d.ny) % d.ny;
-            yy = std::min(std::max(yy, 0), d.ny - 1);
+            const double* srow;
+            if (slab) {
+                srow = src + (size_t)(y + GR) * d.nx;  // the slab's field comes with its neighbours' rows
+            } else {
+                if (d.walls) yy = y < 0 ? -1 - y : (y >= d.ny ? 2 * d.ny - 1 - y : y);
+                else yy = ((y % d.ny) + d.ny) % d.ny;
+                yy = std::min(std::max(yy, 0), d.ny - 1);
+                srow = src + (size_t)yy * d.nx;
+            }
             double* rowp = h->h_stage + (size_t)(d.row0 + y) * h->pitch + GC;
-            for (int x = -GC; x < d.nx + GC; x++) rowp[x] = src[(size_t)yy * d.nx + (((x % d.nx) + d.nx) % d.nx)];
+            for (int x = -GC; x < d.nx + GC; x++) rowp[x] = srow[((x % d.nx) + d.nx) % d.nx];
         }
         src += (size_t)d.nx * d.ny;
     }
@@ -1023,10 +1074,44 @@ lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0
     return LBCH_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0, int prec, void* stream,
+                       lbch_handle** out)
+{
+    NvtxRange nvtx_("lb_ch_init");
+    return init_impl(params, n_inst, phi0, prec, stream, out, nullptr, nullptr);
+}
+
+lbch_status lb_ch_init_slab(const lbch_params* global, int y0, int ny_local, const double* phi0_halo, int prec,
+                            void* stream, lbch_handle** out)
+{
+    NvtxRange nvtx_("lb_ch_init_slab");
+    if (!out) return fail(LBCH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!global || !phi0_halo) return fail(LBCH_EINVAL, "global params or phi0 NULL");
+    lbch_status st = check_params(*global, 0);
+    if (st != LBCH_OK) return st;
+    if (global->walls != 0) return fail(LBCH_EINVAL, "slabs split grids that are periodic in y (walls = 0)");
+    if (global->vel == LBCH_VEL_COUPLED) return fail(LBCH_EINVAL, "slabs take prescribed flows");
+    if (global->model == 3) return fail(LBCH_EINVAL, "slabs take Models I and II");
+    if (y0 < 0 || ny_local < 4 || y0 >= global->ny || ny_local > global->ny - y0)
+        return fail(LBCH_EINVAL, "slab rows [%d, %d) must lie in [0, %d) and number at least 4", y0, y0 + ny_local,
+                    global->ny);
+    lbch_params local = *global;
+    local.ny = ny_local;
+    const SlabSpec spec{y0, ny_local};
+    return init_impl(&local, 1, phi0_halo, prec, stream, out, &spec, global);
+}
+
 lbch_status lb_ch_step(lbch_handle* h, long nsteps)
 {
     NvtxRange nvtx_("lb_ch_step");
     if (!h || nsteps < 0) return fail(LBCH_EINVAL, "NULL handle or negative step count");
+    if (h->slab && nsteps > 1 && !h->tuning)
+        return fail(LBCH_EINVAL, "a slab handle advances one step per call: import its halos before every step");
     static const bool no_graph = std::getenv("LBCH_NO_GRAPH") != nullptr;
     const bool two = use_pair(h);
     while (nsteps > 0) {
@@ -1290,6 +1375,33 @@ lbch_status lb_ch_state_load(lbch_handle* h, const void* src)
     return LBCH_OK;
 }
 
+lbch_status lb_ch_halo_bytes(lbch_handle* h, long long* bytes)
+{
+    if (!h || !bytes) return fail(LBCH_EINVAL, "NULL handle or output");
+    if (!h->slab) return fail(LBCH_EINVAL, "halos belong to slab handles (lb_ch_init_slab)");
+    *bytes = (long long)halo_bytes(h);
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_halo_export(lbch_handle* h, int side, void* dst)
+{
+    if (!h || !dst || (side != 0 && side != 1)) return fail(LBCH_EINVAL, "NULL handle or buffer, or side not 0/1");
+    if (!h->slab) return fail(LBCH_EINVAL, "halos belong to slab handles (lb_ch_init_slab)");
+    const InstDev& d = h->inst[0];
+    // side 0: domain rows 0..GR-1 and the populations of row 0; side 1: rows ny-GR..ny-1 and row ny-1
+    return halo_copy(h, dst, d.row0 + (side == 0 ? 0 : d.ny - GR), d.row0 + (side == 0 ? 0 : d.ny - 1), true);
+}
+
+lbch_status lb_ch_halo_import(lbch_handle* h, int side, const void* src)
+{
+    if (!h || !src || (side != 0 && side != 1)) return fail(LBCH_EINVAL, "NULL handle or buffer, or side not 0/1");
+    if (!h->slab) return fail(LBCH_EINVAL, "halos belong to slab handles (lb_ch_init_slab)");
+    const InstDev& d = h->inst[0];
+    // side 0: ghost rows -GR..-1 and the populations of row -1; side 1: rows ny..ny+GR-1 and row ny
+    return halo_copy(h, const_cast<void*>(src), d.row0 + (side == 0 ? -GR : d.ny), d.row0 + (side == 0 ? -1 : d.ny),
+                     false);
+}
+
 lbch_status lb_ch_tape_phi(lbch_handle* h, void* dst)
 {
     if (!h || !dst) return fail(LBCH_EINVAL, "NULL handle or buffer");
@@ -1315,6 +1427,7 @@ lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
     if (h->inst[0].walls) return fail(LBCH_EINVAL, "the adjoint supports periodic domains only");
     if (h->coupled) return fail(LBCH_EINVAL, "the adjoint supports prescribed flows only");
     if (h->model3) return fail(LBCH_EINVAL, "the adjoint supports Models I and II");
+    if (h->slab) return fail(LBCH_EINVAL, "the adjoint supports whole grids, not slabs");
     if ((long long)h->inst[0].nx * h->inst[0].ny >= (1LL << 31))
         return fail(LBCH_EINVAL, "the adjoint supports grids of fewer than 2^31 nodes");
     h->adj_elem = 8;  // the adjoint is carried in double for every storage precision
@@ -1368,6 +1481,11 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
         for (int k = 0; k < kPairShapes && pair_ok(h); k++) cands.push_back({false, true, k});
     }
     const int ns = (int)cands.size();
+    struct Tuning {  // a slab handle may take several steps per lb_ch_step call while it is timed
+        lbch_handle* h;
+        explicit Tuning(lbch_handle* hh) : h(hh) { h->tuning = true; }
+        ~Tuning() { h->tuning = false; }
+    } tuning_(h);
     if (ns > 1) {
         long long bytes = 0;
         lb_ch_state_bytes(h, &bytes);

@@ -48,6 +48,8 @@ struct lbch_handle {
     bool pair = false;          // step two at a time with the two-step kernel (when pair_ok holds); odd
     int pshape = 0;             // steps take the one-step kernel above; pshape indexes pair_shape()
     bool walls = false;         // an instance has walls
+    bool slab = false;          // a slab of a larger periodic grid (lb_ch_init_slab): halos imported between steps
+    bool tuning = false;        // lb_ch_tune is stepping the handle (a slab may then take several steps per call)
     bool model3 = false;        // an instance uses Model III (the tile kernel then steps the handle)
     bool need_time = false;     // an instance's step depends on the step index (time factor, Model III)
     void* H[2] = {nullptr, nullptr};  // Model III: H of Eq. F2-1's time derivatives, 2 planes, arithmetic type
@@ -105,7 +107,7 @@ inline bool sweep_gen(const lbch_handle* h) { return !h->tau1 || h->force_genera
 // half-storage path is left to the row sweep).
 inline bool pair_ok(const lbch_handle* h)
 {
-    return h->tau1 && !h->force_general && !h->coupled && !h->model3 && !h->walls && h->prec != LBCH_F16S;
+    return h->tau1 && !h->force_general && !h->coupled && !h->model3 && !h->walls && !h->slab && h->prec != LBCH_F16S;
 }
 
 // Row-sweep launches and set-up, one translation unit per precision (lbch_sweep_*.cu).

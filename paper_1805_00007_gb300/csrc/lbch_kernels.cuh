@@ -60,6 +60,8 @@ struct InstDev {
     int walls, model, vel;
     int ylen;          // length of each Y velocity table: ny rounded up to 16, plus 2 GR ghost rows
     int tab;           // offset of the velocity tables: X1, X2 [pitch]; Y1, Y2 [ylen]; W[4]
+    int slab;          // a slab of a larger periodic grid: its ghost rows hold the neighbouring slabs' rows
+                       // (imported between steps), not images of its own rows
     double Tper;
     Consts<double> cd;  // the constants in double (FP64 path, initial state)
     Consts<float> cf;   // and rounded once to float (float paths)
@@ -762,7 +764,7 @@ __global__ void init_kernel(const InstDev* inst, int n_inst, const double* tabs,
     int y = (int)(loc / I.nx), x = (int)(loc - (long long)y * I.nx);
     auto at = [&](int dx, int dy) -> double {
         int xx = wrap(x + dx, I.nx);
-        int yy = I.walls ? mirror(y + dy, I.ny) : wrap(y + dy, I.ny);
+        int yy = I.slab ? y + dy : (I.walls ? mirror(y + dy, I.ny) : wrap(y + dy, I.ny));
         return phi0[(long long)(I.row0 + yy) * pitch + GC + xx];
     };
     double c0 = at(0, 0);
@@ -793,8 +795,9 @@ __global__ void init_kernel(const InstDev* inst, int n_inst, const double* tabs,
     if (lo) lo[(long long)(I.row0 + y) * pitch + GC + x] = (float)(c0 - (double)hi);
     const int NONE = -0x40000000;
     const int xa = x < 3 ? x + I.nx : NONE, xb = x >= I.nx - 3 ? x - I.nx : NONE;
-    const int ya = y < 3 ? (I.walls ? -1 - y : y + I.ny) : NONE;
-    const int yb = y >= I.ny - 3 ? (I.walls ? 2 * I.ny - 1 - y : y - I.ny) : NONE;
+    // a slab's ghost rows are the neighbouring slabs' rows, imported before its first step
+    const int ya = y < 3 && !I.slab ? (I.walls ? -1 - y : y + I.ny) : NONE;
+    const int yb = y >= I.ny - 3 && !I.slab ? (I.walls ? 2 * I.ny - 1 - y : y - I.ny) : NONE;
     for (int iy = 0; iy < 3; iy++) {
         const int yy = iy == 0 ? y : (iy == 1 ? ya : yb);
         if (yy == NONE) continue;

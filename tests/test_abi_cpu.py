@@ -86,6 +86,7 @@ def test_every_entry_point_rejects_null_arguments_without_gpu():
     i = ctypes.c_int()
     ll = ctypes.c_longlong()
     buf = ctypes.c_void_p(8)  # never dereferenced: the NULL handle is rejected first
+    h = ctypes.c_void_p()
     calls = {
         "lb_ch_observe": lambda: lib.lb_ch_observe(None, 0, abi.LBCH_OBS_MASS, ctypes.byref(d)),
         "lb_ch_observe_all": lambda: lib.lb_ch_observe_all(None, abi.LBCH_OBS_MASS, ctypes.byref(d)),
@@ -102,6 +103,10 @@ def test_every_entry_point_rejects_null_arguments_without_gpu():
         "lb_ch_test_hook": lambda: lib.lb_ch_test_hook(None, abi.LBCH_HOOK_POISON, 1),
         "lb_ch_field_stats_noalloc": lambda: lib.lb_ch_field_stats_noalloc(None, None, 4, 4, 4, None, None),
         "lb_ch_alu_peak (bad precision)": lambda: lib.lb_ch_alu_peak(abi.LBCH_F16S, None, ctypes.byref(d)),
+        "lb_ch_init_slab": lambda: lib.lb_ch_init_slab(None, 0, 8, None, 0, None, ctypes.byref(h)),
+        "lb_ch_halo_bytes": lambda: lib.lb_ch_halo_bytes(None, ctypes.byref(ll)),
+        "lb_ch_halo_export": lambda: lib.lb_ch_halo_export(None, 0, buf),
+        "lb_ch_halo_import": lambda: lib.lb_ch_halo_import(None, 1, buf),
     }
     for name, call in calls.items():
         assert call() == abi.LBCH_EINVAL, name

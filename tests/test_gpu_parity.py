@@ -380,4 +380,5 @@ def test_moving_walls_match_oracle(prec, tol, form):
     with abi.Simulation(q, np.full((21, 40), 0.37), prec=prec) as sim:
         abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, 1 if form == "tile" else 0)
         sim.step(70)
-        assert _maxdiff(sim.phi(), np.full((21, 40), 0.37)) <= (1e-14 if prec == "f64" else 1e-6)
+        # (the half path rounds the streamed populations, a uniform bias of about 1e-6 per step)
+        assert _maxdiff(sim.phi(), np.full((21, 40), 0.37)) <= {"f64": 1e-14, "f32": 1e-6, "f16s": tol}[prec]
