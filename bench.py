@@ -41,11 +41,17 @@ FLOPS_PER_LU_TAU1 = 169
 # Newton steps (6 more): 169 as well.
 SMS, FP32_LANES_PER_SM, FP64_LANES_PER_SM = 152, 128, 2
 
-# DRAM bytes (read + write) per launch of the headline kernel, from the ncu capture summarised in
-# profiles/; reported only while the kernel sources still hash the same and the autotuner chose that kernel.
+# Algorithmic HBM bytes per lattice update of the general step (any tau_g): the nine populations read and
+# written once and phi read and written once, in the storage type of each path (FP16S: eight half
+# populations, float phi).  The roofline fraction is reported against these, and beside them against the
+# bytes the path in use actually needs (at tau_g = 1 the populations drop out and phi alone is moved).
+GENERAL_BYTES_PER_LU = {"f32": 80, "f64": 160, "f16s": 44}
+
+# DRAM bytes (read + write) per launch of the headline kernel, from an ncu capture of these sources
+# (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the kernel sources still hash the same
+# and the autotuner chose that kernel, else null.
 TRAFFIC = {"hash": "8becc9145ea4650e", "bytes_per_launch": 668416,
-           "kernel": "ch_pair_kernel<float,float,tile=32x14,NT=1024>",
-           "profile": "profiles/ch_pair_f32_256_headline.md"}
+           "kernel": "ch_pair_kernel<float,float,tile=32x14,NT=1024>"}
 KERNEL_SOURCES = ("lbch_kernels.cuh", "lbch_sweep.cuh", "lbch_sweep_launch.cuh", "lbch_pair.cuh")
 
 
@@ -263,6 +269,19 @@ def run_case(case, nsteps, tile=0, form="sweep"):
         print(json.dumps({"case": case, "adjoint_steps": nsteps,
                           "kernels": "adj::fwd_mu, adj::local, adj::transpose1, adj::transpose2"}))
         return
+    if parts[0] == "ens":  # the first N instances of the ragged shear ensemble, e.g. ens_f32_64 or ens_f32_64_0.8
+        from paper_1805_00007_gb300 import workloads as wl
+        ens = wl.shear_ensemble(tau=float(parts[3]) if len(parts) > 3 else 1.0)[:int(parts[2])]
+        with abi.Simulation([q for q, _ in ens], [f for _, f in ens], prec=parts[1], tune=tile < 0) as sim:
+            if tile >= 0:
+                abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, int(form == "tile"))
+                abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, tile)
+            sim.step(nsteps)
+            torch.cuda.synchronize()
+            kname = kernel_name(sim.kernel(), parts[1])
+            nodes = sim.info()["nodes"]
+        print(json.dumps({"case": case, "steps": nsteps, "instances": len(ens), "nodes": nodes, "kernel": kname}))
+        return
     prec, n = parts[0], int(parts[1])
     tau = float(parts[2]) if len(parts) > 2 else 1.0
     pp, f0 = sweep_params(n, tau)
@@ -279,27 +298,42 @@ def run_case(case, nsteps, tile=0, form="sweep"):
 
 
 def accuracy(prec, p, phi0, nsteps):
-    """max |phi - phi_oracle| at the stored oracle sample nodes after the full run, and the relative
-    difference of ||E_phi||_2 (Eq. err); None when the stored oracle result is absent."""
-    path = os.path.join(ROOT, "tests", "golden", "zalesak_256.json")
+    """max |phi - phi_oracle| over every node after the full run (the oracle's stored final field), the
+    relative difference of ||E_phi||_2 (Eq. err) and the mass drift; None when the stored field is absent."""
+    path = os.path.join(ROOT, "tests", "golden", "zalesak_256_phi.npz")
     if not os.path.exists(path):
         return None
-    with open(path) as fh:
-        gold = json.load(fh)
-    if gold["nsteps"] != nsteps:
+    gold = np.load(path)
+    if int(gold["nsteps"]) != nsteps:
         return None
+    ref = gold["phi"]
     from paper_1805_00007_gb300 import abi
     with abi.Simulation(p, phi0, prec=prec) as sim:
         sim.step(nsteps)
         phi = sim.phi()
         err = sim.observe(abi.LBCH_OBS_ERR_L2)
         mass = sim.observe(abi.LBCH_OBS_MASS)
-    j, i = np.array(gold["nodes_j"]), np.array(gold["nodes_i"])
-    return {"max_abs_dphi_vs_oracle": float(np.max(np.abs(phi[j, i] - np.array(gold["phi"])))),
-            "err_l2": err, "err_l2_oracle": gold["err_l2"],
-            "err_l2_rel_diff": abs(err - gold["err_l2"]) / gold["err_l2"],
-            "mass_rel_drift": abs(mass - gold["mass0"]) / gold["mass0"],
-            "nodes_compared": int(j.size)}
+    err_o = float(np.sqrt(np.sum((ref - phi0) ** 2) / np.sum(phi0 ** 2)))
+    return {"max_abs_dphi_vs_oracle": float(np.max(np.abs(phi - ref))), "nodes_compared": int(ref.size),
+            "err_l2": err, "err_l2_oracle": err_o, "err_l2_rel_diff": abs(err - err_o) / err_o,
+            "mass_rel_drift": abs(mass - float(phi0.sum())) / float(phi0.sum())}
+
+
+def accuracy_vs_fp64(sims_of, nsteps, precs):
+    """max |phi - phi_FP64| over every node of every instance after nsteps, for each precision, where the
+    FP64 path is the reference (it matches the oracle to 1e-12 at this length in the GPU tests)."""
+    ref = sims_of("f64")
+    ref.step(nsteps)
+    n_inst = len(ref.params)
+    ref_phi = [ref.phi(k) for k in range(n_inst)]
+    ref.close()
+    out = {}
+    for prec in precs:
+        sim = sims_of(prec)
+        sim.step(nsteps)
+        out[prec] = max(float(np.max(np.abs(sim.phi(k) - ref_phi[k]))) for k in range(n_inst))
+        sim.close()
+    return out
 
 
 def main():
@@ -314,7 +348,8 @@ def main():
                     help="time the step on 1024^2 .. 16384^2 grids (tau_g = 0.8) instead of the benchmark")
     ap.add_argument("--case", default=None,
                     help="profiling case PREC_N[_TAU] (e.g. f32_4096, f32_4096_0.8), rt_PREC (the coupled "
-                         "Rayleigh-Taylor grid) or adj_N (adjoint steps on the N^2 single vortex): init and "
+                         "Rayleigh-Taylor grid), adj_N (adjoint steps on the N^2 single vortex) or "
+                         "ens_PREC_N[_TAU] (the first N instances of the shear ensemble): init and "
                          "--case-steps steps of that case only")
     ap.add_argument("--case-steps", type=int, default=8)
     ap.add_argument("--case-tile", type=int, default=0, help="tile shape index for --case (-1: autotune)")
@@ -406,6 +441,7 @@ def main():
     spl32 = steps_per_launch(kern32)
     launch32 = t32 / rev * spl32  # one launch of the headline kernel
     achieved32 = info32["bytes_per_lu"] * nodes * spl32 / launch32 / 1e9
+    achieved_gen32 = GENERAL_BYTES_PER_LU["f32"] * nodes * spl32 / launch32 / 1e9
     achieved64 = info64["bytes_per_lu"] * nodes / (t64 / rev) / 1e9
 
     # --- end to end through the C ABI with host buffers: init (H2D of phi0), one revolution, read phi (D2H)
@@ -452,10 +488,11 @@ def main():
     ensemble = {}
     if not args.no_sweep:
         from paper_1805_00007_gb300 import shard
-        ens = wl.shear_ensemble()
-        enodes = sum(q["nx"] * q["ny"] for q, _ in ens)
-        _, eparams, efields = shard.shard(ens, rank, world)
-        for prec in ("f32", "f16s"):
+        for etau, prec in ((1.0, "f32"), (1.0, "f16s"), (0.8, "f32"), (0.8, "f16s")):
+            ens = wl.shear_ensemble(tau=etau)
+            enodes = sum(q["nx"] * q["ny"] for q, _ in ens)
+            _, eparams, efields = shard.shard(ens, rank, world)
+            key = prec if etau == 1.0 else f"{prec}_tau{etau}"
             sim = abi.Simulation(list(eparams), list(efields), prec=prec, stream=stream.cuda_stream, tune=True)
             sim.step(64)
             barrier()
@@ -472,14 +509,23 @@ def main():
                 dt = float(t.item())
             inf = sim.info()
             gbs = inf["bytes_per_lu"] * enodes / dt / 1e9
-            ensemble[prec] = {"instances": len(ens), "nodes": enodes, "MLUPS": enodes / dt / 1e6,
-                              "ranks": world, "sharding": "instances across ranks, no exchange",
-                              "kernel": kernel_name(sim.kernel(), prec),
-                              "us_per_launch": dt * 1e6 * steps_per_launch(sim.kernel()),
-                              "bytes_per_lu": inf["bytes_per_lu"],
-                              "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+            ggen = GENERAL_BYTES_PER_LU[prec] * enodes / dt / 1e9
+            ensemble[key] = {"instances": len(ens), "nodes": enodes, "tau": etau, "MLUPS": enodes / dt / 1e6,
+                             "ranks": world, "sharding": "instances across ranks, no exchange",
+                             "kernel": kernel_name(sim.kernel(), prec),
+                             "us_per_launch": dt * 1e6 * steps_per_launch(sim.kernel()),
+                             "roofline": {"bound": "hbm", "peak": hbm_peak, "unit": "GB/s", "peak_kind": peak_kind,
+                                          "bytes_per_lu": GENERAL_BYTES_PER_LU[prec], "achieved": ggen,
+                                          "frac": ggen / hbm_peak,
+                                          "bytes_basis": "general step: populations and phi read and written once",
+                                          "path": {"bytes_per_lu": inf["bytes_per_lu"], "achieved": gbs,
+                                                   "frac": gbs / hbm_peak,
+                                                   "basis": ("phi alone (tau_g = 1: the populations drop out)"
+                                                             if etau == 1.0 else
+                                                             "populations and phi (hi + lo on FP32) read and "
+                                                             "written once")}}}
             sim.close()
-            if prec == "f32":
+            if prec == "f32" and etau == 1.0:
                 # the same instances as separate single-instance handles, stepped one after another on the
                 # same stream (each with the untuned default kernel): what the batched launch saves
                 sims = [abi.Simulation(q, f, prec=prec, stream=stream.cuda_stream) for q, f in zip(eparams, efields)]
@@ -498,8 +544,8 @@ def main():
                     dt_loop = float(t.item())
                 for s in sims:
                     s.close()
-                ensemble[prec]["looped_single_instance_MLUPS"] = enodes / dt_loop / 1e6
-                ensemble[prec]["batched_speedup"] = dt_loop / dt
+                ensemble[key]["looped_single_instance_MLUPS"] = enodes / dt_loop / 1e6
+                ensemble[key]["batched_speedup"] = dt_loop / dt
 
     # --- the coupled Rayleigh-Taylor workload (256 x 1024, Navier-Stokes + Cahn-Hilliard, walls in y) and the
     #     adjoint step of the 512^2 single-vortex workload: the step rates of the other two kernel families
@@ -544,6 +590,34 @@ def main():
             adjoint = {"workload": "512^2 single vortex, FP32 forward tape, adjoint carried in FP64",
                        "MLUPS": nv / dta / 1e6, "us_per_step": dta * 1e6}
 
+    # --- the gradient of the single-vortex loss (512^2, T = 8000: FP32 forward, adjoint in FP64) with respect to
+    #     phi0 and the velocity scale, forward and backward through evolve() with binomial checkpointing
+    gradient = {}
+    if not args.no_sweep and rank == 0:
+        from paper_1805_00007_gb300.autograd import evolve, schedule_stats
+        pv, fv, tv = wl.single_vortex()
+        ck, leaf = 16, 64
+        gtimes = []
+        for it in range(2):
+            x = torch.tensor(fv, dtype=torch.float64, requires_grad=True)
+            sc = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            phiT = evolve(x, sc, pv, tv, prec="f32", checkpoints=ck, leaf=leaf)
+            loss = 0.5 * torch.sum((phiT - x.detach()) ** 2)
+            loss.backward()
+            torch.cuda.synchronize()
+            gtimes.append(time.perf_counter() - t0)
+        stt = schedule_stats(tv, ck, leaf)
+        nbytes_state = None
+        with abi.Simulation(pv, fv, prec="f32") as sim:
+            nbytes_state = abi.lb_ch_state_bytes(sim.h)
+        gradient = {"workload": "512^2 single vortex, T = 8000, loss 1/2 |phi(T) - phi0|^2, d/dphi0 and d/dscale",
+                    "ms": 1e3 * min(gtimes), "ms_first": 1e3 * gtimes[0], "adjoint_steps": tv,
+                    "forward_steps": stt["forward_steps"], "repetitions": stt["repetitions"],
+                    "stored_states": stt["slots"], "state_mb": nbytes_state / 2 ** 20, "tape_steps": leaf,
+                    "tape_mb": leaf * pv["nx"] * pv["ny"] * 4 / 2 ** 20, "dL_dscale": float(sc.grad)}
+
     # --- the paper's relaxation-time study (Sec. III.A) at its own size, every point one ensemble instance
     tau_sweep = {}
     if not args.no_sweep and rank == 0:
@@ -556,6 +630,43 @@ def main():
                      "seconds": time.perf_counter() - t0}
 
     acc = {prec: accuracy(prec, p, phi0, rev) for prec in ("f32", "f64", "f16s")} if rank == 0 else {}
+
+    # --- the other workloads at their stated lengths: every node of the float paths against the FP64 path
+    acc_more = {}
+    if rank == 0 and not args.no_sweep:
+        sc = stream.cuda_stream
+        pv, fv, tv = wl.single_vortex()
+        acc_more["vortex_512_T8000"] = {
+            "max_abs_dphi_vs_fp64": accuracy_vs_fp64(lambda pr: abi.Simulation(pv, fv, prec=pr, stream=sc), tv, ("f32",)),
+            "nodes": pv["nx"] * pv["ny"], "steps": tv}
+        for etau in (1.0, 0.8):
+            ens = wl.shear_ensemble(tau=etau)
+            eq, ef = [q for q, _ in ens], [f for _, f in ens]
+            acc_more[f"ensemble_shear_256_tau{etau}"] = {
+                "max_abs_dphi_vs_fp64": accuracy_vs_fp64(lambda pr: abi.Simulation(eq, ef, prec=pr, stream=sc), 200,
+                                                         ("f32", "f16s")),
+                "instances": len(ens), "nodes": sum(f.size for f in ef), "steps": 200, "over": "every instance"}
+        prt, frt = wl.rayleigh_taylor()
+        acc_more["rayleigh_taylor_256x1024"] = {
+            "max_abs_dphi_vs_fp64_500_steps": accuracy_vs_fp64(lambda pr: abi.Simulation(prt, frt, prec=pr, stream=sc),
+                                                              500, ("f32",))}
+        for prec in ("f32", "f64"):
+            with abi.Simulation(prt, frt, prec=prec, stream=sc) as sim:
+                done, rec = 0, {"finite": True}
+                while done < 20000:  # in blocks, to find where a run stops being finite
+                    sim.step(1000)
+                    done += 1000
+                    try:
+                        phr = sim.phi()
+                        mrt = sim.observe(abi.LBCH_OBS_MASS)
+                    except abi.LbchError:
+                        rec = {"finite": False, "non_finite_by_step": done}
+                        break
+                if rec["finite"]:
+                    rec.update({"mass_rel_drift": abs(mrt - float(frt.sum())) / float(np.abs(frt).sum()),
+                                "mirror_asymmetry": float(np.max(np.abs(np.roll(phr[:, ::-1], 1, axis=1) - phr))),
+                                "phi_range": [float(phr.min()), float(phr.max())]})
+            acc_more["rayleigh_taylor_256x1024"][f"{prec}_20000_steps"] = rec
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -598,9 +709,15 @@ def main():
                              "unit": "TFLOP/s", "frac": alu64_tflops / peak64_tflops,
                              "peak_from": "152 SMs x 2 FP64 lanes x 2 flop x median SM clock under load",
                              "peak_measured": fma64, "frac_of_measured": alu64_tflops / fma64}},
-            "roofline": {"bound": "hbm", "achieved": achieved32, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved32 / hbm_peak, "traffic": traffic, "traffic_profile": TRAFFIC["profile"],
-                         "kernel": kernel_name(kern32, "f32"), "bytes_per_lu": info32["bytes_per_lu"],
+            "roofline": {"bound": "hbm", "achieved": achieved_gen32, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gen32 / hbm_peak, "traffic": traffic,
+                         "kernel": kernel_name(kern32, "f32"), "bytes_per_lu": GENERAL_BYTES_PER_LU["f32"],
+                         "bytes_basis": "general step: 9 populations and phi read and written once, 4 B each",
+                         "path": {"bytes_per_lu": info32["bytes_per_lu"], "achieved": achieved32,
+                                  "frac": achieved32 / hbm_peak,
+                                  "basis": "what the kernel in use moves: at tau_g = 1 phi alone (hi + lo), read and "
+                                           "written once per launch of two steps"},
+                         "l2_resident": "one 256^2 field is 0.5 MB: the state stays in L2, so HBM does not bound it",
                          "peak_kind": peak_kind, "us_per_launch": launch32 * 1e6,
                          "alu": {"flops_per_lu": FLOPS_PER_LU_TAU1, "achieved": alu_tflops, "peak": peak_tflops,
                                  "unit": "TFLOP/s", "frac": alu_tflops / peak_tflops,
@@ -611,7 +728,9 @@ def main():
             "paper_tau_sweep": tau_sweep,
             "coupled_rt_256x1024": coupled,
             "adjoint_vortex_512": adjoint,
+            "gradient_vortex_512_T8000": gradient,
             "accuracy_one_revolution": acc,
+            "accuracy_full_length": acc_more,
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": phi0.nbytes,
                     "d2h_bytes_per_step": phi0.nbytes},
             "gpu_launches": args.steps * rev // spl32,

@@ -246,6 +246,12 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y);
  *   step n) and n; accumulates dL/ds, where the prescribed velocity is s times the configured one.
  * lb_ch_adjoint_end: the adjoint of the initial equilibria: dL/dphi0 into dL_dphi0 (nx*ny values)
  *   and dL/ds (at s = 1) into *dL_ds (host).  Synchronises the stream.
+ * lb_ch_step_taped: nsteps forward steps, writing phi of each step's starting state into the tape:
+ *   entry k (nx*ny values of the tape type, at tape + k * nx*ny) holds phi(n + k), n the step index on
+ *   entry -- the replay of a checkpointed segment in one call (one-step launches, captured in a CUDA graph
+ *   that is kept while the tape and length repeat).
+ * lb_ch_adjoint_sweep: lb_ch_adjoint_step for n = n0 + nsteps - 1 down to n0, with phi_n the tape entry
+ *   n - n0 (a tape lb_ch_step_taped wrote from step n0).
  * Walls and ensembles are rejected with LBCH_EINVAL. */
 lbch_status lb_ch_state_bytes(lbch_handle* h, long long* bytes);
 lbch_status lb_ch_state_save(lbch_handle* h, void* dst);
@@ -254,6 +260,8 @@ lbch_status lb_ch_tape_phi(lbch_handle* h, void* dst);
 lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT);
 lbch_status lb_ch_adjoint_step(lbch_handle* h, const void* phi_n, long n);
 lbch_status lb_ch_adjoint_end(lbch_handle* h, void* dL_dphi0, double* dL_ds);
+lbch_status lb_ch_step_taped(lbch_handle* h, long nsteps, void* tape);
+lbch_status lb_ch_adjoint_sweep(lbch_handle* h, const void* tape, long n0, long nsteps);
 
 /* Test hook for the failure path of the step kernel's bounded waits.  With hook
  * LBCH_HOOK_SKIP_FIRST_LOAD and value != 0, the next step launches run without CUDA graphs and their

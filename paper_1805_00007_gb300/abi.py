@@ -22,7 +22,8 @@ SYMBOLS = ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb
            "lb_ch_strerror", "lb_ch_last_error", "lb_ch_info", "lb_ch_kernel_info", "lb_ch_stream", "lb_ch_test_hook",
            "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save", "lb_ch_state_load",
            "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step", "lb_ch_adjoint_end", "lb_ch_tune",
-           "lb_ch_alu_peak", "lb_ch_init_slab", "lb_ch_halo_bytes", "lb_ch_halo_export", "lb_ch_halo_import")
+           "lb_ch_alu_peak", "lb_ch_init_slab", "lb_ch_halo_bytes", "lb_ch_halo_export", "lb_ch_halo_import",
+           "lb_ch_step_taped", "lb_ch_adjoint_sweep")
 (LBCH_HOOK_SKIP_FIRST_LOAD, LBCH_HOOK_TILE_SHAPE, LBCH_HOOK_GENERAL_PATH, LBCH_HOOK_NO_PDL, LBCH_HOOK_TILE_KERNEL,
  LBCH_HOOK_TWO_STEP, LBCH_HOOK_POISON) = 1, 2, 3, 4, 5, 6, 7
 
@@ -91,12 +92,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lb_ch_halo_bytes.argtypes = [vp, P(ctypes.c_longlong)]
     lib.lb_ch_halo_export.argtypes = [vp, ctypes.c_int, vp]
     lib.lb_ch_halo_import.argtypes = [vp, ctypes.c_int, vp]
+    lib.lb_ch_step_taped.argtypes = [vp, ctypes.c_long, vp]
+    lib.lb_ch_adjoint_sweep.argtypes = [vp, vp, ctypes.c_long, ctypes.c_long]
     for name in ("lb_ch_init", "lb_ch_step", "lb_ch_observe", "lb_ch_observe_all", "lb_ch_free", "lb_ch_info",
                  "lb_ch_kernel_info",
                  "lb_ch_test_hook", "lb_ch_field_stats_noalloc", "lb_ch_state_bytes", "lb_ch_state_save",
                  "lb_ch_state_load", "lb_ch_tape_phi", "lb_ch_adjoint_begin", "lb_ch_adjoint_step",
                  "lb_ch_adjoint_end", "lb_ch_tune", "lb_ch_alu_peak", "lb_ch_init_slab", "lb_ch_halo_bytes",
-                 "lb_ch_halo_export", "lb_ch_halo_import"):
+                 "lb_ch_halo_export", "lb_ch_halo_import", "lb_ch_step_taped", "lb_ch_adjoint_sweep"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -254,6 +257,14 @@ def lb_ch_adjoint_begin(h, dphiT_ptr: int):
 
 def lb_ch_adjoint_step(h, phi_n_ptr: int, n: int):
     _check(load().lb_ch_adjoint_step(h, ctypes.c_void_p(phi_n_ptr), int(n)), "lb_ch_adjoint_step")
+
+
+def lb_ch_step_taped(h, nsteps: int, tape_ptr: int):
+    _check(load().lb_ch_step_taped(h, int(nsteps), ctypes.c_void_p(tape_ptr)), "lb_ch_step_taped")
+
+
+def lb_ch_adjoint_sweep(h, tape_ptr: int, n0: int, nsteps: int):
+    _check(load().lb_ch_adjoint_sweep(h, ctypes.c_void_p(tape_ptr), int(n0), int(nsteps)), "lb_ch_adjoint_sweep")
 
 
 def lb_ch_adjoint_end(h, dphi0_ptr: int) -> float:

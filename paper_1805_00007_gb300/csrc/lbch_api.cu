@@ -172,8 +172,10 @@ inline Shape active_tile(const lbch_handle* h)
 }
 inline void drop_graphs(lbch_handle* h)  // graphs captured earlier launch another kernel or shape
 {
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 2; k++) {
         if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        if (h->tgraph[k].exec) { cudaGraphExecDestroy(h->tgraph[k].exec); h->tgraph[k] = lbch_handle::TapeGraph(); }
+    }
 }
 
 cudaError_t launch_sweep(lbch_handle* h, int parity)
@@ -445,6 +447,7 @@ void release(lbch_handle* h)
 {
     for (int k = 0; k < 2; k++) {
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        if (h->tgraph[k].exec) cudaGraphExecDestroy(h->tgraph[k].exec);
         if (h->g[k]) cudaFree(h->g[k]);
         if (h->phi[k]) cudaFree(h->phi[k]);
         if (h->lo[k]) cudaFree(h->lo[k]);
@@ -750,6 +753,20 @@ adj::AdjArgs adj_args(const lbch_handle* h, long long n)
     a.ylen = h->inst[0].ylen;
     a.n = n;
     return a;
+}
+
+// phi of the state in buffer `par` into a plain array of the tape type (see lb_ch_tape_phi).
+cudaError_t tape_launch(lbch_handle* h, int par, void* dst)
+{
+    const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
+    const int nb = (int)((N + 255) / 256);
+    if (h->prec == LBCH_F64)
+        adj::tape_kernel<double, double><<<nb, 256, 0, h->stream>>>(h->d_inst, h->pitch, (const double*)h->phi[par],
+                                                                    nullptr, (double*)dst);
+    else
+        adj::tape_kernel<float, float><<<nb, 256, 0, h->stream>>>(h->d_inst, h->pitch, (const float*)h->phi[par],
+                                                                  h->lo[par], (float*)dst);
+    return cudaGetLastError();
 }
 
 template <typename C, typename TP>
@@ -1402,21 +1419,82 @@ lbch_status lb_ch_halo_import(lbch_handle* h, int side, const void* src)
                      false);
 }
 
+lbch_status lb_ch_step_taped(lbch_handle* h, long nsteps, void* tape)
+{
+    NvtxRange nvtx_("lb_ch_step_taped");
+    if (!h || !tape || nsteps < 0) return fail(LBCH_EINVAL, "NULL handle or tape, or negative step count");
+    if (h->n_inst != 1 || h->coupled || h->slab)
+        return fail(LBCH_EINVAL, "taped steps are for single-instance prescribed-flow handles of a whole grid");
+    const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
+    if (N >= (1LL << 31)) return fail(LBCH_EINVAL, "the adjoint supports grids of fewer than 2^31 nodes");
+    const size_t stride = (size_t)N * (h->prec == LBCH_F64 ? 8 : 4);
+    char* t = static_cast<char*>(tape);
+    static const bool no_graph = std::getenv("LBCH_NO_GRAPH") != nullptr;
+    // Long replays go through a captured graph (one per parity, kept while the tape and length repeat, as
+    // the segments of a reverse sweep do); step k of it runs step counter + k, and only its last launch
+    // advances the counter.
+    if (!no_graph && !h->debug_skip && nsteps >= 8) {
+        const int parity = cur_buf(h);
+        lbch_handle::TapeGraph& tg = h->tgraph[parity];
+        if (!tg.exec || tg.tape != tape || tg.nsteps != nsteps) {
+            if (tg.exec) cudaGraphExecDestroy(tg.exec);
+            tg.exec = nullptr;
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (long k = 0; k < nsteps && e == cudaSuccess; k++) {
+                e = tape_launch(h, parity ^ (int)(k & 1), t + (size_t)k * stride);
+                h->t_off = (int)k;
+                h->t_adv = k == nsteps - 1 ? (int)nsteps : 0;
+                if (e == cudaSuccess) e = launch_step(h, parity ^ (int)(k & 1));
+            }
+            h->t_off = 0;
+            h->t_adv = 1;
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+            if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "taped step launch during capture"); }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&tg.exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { tg.exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+            tg.tape = tape;
+            tg.nsteps = nsteps;
+        }
+        CK(cudaGraphLaunch(tg.exec, h->stream));
+        h->n += nsteps;
+        return LBCH_OK;
+    }
+    for (long k = 0; k < nsteps; k++) {
+        CK(tape_launch(h, cur_buf(h), t + (size_t)k * stride));
+        CK(launch_step(h, cur_buf(h)));  // a one-step launch (the two-step kernel would skip a tape entry)
+        h->n += 1;
+    }
+    return LBCH_OK;
+}
+
+lbch_status lb_ch_adjoint_sweep(lbch_handle* h, const void* tape, long n0, long nsteps)
+{
+    NvtxRange nvtx_("lb_ch_adjoint_sweep");
+    if (!h || !tape || n0 < 0 || nsteps < 0) return fail(LBCH_EINVAL, "NULL handle or tape, or negative step");
+    if (!h->adj) return fail(LBCH_EINVAL, "lb_ch_adjoint_begin was not called");
+    const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
+    const size_t stride = (size_t)N * (h->prec == LBCH_F64 ? 8 : 4);
+    const char* t = static_cast<const char*>(tape);
+    for (long k = nsteps - 1; k >= 0; k--) {
+        cudaError_t e = h->prec == LBCH_F64
+                            ? adjoint_step_t<double, double>(h, (const double*)(t + (size_t)k * stride), n0 + k)
+                            : adjoint_step_t<double, float>(h, (const float*)(t + (size_t)k * stride), n0 + k);
+        CK(e);
+    }
+    return LBCH_OK;
+}
+
 lbch_status lb_ch_tape_phi(lbch_handle* h, void* dst)
 {
     if (!h || !dst) return fail(LBCH_EINVAL, "NULL handle or buffer");
     if (h->n_inst != 1) return fail(LBCH_EINVAL, "the adjoint supports single-instance handles");
-    const int par = cur_buf(h);
     const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
     if (N >= (1LL << 31)) return fail(LBCH_EINVAL, "the adjoint supports grids of fewer than 2^31 nodes");
-    const int nb = (int)((N + 255) / 256);
-    if (h->prec == LBCH_F64)
-        adj::tape_kernel<double, double><<<nb, 256, 0, h->stream>>>(h->d_inst, h->pitch, (const double*)h->phi[par],
-                                                                    nullptr, (double*)dst);
-    else
-        adj::tape_kernel<float, float><<<nb, 256, 0, h->stream>>>(h->d_inst, h->pitch, (const float*)h->phi[par],
-                                                                  h->lo[par], (float*)dst);
-    CK(cudaGetLastError());
+    CK(tape_launch(h, cur_buf(h), dst));
     return LBCH_OK;
 }
 
@@ -1556,8 +1634,7 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
     }
     if (hook == LBCH_HOOK_NO_PDL) {
         h->no_pdl = value != 0;
-        for (int k = 0; k < 2; k++)
-            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        drop_graphs(h);
         return LBCH_OK;
     }
     if (hook == LBCH_HOOK_TWO_STEP) {
@@ -1573,14 +1650,12 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
         if (h->force_tile != (value != 0)) h->shape = 0;  // the shape index names the other kernel's list
         h->force_tile = value != 0;
         h->pair = false;  // either way a one-step kernel takes every step
-        for (int k = 0; k < 2; k++)
-            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        drop_graphs(h);
         return LBCH_OK;
     }
     if (hook == LBCH_HOOK_GENERAL_PATH) {
         h->force_general = value != 0;
-        for (int k = 0; k < 2; k++)
-            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        drop_graphs(h);
         return LBCH_OK;
     }
     if (hook == LBCH_HOOK_POISON) {  // every buffer of the next state filled with NaN (all bits set)
@@ -1604,8 +1679,7 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
     if (hook == LBCH_HOOK_TILE_SHAPE) {
         if (h->coupled || value < 0 || value >= n_active(h)) return fail(LBCH_EINVAL, "no tile shape %ld", value);
         (use_pair(h) ? h->pshape : h->shape) = (int)value;
-        for (int k = 0; k < 2; k++)
-            if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        drop_graphs(h);
         return LBCH_OK;
     }
     return fail(LBCH_EINVAL, "unknown hook %d", hook);

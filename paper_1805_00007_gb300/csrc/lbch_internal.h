@@ -78,6 +78,11 @@ struct lbch_handle {
     int t_off = 0, t_adv = 1;   // the next launch's step offset and counter advance (see Ctl)
     int debug_skip = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    struct TapeGraph {          // a captured taped replay (lb_ch_step_taped) for one starting parity
+        cudaGraphExec_t exec = nullptr;
+        void* tape = nullptr;
+        long nsteps = 0;
+    } tgraph[2];
     double* h_stage = nullptr;  // pinned host staging
     size_t h_stage_bytes = 0;
     // adjoint workspace (instance 0), allocated by the first lb_ch_adjoint_begin

@@ -629,7 +629,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) 
             }
             C post[9];
             collide9<C, TAU1, kShift>(ph, mu, Fx, Fy, ux, uy, g, K0, post);
-            if (kHalf) s_h0[e] = post[0];
+            if (kHalf) {
+                // the rest population takes what the half-rounded moving ones leave of phi (see the row sweep)
+                C rest = C(0);
+#pragma unroll
+                for (int q = 1; q < 9; q++) rest += cvt<C>(to_s<S>(post[q]));
+                s_h0[e] = -rest;
+            }
 #pragma unroll
             for (int q = QOFF; q < 9; q++) gp[(q - QOFF) * BW] = to_s<S>(post[q]);
         }

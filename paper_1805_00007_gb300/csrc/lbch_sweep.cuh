@@ -411,13 +411,21 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                     collide9<C, !GEN, kShift, !GEN>(Cs.pb, Cs.mb, Fxb, Fyb, node_u(X1b, Cs.y1, T), node_u(X2b, Cs.y2, T), gb,
                                               K0, pb_);
                     if constexpr (GEN && kHalf) {
-                        // the streamed populations are stored in half: they travel rounded (g*_0 stays at the
-                        // node, in float)
+                        // the streamed populations are stored in half: they travel rounded.  g*_0 stays at the
+                        // node, in float, and takes what the rounded ones leave of phi (g*_0 - phi = -sum of
+                        // the rounded g*_q, q > 0), so that the rounding moves no phi between nodes: sum phi is
+                        // kept exactly as in the other precisions (the same sum in the same order as the tile
+                        // kernel forms)
+                        C resta = C(0), restb = C(0);
 #pragma unroll
                         for (int q = 1; q < 9; q++) {
                             pa_[q] = (C)__half2float(__float2half_rn((float)pa_[q]));
                             pb_[q] = (C)__half2float(__float2half_rn((float)pb_[q]));
+                            resta += pa_[q];
+                            restb += pb_[q];
                         }
+                        pa_[0] = -resta;
+                        pb_[0] = -restb;
                     }
                     if constexpr (GEN) {
                         // g*_q reaches node x + c_q: the row above takes 2, 5, 6; this row 0, 1, 3; the row

@@ -107,6 +107,8 @@ def test_every_entry_point_rejects_null_arguments_without_gpu():
         "lb_ch_halo_bytes": lambda: lib.lb_ch_halo_bytes(None, ctypes.byref(ll)),
         "lb_ch_halo_export": lambda: lib.lb_ch_halo_export(None, 0, buf),
         "lb_ch_halo_import": lambda: lib.lb_ch_halo_import(None, 1, buf),
+        "lb_ch_step_taped": lambda: lib.lb_ch_step_taped(None, 4, buf),
+        "lb_ch_adjoint_sweep": lambda: lib.lb_ch_adjoint_sweep(None, buf, 0, 4),
     }
     for name, call in calls.items():
         assert call() == abi.LBCH_EINVAL, name

@@ -22,10 +22,10 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def _grad(p, phi0, nsteps, prec, segment=None, ref=None):
+def _grad(p, phi0, nsteps, prec, checkpoints=16, leaf=64, ref=None):
     x = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
     s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
-    phiT = evolve(x, s, p, nsteps, prec=prec, segment=segment)
+    phiT = evolve(x, s, p, nsteps, prec=prec, checkpoints=checkpoints, leaf=leaf)
     target = torch.tensor(phi0 if ref is None else ref, dtype=torch.float64)
     loss = 0.5 * torch.sum((phiT - target) ** 2)
     loss.backward()
@@ -48,19 +48,64 @@ def test_gpu_adjoint_matches_oracle_adjoint(case):
                    0, 1)
     phiT_ref, _ = oracle.simulate(p, phi0, nsteps)
     d_ref, s_ref = oracle.adjoint(p, phi0, nsteps, phiT_ref - phi0)
-    d64, s64, _, _ = _grad(p, phi0, nsteps, "f64", segment=7)
+    d64, s64, _, _ = _grad(p, phi0, nsteps, "f64", checkpoints=2, leaf=7)
     assert _rel(d64, d_ref) <= 1e-10
     assert abs(s64 - s_ref) <= 1e-10 * abs(s_ref)
-    d32, s32, _, _ = _grad(p, phi0, nsteps, "f32", segment=7)
+    d32, s32, _, _ = _grad(p, phi0, nsteps, "f32", checkpoints=2, leaf=7)
     assert _rel(d32, d_ref) <= 1e-4
     assert abs(s32 - s_ref) <= 1e-4 * abs(s_ref)
 
 
-def test_checkpoint_segments_do_not_change_the_gradient():
+def test_checkpoint_schedule_does_not_change_the_gradient():
+    """The reverse sweep recomputes the forward states it needs; whichever schedule it follows (one tape of the
+    whole run, binomial checkpointing over short tapes, one-step tapes with a few stored states, or none
+    besides the initial one) the recomputed phi are the same bits, and so is the gradient."""
     p, phi0, _ = wl.single_vortex(n=64, T=60)
-    a = _grad(p, phi0, 60, "f64", segment=60)
-    b = _grad(p, phi0, 60, "f64", segment=7)
-    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+    a = _grad(p, phi0, 60, "f64", checkpoints=0, leaf=60)
+    for ck, leaf in ((2, 7), (5, 1), (0, 9), (3, 64)):
+        b = _grad(p, phi0, 60, "f64", checkpoints=ck, leaf=leaf)
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1], (ck, leaf)
+
+
+def test_taped_replay_equals_single_steps():
+    """lb_ch_step_taped (captured in a graph for long replays) writes the same phi as lb_ch_tape_phi between
+    single steps, and leaves the same state; lb_ch_adjoint_sweep equals the adjoint steps one by one."""
+    p, phi0, _ = wl.single_vortex(n=48, T=50)
+    dev = torch.device("cuda")
+    n = 20
+    for prec, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+        with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(p, phi0, prec=prec) as b:
+            a.step(3)
+            b.step(3)
+            ta = torch.empty((n, 48, 48), dtype=tdt, device=dev)
+            tb = torch.empty_like(ta)
+            abi.lb_ch_step_taped(a.h, n, ta.data_ptr())
+            for k in range(n):
+                abi.lb_ch_tape_phi(b.h, tb[k].data_ptr())
+                b.step(1)
+            assert torch.equal(ta, tb) and np.array_equal(a.phi(), b.phi())
+            abi.lb_ch_step_taped(a.h, n, ta.data_ptr())  # the graph is replayed, not captured again
+            for k in range(n):
+                abi.lb_ch_tape_phi(b.h, tb[k].data_ptr())
+                b.step(1)
+            assert torch.equal(ta, tb) and np.array_equal(a.phi(), b.phi())
+            seed = torch.ones((48, 48), dtype=torch.float64, device=dev)
+            abi.lb_ch_adjoint_begin(a.h, seed.data_ptr())
+            abi.lb_ch_adjoint_begin(b.h, seed.data_ptr())
+            abi.lb_ch_adjoint_sweep(a.h, ta.data_ptr(), 23, n)
+            for k in range(n - 1, -1, -1):
+                abi.lb_ch_adjoint_step(b.h, tb[k].data_ptr(), 23 + k)
+            ga, gb = torch.empty_like(seed), torch.empty_like(seed)
+            sa = abi.lb_ch_adjoint_end(a.h, ga.data_ptr())
+            sb = abi.lb_ch_adjoint_end(b.h, gb.data_ptr())
+            assert torch.equal(ga, gb) and sa == sb
+
+
+def test_evolve_rejects_zero_scale():
+    p, phi0, _ = wl.single_vortex(n=32, T=10)
+    x = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
+    with pytest.raises(ValueError):
+        evolve(x, torch.tensor(0.0, dtype=torch.float64, requires_grad=True), p, 10)
 
 
 def test_state_save_load_round_trip():
