@@ -457,8 +457,10 @@ void release(lbch_handle* h)
     if (h->d_tabs_f) cudaFree(h->d_tabs_f);
     for (int k = 0; k < kMaxShapes; k++)
         if (h->ps[k].d_tile_begin) cudaFree(h->ps[k].d_tile_begin);
-    for (int k = 0; k < kSweepShapes; k++)
+    for (int k = 0; k < kSweepShapes; k++) {
         if (h->sw[k].d_tile_begin) cudaFree(h->sw[k].d_tile_begin);
+        if (h->sw[k].d_tiles) cudaFree(h->sw[k].d_tiles);
+    }
     for (int k = 0; k < kPairShapes; k++) {
         if (h->pr[k].d_tile_begin) cudaFree(h->pr[k].d_tile_begin);
         if (h->pr[k].d_ttabs) cudaFree(h->pr[k].d_ttabs);
@@ -925,6 +927,22 @@ lbch_status init_impl(const lbch_params* params, int n_inst, const double* phi0,
             CKI(cudaMalloc(&h->sw[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
             CKI(cudaMemcpy(h->sw[sk].d_tile_begin, sweep_begin[sk].data(), sizeof(int) * (n_inst + 1),
                            cudaMemcpyHostToDevice));
+            // the tiles of every instance, those that need the wall body (their collision rows or the rows
+            // their stencils read come within two rows of a wall) after all the others
+            const Shape sh = sweep_tile(sk);
+            std::vector<int4> inner, edge;
+            for (int k = 0; k < n_inst; k++) {
+                const lbch_params& p = params[k];
+                const int tiles_x = (p.nx + sh.tx - 1) / sh.tx, tiles_y = (p.ny + sh.ty - 1) / sh.ty;
+                for (int l = 0; l < tiles_x * tiles_y; l++) {
+                    const int x0 = (l % tiles_x) * sh.tx, y0 = (l / tiles_x) * sh.ty;
+                    const bool w = p.walls && (y0 < 2 || y0 + sh.ty + 1 > p.ny - 1);
+                    (w ? edge : inner).push_back(make_int4(k, x0, y0, w ? 1 : 0));
+                }
+            }
+            inner.insert(inner.end(), edge.begin(), edge.end());
+            CKI(cudaMalloc(&h->sw[sk].d_tiles, sizeof(int4) * inner.size()));
+            CKI(cudaMemcpy(h->sw[sk].d_tiles, inner.data(), sizeof(int4) * inner.size(), cudaMemcpyHostToDevice));
         }
         for (int sk = 0; sk < kPairShapes && prec != LBCH_F16S; sk++) {
             CKI(lbch_prepare_pair(h, sk));

@@ -60,6 +60,8 @@ struct lbch_handle {
         int grid = 0;           // persistent CTAs per step launch
         int grid_gen = 0;       // row sweep with the populations (the tile kernel uses grid)
         int* d_tile_begin = nullptr;
+        int4* d_tiles = nullptr;  // row-sweep configurations: each tile's (instance, x0, y0, wall body needed),
+                                  // interior tiles first (see lbch_sweep.cuh)
         void* d_ttabs = nullptr;  // two-step shapes: each tile's velocity tables, contiguous (see lbch_pair.cuh)
         CUtensorMap tm_g[2], tm_phi[2], tm_lo[2];
     } ps[kMaxShapes], sw[kSweepShapes], pr[kPairShapes];  // tile kernel shapes; row-sweep configurations

@@ -40,6 +40,8 @@ struct SweepArgs {
     InstDev inst0;          // the record of instance 0, for single-instance handles (read from the parameters)
     const InstDev* inst;
     const int* tile_begin;  // first tile of each instance (n_inst + 1 entries)
+    const int4* tiles;      // several instances: tile t's (instance, x0, y0, wall body needed), interior tiles
+                            // of every instance first and the tiles next to walls last (see the tile loop)
     const C* tabs;          // velocity tables in the arithmetic type
     int n_inst;
     int total_tiles;
@@ -208,16 +210,26 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     // the waits): X by stored column (clamped: the clamped columns feed halo lanes only), Y by row of the
     // instance's stored band, one row of the warp per lane.
     int k_t = 0, x0 = 0, y0 = 0;
+    bool w_t = false;  // the tile needs the wall body
     C X1m, X1a, X1b, X1p, X2m, X2a, X2b, X2p, ly1, ly2;
     auto locate = [&](int t) {
-        k_t = SINGLE ? 0 : find_inst(a.tile_begin, a.n_inst, t);
-        const int local = SINGLE ? t : t - a.tile_begin[k_t];
-        const int nx_t = SINGLE ? a.inst0.nx : a.inst[k_t].nx;
-        const int tab_t = SINGLE ? a.inst0.tab : a.inst[k_t].tab;
-        const int ylen = SINGLE ? a.inst0.ylen : a.inst[k_t].ylen;
-        const int tiles_x = (nx_t + L::W - 1) / L::W;
-        x0 = (local % tiles_x) * L::W;
-        y0 = (local / tiles_x) * TH;
+        int tab_t, ylen;
+        if constexpr (SINGLE) {
+            const int tiles_x = (a.inst0.nx + L::W - 1) / L::W;
+            x0 = (t % tiles_x) * L::W;
+            y0 = (t / tiles_x) * TH;
+            w_t = a.inst0.walls && (y0 < 2 || y0 + TH + 1 > a.inst0.ny - 1);
+            tab_t = a.inst0.tab;
+            ylen = a.inst0.ylen;
+        } else {
+            const int4 tt = a.tiles[t];
+            k_t = tt.x;
+            x0 = tt.y;
+            y0 = tt.z;
+            w_t = tt.w != 0;
+            tab_t = a.inst[k_t].tab;
+            ylen = a.inst[k_t].ylen;
+        }
         const C* tX1 = a.tabs + tab_t;
         const C* tX2 = tX1 + a.pitch;
         const C* tY1 = tX2 + a.pitch;
@@ -235,7 +247,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         fence_mbar_init();
         s_tile_inst = -1;
         if ((int)blockIdx.x < a.total_tiles) {  // instance data are constant: read before the dependency wait
-            const int k = SINGLE ? 0 : find_inst(a.tile_begin, a.n_inst, blockIdx.x);
+            const int k = SINGLE ? 0 : a.tiles[blockIdx.x].x;
             s_I = SINGLE ? a.inst0 : a.inst[k];
             s_tile_inst = k;
         }
@@ -244,16 +256,23 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
 
     // producer: thread 0 issues the boxes of tile t into stage s
     auto issue = [&](int t, int s) {
-        const int k = SINGLE ? 0 : find_inst(a.tile_begin, a.n_inst, t);
-        const InstDev& I = pick_inst<SINGLE>(a.inst0, a.inst[k]);
-        const int local = SINGLE ? t : t - a.tile_begin[k];
-        const int tiles_x = (I.nx + L::W - 1) / L::W;
-        const int bx = (local % tiles_x) * L::W, by = (local / tiles_x) * TH;
+        int bx, by, row0;
+        if constexpr (SINGLE) {
+            const int tiles_x = (a.inst0.nx + L::W - 1) / L::W;
+            bx = (t % tiles_x) * L::W;
+            by = (t / tiles_x) * TH;
+            row0 = a.inst0.row0;
+        } else {
+            const int4 tt = a.tiles[t];
+            bx = tt.y;
+            by = tt.z;
+            row0 = a.inst[tt.x].row0;
+        }
         fence_proxy_async();
         mbar_expect_tx(&mbar[s], L::PBOX_BYTES + L::LBOX_BYTES);
         // box column origin: domain bx - 4 is stored column bx (a multiple of 4: 16-byte aligned)
-        tma_load_2d(stage(s), &tm_phi, bx, I.row0 + by - 3, &mbar[s]);
-        if (FF && !GEN) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, bx, I.row0 + by, &mbar[s]);
+        tma_load_2d(stage(s), &tm_phi, bx, row0 + by - 3, &mbar[s]);
+        if (FF && !GEN) tma_load_2d(stage(s) + L::OFF_L, &tm_lo, bx, row0 + by, &mbar[s]);
     };
 
     // Launched as a programmatic dependent of the previous step: nothing that step writes (phi, the step
@@ -549,11 +568,11 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                         for (int q = QOFF; q < 9; q++) go[(long long)(q - QOFF) * pitch] = to_s<S>(va_[q]);
                     }
                     if (va) {
-                        store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xa, yo, hia);
+                        store_images(a.phi_out, row0, pitch, nx, ny, I.walls, xa, yo, hia);
                         store_g_images<S, C, QOFF, WALLS>(a.g_out, row0, pitch, nx, ny, xa, yo, va_);
                     }
                     if (vb) {
-                        store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xb, yo, hib);
+                        store_images(a.phi_out, row0, pitch, nx, ny, I.walls, xb, yo, hib);
                         store_g_images<S, C, QOFF, WALLS>(a.g_out, row0, pitch, nx, ny, xb, yo, vb_);
                     }
                 }
@@ -624,8 +643,8 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                         a.phi_out[node] = hia;
                         if (FF) a.lo_out[node] = loa;
                     }
-                    if (va) store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xa, yo, hia);
-                    if (vb) store_images(a.phi_out, row0, pitch, nx, ny, (int)WALLS, xb, yo, hib);
+                    if (va) store_images(a.phi_out, row0, pitch, nx, ny, I.walls, xa, yo, hia);
+                    if (vb) store_images(a.phi_out, row0, pitch, nx, ny, I.walls, xb, yo, hib);
                 }
             }
         };
@@ -689,13 +708,30 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         }
         // (this barrier also keeps the warps of a CTA in step from tile to tile, which measured faster than
         // letting them drift: 324 against 334 us per step at 4096^2 with the populations)
-        if (tid == 0 && k_t != s_tile_inst) {
-            s_I = a.inst[k_t];
-            s_tile_inst = k_t;
-            s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
+        if (k_t != s_tile_inst) {  // (the same for every thread: k_t and s_tile_inst are block-uniform)
+            // the tile's instance record, copied by the whole block (with one thread copying it word by word,
+            // a serial stall at every change of instance -- every tile in the interior-first order -- the
+            // ragged shear ensemble ran 60.7 instead of 65.2 GLUPS)
+            const int* src = reinterpret_cast<const int*>(a.inst + k_t);
+            int* dst = reinterpret_cast<int*>(&s_I);
+            for (int w = tid; w < (int)(sizeof(InstDev) / 4); w += NW * 32) dst[w] = src[w];
+            __syncthreads();
+            if (tid == 0) {
+                s_tile_inst = k_t;
+                s_T = (C)vel_t(s_I.vel, s_I.Tper, s_time + a.t_off);
+            }
         }
         __syncthreads();
-        if (pick_inst<SINGLE>(a.inst0, s_I).walls) sweep(std::true_type(), s);
+        // The wall body (bounce-back rows, mu and D of the ghost rows taken from the mirror rows) is needed only
+        // by a tile whose collision rows y0 - 1 .. y0 + TH, or the rows their stencils read, come within two rows
+        // of a wall: elsewhere every operand is a domain value and the periodic body gives the same bits (the
+        // ghost images it writes follow the instance's boundary).  The choice is per tile, so that the warps of
+        // a block run one body; for several instances the tile order puts every interior tile first and the
+        // wall tiles last, so that the blocks of an SM mostly run the same body (two bodies at once measured
+        // slower than the wall body alone: their code does not stay in the instruction caches together).  A
+        // single instance keeps one body for all its tiles: a per-tile choice there cost 6% on the step with
+        // the populations (57.6 against 54.6 GLUPS at 4096^2, same box), through the code it generates.
+        if (SINGLE ? (bool)a.inst0.walls : w_t) sweep(std::true_type(), s);
         else sweep(std::false_type(), s);
         if (GEN && !ring_ok && lane == 0) atomicOr(&a.ctl->err, 1u);
         __syncthreads();  // the stage is free again

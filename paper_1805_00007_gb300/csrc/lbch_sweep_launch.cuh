@@ -15,6 +15,7 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     a.inst0 = h->inst[0];
     a.inst = h->d_inst;
     a.tile_begin = ps.d_tile_begin;
+    a.tiles = ps.d_tiles;
     a.tabs = tables<C>(h);
     a.n_inst = h->n_inst;
     a.total_tiles = ps.total_tiles;

@@ -83,11 +83,13 @@ def test_taped_replay_equals_single_steps():
             for k in range(n):
                 abi.lb_ch_tape_phi(b.h, tb[k].data_ptr())
                 b.step(1)
+            torch.cuda.synchronize()  # the handles' own streams do not synchronise with torch's
             assert torch.equal(ta, tb) and np.array_equal(a.phi(), b.phi())
             abi.lb_ch_step_taped(a.h, n, ta.data_ptr())  # the graph is replayed, not captured again
             for k in range(n):
                 abi.lb_ch_tape_phi(b.h, tb[k].data_ptr())
                 b.step(1)
+            torch.cuda.synchronize()
             assert torch.equal(ta, tb) and np.array_equal(a.phi(), b.phi())
             seed = torch.ones((48, 48), dtype=torch.float64, device=dev)
             abi.lb_ch_adjoint_begin(a.h, seed.data_ptr())
@@ -150,6 +152,7 @@ def test_state_load_rejects_a_buffer_of_another_layout():
         assert ei.value.status == abi.LBCH_EINVAL
     with abi.Simulation(p_small, f_small, prec="f32") as sim:
         zeros = torch.zeros_like(buf)
+        torch.cuda.synchronize()  # the fill runs on torch's stream, the load on the handle's
         with pytest.raises(abi.LbchError) as ei:
             abi.lb_ch_state_load(sim.h, zeros.data_ptr())
         assert ei.value.status == abi.LBCH_EINVAL and "does not hold a saved state" in str(ei.value)

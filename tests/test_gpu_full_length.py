@@ -112,18 +112,20 @@ def _rt_run(p, phi0, prec, nsteps):
 
 def test_rayleigh_taylor_long_runs():
     """The workload's 2e4 steps.  At Re = 3000 (tau_f = 0.506, near the single-relaxation-time limit) the run
-    stays finite, conserves sum(phi) (summed in FP64) and keeps the mirror symmetry x -> -x of its interface
+    stays finite, conserves sum(phi) (summed in FP64; to rounding of the stored populations, which are plain
+    floats on the FP32 path) and keeps the mirror symmetry x -> -x of its interface
     through 15000 steps in both precisions, and then stops being finite in both (between 15000 and 15500
     steps, after the interface has broken up): a limit of the flow solver at this viscosity, not of the
     precision.  At Re = 1000 (tau_f = 0.518) all 2e4 steps are finite."""
     p, phi0 = wl.rayleigh_taylor()
-    for prec, sym_tol in (("f64", 1e-9), ("f32", 1e-2)):
+    # sum(phi) drifts by float rounding of the stored populations on the FP32 path (plain float storage)
+    for prec, sym_tol, mass_tol in (("f64", 1e-9, 1e-10), ("f32", 1e-2, 1e-4)):
         phi, sym, drift = _rt_run(p, phi0, prec, 15000)
         print(f"rayleigh-taylor Re 3000 {prec} 15000 steps: mass drift {drift:.2e}, mirror asymmetry {sym:.2e}, "
               f"phi in [{phi.min():.4f}, {phi.max():.4f}]")
-        assert np.all(np.isfinite(phi)) and drift <= 1e-5 and sym <= sym_tol
+        assert np.all(np.isfinite(phi)) and drift <= mass_tol and sym <= sym_tol
     p1, f1 = wl.rayleigh_taylor(Re=1000.0)
-    for prec, sym_tol in (("f64", 1e-9), ("f32", 1e-2)):
+    for prec, sym_tol, mass_tol in (("f64", 1e-9, 1e-10), ("f32", 1e-2, 1e-4)):
         phi, sym, drift = _rt_run(p1, f1, prec, 20000)
         print(f"rayleigh-taylor Re 1000 {prec} 20000 steps: mass drift {drift:.2e}, mirror asymmetry {sym:.2e}")
-        assert np.all(np.isfinite(phi)) and drift <= 1e-5 and sym <= sym_tol
+        assert np.all(np.isfinite(phi)) and drift <= mass_tol and sym <= sym_tol
