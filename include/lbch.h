@@ -103,8 +103,9 @@ typedef struct {
     int walls;           /* 0: periodic in y; 1: moving bounce-back walls at y = -1/2 and ny - 1/2 */
     int model;           /* 1: Model I; 2: Model II (Eq. mark3 force added); 3: Model II with the complete
                             diffusive-scale force of Eq. F2-1, whose time derivatives are backward
-                            differences over one step (zero at step 0); steps with the tile kernel, not
-                            with the adjoint or the coupled flow */
+                            differences over one step (zero at step 0); steps with the row sweep's
+                            Model III build (its two unrolled configurations) or the tile kernel, not
+                            with the adjoint, the coupled flow or slabs */
     int vel;             /* lbch_vel */
     int nvort;           /* vortex count of the deformation field */
     double phiA, phiB;   /* bulk values of phi */

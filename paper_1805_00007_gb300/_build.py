@@ -10,7 +10,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbch.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("lbch_api.cu", "lbch_sweep_f32.cu", "lbch_sweep_f64.cu",
-                                          "lbch_sweep_f16s.cu", "lbch_noalloc.cu", "lbch_pair.cu", "lbch_probe.cu")]
+                                          "lbch_sweep_f16s.cu", "lbch_sweep_f32_m3.cu", "lbch_sweep_f64_m3.cu",
+                                          "lbch_sweep_f16s_m3.cu", "lbch_noalloc.cu", "lbch_pair.cu",
+                                          "lbch_probe.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(ROOT, "include", "lbch.h")]
 

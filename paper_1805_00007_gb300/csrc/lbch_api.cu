@@ -152,10 +152,12 @@ cudaError_t launch_step_t(lbch_handle* h, int parity)
 // two-step kernel is selected (and applies), it takes the steps two at a time and the one-step kernel
 // takes an odd last step.
 inline bool use_pair(const lbch_handle* h) { return h->pair && pair_ok(h); }
-inline bool use_sweep(const lbch_handle* h) { return !h->force_tile && !h->coupled && !h->model3; }
+inline bool use_sweep(const lbch_handle* h) { return !h->force_tile && !h->coupled; }
+// sweep configurations built for the handle (those with Model III: the two unrolled ones)
+inline int n_sweep_shapes(const lbch_handle* h) { return h->model3 ? kM3SweepShapes : kSweepShapes; }
 inline int n_active(const lbch_handle* h)
 {
-    return h->coupled ? 1 : (use_pair(h) ? kPairShapes : (use_sweep(h) ? kSweepShapes : n_shapes(h->prec)));
+    return h->coupled ? 1 : (use_pair(h) ? kPairShapes : (use_sweep(h) ? n_sweep_shapes(h) : n_shapes(h->prec)));
 }
 inline const lbch_handle::PerShape& active_ps(const lbch_handle* h)
 {
@@ -180,6 +182,13 @@ inline void drop_graphs(lbch_handle* h)  // graphs captured earlier launch anoth
 
 cudaError_t launch_sweep(lbch_handle* h, int parity)
 {
+    if (h->model3) {
+        switch (h->prec) {
+        case LBCH_F64: return lbch_launch_sweep_f64_m3(h, parity);
+        case LBCH_F32: return lbch_launch_sweep_f32_m3(h, parity);
+        default: return lbch_launch_sweep_f16s_m3(h, parity);
+        }
+    }
     switch (h->prec) {
     case LBCH_F64: return lbch_launch_sweep_f64(h, parity);
     case LBCH_F32: return lbch_launch_sweep_f32(h, parity);
@@ -189,6 +198,13 @@ cudaError_t launch_sweep(lbch_handle* h, int parity)
 
 cudaError_t prepare_sweep(lbch_handle* h, int k)
 {
+    if (h->model3 && k < kM3SweepShapes) {
+        switch (h->prec) {
+        case LBCH_F64: return lbch_prepare_sweep_f64_m3(h, k);
+        case LBCH_F32: return lbch_prepare_sweep_f32_m3(h, k);
+        default: return lbch_prepare_sweep_f16s_m3(h, k);
+        }
+    }
     switch (h->prec) {
     case LBCH_F64: return lbch_prepare_sweep_f64(h, k);
     case LBCH_F32: return lbch_prepare_sweep_f32(h, k);
@@ -1571,7 +1587,7 @@ lbch_status lb_ch_tune(lbch_handle* h, int steps, int* tile_x, int* tile_y)
     struct Cand { bool tile, pair; int shape; };
     std::vector<Cand> cands;
     if (!h->coupled) {
-        for (int k = 0; k < kSweepShapes && !h->model3; k++) cands.push_back({false, false, k});
+        for (int k = 0; k < n_sweep_shapes(h); k++) cands.push_back({false, false, k});
         if (!(h->prec == LBCH_F16S && h->tau1 && !h->force_general))
             for (int k = 0; k < n_shapes(h->prec); k++) cands.push_back({true, false, k});
         for (int k = 0; k < kPairShapes && pair_ok(h); k++) cands.push_back({false, true, k});

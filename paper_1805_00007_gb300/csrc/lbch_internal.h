@@ -15,6 +15,7 @@ struct Shape { int tx, ty, nt; };  // output nodes of a tile, threads per block
 struct SweepCfg { int ty, nw; bool compact; };
 constexpr SweepCfg kSweep[4] = {{12, 4, false}, {6, 4, false}, {6, 2, true}, {3, 4, true}};
 constexpr int kSweepShapes = 4;
+constexpr int kM3SweepShapes = 2;  // configurations built for handles with a Model III instance
 constexpr int kSweepW = 56;
 inline Shape sweep_tile(int k) { return Shape{kSweepW, kSweep[k].ty * kSweep[k].nw, 32 * kSweep[k].nw}; }
 
@@ -50,7 +51,7 @@ struct lbch_handle {
     bool walls = false;         // an instance has walls
     bool slab = false;          // a slab of a larger periodic grid (lb_ch_init_slab): halos imported between steps
     bool tuning = false;        // lb_ch_tune is stepping the handle (a slab may then take several steps per call)
-    bool model3 = false;        // an instance uses Model III (the tile kernel then steps the handle)
+    bool model3 = false;        // an instance uses Model III (the row sweep's Model III build, or the tile kernel)
     bool need_time = false;     // an instance's step depends on the step index (time factor, Model III)
     void* H[2] = {nullptr, nullptr};  // Model III: H of Eq. F2-1's time derivatives, 2 planes, arithmetic type
     size_t c_elem() const { return prec == LBCH_F64 ? 8 : 4; }
@@ -125,6 +126,13 @@ LBCH_INTERNAL cudaError_t lbch_launch_sweep_f16s(lbch_handle* h, int parity);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f64(lbch_handle* h, int k);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f32(lbch_handle* h, int k);
 LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f16s(lbch_handle* h, int k);
+// The same for handles with a Model III instance (lbch_sweep_*_m3.cu; configurations 0 and 1).
+LBCH_INTERNAL cudaError_t lbch_launch_sweep_f64_m3(lbch_handle* h, int parity);
+LBCH_INTERNAL cudaError_t lbch_launch_sweep_f32_m3(lbch_handle* h, int parity);
+LBCH_INTERNAL cudaError_t lbch_launch_sweep_f16s_m3(lbch_handle* h, int parity);
+LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f64_m3(lbch_handle* h, int k);
+LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f32_m3(lbch_handle* h, int k);
+LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f16s_m3(lbch_handle* h, int k);
 // Two-step launches and set-up (lbch_pair.cu); pshape names a pair_shape().
 LBCH_INTERNAL cudaError_t lbch_launch_pair(lbch_handle* h, int parity);
 LBCH_INTERNAL cudaError_t lbch_prepare_pair(lbch_handle* h, int k);

@@ -55,6 +55,9 @@ struct SweepArgs {
     int need_time;          // some instance needs the step index (a time-dependent flow)
     S* g_out;               // populations (GEN): g[(row * nq + plane) * pitch + column]
     int rows;               // stored rows of the population arrays
+    const C* H_in;          // M3 (Model III): H(t - 1) of Eq. F2-1's time derivatives, two planes (x, y) of
+    C* H_out;               // rows x pitch values; H(t) is written for the warp's own nodes and their images
+    long long H_plane;      // values per plane of H
 };
 
 template <typename P, typename S, bool FF, int TY, int NW, bool GEN>
@@ -177,7 +180,12 @@ __device__ __forceinline__ const InstDev& pick_inst(const InstDev& param, const 
     else return shared;
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT, bool SINGLE>
+// M3: some instance uses Model III (the complete diffusive-scale force of Eq. F2-1): at every collision the
+// force takes the backward difference of H = (2 tau - 1 + 3K) F1 + 3 c_s^2 eta K grad mu over one step
+// (reading R15), with H(t - 1) read at the collided node and H(t) stored for the warp's own nodes, as the
+// tile kernel does.
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT, bool SINGLE,
+          bool M3 = false>
 __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     ch_sweep_kernel(const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lo,
                     const __grid_constant__ CUtensorMap tm_grow, const __grid_constant__ CUtensorMap tm_lorow,
@@ -311,7 +319,9 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         const Consts<C>& K0 = consts<C>(I);
         const C beta = K0.beta, kappa = K0.kappa, phiA = K0.phiA, phiB = K0.phiB;
         const C ra = K0.a, rb = K0.b, K = K0.K;
-        const bool model2 = I.model == 2;
+        const bool model2 = M3 ? I.model >= 2 : I.model == 2;  // D = div(phi u) is needed (Models II, III)
+        [[maybe_unused]] const bool model3 = M3 && I.model == 3;
+        [[maybe_unused]] const bool first = M3 && s_time + a.t_off == 0;  // no H(t - 1) at the first step
         const C T = s_T;
         const int pitch = a.pitch;
         // this lane's column pair in the box, from the warp's first row (box row warp TY = domain wy0 - 3)
@@ -422,8 +432,28 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
                         grad9(Cs.dR, Cs.da, B.db, A.db, B.dR, B.da, A.dR, A.da, gDxb, gDyb);
                     }
                     C Fxa, Fya, Fxb, Fyb;
-                    node_force(Cs.pa, gmxa, gmya, gDxa, gDya, model2, ra, rb, K, Fxa, Fya);
-                    node_force(Cs.pb, gmxb, gmyb, gDxb, gDyb, model2, ra, rb, K, Fxb, Fyb);
+                    if (M3 && model3) {
+                        // H(t - 1) at the collided nodes: rows -1 .. ny hold it (images one deep); other rows
+                        // and columns past the stored ones collide for no output and read nothing
+                        const bool hrow = !first && yc >= -1 && yc <= ny;
+                        const long long hn = (row0 + yc) * pitch + sa;
+                        const C Hpxa = hrow && sa < pitch ? a.H_in[hn] : C(0);
+                        const C Hpya = hrow && sa < pitch ? a.H_in[a.H_plane + hn] : C(0);
+                        const C Hpxb = hrow && sa + 1 < pitch ? a.H_in[hn + 1] : C(0);
+                        const C Hpyb = hrow && sa + 1 < pitch ? a.H_in[a.H_plane + hn + 1] : C(0);
+                        C Hxa, Hya, Hxb, Hyb;
+                        node_force_full(Cs.pa, gmxa, gmya, gDxa, gDya, Hpxa, Hpya, first, ra, rb, K, K0.cF1, K0.cmu,
+                                        Fxa, Fya, Hxa, Hya);
+                        node_force_full(Cs.pb, gmxb, gmyb, gDxb, gDyb, Hpxb, Hpyb, first, ra, rb, K, K0.cF1, K0.cmu,
+                                        Fxb, Fyb, Hxb, Hyb);
+                        if (yc >= wy0 && yc < wy0 + TY && yc < ny) {  // the warp's own nodes
+                            if (va) store_h(a.H_out, a.H_plane, (int)row0, pitch, nx, ny, I.walls, xa, yc, Hxa, Hya);
+                            if (vb) store_h(a.H_out, a.H_plane, (int)row0, pitch, nx, ny, I.walls, xb, yc, Hxb, Hyb);
+                        }
+                    } else {
+                        node_force(Cs.pa, gmxa, gmya, gDxa, gDya, model2, ra, rb, K, Fxa, Fya);
+                        node_force(Cs.pb, gmxb, gmyb, gDxb, gDyb, model2, ra, rb, K, Fxb, Fyb);
+                    }
                     C pa_[9], pb_[9];
                     collide9<C, !GEN, kShift, !GEN>(Cs.pa, Cs.ma, Fxa, Fya, node_u(X1a, Cs.y1, T), node_u(X2a, Cs.y2, T), ga,
                                               K0, pa_);

@@ -3,10 +3,10 @@
 
 cudaError_t lbch_launch_sweep_f16s(lbch_handle* h, int parity)
 {
-    return lbch::launch_sweep_t<float, __half, float, false>(h, parity);
+    return lbch::launch_sweep_t<float, __half, float, false, false>(h, parity);
 }
 
 cudaError_t lbch_prepare_sweep_f16s(lbch_handle* h, int k)
 {
-    return lbch::prepare_sweep_t<float, __half, float, false>(h, k);
+    return lbch::prepare_sweep_t<float, __half, float, false, false>(h, k);
 }

@@ -3,10 +3,10 @@
 
 cudaError_t lbch_launch_sweep_f32(lbch_handle* h, int parity)
 {
-    return lbch::launch_sweep_t<float, float, float, true>(h, parity);
+    return lbch::launch_sweep_t<float, float, float, true, false>(h, parity);
 }
 
 cudaError_t lbch_prepare_sweep_f32(lbch_handle* h, int k)
 {
-    return lbch::prepare_sweep_t<float, float, float, true>(h, k);
+    return lbch::prepare_sweep_t<float, float, float, true, false>(h, k);
 }

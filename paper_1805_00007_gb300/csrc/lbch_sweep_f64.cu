@@ -3,10 +3,10 @@
 
 cudaError_t lbch_launch_sweep_f64(lbch_handle* h, int parity)
 {
-    return lbch::launch_sweep_t<double, double, double, false>(h, parity);
+    return lbch::launch_sweep_t<double, double, double, false, false>(h, parity);
 }
 
 cudaError_t lbch_prepare_sweep_f64(lbch_handle* h, int k)
 {
-    return lbch::prepare_sweep_t<double, double, double, false>(h, k);
+    return lbch::prepare_sweep_t<double, double, double, false, false>(h, k);
 }

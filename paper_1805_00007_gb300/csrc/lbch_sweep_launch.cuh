@@ -6,7 +6,7 @@
 
 namespace lbch {
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT, bool M3>
 cudaError_t launch_sweep_v(lbch_handle* h, int parity)
 {
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
@@ -29,6 +29,9 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     a.need_time = h->need_time;
     a.g_out = static_cast<S*>(h->g[parity ^ 1]);
     a.rows = h->rows;
+    a.H_in = M3 ? static_cast<const C*>(h->H[parity]) : nullptr;
+    a.H_out = M3 ? static_cast<C*>(h->H[parity ^ 1]) : nullptr;
+    a.H_plane = (long long)h->rows * h->pitch;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(GEN ? ps.grid_gen : ps.grid);
     cfg.blockDim = dim3(NW * 32);
@@ -41,39 +44,48 @@ cudaError_t launch_sweep_v(lbch_handle* h, int parity)
     cfg.numAttrs = 1;
     // a single instance's record is read from the launch parameters (ch_sweep_kernel's SINGLE form)
     if (h->n_inst == 1)
-        return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true>, ps.tm_phi[parity],
-                                  ps.tm_lo[parity], h->tm_grow[parity], h->tm_lorow[parity], a);
-    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false>, ps.tm_phi[parity],
+        return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true, M3>,
+                                  ps.tm_phi[parity], ps.tm_lo[parity], h->tm_grow[parity], h->tm_lorow[parity], a);
+    return cudaLaunchKernelEx(&cfg, ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false, M3>, ps.tm_phi[parity],
                               ps.tm_lo[parity], h->tm_grow[parity], h->tm_lorow[parity], a);
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool COMPACT>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool COMPACT, bool M3>
 cudaError_t launch_sweep_g(lbch_handle* h, int parity)
 {
-    return sweep_gen(h) ? launch_sweep_v<C, S, P, FF, TY, NW, true, COMPACT>(h, parity)
-                        : launch_sweep_v<C, S, P, FF, TY, NW, false, COMPACT>(h, parity);
+    return sweep_gen(h) ? launch_sweep_v<C, S, P, FF, TY, NW, true, COMPACT, M3>(h, parity)
+                        : launch_sweep_v<C, S, P, FF, TY, NW, false, COMPACT, M3>(h, parity);
 }
 
-template <typename C, typename S, typename P, bool FF>
+// M3 (Model III handles) is built for the two unrolled configurations only (kM3SweepShapes).
+template <typename C, typename S, typename P, bool FF, bool M3>
 cudaError_t launch_sweep_t(lbch_handle* h, int parity)
 {
-    switch (h->shape) {
-    case 0: return launch_sweep_g<C, S, P, FF, 12, 4, false>(h, parity);
-    case 1: return launch_sweep_g<C, S, P, FF, 6, 4, false>(h, parity);
-    case 2: return launch_sweep_g<C, S, P, FF, 6, 2, true>(h, parity);
-    default: return launch_sweep_g<C, S, P, FF, 3, 4, true>(h, parity);
+    if constexpr (M3) {
+        switch (h->shape) {
+        case 0: return launch_sweep_g<C, S, P, FF, 12, 4, false, true>(h, parity);
+        case 1: return launch_sweep_g<C, S, P, FF, 6, 4, false, true>(h, parity);
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (h->shape) {
+        case 0: return launch_sweep_g<C, S, P, FF, 12, 4, false, false>(h, parity);
+        case 1: return launch_sweep_g<C, S, P, FF, 6, 4, false, false>(h, parity);
+        case 2: return launch_sweep_g<C, S, P, FF, 6, 2, true, false>(h, parity);
+        default: return launch_sweep_g<C, S, P, FF, 3, 4, true, false>(h, parity);
+        }
     }
 }
 
 // Dynamic shared memory of one sweep kernel and the persistent grid that fits the device.
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN, bool COMPACT, bool M3>
 cudaError_t prepare_sweep_v(lbch_handle* h, int k)
 {
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
-    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false>;
+    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false, M3>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true>,
+        e = cudaFuncSetAttribute(ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true, M3>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -86,20 +98,26 @@ cudaError_t prepare_sweep_v(lbch_handle* h, int k)
     return cudaSuccess;
 }
 
-template <typename C, typename S, typename P, bool FF, int TY, int NW, bool COMPACT>
+template <typename C, typename S, typename P, bool FF, int TY, int NW, bool COMPACT, bool M3>
 cudaError_t prepare_sweep_g(lbch_handle* h, int k)
 {
-    cudaError_t e = prepare_sweep_v<C, S, P, FF, TY, NW, true, COMPACT>(h, k);
-    if (e == cudaSuccess && h->tau1) e = prepare_sweep_v<C, S, P, FF, TY, NW, false, COMPACT>(h, k);
+    cudaError_t e = prepare_sweep_v<C, S, P, FF, TY, NW, true, COMPACT, M3>(h, k);
+    if (e == cudaSuccess && h->tau1) e = prepare_sweep_v<C, S, P, FF, TY, NW, false, COMPACT, M3>(h, k);
     return e;
 }
 
-template <typename C, typename S, typename P, bool FF>
+template <typename C, typename S, typename P, bool FF, bool M3>
 cudaError_t prepare_sweep_t(lbch_handle* h, int k)
 {
-    return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4, false>(h, k)
-         : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4, false>(h, k)
-         : k == 2 ? prepare_sweep_g<C, S, P, FF, 6, 2, true>(h, k) : prepare_sweep_g<C, S, P, FF, 3, 4, true>(h, k);
+    if constexpr (M3) {
+        return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4, false, true>(h, k)
+             : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4, false, true>(h, k) : cudaErrorInvalidValue;
+    } else {
+        return k == 0 ? prepare_sweep_g<C, S, P, FF, 12, 4, false, false>(h, k)
+             : k == 1 ? prepare_sweep_g<C, S, P, FF, 6, 4, false, false>(h, k)
+             : k == 2 ? prepare_sweep_g<C, S, P, FF, 6, 2, true, false>(h, k)
+                      : prepare_sweep_g<C, S, P, FF, 3, 4, true, false>(h, k);
+    }
 }
 
 }  // namespace lbch

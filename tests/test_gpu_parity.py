@@ -308,28 +308,45 @@ def test_dependent_launch_gives_the_same_bits(prec):
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5), ("f16s", 2e-3)])
 def test_model3_matches_oracle(prec, tol):
     """Model III (the complete force of Eq. F2-1, time derivatives as one-step backward differences) on a
-    periodic time-dependent flow at tau_g = 0.8 and 1.3 and on a ragged ensemble with walls that mixes
-    Models II and III; graph replays and single launches (the stored H crosses both)."""
+    periodic time-dependent flow at tau_g = 0.8, 1 (no populations kept) and 1.3, and on a ragged ensemble
+    with walls that mixes Models II and III; graph replays and single launches (the stored H crosses both).
+    Both kernel forms -- the row sweep (its Model III build, the default) in each of its configurations and
+    the tile kernel -- against the oracle and against each other bit for bit (on the half path at tau_g = 1
+    the tile kernel streams half-rounded populations, so there the two agree to the tolerance)."""
     nsteps = 131 if prec != "f16s" else 50
-    for tau in (0.8, 1.3):
+
+    def run(params, fields, form, shape=0):
+        with abi.Simulation(params, fields, prec=prec) as sim:
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, 1 if form == "tile" else 0)
+            abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_SHAPE, shape)
+            assert sim.kernel()["form"] in (("tile", "tile_tau1") if form == "tile" else ("sweep", "sweep_tau1"))
+            sim.step(nsteps)
+            return [sim.phi(k) for k in range(len(sim.params))]
+
+    for tau in (0.8, 1.0, 1.3):
         p = wl.make_params(nx=45, ny=37, vel=wl.VEL_VORTEX, U0=0.05, Tper=60.0, M=0.02, sigma=0.03, W=3.0,
                            rhoB=0.4, tau=tau, model=3)
         phi0 = np.clip(wl.random_smooth_phi(45, 37, seed=5) + 0.6 * wl.circle_phi(45, 37, 20.0, 18.0, 9.0, 3.0) - 0.3,
                        0, 1)
         ref, _ = oracle.simulate(p, phi0, nsteps)
         with abi.Simulation(p, phi0, prec=prec) as sim:
-            assert sim.kernel()["form"] == "tile"
-            sim.step(nsteps)
-            assert _maxdiff(sim.phi(), ref) <= tol
+            assert sim.kernel()["form"] in ("sweep", "sweep_tau1")  # the untuned default
+        sweeps = [run(p, phi0, "sweep", k)[0] for k in range(2)]
+        tile = run(p, phi0, "tile")[0]
+        for got in sweeps + [tile]:
+            assert _maxdiff(got, ref) <= tol
+        assert np.array_equal(sweeps[0], sweeps[1])
+        if not (prec == "f16s" and tau == 1.0):
+            assert np.array_equal(sweeps[0], tile)
     ens = wl.shear_ensemble(n_inst=3, sides=(37, 64, 16), seed=6, tau=0.9)
     ens = [(dict(q, shear=q["shear"] * 30.0, Ustar=q["Ustar"] * 30.0, model=3 if k != 1 else 2), f)
            for k, (q, f) in enumerate(ens)]
-    params, fields = zip(*ens)
-    with abi.Simulation(list(params), list(fields), prec=prec) as sim:
-        sim.step(nsteps)
-        for k, (q, f) in enumerate(ens):
-            ref, _ = oracle.simulate(q, f, nsteps)
-            assert _maxdiff(sim.phi(k), ref) <= tol
+    params, fields = [q for q, _ in ens], [f for _, f in ens]
+    by_form = {form: run(params, fields, form) for form in ("sweep", "tile")}
+    for k, (q, f) in enumerate(ens):
+        ref, _ = oracle.simulate(q, f, nsteps)
+        assert _maxdiff(by_form["sweep"][k], ref) <= tol
+        assert np.array_equal(by_form["sweep"][k], by_form["tile"][k])
 
 
 def test_model3_state_save_load_round_trip():
