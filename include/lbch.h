@@ -282,7 +282,8 @@ lbch_status lb_ch_adjoint_sweep(lbch_handle* h, const void* tape, long n0, long 
  * step launches are ordinary stream-ordered launches instead of programmatic dependents of the previous
  * step (whose launch and prologue overlap that step's tail); the results are the same bits.  With hook
  * LBCH_HOOK_POISON (value ignored), every device buffer the next step writes -- phi, its low part, the
- * populations and Model III's H of the next state, or on coupled handles f, g, u, p and mu -- is filled
+ * populations and Model III's H of the next state, or on coupled handles f, g, u, p, mu and phi of the
+ * current state (which a coupled step forms from the populations) -- is filled
  * with all bits set (NaN in every storage type), stream-ordered before the next step; a step that reads
  * a cell it did not write first carries NaN into phi.  Not for production use. */
 enum {

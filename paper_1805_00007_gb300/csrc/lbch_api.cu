@@ -278,17 +278,32 @@ ns::NsArgs<C> ns_args(lbch_handle* h, int parity)
     return a;
 }
 
-// One coupled step: the flow's u and p; both collisions with push streaming; phi(t+1).
+// One coupled step: phi = sum g of the current state with the flow's u and p; both collisions with push
+// streaming.  phi of the new state is formed by the next step (or by coupled_phi before an observation).
 template <typename C>
 cudaError_t launch_ns_t(lbch_handle* h, int parity)
 {
     ns::NsArgs<C> a = ns_args<C>(h, parity);
     const int tiles = ns::tiles_of(a.nx, a.ny);
-    const int nb = (int)(((long long)a.nx * a.ny + 255) / 256);
     ns::fields_kernel<C><<<tiles, ns::NT, 0, h->stream>>>(a);
     ns::collide_kernel<C><<<tiles, ns::NT, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+// phi of the current state of a coupled handle into its phi array (the steps leave it to the next step).
+template <typename C>
+cudaError_t coupled_phi_t(lbch_handle* h)
+{
+    ns::NsArgs<C> a = ns_args<C>(h, cur_buf(h));
+    const int nb = (int)(((long long)a.nx * a.ny + 255) / 256);
     ns::phi_kernel<C><<<nb, 256, 0, h->stream>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t coupled_phi(lbch_handle* h)
+{
+    if (!h->coupled) return cudaSuccess;
+    return h->prec == LBCH_F64 ? coupled_phi_t<double>(h) : coupled_phi_t<float>(h);
 }
 
 // The flow's u and p of the current state (for observation).
@@ -1214,6 +1229,7 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out)
         *out = (double)h->n;
         return LBCH_OK;
     }
+    CK(coupled_phi(h));
     if (what == LBCH_OBS_PHI) {
         const InstDev& d = h->inst[inst];
         int parity = cur_buf(h);
@@ -1278,6 +1294,7 @@ lbch_status lb_ch_observe_all(lbch_handle* h, int what, double* out)
 {
     if (!h || !out) return fail(LBCH_EINVAL, "NULL handle or output");
     if (what < LBCH_OBS_MASS || what > LBCH_OBS_MIN) return fail(LBCH_EINVAL, "observable %d is not a scalar", what);
+    CK(coupled_phi(h));
     lbch_status s = run_reduce(h);
     if (s != LBCH_OK) return s;
     std::vector<double> r((size_t)RED_NV * h->n_inst);
@@ -1701,6 +1718,8 @@ lbch_status lb_ch_test_hook(lbch_handle* h, int hook, long value)
             CK(cudaMemsetAsync(p + (size_t)nxt * 9 * N * e, 0xFF, 9 * N * e, h->stream));         // f
             CK(cudaMemsetAsync(p + (18 + (size_t)nxt * 9) * N * e, 0xFF, 9 * N * e, h->stream));  // g
             CK(cudaMemsetAsync(p + 36 * N * e, 0xFF, 4 * N * e, h->stream));                      // u, p, mu
+            // phi of the current state: the next step forms it from the populations before reading it
+            CK(cudaMemsetAsync(h->phi[nxt ^ 1], 0xFF, (size_t)h->rows * h->pitch * h->phi_elem, h->stream));
         } else {
             const size_t cells = (size_t)h->rows * h->pitch;
             CK(cudaMemsetAsync(h->g[nxt], 0xFF, cells * h->nq * h->g_elem, h->stream));

@@ -13,12 +13,13 @@
 // (Eq. t0-phiu) plus the Eq. mark3 term.  Walls: halfway bounce-back for both lattices at rest; stencil
 // operands at ghost rows take the mirror values.
 //
-// One step is three kernels.  The first two work on 32 x 8 tiles of nodes, one node per thread, with the
-// stencil operands staged in shared memory.  fields_kernel stages phi on tile + 2, forms mu on tile + 1
-// and gives mu, u and p at the tile's nodes.  collide_kernel stages phi (and phi u) on tile + 2 and mu and
-// p on tile + 1, forms D = div(phi u) on tile + 1 for Model II (kept there rather than stored), collides
-// both lattices and pushes them to the neighbours (bounce-back at walls).  phi_kernel sums
-// phi(t+1) = sum_q g_q into the handle's padded phi array (which observations read).  A stencil operand
+// One step is two kernels on 32 x 8 tiles of nodes, one node per thread, with the stencil operands staged
+// in shared memory.  fields_kernel sums phi = sum_q g_q on tile + 2 (storing it for the tile's nodes),
+// forms mu on tile + 1 and gives mu, u and p at the tile's nodes.  collide_kernel stages phi (and phi u)
+// on tile + 2 and mu and p on tile + 1, forms D = div(phi u) on tile + 1 for Model II (kept there rather
+// than stored), collides both lattices and pushes them to the neighbours (bounce-back at walls).  phi of
+// the state a step leaves is therefore formed by the next step's fields kernel; phi_kernel forms it on
+// demand before an observation.  A stencil operand
 // at a ghost row beyond a wall takes the value of the mirror node: a staged operand is read at that node,
 // and a derived one is formed at the mirror row of the tile's region.
 #pragma once
@@ -118,14 +119,25 @@ __device__ __forceinline__ void tile_origin(int nx, int& x0, int& y0)
     y0 = ((int)blockIdx.x / tiles_x) * TY;
 }
 
-// phi on tile + 2 into s2 (and, with jx, the components of phi u there)
-template <typename C>
+// phi = sum_q g_q (Eq. macroscopicg) at node k of the [q][node] populations g, summed in the order of q
+template <typename C> __device__ __forceinline__ C sum_g(const C* g, long long N, long long k)
+{
+    C s = C(0);
+#pragma unroll
+    for (int q = 0; q < 9; q++) s += g[q * N + k];
+    return s;
+}
+
+// phi on tile + 2 into s2 (and, with jx, the components of phi u there).  FROM_G: phi is summed from the
+// populations of the current state instead of read from the phi array (the fields kernel, which then
+// stores it for the tile's own nodes).
+template <typename C, bool FROM_G = false>
 __device__ __forceinline__ void stage_phi(const NsArgs<C>& a, int x0, int y0, C* s2, C* jx, C* jy)
 {
     for (int e = threadIdx.x; e < N2; e += NT) {
         const int j = e / W2, i = e - j * W2;
         const int2 v = node_at(a.nx, a.ny, a.walls, x0 - 2 + i, y0 - 2 + j);
-        const C ph = phi_xy(a, v.x, v.y);
+        const C ph = FROM_G ? sum_g(a.g_in, (long long)a.nx * a.ny, (long long)v.y * a.nx + v.x) : phi_xy(a, v.x, v.y);
         s2[e] = ph;
         if (jx) {
             const int k = v.y * a.nx + v.x;
@@ -146,20 +158,24 @@ __device__ __forceinline__ void form_mu(const NsArgs<C>& a, int y0, const C* s2,
     }
 }
 
-// mu and the flow's velocity and pressure at every node
+// phi = sum_q g_q of the current state, then mu and the flow's velocity and pressure at every node; phi is
+// stored into the current state's phi array for the collision kernel that follows and for observation (so a
+// step is two kernels: the sum of the populations streamed by the previous step is formed here, where its
+// neighbourhood is staged anyway)
 template <typename C>
 __global__ void __launch_bounds__(NT) fields_kernel(NsArgs<C> a)
 {
     __shared__ C s2[N2], mu1[N1];
     int x0, y0;
     tile_origin(a.nx, x0, y0);
-    stage_phi<C>(a, x0, y0, s2, nullptr, nullptr);
+    stage_phi<C, true>(a, x0, y0, s2, nullptr, nullptr);
     __syncthreads();
     form_mu(a, y0, s2, mu1);
     __syncthreads();
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, x = x0 + tx, y = y0 + ty;
     if (x >= a.nx || y >= a.ny) return;
     const int c1 = (ty + 1) * W1 + tx + 1, c2 = (ty + 2) * W2 + tx + 2;
+    a.phi_in[(long long)(a.row0 + y) * a.pitch + GC + x] = s2[c2];
     const long long N = (long long)a.nx * a.ny;  // plane size of the [q][node] arrays
     const int k = y * a.nx + x;
     const C gmx = sgx<C, W1>(mu1, c1), gmy = sgy<C, W1>(mu1, c1), lap = slap<C, W1>(mu1, c1);
@@ -298,7 +314,7 @@ __global__ void __launch_bounds__(NT) collide_kernel(NsArgs<C> a)
     }
 }
 
-// phi(t+1) = sum_q g_q into the padded phi array; one thread per node
+// phi = sum_q g_q of the current state into its padded phi array (before an observation); one thread per node
 template <typename C>
 __global__ void phi_kernel(NsArgs<C> a)
 {
@@ -306,10 +322,7 @@ __global__ void phi_kernel(NsArgs<C> a)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const int y = k / a.nx, x = k - y * a.nx;
-    C s = C(0);
-#pragma unroll
-    for (int q = 0; q < 9; q++) s += a.g_out[q * N + k];
-    a.phi_out[(long long)(a.row0 + y) * a.pitch + GC + x] = s;
+    a.phi_in[(long long)(a.row0 + y) * a.pitch + GC + x] = sum_g(a.g_in, N, k);
 }
 
 // initial state: g = g_eq(phi0, mu0, 0), f = f_eq(0, rho(phi0), 0) = 0; phi = phi0
