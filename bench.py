@@ -50,7 +50,7 @@ GENERAL_BYTES_PER_LU = {"f32": 80, "f64": 160, "f16s": 44}
 # DRAM bytes (read + write) per launch of the headline kernel, from an ncu capture of these sources
 # (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the kernel sources still hash the same
 # and the autotuner chose that kernel, else null.
-TRAFFIC = {"hash": "8becc9145ea4650e", "bytes_per_launch": 668416,
+TRAFFIC = {"hash": "02c6054cec75bea3", "bytes_per_launch": 669440,
            "kernel": "ch_pair_kernel<float,float,tile=32x14,NT=1024>"}
 KERNEL_SOURCES = ("lbch_kernels.cuh", "lbch_sweep.cuh", "lbch_sweep_launch.cuh", "lbch_pair.cuh")
 
@@ -191,11 +191,12 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def sweep_params(n, tau=1.0):
-    """A square rotation workload of side n (the Zalesak flow and parameters scaled to n)."""
-    pp = wl.make_params(nx=n, ny=n, vel=wl.VEL_ROTATION, U0=0.02, xc=n / 2, yc=n / 2, half=n / 2,
+def sweep_params(n, tau=1.0, ny=None):
+    """A rotation workload of n x ny nodes (square by default; the Zalesak flow and parameters scaled to n)."""
+    ny = n if ny is None else ny
+    pp = wl.make_params(nx=n, ny=ny, vel=wl.VEL_ROTATION, U0=0.02, xc=n / 2, yc=ny / 2, half=n / 2,
                         W=4.0, M=0.005, tau=tau)
-    return pp, wl.circle_phi(n, n, n / 2, 5 * n / 8, n / 4, 4.0)
+    return pp, wl.circle_phi(n, ny, n / 2, 5 * ny / 8, min(n, ny) / 4, 4.0)
 
 
 def steps_per_launch(k: dict) -> int:
@@ -282,9 +283,10 @@ def run_case(case, nsteps, tile=0, form="sweep"):
             nodes = sim.info()["nodes"]
         print(json.dumps({"case": case, "steps": nsteps, "instances": len(ens), "nodes": nodes, "kernel": kname}))
         return
-    prec, n = parts[0], int(parts[1])
+    prec = parts[0]
+    n, ny = (int(v) for v in parts[1].split("x")) if "x" in parts[1] else (int(parts[1]), None)
     tau = float(parts[2]) if len(parts) > 2 else 1.0
-    pp, f0 = sweep_params(n, tau)
+    pp, f0 = sweep_params(n, tau, ny)
     with abi.Simulation(pp, f0, prec=prec, tune=tile < 0) as sim:
         if tile >= 0:
             abi.lb_ch_test_hook(sim.h, abi.LBCH_HOOK_TILE_KERNEL, int(form == "tile"))
@@ -347,7 +349,7 @@ def main():
     ap.add_argument("--size-sweep", action="store_true",
                     help="time the step on 1024^2 .. 16384^2 grids (tau_g = 0.8) instead of the benchmark")
     ap.add_argument("--case", default=None,
-                    help="profiling case PREC_N[_TAU] (e.g. f32_4096, f32_4096_0.8), rt_PREC (the coupled "
+                    help="profiling case PREC_N[xNY][_TAU] (e.g. f32_4096, f32_4096_0.8, f32_8192x1024_0.8), rt_PREC (the coupled "
                          "Rayleigh-Taylor grid), adj_N (adjoint steps on the N^2 single vortex) or "
                          "ens_PREC_N[_TAU] (the first N instances of the shear ensemble): init and "
                          "--case-steps steps of that case only")

@@ -106,3 +106,59 @@ def test_noalloc_counts_non_finite_values_and_leaves_them_out():
     _check(_noalloc(phi, phi0), {abi.LBCH_OBS_MASS: float(phi.sum()),
                                  abi.LBCH_OBS_ERR_L2: float(np.sqrt(((phi - phi0) ** 2).sum() / (phi0 ** 2).sum())),
                                  abi.LBCH_OBS_MAX: float(phi.max()), abi.LBCH_OBS_MIN: float(phi.min())})
+
+
+_THREADED = r"""
+import sys, threading
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_1805_00007_gb300 import abi
+from paper_1805_00007_gb300 import workloads as wl
+p, phi0, _ = wl.zalesak(n=64)
+with abi.Simulation(p, phi0, prec="f64") as sim:
+    sim.step(20)
+    phi = sim.phi()
+    mass = sim.observe(abi.LBCH_OBS_MASS)
+dev = torch.device("cuda", 0)
+d_phi = torch.from_numpy(phi).to(dev)
+d_phi0 = torch.from_numpy(phi0).to(dev)
+outs = [torch.full((6,), float("nan"), dtype=torch.float64, device=dev) for _ in range(8)]
+streams = [torch.cuda.Stream(device=dev) for _ in range(8)]
+torch.cuda.synchronize()
+errors = []
+go = threading.Barrier(8)
+def work(k):
+    try:
+        go.wait()  # every thread makes its first call at once
+        abi.lb_ch_field_stats_noalloc(d_phi.data_ptr(), d_phi0.data_ptr(), 64, 64, 64, outs[k].data_ptr(),
+                                      streams[k].cuda_stream)
+        streams[k].synchronize()
+    except Exception as e:
+        errors.append(repr(e))
+threads = [threading.Thread(target=work, args=(k,)) for k in range(8)]
+for t in threads: t.start()
+for t in threads: t.join()
+assert not errors, errors
+# the calls ran on different streams and shared the scratch array, so they may have raced (as documented);
+# one more call alone must give the right answer
+out = torch.full((6,), float("nan"), dtype=torch.float64, device=dev)
+abi.lb_ch_field_stats_noalloc(d_phi.data_ptr(), d_phi0.data_ptr(), 64, 64, 64, out.data_ptr(), 0)
+torch.cuda.synchronize()
+o = out.cpu().numpy()
+assert abs(o[0] - mass) <= 1e-12 * abs(mass) and o[5] == 0.0, o
+print("ok")
+"""
+
+
+def test_noalloc_first_calls_from_several_threads_at_once(tmp_path):
+    """The first calls in a fresh process, from eight host threads at once, all set up the scratch address
+    without error (the per-context cache is filled under a lock), and the next call is correct."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "threaded.py"
+    script.write_text(_THREADED)
+    r = subprocess.run([sys.executable, str(script), root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
