@@ -10,8 +10,8 @@
 // The partial sums are written to a static __device__ array of LBCH_NOALLOC_MAX_BLOCKS x 6 doubles
 // (48 KiB) that every GPU which loads this library holds until the process exits.  Host code never
 // uses the array's name as an address: the first call in a CUDA context (with that context's device
-// current) asks the runtime for the array's device address (cudaGetSymbolAddress) and caches it for
-// that context, under a lock, so concurrent first calls from several host threads are safe and a
+// current) asks the runtime for the array's device address (cudaGetSymbolAddress) and caches it under the
+// context's unique ID, under a lock, so concurrent first calls from several host threads are safe and a
 // context created later (after cudaDeviceReset, say) gets its own lookup.  That first call should
 // happen before any stream capture.  All calls share the array; each call overwrites the slots it uses
 // before reading them, so nothing needs clearing, but calls whose kernels overlap on the GPU (on
@@ -92,37 +92,43 @@ __global__ void __launch_bounds__(NA_NT) na_final_kernel(const double* partials,
         for (int k = 0; k < NA_NV; k++) out[k] = v[k];
 }
 
-// Device address of the partials array in each CUDA context it has been looked up in.  The context (not
-// the device ordinal) is the key: an address belongs to the context it was taken in.
-typedef int (*CtxGetCurrentFn)(void**);  // cuCtxGetCurrent, reached through the runtime's entry-point query
+// Device address of the partials array in each CUDA context it has been looked up in.  The key is the
+// context's unique ID (cuCtxGetId), not its handle or the device ordinal: an address belongs to the context
+// it was taken in, and a context created later (after cudaDeviceReset, say) may reuse an old handle value
+// but never an old ID.
+typedef int (*CtxGetCurrentFn)(void**);                      // cuCtxGetCurrent
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);        // cuCtxGetId
 constexpr int kMaxContexts = 64;
-struct AddrEntry { void* ctx; double* addr; };
+struct AddrEntry { unsigned long long ctx_id; double* addr; };
 AddrEntry g_addr[kMaxContexts];
 int g_n_addr = 0;
 std::mutex g_addr_mu;
 
-CtxGetCurrentFn ctx_get_current()
+void* driver_fn(const char* name)
 {
-    static CtxGetCurrentFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<CtxGetCurrentFn>(p);
-    });
-    return fn;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return p;
+    return nullptr;
 }
 
 // The partials array's address in the current context (set-up on first use in that context).
 cudaError_t partials_addr(double** out)
 {
+    static CtxGetCurrentFn get_ctx = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        get_ctx = reinterpret_cast<CtxGetCurrentFn>(driver_fn("cuCtxGetCurrent"));
+        get_id = reinterpret_cast<CtxGetIdFn>(driver_fn("cuCtxGetId"));
+    });
     *out = nullptr;
     void* ctx = nullptr;
-    CtxGetCurrentFn get = ctx_get_current();
-    if (!get || get(&ctx) != 0 || !ctx) {
-        // no context to key on: look the address up on every call instead of caching it
+    unsigned long long id = 0;
+    if (!get_ctx || !get_id || get_ctx(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) {
+        // nothing to key on: look the address up on every call instead of caching it
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         *out = static_cast<double*>(p);
@@ -130,11 +136,11 @@ cudaError_t partials_addr(double** out)
     }
     std::lock_guard<std::mutex> lock(g_addr_mu);
     for (int i = 0; i < g_n_addr; i++)
-        if (g_addr[i].ctx == ctx) { *out = g_addr[i].addr; return cudaSuccess; }
+        if (g_addr[i].ctx_id == id) { *out = g_addr[i].addr; return cudaSuccess; }
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess || !p) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
-    if (g_n_addr < kMaxContexts) g_addr[g_n_addr++] = AddrEntry{ctx, static_cast<double*>(p)};
+    if (g_n_addr < kMaxContexts) g_addr[g_n_addr++] = AddrEntry{id, static_cast<double*>(p)};
     *out = static_cast<double*>(p);
     return cudaSuccess;
 }

@@ -109,7 +109,8 @@ class SlabStack:
         pr = abi.PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         dev = torch.device("cuda", torch.cuda.current_device())
         if stream is None:  # one stream for every slab: the exports, imports and steps are then stream-ordered
-            stream = torch.cuda.current_stream(dev).cuda_stream
+            self._own_stream = torch.cuda.Stream(device=dev)
+            stream = self._own_stream.cuda_stream
         self.handles = [abi.lb_ch_init_slab(self.params, y0, n, halo_field(phi0, y0, n), pr, stream)
                         for y0, n in self.rows]
         nb = abi.lb_ch_halo_bytes(self.handles[0])
@@ -162,34 +163,53 @@ class SlabStack:
 
 class SlabRank:
     """This rank's slab of one periodic grid (one process per GPU): the CUDA library steps it, and the halos
-    travel between ranks by `exchange` (NCCL sends and receives into each GPU's own memory) before every
-    step.  The library enqueues on torch's current stream, which the process group orders its transfers
-    after."""
+    travel between ranks by `exchange` before every step -- NCCL sends and receives into each GPU's own
+    memory, or, with a gloo process group (staging=True, the default for gloo), through pinned host buffers.
+    The library, the staging copies and the process group share one stream of the rank's own."""
 
-    def __init__(self, params: dict, phi0, prec="f64", rank: int = 0, world: int = 1, group=None):
+    def __init__(self, params: dict, phi0, prec="f64", rank: int = 0, world: int = 1, group=None,
+                 staging: bool | None = None):
         import torch
         from . import abi
         self.rank, self.world, self.group = rank, world, group
         self.params = dict(params)
         self.y0, self.ny = slab_rows(int(params["ny"]), world)[rank]
         dev = torch.device("cuda", torch.cuda.current_device())
-        stream = torch.cuda.current_stream(dev).cuda_stream
+        # the library's work, the staging copies and the process group's transfers all run on this stream
+        # (torch's default stream would be the legacy NULL stream, which the library replaces by one of its own)
+        self.stream = torch.cuda.Stream(device=dev)
         pr = abi.PRECISIONS[prec] if isinstance(prec, str) else int(prec)
-        self.h = abi.lb_ch_init_slab(self.params, self.y0, self.ny, halo_field(phi0, self.y0, self.ny), pr, stream)
+        self.h = abi.lb_ch_init_slab(self.params, self.y0, self.ny, halo_field(phi0, self.y0, self.ny), pr,
+                                     self.stream.cuda_stream)
         nb = abi.lb_ch_halo_bytes(self.h)
         self.bufs = [torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(4)]
+        if staging is None:
+            import torch.distributed as dist
+            staging = world > 1 and dist.get_backend(group) == "gloo"
+        self.host = [torch.empty(nb, dtype=torch.uint8).pin_memory() for _ in range(4)] if staging else None
         self._abi = abi
 
     def step(self, nsteps: int):
+        import torch
         abi = self._abi
         send_lo, send_hi, recv_lo, recv_hi = self.bufs
-        for _ in range(int(nsteps)):
-            abi.lb_ch_halo_export(self.h, 0, send_lo.data_ptr())
-            abi.lb_ch_halo_export(self.h, 1, send_hi.data_ptr())
-            exchange(send_lo, send_hi, recv_lo, recv_hi, self.rank, self.world, self.group)
-            abi.lb_ch_halo_import(self.h, 0, recv_lo.data_ptr())
-            abi.lb_ch_halo_import(self.h, 1, recv_hi.data_ptr())
-            abi.lb_ch_step(self.h, 1)
+        with torch.cuda.stream(self.stream):
+            for _ in range(int(nsteps)):
+                abi.lb_ch_halo_export(self.h, 0, send_lo.data_ptr())
+                abi.lb_ch_halo_export(self.h, 1, send_hi.data_ptr())
+                if self.host is None:
+                    exchange(send_lo, send_hi, recv_lo, recv_hi, self.rank, self.world, self.group)
+                else:
+                    h_slo, h_shi, h_rlo, h_rhi = self.host
+                    h_slo.copy_(send_lo)
+                    h_shi.copy_(send_hi)
+                    self.stream.synchronize()
+                    exchange(h_slo, h_shi, h_rlo, h_rhi, self.rank, self.world, self.group)
+                    recv_lo.copy_(h_rlo)
+                    recv_hi.copy_(h_rhi)
+                abi.lb_ch_halo_import(self.h, 0, recv_lo.data_ptr())
+                abi.lb_ch_halo_import(self.h, 1, recv_hi.data_ptr())
+                abi.lb_ch_step(self.h, 1)
         return self
 
     def phi(self):

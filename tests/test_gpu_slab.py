@@ -89,3 +89,41 @@ def test_slab_rejections():
     with abi.Simulation(p, phi0, prec="f64") as sim:  # halos belong to slab handles
         with pytest.raises(abi.LbchError):
             abi.lb_ch_halo_bytes(sim.h)
+
+
+def _rank_main(rank, world, port, prec, nsteps, out_path):
+    """One process per slab, both on the one GPU here (the kernels of one rank never wait on another's: the
+    halos move between steps through the host, by gloo)."""
+    import os
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    p, phi0 = CASES["vortex"]()
+    sl = shard.SlabRank(p, phi0, prec=prec, rank=rank, world=world)
+    sl.step(nsteps)
+    parts = [None] * world
+    dist.all_gather_object(parts, (sl.y0, sl.phi()))
+    sl.close()
+    if rank == 0:
+        np.save(out_path, np.concatenate([ph for _, ph in sorted(parts, key=lambda t: t[0])], axis=0))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_ranks_equal_the_whole_grid(tmp_path, world):
+    """shard.SlabRank, the one-slab-per-rank driver, in separate processes exchanging through a gloo process
+    group: the gathered slabs equal the whole-grid handle bit for bit."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    out = tmp_path / "phi.npy"
+    nsteps = 15
+    mp.start_processes(_rank_main, args=(world, port, "f32", nsteps, str(out)), nprocs=world, join=True,
+                       start_method="spawn")
+    p, phi0 = CASES["vortex"]()
+    assert np.array_equal(np.load(out), _whole(p, phi0, nsteps, "f32"))
