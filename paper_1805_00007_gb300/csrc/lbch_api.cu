@@ -64,9 +64,11 @@ static_assert(kGraphChunk % 4 == 0, "a graph of two-step launches must hold an e
 // times them on the handle's own problem and keeps the fastest; the first one is the default.  Every
 // TX divides 32 and every TY divides 16, so one storage layout serves all shapes.
 constexpr int NT = 256;
-constexpr Shape kShapes64[3] = {{32, 8, 256}, {16, 8, 256}, {32, 8, 512}};
+// FP64 32 x 16 with 512 threads: 128 tiles at 256^2, at most one per SM, and the least recomputed halo of
+// the shapes that fit that count (the FP64 step is bound by the FP64 pipe, so the halo's share counts).
+constexpr Shape kShapes64[4] = {{32, 8, 256}, {16, 8, 256}, {32, 8, 512}, {32, 16, 512}};
 constexpr Shape kShapesF[4] = {{32, 16, 256}, {32, 8, 256}, {16, 8, 256}, {32, 16, 768}};
-inline int n_shapes(int prec) { return prec == LBCH_F64 ? 3 : 4; }
+inline int n_shapes(int) { return 4; }
 inline Shape shape_of(int prec, int k) { return prec == LBCH_F64 ? kShapes64[k] : kShapesF[k]; }
 
 
@@ -238,7 +240,9 @@ cudaError_t prepare_step(lbch_handle* h, int k)
     switch (h->prec) {
     case LBCH_F64:
         return k == 0 ? prepare_step_t<double, double, double, 32, 8>(h, k)
-             : k == 1 ? prepare_step_t<double, double, double, 16, 8>(h, k) : prepare_step_t<double, double, double, 32, 8, 512>(h, k);
+             : k == 1 ? prepare_step_t<double, double, double, 16, 8>(h, k)
+             : k == 2 ? prepare_step_t<double, double, double, 32, 8, 512>(h, k)
+                      : prepare_step_t<double, double, double, 32, 16, 512>(h, k);
     case LBCH_F32:
         return k == 0 ? prepare_step_t<float, float, float, 32, 16>(h, k)
              : k == 1 ? prepare_step_t<float, float, float, 32, 8>(h, k)
@@ -323,7 +327,9 @@ cudaError_t launch_step(lbch_handle* h, int parity)
     switch (h->prec) {
     case LBCH_F64:
         return k == 0 ? launch_step_t<double, double, double, 32, 8>(h, parity)
-             : k == 1 ? launch_step_t<double, double, double, 16, 8>(h, parity) : launch_step_t<double, double, double, 32, 8, 512>(h, parity);
+             : k == 1 ? launch_step_t<double, double, double, 16, 8>(h, parity)
+             : k == 2 ? launch_step_t<double, double, double, 32, 8, 512>(h, parity)
+                      : launch_step_t<double, double, double, 32, 16, 512>(h, parity);
     case LBCH_F32:
         return k == 0 ? launch_step_t<float, float, float, 32, 16>(h, parity)
              : k == 1 ? launch_step_t<float, float, float, 32, 8>(h, parity)
