@@ -57,8 +57,13 @@ struct NvtxRange {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
     } while (0)
 
-constexpr int kGraphChunk = 64;  // steps per captured graph (even, so the ping-pong parity is preserved)
-static_assert(kGraphChunk % 4 == 0, "a graph of two-step launches must hold an even number of launches");
+// Steps per captured graph (a multiple of 4, so that a graph of two-step launches holds an even number of
+// launches and ends in the buffer it starts from).  A call of many steps replays graphs of kGraphBig steps
+// and finishes with graphs of kGraphChunk: a launch that follows a graph cannot overlap its tail (the
+// programmatic dependence holds only within a graph), so fewer, longer graphs leave fewer such gaps.
+constexpr int kGraphChunk = 64;
+constexpr int kGraphBig = 512;
+static_assert(kGraphChunk % 4 == 0 && kGraphBig % kGraphChunk == 0, "graph sizes");
 
 // Tile shapes the step kernel is built for (output nodes per tile; 256 threads per CTA).  lb_ch_tune
 // times them on the handle's own problem and keeps the fastest; the first one is the default.  Every
@@ -177,7 +182,8 @@ inline Shape active_tile(const lbch_handle* h)
 inline void drop_graphs(lbch_handle* h)  // graphs captured earlier launch another kernel or shape
 {
     for (int k = 0; k < 2; k++) {
-        if (h->graph[k]) { cudaGraphExecDestroy(h->graph[k]); h->graph[k] = nullptr; }
+        for (int z = 0; z < 2; z++)
+            if (h->graph[z][k]) { cudaGraphExecDestroy(h->graph[z][k]); h->graph[z][k] = nullptr; }
         if (h->tgraph[k].exec) { cudaGraphExecDestroy(h->tgraph[k].exec); h->tgraph[k] = lbch_handle::TapeGraph(); }
     }
 }
@@ -483,7 +489,8 @@ void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<doub
 void release(lbch_handle* h)
 {
     for (int k = 0; k < 2; k++) {
-        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        for (int z = 0; z < 2; z++)
+            if (h->graph[z][k]) cudaGraphExecDestroy(h->graph[z][k]);
         if (h->tgraph[k].exec) cudaGraphExecDestroy(h->tgraph[k].exec);
         if (h->g[k]) cudaFree(h->g[k]);
         if (h->phi[k]) cudaFree(h->phi[k]);
@@ -1189,17 +1196,19 @@ lbch_status lb_ch_step(lbch_handle* h, long nsteps)
     while (nsteps > 0) {
         int parity = cur_buf(h);
         if (!no_graph && !h->debug_skip && nsteps >= kGraphChunk) {
-            if (!h->graph[parity]) {
+            const int z = nsteps >= kGraphBig ? 1 : 0, chunk = z ? kGraphBig : kGraphChunk;
+            cudaGraphExec_t& gx = h->graph[z][parity];
+            if (!gx) {
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
                 cudaError_t e = cudaSuccess;
                 // step k of the graph is the counter + k; only the last launch advances the counter.  With
                 // the two-step kernel, launch s takes steps 2s and 2s + 1; the chunk's launch count is even,
                 // so the graph ends in the buffer it starts from, as the one-step graph does.
-                const int per = two ? 2 : 1, launches = kGraphChunk / per;
+                const int per = two ? 2 : 1, launches = chunk / per;
                 for (int s = 0; s < launches && e == cudaSuccess; s++) {
                     h->t_off = s * per;
-                    h->t_adv = s == launches - 1 ? kGraphChunk : 0;
+                    h->t_adv = s == launches - 1 ? chunk : 0;
                     e = two ? lbch_launch_pair(h, parity ^ (s & 1)) : launch_step(h, parity ^ (s & 1));
                 }
                 h->t_off = 0;
@@ -1207,13 +1216,13 @@ lbch_status lb_ch_step(lbch_handle* h, long nsteps)
                 cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
                 if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(e, "step launch during capture"); }
                 if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-                e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+                e = cudaGraphInstantiate(&gx, g, 0);
                 cudaGraphDestroy(g);
-                if (e != cudaSuccess) { h->graph[parity] = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+                if (e != cudaSuccess) { gx = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
             }
-            CK(cudaGraphLaunch(h->graph[parity], h->stream));
-            h->n += kGraphChunk;
-            nsteps -= kGraphChunk;
+            CK(cudaGraphLaunch(gx, h->stream));
+            h->n += chunk;
+            nsteps -= chunk;
         } else if (two && nsteps >= 2) {
             CK(launch_pair_now(h));
             nsteps -= 2;

@@ -80,7 +80,7 @@ struct lbch_handle {
     int flip = 0;               // the state of step n is in buffer (n & 1) ^ flip (two-step launches toggle it)
     int t_off = 0, t_adv = 1;   // the next launch's step offset and counter advance (see Ctl)
     int debug_skip = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [chunk size][starting parity]
     struct TapeGraph {          // a captured taped replay (lb_ch_step_taped) for one starting parity
         cudaGraphExec_t exec = nullptr;
         void* tape = nullptr;

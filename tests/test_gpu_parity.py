@@ -156,13 +156,21 @@ def test_f16s_parity():
     assert abs(mass - phi0.sum()) <= 1e-5 * phi0.sum()
 
 
-def test_steps_split_across_calls_equal_one_call():
-    """Graph replays, single launches and their mix advance the same state (bitwise in FP64)."""
-    p, phi0, _ = wl.single_vortex(n=64, T=100)
-    with abi.Simulation(p, phi0, prec="f64") as a, abi.Simulation(p, phi0, prec="f64") as b:
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_steps_split_across_calls_equal_one_call(prec):
+    """Graph replays (of 512 and of 64 steps), single launches and their mix advance the same state, bit for
+    bit, and the time-dependent flow sees the right step index throughout (FP32 at 64^2 runs the two-step
+    kernel, FP64 a one-step form)."""
+    p, phi0, _ = wl.single_vortex(n=64, T=400)
+    with abi.Simulation(p, phi0, prec=prec) as a, abi.Simulation(p, phi0, prec=prec) as b:
         a.step(131)
         for k in (1, 64, 3, 63):
             b.step(k)
+        assert np.array_equal(a.phi(), b.phi())
+        a.step(1150)  # two graphs of 512, two of 64, then single launches
+        for k in (600, 37, 513):
+            b.step(k)
+        assert a.observe(abi.LBCH_OBS_STEP) == b.observe(abi.LBCH_OBS_STEP) == 1281
         assert np.array_equal(a.phi(), b.phi())
 
 
