@@ -296,7 +296,7 @@ cudaError_t launch_ns_t(lbch_handle* h, int parity)
     ns::NsArgs<C> a = ns_args<C>(h, parity);
     const int tiles = ns::tiles_of(a.nx, a.ny);
     ns::fields_kernel<C><<<tiles, ns::NT, 0, h->stream>>>(a);
-    ns::collide_kernel<C><<<tiles, ns::NT, 0, h->stream>>>(a);
+    ns::collide_kernel<C><<<tiles, ns::NTC, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
 
