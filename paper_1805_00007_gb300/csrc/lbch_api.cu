@@ -71,9 +71,12 @@ static_assert(kGraphChunk % 4 == 0 && kGraphBig % kGraphChunk == 0, "graph sizes
 constexpr int NT = 256;
 // FP64 32 x 16 with 512 threads: 128 tiles at 256^2, at most one per SM, and the least recomputed halo of
 // the shapes that fit that count (the FP64 step is bound by the FP64 pipe, so the halo's share counts).
-constexpr Shape kShapes64[4] = {{32, 8, 256}, {16, 8, 256}, {32, 8, 512}, {32, 16, 512}};
+// FP64 32 x 14 with 576 threads: 152 tiles at 256^2, one per SM, with a little less halo per SM than
+// 32 x 16; 576 threads collide the tile + 1 (544 nodes) in one pass.  (Only for FP64: its per-tile copy of
+// the Y tables starts at row y0, which is 16-byte aligned for 8-byte entries and even y0 only.)
+constexpr Shape kShapes64[5] = {{32, 8, 256}, {16, 8, 256}, {32, 8, 512}, {32, 16, 512}, {32, 14, 576}};
 constexpr Shape kShapesF[4] = {{32, 16, 256}, {32, 8, 256}, {16, 8, 256}, {32, 16, 768}};
-inline int n_shapes(int) { return 4; }
+inline int n_shapes(int prec) { return prec == LBCH_F64 ? 5 : 4; }
 inline Shape shape_of(int prec, int k) { return prec == LBCH_F64 ? kShapes64[k] : kShapesF[k]; }
 
 
@@ -248,7 +251,8 @@ cudaError_t prepare_step(lbch_handle* h, int k)
         return k == 0 ? prepare_step_t<double, double, double, 32, 8>(h, k)
              : k == 1 ? prepare_step_t<double, double, double, 16, 8>(h, k)
              : k == 2 ? prepare_step_t<double, double, double, 32, 8, 512>(h, k)
-                      : prepare_step_t<double, double, double, 32, 16, 512>(h, k);
+             : k == 3 ? prepare_step_t<double, double, double, 32, 16, 512>(h, k)
+                      : prepare_step_t<double, double, double, 32, 14, 576>(h, k);
     case LBCH_F32:
         return k == 0 ? prepare_step_t<float, float, float, 32, 16>(h, k)
              : k == 1 ? prepare_step_t<float, float, float, 32, 8>(h, k)
@@ -335,7 +339,8 @@ cudaError_t launch_step(lbch_handle* h, int parity)
         return k == 0 ? launch_step_t<double, double, double, 32, 8>(h, parity)
              : k == 1 ? launch_step_t<double, double, double, 16, 8>(h, parity)
              : k == 2 ? launch_step_t<double, double, double, 32, 8, 512>(h, parity)
-                      : launch_step_t<double, double, double, 32, 16, 512>(h, parity);
+             : k == 3 ? launch_step_t<double, double, double, 32, 16, 512>(h, parity)
+                      : launch_step_t<double, double, double, 32, 14, 576>(h, parity);
     case LBCH_F32:
         return k == 0 ? launch_step_t<float, float, float, 32, 16>(h, parity)
              : k == 1 ? launch_step_t<float, float, float, 32, 8>(h, parity)
@@ -903,7 +908,9 @@ lbch_status init_impl(const lbch_params* params, int n_inst, const double* phi0,
         d.ny = p.ny;
         d.slab = slab ? 1 : 0;
         d.row0 = row + GR;
-        d.ylen = (p.ny + 15) / 16 * 16 + 8;  // the Y slice of a tile spans TY + 8 rows from its first halo row
+        // the Y slice of a tile spans TY + 8 rows from its first halo row; the last tile of a shape whose TY does
+        // not divide 16 (FP64 32 x 14) reaches up to 15 rows past ny rounded up to 16, so 16 more entries
+        d.ylen = (p.ny + 15) / 16 * 16 + 8 + 16;
         row += p.ny + 2 * GR;
         max_w = std::max(max_w, (p.nx + 31) / 32 * 32);
         h->node_begin[k] = h->nodes;

@@ -7,7 +7,7 @@
 #include "lbch_kernels.cuh"
 #include "lbch_ns.cuh"
 
-constexpr int kMaxShapes = 4;
+constexpr int kMaxShapes = 5;
 struct Shape { int tx, ty, nt; };  // output nodes of a tile, threads per block
 
 // Configurations of the row-sweep kernel (tau_g = 1): TY output rows per warp, NW warps per CTA; a tile

@@ -58,7 +58,8 @@ struct InstDev {
     int nx, ny;
     int row0;          // stored row of domain row 0 (the instance's first ghost row is row0 - GR)
     int walls, model, vel;
-    int ylen;          // length of each Y velocity table: ny rounded up to 16, plus 2 GR ghost rows
+    int ylen;          // length of each Y velocity table: ny rounded up to 16, plus 24 (ghost rows and the
+                       // reach of the last tile's slice)
     int tab;           // offset of the velocity tables: X1, X2 [pitch]; Y1, Y2 [ylen]; W[4]
     int slab;          // a slab of a larger periodic grid: its ghost rows hold the neighbouring slabs' rows
                        // (imported between steps), not images of its own rows

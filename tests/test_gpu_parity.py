@@ -185,8 +185,8 @@ def test_nonfinite_is_reported():
         assert ei.value.status == abi.LBCH_ENONFINITE
 
 
-@pytest.mark.parametrize("prec,nshapes,tile,general", [("f64", 4, 1, 1), ("f32", 4, 1, 1), ("f16s", 4, 1, 1),
-                                                      ("f64", 4, 1, 0), ("f32", 4, 1, 0),
+@pytest.mark.parametrize("prec,nshapes,tile,general", [("f64", 5, 1, 1), ("f32", 4, 1, 1), ("f16s", 4, 1, 1),
+                                                      ("f64", 5, 1, 0), ("f32", 4, 1, 0),
                                                       ("f64", 4, 0, 1), ("f32", 4, 0, 1), ("f16s", 4, 0, 1),
                                                       ("f64", 4, 0, 0), ("f32", 4, 0, 0), ("f16s", 4, 0, 0)])
 def test_every_tile_shape_gives_the_same_bits(prec, nshapes, tile, general):
