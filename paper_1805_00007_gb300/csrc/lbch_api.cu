@@ -19,7 +19,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 using namespace lbch;
@@ -98,6 +101,55 @@ EncodeTiledFn encode_fn()
 }
 
 }  // namespace
+
+cudaError_t lbch_kernel_smem(const void* kern, int device, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> set;  // (kernel, device) -> the bytes allowed so far
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(kern, device);
+    auto it = set.find(key);
+    if (it != set.end() && it->second >= smem) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set[key] = smem;
+    return e;
+}
+
+cudaError_t lbch_kernel_fit(const void* kern, int device, int threads, size_t smem, int* per_sm, int* sms)
+{
+    struct Key {
+        const void* kern;
+        int device, threads;
+        size_t smem;
+        bool operator<(const Key& o) const
+        {
+            return kern != o.kern ? kern < o.kern
+                 : device != o.device ? device < o.device : threads != o.threads ? threads < o.threads : smem < o.smem;
+        }
+    };
+    static std::mutex mu;
+    static std::map<Key, int> fits;
+    static std::map<int, int> sm_count;
+    std::lock_guard<std::mutex> lock(mu);
+    auto s = sm_count.find(device);
+    if (s == sm_count.end()) {
+        int n = 0;
+        const cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return e;
+        s = sm_count.emplace(device, n).first;
+    }
+    *sms = s->second;
+    const Key key{kern, device, threads, smem};
+    auto it = fits.find(key);
+    if (it == fits.end()) {
+        int n = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        it = fits.emplace(key, n).first;
+    }
+    *per_sm = it->second;
+    return cudaSuccess;
+}
 
 // Used by the allocation-free entry point (another translation unit) to report its failures through
 // lb_ch_last_error(); not exported.
@@ -228,16 +280,13 @@ template <typename C, typename S, typename P, int TX, int TY, int NTT = NT>
 cudaError_t prepare_step_t(lbch_handle* h, int k)
 {
     using L = StepShape<C, S, P, TX, TY>;
-    auto kern = ch_step_kernel<C, S, P, TX, TY, NTT, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    const void* kern = reinterpret_cast<const void*>(ch_step_kernel<C, S, P, TX, TY, NTT, false>);
+    cudaError_t e = lbch_kernel_smem(kern, h->device, L::BYTES);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(ch_step_kernel<C, S, P, TX, TY, NTT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L::BYTES);
+    e = lbch_kernel_smem(reinterpret_cast<const void*>(ch_step_kernel<C, S, P, TX, TY, NTT, true>), h->device, L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTT, L::BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    e = lbch_kernel_fit(kern, h->device, NTT, L::BYTES, &per_sm, &sms);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     h->ps[k].grid = std::max(1, std::min(h->ps[k].total_tiles, per_sm * sms));
@@ -491,49 +540,160 @@ void velocity_tables(const lbch_params& p, int pitch, int ylen, std::vector<doub
     Y((double)p.ny - 0.5, W[1], W[3]);
 }
 
+// ---------------------------------------------------------------------------------------- handle memory
+// A handle's device buffers come from one stream-ordered memory pool per device, allocated and freed on the
+// handle's stream; the pool keeps up to kPoolKeep bytes of freed memory for the next handle.  Where a handle
+// is made and freed per problem, set-up and release then cost microseconds per buffer instead of a
+// cudaMalloc and a device-synchronising cudaFree each (measured: init 1.25 ms and free 0.87 ms for one
+// 256^2 handle before).  The pinned host staging buffers are kept between handles likewise, up to
+// kStageKeep of them and kStageKeepBytes in all (pinning host memory costs far more than a copy through it).
+constexpr unsigned long long kPoolKeep = 2ull << 30;
+constexpr size_t kStageKeep = 4, kStageKeepBytes = size_t(256) << 20;
+
+cudaError_t device_pool(int device, cudaMemPool_t* out)
+{
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(device);
+    if (it != pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    unsigned long long keep = kPoolKeep;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+    }
+    pools[device] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
+// bytes of device memory for the handle, ordered on its stream; 256-byte aligned (the tensor maps need 16)
+template <typename T>
+cudaError_t dalloc(lbch_handle* h, T** p, size_t bytes)
+{
+    void* v = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&v, bytes, h->pool, h->stream);
+    if (e != cudaSuccess) return e;
+    if (reinterpret_cast<uintptr_t>(v) % 256 != 0) {
+        cudaFreeAsync(v, h->stream);
+        return cudaErrorMisalignedAddress;
+    }
+    *p = static_cast<T*>(v);
+    return cudaSuccess;
+}
+
+template <typename T>
+void dfree(lbch_handle* h, T*& p)
+{
+    if (p) cudaFreeAsync(p, h->stream);
+    p = nullptr;
+}
+
+struct StageCache {
+    std::mutex mu;
+    std::vector<std::pair<void*, size_t>> kept;
+};
+StageCache& stage_cache()
+{
+    static StageCache c;
+    return c;
+}
+
+// a kept pinned buffer of at least `bytes` (the smallest such), else a new one
+cudaError_t stage_take(size_t bytes, double** p, size_t* got)
+{
+    {
+        StageCache& c = stage_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        int best = -1;
+        for (int i = 0; i < (int)c.kept.size(); i++)
+            if (c.kept[i].second >= bytes && (best < 0 || c.kept[i].second < c.kept[best].second)) best = i;
+        if (best >= 0) {
+            *p = static_cast<double*>(c.kept[best].first);
+            *got = c.kept[best].second;
+            c.kept.erase(c.kept.begin() + best);
+            return cudaSuccess;
+        }
+    }
+    void* v = nullptr;
+    cudaError_t e = cudaMallocHost(&v, bytes);
+    if (e != cudaSuccess) return e;
+    *p = static_cast<double*>(v);
+    *got = bytes;
+    return cudaSuccess;
+}
+
+// back to the cache, or freed when the cache is full (the smallest kept buffer makes room for a larger one)
+void stage_give(double* p, size_t bytes)
+{
+    if (!p) return;
+    if (bytes <= kStageKeepBytes) {
+        StageCache& c = stage_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        size_t total = bytes;
+        for (auto& k : c.kept) total += k.second;
+        if (c.kept.size() < kStageKeep && total <= kStageKeepBytes) {
+            c.kept.push_back({p, bytes});
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
 void release(lbch_handle* h)
 {
     for (int k = 0; k < 2; k++) {
         for (int z = 0; z < 2; z++)
             if (h->graph[z][k]) cudaGraphExecDestroy(h->graph[z][k]);
         if (h->tgraph[k].exec) cudaGraphExecDestroy(h->tgraph[k].exec);
-        if (h->g[k]) cudaFree(h->g[k]);
-        if (h->phi[k]) cudaFree(h->phi[k]);
-        if (h->lo[k]) cudaFree(h->lo[k]);
-        if (h->H[k]) cudaFree(h->H[k]);
+        dfree(h, h->g[k]);
+        dfree(h, h->phi[k]);
+        dfree(h, h->lo[k]);
+        dfree(h, h->H[k]);
     }
-    if (h->d_inst) cudaFree(h->d_inst);
-    if (h->d_tabs_f) cudaFree(h->d_tabs_f);
-    for (int k = 0; k < kMaxShapes; k++)
-        if (h->ps[k].d_tile_begin) cudaFree(h->ps[k].d_tile_begin);
+    dfree(h, h->d_inst);
+    dfree(h, h->d_tabs_f);
+    for (int k = 0; k < kMaxShapes; k++) dfree(h, h->ps[k].d_tile_begin);
     for (int k = 0; k < kSweepShapes; k++) {
-        if (h->sw[k].d_tile_begin) cudaFree(h->sw[k].d_tile_begin);
-        if (h->sw[k].d_tiles) cudaFree(h->sw[k].d_tiles);
+        dfree(h, h->sw[k].d_tile_begin);
+        dfree(h, h->sw[k].d_tiles);
     }
     for (int k = 0; k < kPairShapes; k++) {
-        if (h->pr[k].d_tile_begin) cudaFree(h->pr[k].d_tile_begin);
-        if (h->pr[k].d_ttabs) cudaFree(h->pr[k].d_ttabs);
+        dfree(h, h->pr[k].d_tile_begin);
+        dfree(h, h->pr[k].d_ttabs);
     }
-    if (h->d_node_begin) cudaFree(h->d_node_begin);
-    if (h->d_tabs) cudaFree(h->d_tabs);
-    if (h->phi0) cudaFree(h->phi0);
-    if (h->ctl) cudaFree(h->ctl);
-    if (h->partials) cudaFree(h->partials);
-    if (h->result) cudaFree(h->result);
-    if (h->h_stage) cudaFreeHost(h->h_stage);
-    if (h->adj) cudaFree(h->adj);
-    if (h->ns) cudaFree(h->ns);
+    dfree(h, h->d_node_begin);
+    dfree(h, h->d_tabs);
+    dfree(h, h->phi0);
+    dfree(h, h->ctl);
+    dfree(h, h->partials);
+    dfree(h, h->result);
+    dfree(h, h->ns);
+    stage_give(h->h_stage, h->h_stage_bytes);
+    h->h_stage = nullptr;
+    h->h_stage_bytes = 0;
+    if (h->adj) cudaFree(h->adj);  // the adjoint's workspace is a plain allocation (lb_ch_adjoint_begin)
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
 lbch_status stage(lbch_handle* h, size_t bytes)
 {
     if (h->h_stage_bytes >= bytes) return LBCH_OK;
-    if (h->h_stage) cudaFreeHost(h->h_stage);
+    stage_give(h->h_stage, h->h_stage_bytes);
     h->h_stage = nullptr;
     h->h_stage_bytes = 0;
-    CK(cudaMallocHost(&h->h_stage, bytes));
-    h->h_stage_bytes = bytes;
+    CK(stage_take(bytes, &h->h_stage, &h->h_stage_bytes));
     return LBCH_OK;
 }
 
@@ -967,17 +1127,27 @@ lbch_status init_impl(const lbch_params* params, int n_inst, const double* phi0,
         if (e != cudaSuccess) return bail(cuda_fail(e, #call));      \
     } while (0)
     CKI(cudaGetDevice(&h->device));
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CKI(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CKI(device_pool(h->device, &h->pool));
+    // (every buffer below is allocated and filled in the order of the handle's stream; the uploads from
+    // pageable host memory return once the driver has taken the data, so the host vectors may go)
     for (int sk = 0; sk < n_shapes(prec); sk++) {
         CKI(prepare_step(h, sk));
-        CKI(cudaMalloc(&h->ps[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
-        CKI(cudaMemcpy(h->ps[sk].d_tile_begin, tile_begin[sk].data(), sizeof(int) * (n_inst + 1), cudaMemcpyHostToDevice));
+        CKI(dalloc(h, &h->ps[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
+        CKI(cudaMemcpyAsync(h->ps[sk].d_tile_begin, tile_begin[sk].data(), sizeof(int) * (n_inst + 1),
+                            cudaMemcpyHostToDevice, h->stream));
     }
     if (!coupled) {
         for (int sk = 0; sk < kSweepShapes; sk++) {
             CKI(prepare_sweep(h, sk));
-            CKI(cudaMalloc(&h->sw[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
-            CKI(cudaMemcpy(h->sw[sk].d_tile_begin, sweep_begin[sk].data(), sizeof(int) * (n_inst + 1),
-                           cudaMemcpyHostToDevice));
+            CKI(dalloc(h, &h->sw[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
+            CKI(cudaMemcpyAsync(h->sw[sk].d_tile_begin, sweep_begin[sk].data(), sizeof(int) * (n_inst + 1),
+                                cudaMemcpyHostToDevice, h->stream));
             // the tiles of every instance, those that need the wall body (their collision rows or the rows
             // their stencils read come within two rows of a wall) after all the others
             const Shape sh = sweep_tile(sk);
@@ -992,14 +1162,15 @@ lbch_status init_impl(const lbch_params* params, int n_inst, const double* phi0,
                 }
             }
             inner.insert(inner.end(), edge.begin(), edge.end());
-            CKI(cudaMalloc(&h->sw[sk].d_tiles, sizeof(int4) * inner.size()));
-            CKI(cudaMemcpy(h->sw[sk].d_tiles, inner.data(), sizeof(int4) * inner.size(), cudaMemcpyHostToDevice));
+            CKI(dalloc(h, &h->sw[sk].d_tiles, sizeof(int4) * inner.size()));
+            CKI(cudaMemcpyAsync(h->sw[sk].d_tiles, inner.data(), sizeof(int4) * inner.size(), cudaMemcpyHostToDevice,
+                                h->stream));
         }
         for (int sk = 0; sk < kPairShapes && prec != LBCH_F16S; sk++) {
             CKI(lbch_prepare_pair(h, sk));
-            CKI(cudaMalloc(&h->pr[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
-            CKI(cudaMemcpy(h->pr[sk].d_tile_begin, pair_begin[sk].data(), sizeof(int) * (n_inst + 1),
-                           cudaMemcpyHostToDevice));
+            CKI(dalloc(h, &h->pr[sk].d_tile_begin, sizeof(int) * (n_inst + 1)));
+            CKI(cudaMemcpyAsync(h->pr[sk].d_tile_begin, pair_begin[sk].data(), sizeof(int) * (n_inst + 1),
+                                cudaMemcpyHostToDevice, h->stream));
             // each tile's velocity tables over the tile + 6 (periodically wrapped), contiguous per tile so that
             // one bulk copy brings them (the layout of PairShape: X1, X2 by column, Y1, Y2 by row, 16-byte
             // padded)
@@ -1030,42 +1201,36 @@ lbch_status init_impl(const lbch_params* params, int n_inst, const double* phi0,
                     }
                 }
             }
-            CKI(cudaMalloc(&h->pr[sk].d_ttabs, tt.size() * esz));
+            CKI(dalloc(h, &h->pr[sk].d_ttabs, tt.size() * esz));
             if (prec == LBCH_F64) {
-                CKI(cudaMemcpy(h->pr[sk].d_ttabs, tt.data(), tt.size() * esz, cudaMemcpyHostToDevice));
+                CKI(cudaMemcpyAsync(h->pr[sk].d_ttabs, tt.data(), tt.size() * esz, cudaMemcpyHostToDevice, h->stream));
             } else {
                 std::vector<float> tf(tt.begin(), tt.end());  // rounded as the float tables are
-                CKI(cudaMemcpy(h->pr[sk].d_ttabs, tf.data(), tf.size() * esz, cudaMemcpyHostToDevice));
+                CKI(cudaMemcpyAsync(h->pr[sk].d_ttabs, tf.data(), tf.size() * esz, cudaMemcpyHostToDevice, h->stream));
             }
         }
-    }
-    if (stream) {
-        h->stream = static_cast<cudaStream_t>(stream);
-    } else {
-        CKI(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
-        h->own_stream = true;
     }
     const size_t cells = (size_t)h->rows * h->pitch;
     const size_t gbytes = cells * h->nq * h->g_elem;
     const size_t pbytes = cells * h->phi_elem;
     for (int k = 0; k < 2; k++) {
-        CKI(cudaMalloc(&h->g[k], gbytes));
-        CKI(cudaMalloc(&h->phi[k], pbytes));
-        if (prec == LBCH_F32) CKI(cudaMalloc(&h->lo[k], cells * sizeof(float)));
-        if (h->model3) CKI(cudaMalloc(&h->H[k], 2 * cells * h->c_elem()));
+        CKI(dalloc(h, &h->g[k], gbytes));
+        CKI(dalloc(h, &h->phi[k], pbytes));
+        if (prec == LBCH_F32) CKI(dalloc(h, &h->lo[k], cells * sizeof(float)));
+        if (h->model3) CKI(dalloc(h, &h->H[k], 2 * cells * h->c_elem()));
     }
-    CKI(cudaMalloc(&h->phi0, cells * sizeof(double)));
-    CKI(cudaMalloc(&h->d_inst, sizeof(InstDev) * n_inst));
-    CKI(cudaMalloc(&h->d_node_begin, sizeof(long long) * (n_inst + 1)));
-    CKI(cudaMalloc(&h->d_tabs, sizeof(double) * tabs.size()));
-    CKI(cudaMalloc(&h->d_tabs_f, sizeof(float) * tabs_f.size()));
-    CKI(cudaMalloc(&h->ctl, sizeof(Ctl)));
+    CKI(dalloc(h, &h->phi0, cells * sizeof(double)));
+    CKI(dalloc(h, &h->d_inst, sizeof(InstDev) * n_inst));
+    CKI(dalloc(h, &h->d_node_begin, sizeof(long long) * (n_inst + 1)));
+    CKI(dalloc(h, &h->d_tabs, sizeof(double) * tabs.size()));
+    CKI(dalloc(h, &h->d_tabs_f, sizeof(float) * tabs_f.size()));
+    CKI(dalloc(h, &h->ctl, sizeof(Ctl)));
     long long max_nodes = 0;
     for (auto& d : h->inst) max_nodes = std::max(max_nodes, (long long)d.nx * d.ny);
     h->chunks = (int)std::min<long long>(1024, (max_nodes + RED_NT * 8 - 1) / (RED_NT * 8));
     if (h->chunks < 1) h->chunks = 1;
-    CKI(cudaMalloc(&h->partials, sizeof(double) * RED_NV * (size_t)h->chunks * n_inst));
-    CKI(cudaMalloc(&h->result, sizeof(double) * RED_NV * (size_t)n_inst));
+    CKI(dalloc(h, &h->partials, sizeof(double) * RED_NV * (size_t)h->chunks * n_inst));
+    CKI(dalloc(h, &h->result, sizeof(double) * RED_NV * (size_t)n_inst));
     lbch_status st = LBCH_OK;
     for (int sk = 0; sk < n_shapes(prec) && st == LBCH_OK; sk++) st = encode_maps(h, sk);
     for (int sk = 0; !coupled && sk < kSweepShapes && st == LBCH_OK; sk++) st = encode_sweep_maps(h, sk);
@@ -1134,7 +1299,7 @@ lbch_status init_impl(const lbch_params* params, int n_inst, const double* phi0,
         h->nsd.itauf = 1.0 / h->nsd.tauf; h->nsd.omtf = 1.0 - h->nsd.itauf; h->nsd.srcf = 1.0 - 0.5 / h->nsd.tauf;
         h->nsf.itauf = (float)h->nsd.itauf; h->nsf.omtf = (float)h->nsd.omtf; h->nsf.srcf = (float)h->nsd.srcf;
         const size_t N = (size_t)d.nx * d.ny, esz = prec == LBCH_F64 ? 8 : 4;
-        CKI(cudaMalloc(&h->ns, 40 * N * esz));  // f, g (two buffers each), u, p, mu
+        CKI(dalloc(h, &h->ns, 40 * N * esz));  // f, g (two buffers each), u, p, mu
         CKI(cudaMemsetAsync(h->ns, 0, 40 * N * esz, h->stream));
         const int nbn = (int)((N + 255) / 256);
         if (prec == LBCH_F64) {

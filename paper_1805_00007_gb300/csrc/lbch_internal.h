@@ -31,6 +31,7 @@ struct lbch_handle {
     int n_inst = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaMemPool_t pool = nullptr;  // the device's pool the handle's buffers come from (stream-ordered, on `stream`)
     std::vector<lbch::InstDev> inst;
     std::vector<long long> node_begin;  // first linear node index of each instance (+ total)
     lbch::InstDev* d_inst = nullptr;
@@ -136,3 +137,9 @@ LBCH_INTERNAL cudaError_t lbch_prepare_sweep_f16s_m3(lbch_handle* h, int k);
 // Two-step launches and set-up (lbch_pair.cu); pshape names a pair_shape().
 LBCH_INTERNAL cudaError_t lbch_launch_pair(lbch_handle* h, int parity);
 LBCH_INTERNAL cudaError_t lbch_prepare_pair(lbch_handle* h, int k);
+// Launch limits of a kernel on a device, set and queried once per process (they depend on nothing else) and
+// served from a table afterwards, so that making a handle does not repeat them for every kernel it may run:
+// lbch_kernel_smem lets `kern` use `smem` bytes of dynamic shared memory; lbch_kernel_fit gives how many CTAs
+// of `threads` threads with `smem` bytes one SM holds, and the device's SM count (lbch_api.cu).
+LBCH_INTERNAL cudaError_t lbch_kernel_smem(const void* kern, int device, size_t smem);
+LBCH_INTERNAL cudaError_t lbch_kernel_fit(const void* kern, int device, int threads, size_t smem, int* per_sm, int* sms);

@@ -46,15 +46,13 @@ template <typename C, typename P, int TX, int TY, int NT>
 cudaError_t prepare_pair_v(lbch_handle* h, int k)
 {
     using L = PairShape<C, P, TX, TY>;
-    auto kern = ch_pair_kernel<C, P, TX, TY, NT, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    const void* kern = reinterpret_cast<const void*>(ch_pair_kernel<C, P, TX, TY, NT, false>);
+    cudaError_t e = lbch_kernel_smem(kern, h->device, L::BYTES);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ch_pair_kernel<C, P, TX, TY, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L::BYTES);
+        e = lbch_kernel_smem(reinterpret_cast<const void*>(ch_pair_kernel<C, P, TX, TY, NT, true>), h->device, L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, L::BYTES);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    e = lbch_kernel_fit(kern, h->device, NT, L::BYTES, &per_sm, &sms);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     h->pr[k].grid = std::max(1, std::min(h->pr[k].total_tiles, per_sm * sms));

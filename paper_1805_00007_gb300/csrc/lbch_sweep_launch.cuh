@@ -82,16 +82,14 @@ template <typename C, typename S, typename P, bool FF, int TY, int NW, bool GEN,
 cudaError_t prepare_sweep_v(lbch_handle* h, int k)
 {
     using L = SweepShape<P, S, FF, TY, NW, GEN>;
-    auto kern = ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false, M3>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    const void* kern = reinterpret_cast<const void*>(ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, false, M3>);
+    cudaError_t e = lbch_kernel_smem(kern, h->device, L::BYTES);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true, M3>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+        e = lbch_kernel_smem(reinterpret_cast<const void*>(ch_sweep_kernel<C, S, P, FF, TY, NW, GEN, COMPACT, true, M3>),
+                             h->device, L::BYTES);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, L::BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    e = lbch_kernel_fit(kern, h->device, NW * 32, L::BYTES, &per_sm, &sms);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     (GEN ? h->sw[k].grid_gen : h->sw[k].grid) = std::max(1, std::min(h->sw[k].total_tiles, per_sm * sms));
