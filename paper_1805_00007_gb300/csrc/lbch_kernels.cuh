@@ -284,6 +284,15 @@ __device__ __forceinline__ C stream_sum(C v1, C v2, C v3, C v4, C v5, C v6, C v7
 // ------------------------------------------------------------------------------------------ TMA / mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// The dynamic shared memory of a kernel from its first 128-byte boundary.  The offset is added to the shared
+// array itself (not formed by a round trip through an integer address), so the compiler still knows every
+// pointer derived from it addresses shared memory and issues shared-memory loads and stores rather than
+// generic ones.
+__device__ __forceinline__ unsigned char* smem_aligned128(unsigned char* raw)
+{
+    return raw + ((128u - (unsigned)(reinterpret_cast<uintptr_t>(raw) & 127u)) & 127u);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -436,7 +445,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (sizeof(C) == 8 ? 2 : 3)) 
     constexpr int NONE = -0x40000000;
 
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char* base = smem_aligned128(smem_raw);
     auto stage = [&](int k) { return base + (size_t)k * L::STAGE; };
     C* s_mu = reinterpret_cast<C*>(base + 2 * L::STAGE);
     C* s_D = s_mu + L::NM;

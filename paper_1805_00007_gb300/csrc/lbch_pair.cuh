@@ -169,7 +169,7 @@ struct PairSmem {
     __device__ explicit PairSmem(unsigned char* raw)
     {
         using L = PairShape<C, P, TX, TY>;
-        unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+        unsigned char* base = smem_aligned128(raw);
         phi0 = reinterpret_cast<P*>(base);
         lo0 = reinterpret_cast<float*>(base + L::OFF_LO0);
         hi1 = reinterpret_cast<P*>(base + L::OFF_HI1);

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
     constexpr int QOFF = kHalf ? 1 : 0;         // stored plane of population q is q - QOFF
 
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char* base = smem_aligned128(smem_raw);
     auto stage = [&](int k) { return base + (size_t)k * L::STAGE; };
     uint64_t* mbar = reinterpret_cast<uint64_t*>(base + L::OFF_MBAR);
 
