@@ -128,8 +128,10 @@ typedef struct lbch_handle lbch_handle;
  * different sizes and parameters but share the precision).  params: n_inst structs (host).  phi0: the
  * initial order parameter of every instance, concatenated in instance order, each ny*nx row-major
  * doubles (host).  The initial distributions are the equilibria of phi0, mu(phi0) and u(t = 0).
- * stream: a cudaStream_t, or NULL for a stream the library creates.  On success *out receives the
- * handle and the state is at step 0. */
+ * stream: a cudaStream_t, or NULL for a stream the library creates; a caller's stream must outlive the
+ * handle (the handle's device memory is allocated and released in its order, from a pool per device that
+ * keeps freed memory for the next handle).  On success *out receives the handle and the state is at
+ * step 0. */
 lbch_status lb_ch_init(const lbch_params* params, int n_inst, const double* phi0, int prec,
                        void* stream, lbch_handle** out);
 
@@ -183,7 +185,9 @@ lbch_status lb_ch_observe(lbch_handle* h, int inst, int what, double* out);
 /* One scalar observable (MASS, ERR_L2, MAX or MIN) for every instance: out receives n_inst values. */
 lbch_status lb_ch_observe_all(lbch_handle* h, int what, double* out);
 
-/* Release every resource of the handle (safe on NULL). */
+/* Release every resource of the handle (safe on NULL): waits for the handle's stream, then returns the
+ * device memory to the device's pool in that stream's order (up to 2 GB of it stays reserved for later
+ * handles) and the pinned staging buffer to a small cache of the library's. */
 lbch_status lb_ch_free(lbch_handle* h);
 
 /* Human-readable name of a status, and the message of the last failure on this thread. */
