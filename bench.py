@@ -165,6 +165,44 @@ def oracle_baseline(p, phi0, nsteps, threads=0):
     return p["nx"] * p["ny"] * nsteps / dt / 1e6, dt, used
 
 
+def oracle_by_config():
+    """The FP64 oracle as it stands on each configuration's workload, on the host's threads (its default): the
+    translation in full, the others on a bounded number of steps.  Lattice updates per second, and the wall time
+    the configuration's full length would take at that rate (reported, not a target)."""
+    import oracle
+    out = {}
+
+    def record(name, lu, dt, used, steps, full_lu):
+        out[name] = {"MLUPS": lu / dt / 1e6, "steps": steps, "seconds": dt, "threads": used,
+                     "full_run_s": full_lu / (lu / dt)}
+
+    p, f, n = wl.translation()
+    v, dt, used = oracle_baseline(p, f, n)
+    record("translation_100_2500_steps", p["nx"] * p["ny"] * n, dt, used, n, p["nx"] * p["ny"] * n)
+    p, f, rev = wl.zalesak(n=REV_N)
+    v, dt, used = oracle_baseline(p, f, 300)
+    record("zalesak_256_one_revolution", p["nx"] * p["ny"] * 300, dt, used, 300, p["nx"] * p["ny"] * rev)
+    p, f, tv = wl.single_vortex()
+    v, dt, used = oracle_baseline(p, f, 40)
+    record("single_vortex_512_T8000", p["nx"] * p["ny"] * 40, dt, used, 40, p["nx"] * p["ny"] * tv)
+    ens = wl.shear_ensemble()
+    lu = dt = 0.0
+    for q, f in ens:  # every instance, a few steps each
+        _, d, used = oracle_baseline(q, f, 3)
+        lu += q["nx"] * q["ny"] * 3
+        dt += d
+    record("shear_ensemble_256_5000_steps", lu, dt, used, 3, lu / 3 * 5000)
+    p, f = wl.rayleigh_taylor()
+    t0 = time.perf_counter()
+    oracle.ns_simulate(p, f, 10)
+    dt = time.perf_counter() - t0
+    record("rayleigh_taylor_256x1024_2e4_steps", p["nx"] * p["ny"] * 10, dt, oracle.set_threads(0), 10,
+           p["nx"] * p["ny"] * 20000)
+    out["rayleigh_taylor_256x1024_2e4_steps"]["threads_note"] = \
+        "the coupled step's stencils run on the threads, its per-node collision loop on one"
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -678,7 +716,8 @@ def main():
         cpu = {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle",
                "sample": f"{sample} lattice steps of the 256x256 Zalesak workload ({dt:.1f} s)",
                "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1,
-                                 "sample": f"{sample1} lattice steps of the same workload ({dt1:.1f} s)"}}
+                                 "sample": f"{sample1} lattice steps of the same workload ({dt1:.1f} s)"},
+               "by_config": oracle_by_config()}
 
     clocks = clk.summary()
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
