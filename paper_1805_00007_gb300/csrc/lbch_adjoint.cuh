@@ -16,6 +16,11 @@
 // forward phi in the precision of the forward path, so the gradient is that of the path actually run.
 // Four one-thread-per-node kernels per adjoint step (forward mu; local adjoints; mu_bar and D_bar; phi_bar
 // and the new lambda), and one deterministic sum of dL/ds at the end of the sweep.
+//
+// ONE (tau_g = 1): lambda_q = (1 - 1/tau) lambda'_q(x + c_q) + phi_bar(x) is phi_bar(x) for every q, since
+// 1 - 1/tau is exactly 0, so lambda is kept as one plane instead of nine.  The kernels read that plane where
+// they would read plane q and write it once; the values are those of the nine-plane form bit for bit (for
+// finite lambda, 0 * lambda' + phi_bar is phi_bar).
 
 #pragma once
 #include "lbch_kernels.cuh"
@@ -130,7 +135,7 @@ __global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const TP* phi, C* 
 }
 
 // local adjoints of collision, g_eq, S and F1 (lambda itself is written by transpose2_kernel)
-template <typename C, typename TP>
+template <typename C, typename TP, bool ONE>
 __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
                              const C* mu, const C* lam_next, C* lam, C* gmb, C* Fb, C* phib, C* mub, C* ub)
 {
@@ -148,7 +153,7 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
 #pragma unroll
     for (int q = 0; q < 9; q++) {
         // reverse streaming: post_q(x) was sent to x + c_q
-        pb[q] = lam_next[q * N + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
+        pb[q] = lam_next[(ONE ? 0 : q * N) + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)];
     }
     // post_q takes g_eq_q / tau and (1 - 1/(2 tau)) S_q, S_q = w_q c_q . F / c_s^2
     C pl, ml, bx, by, m1x, m1y;
@@ -187,7 +192,7 @@ __global__ void transpose1_kernel(const InstDev* inst, AdjArgs a, const C* gmb, 
 
 // phi_bar = local + f''(phi) mu_bar - kappa L^T mu_bar + u . G^T D_bar;
 // lambda_q(x) = (1 - 1/tau) lambda_next_q(x + c_q) + phi_bar(x); dL/ds per node
-template <typename C, typename TP>
+template <typename C, typename TP, bool ONE>
 __global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
                                   const C* phib, const C* mub, const C* Db, const C* ub, const C* lam_next, C* lam,
                                   double* ds)
@@ -211,13 +216,17 @@ __global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjAr
     }
     // u = s u_ref: du/ds = u.  Accumulated per node over the adjoint steps and summed once at the end.
     ds[k] += (double)bx * (double)ux + (double)by * (double)uy;
+    if constexpr (ONE) {
+        lam[k] = pb;  // (1 - 1/tau) = 0: the reverse streaming and collision leave phi_bar alone
+    } else {
 #pragma unroll
-    for (int q = 0; q < 9; q++)  // reverse streaming and collision, plus phi = sum_q g_q
-        lam[q * N + k] = K0.omt * lam_next[q * N + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)] + pb;
+        for (int q = 0; q < 9; q++)  // reverse streaming and collision, plus phi = sum_q g_q
+            lam[q * N + k] = K0.omt * lam_next[q * N + (long long)wp(y + cy(q), a.ny) * a.nx + wp(x + cx(q), a.nx)] + pb;
+    }
 }
 
 // adjoint of the initial equilibria: dL/dphi0 (two kernels: local, then the mu transpose)
-template <typename C>
+template <typename C, bool ONE>
 __global__ void init_local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const double* phi0,
                                   int pitch0, const C* lam, C* mub, C* dphi0, double* ds)
 {
@@ -232,7 +241,7 @@ __global__ void init_local_kernel(const InstDev* inst, const double* tabs, AdjAr
     vel_at(I, tabs, a, x, y, T, ux, uy);
     C l[9];
 #pragma unroll
-    for (int q = 0; q < 9; q++) l[q] = lam[q * N + k];
+    for (int q = 0; q < 9; q++) l[q] = lam[(ONE ? 0 : q * N) + k];
     C pl, ml, bx, by, m1x, m1y;
     geq_contract(l, ph, ux, uy, K0.eta, pl, ml, bx, by, m1x, m1y);
     dphi0[k] = pl;
@@ -281,15 +290,14 @@ __global__ void tape_kernel(const InstDev* inst, int pitch, const P* phi, const 
     out[k] = (C)((double)phi[gi] + (lo ? (double)lo[gi] : 0.0));
 }
 
-// lambda_T: dL/dg_q = dL/dphi(T) for every q
+// lambda_T: dL/dg_q = dL/dphi(T) for every q (nq planes: 9, or 1 with ONE)
 template <typename C>
-__global__ void adj_begin_kernel(long long N, const C* dphiT, C* lam)
+__global__ void adj_begin_kernel(long long N, int nq, const C* dphiT, C* lam)
 {
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     C v = dphiT[k];
-#pragma unroll
-    for (int q = 0; q < 9; q++) lam[q * N + k] = v;
+    for (int q = 0; q < nq; q++) lam[q * N + k] = v;
 }
 
 }  // namespace adj

@@ -926,14 +926,17 @@ struct AdjView {  // pointers into the adjoint workspace
     double* dLds;
 };
 
+// planes of each lambda buffer: 9, or 1 at tau_g = 1 (the nine are equal there; lbch_adjoint.cuh, ONE)
+inline int adj_planes(const lbch_handle* h) { return h->tau1 ? 1 : 9; }
+
 AdjView adj_view(lbch_handle* h)
 {
     const size_t N = (size_t)h->inst[0].nx * h->inst[0].ny, e = h->adj_elem;
     char* p = static_cast<char*>(h->adj);
     AdjView v;
     auto take = [&](size_t n) { void* r = p; p += (n * e + 255) / 256 * 256; return r; };
-    v.lam[0] = take(9 * N);
-    v.lam[1] = take(9 * N);
+    v.lam[0] = take(adj_planes(h) * N);
+    v.lam[1] = take(adj_planes(h) * N);
     v.mu = take(N);
     v.gmb = take(2 * N);
     v.Fb = take(2 * N);
@@ -951,7 +954,7 @@ size_t adj_bytes(const lbch_handle* h)
 {
     const size_t N = (size_t)h->inst[0].nx * h->inst[0].ny, e = h->adj_elem;
     auto r = [](size_t b) { return (b + 255) / 256 * 256; };
-    return 2 * r(9 * N * e) + r(N * e) + 2 * r(2 * N * e) + 3 * r(N * e) + r(2 * N * e) + r(N * 8) + 256;
+    return 2 * r(adj_planes(h) * N * e) + r(N * e) + 2 * r(2 * N * e) + 3 * r(N * e) + r(2 * N * e) + r(N * 8) + 256;
 }
 
 adj::AdjArgs adj_args(const lbch_handle* h, long long n)
@@ -991,12 +994,15 @@ cudaError_t adjoint_step_t(lbch_handle* h, const TP* phi_n, long long n)
     const C* lam_next = static_cast<const C*>(v.lam[h->adj_par]);
     C* lam = static_cast<C*>(v.lam[h->adj_par ^ 1]);
     adj::fwd_mu_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, a, phi_n, (C*)v.mu);
-    adj::local_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.mu, lam_next, lam,
-                                                    (C*)v.gmb, (C*)v.Fb, (C*)v.phib, (C*)v.mub, (C*)v.ub);
+    const bool one = adj_planes(h) == 1;
+    (one ? adj::local_kernel<C, TP, true> : adj::local_kernel<C, TP, false>)<<<nb, 256, 0, h->stream>>>(
+        h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.mu, lam_next, lam, (C*)v.gmb, (C*)v.Fb, (C*)v.phib, (C*)v.mub,
+        (C*)v.ub);
     adj::transpose1_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, (const C*)v.gmb, (const C*)v.Fb, (C*)v.mub,
                                                          (C*)v.Db);
-    adj::transpose2_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib,
-                                                         (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam_next, lam, v.ds);
+    (one ? adj::transpose2_kernel<C, TP, true> : adj::transpose2_kernel<C, TP, false>)<<<nb, 256, 0, h->stream>>>(
+        h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib, (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam_next,
+        lam, v.ds);
     h->adj_par ^= 1;
     return cudaGetLastError();
 }
@@ -1010,8 +1016,8 @@ cudaError_t adjoint_end_t(lbch_handle* h, C* dphi0)
     const int nb = (int)((N + 255) / 256);
     const double T = vel_t(h->inst[0].vel, h->inst[0].Tper, 0);
     const C* lam = static_cast<const C*>(v.lam[h->adj_par]);
-    adj::init_local_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, h->d_tabs, a, T, h->phi0, h->pitch, lam,
-                                                         (C*)v.mub, dphi0, v.ds);
+    (adj_planes(h) == 1 ? adj::init_local_kernel<C, true> : adj::init_local_kernel<C, false>)<<<nb, 256, 0, h->stream>>>(
+        h->d_inst, h->d_tabs, a, T, h->phi0, h->pitch, lam, (C*)v.mub, dphi0, v.ds);
     adj::init_transpose_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, h->phi0, h->pitch, (const C*)v.mub, dphi0);
     adj::sum_into_kernel<<<1, 256, 0, h->stream>>>(v.ds, N, v.dLds);
     return cudaGetLastError();
@@ -1752,7 +1758,8 @@ lbch_status lb_ch_adjoint_begin(lbch_handle* h, const void* dL_dphiT)
     const long long N = (long long)h->inst[0].nx * h->inst[0].ny;
     const int nb = (int)((N + 255) / 256);
     h->adj_par = 0;
-    adj::adj_begin_kernel<double><<<nb, 256, 0, h->stream>>>(N, (const double*)dL_dphiT, (double*)v.lam[0]);
+    adj::adj_begin_kernel<double><<<nb, 256, 0, h->stream>>>(N, adj_planes(h), (const double*)dL_dphiT,
+                                                            (double*)v.lam[0]);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(v.dLds, 0, sizeof(double), h->stream));
     CK(cudaMemsetAsync(v.ds, 0, (size_t)N * sizeof(double), h->stream));  // per-node dL/ds, summed at the end
