@@ -17,6 +17,10 @@
 // Four one-thread-per-node kernels per adjoint step (forward mu; local adjoints; mu_bar and D_bar; phi_bar
 // and the new lambda), and one deterministic sum of dL/ds at the end of the sweep.
 //
+// CF: the type the forward quantities are formed in (mu, its gradient, the velocity, rho and the force's
+// coefficient, f''(phi)) -- float for a float tape, as the float forward step formed them, double for a double
+// tape.  Everything that carries lambda is double in either case.
+//
 // ONE (tau_g = 1): lambda_q = (1 - 1/tau) lambda'_q(x + c_q) + phi_bar(x) is phi_bar(x) for every q, since
 // 1 - 1/tau is exactly 0, so lambda is kept as one plane instead of nine.  The kernels read that plane where
 // they would read plane q and write it once; the values are those of the nine-plane form bit for bit (for
@@ -37,16 +41,18 @@ struct AdjArgs {
 
 __device__ __forceinline__ int wp(int i, int n) { return i >= n ? i - n : (i < 0 ? i + n : i); }
 
-template <typename C>
-__device__ __forceinline__ void vel_at(const InstDev& I, const double* tabs, const AdjArgs& a, int x, int y,
-                                       double T, C& ux, C& uy)
+// the prescribed velocity at node (x, y) from the velocity tables of type CF (the forward step's), as the
+// forward step forms it: X Y T, two rounded products
+template <typename CF>
+__device__ __forceinline__ void vel_at(const InstDev& I, const CF* tabs, const AdjArgs& a, int x, int y, CF T, CF& ux,
+                                       CF& uy)
 {
-    const double* tX1 = tabs + I.tab;
-    const double* tX2 = tX1 + a.pitch;
-    const double* tY1 = tX2 + a.pitch;
-    const double* tY2 = tY1 + a.ylen;
-    ux = (C)(tX1[x + GC] * tY1[y + GR] * T);
-    uy = (C)(tX2[x + GC] * tY2[y + GR] * T);
+    const CF* tX1 = tabs + I.tab;
+    const CF* tX2 = tX1 + a.pitch;
+    const CF* tY1 = tX2 + a.pitch;
+    const CF* tY2 = tY1 + a.ylen;
+    ux = node_u(tX1[x + GC], tY1[y + GR], T);
+    uy = node_u(tX2[x + GC], tY2[y + GR], T);
 }
 
 template <typename C> __device__ __forceinline__ C d2f(C phi, C beta, C phiA, C phiB)
@@ -122,33 +128,39 @@ __device__ __forceinline__ C lapT(const C* v, int nx, int ny, int x, int y)
     return lap_c<C>(v, nx, ny, x, y);
 }
 
-// forward mu = f'(phi) - kappa lap phi at step n (phi from the tape, of type TP)
-template <typename C, typename TP>
-__global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const TP* phi, C* mu)
+// forward mu = f'(phi) - kappa lap phi at step n (phi from the tape, of type TP), in the forward type CF
+template <typename CF, typename TP>
+__global__ void fwd_mu_kernel(const InstDev* inst, AdjArgs a, const TP* phi, CF* mu)
 {
     const InstDev& I = inst[0];
-    const Consts<C>& K0 = consts<C>(I);
+    const Consts<CF>& K0 = consts<CF>(I);
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)a.nx * a.ny) return;
     int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
-    mu[k] = dfdphi((C)phi[k], K0.beta, K0.phiA, K0.phiB) - K0.kappa * lap_c<C>(phi, a.nx, a.ny, x, y);
+    mu[k] = dfdphi((CF)phi[k], K0.beta, K0.phiA, K0.phiB) - K0.kappa * lap_c<CF>(phi, a.nx, a.ny, x, y);
 }
 
 // local adjoints of collision, g_eq, S and F1 (lambda itself is written by transpose2_kernel)
-template <typename C, typename TP, bool ONE>
-__global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
-                             const C* mu, const C* lam_next, C* lam, C* gmb, C* Fb, C* phib, C* mub, C* ub)
+template <typename C, typename CF, typename TP, bool ONE>
+__global__ void local_kernel(const InstDev* inst, const CF* tabs, AdjArgs a, CF T, const TP* phi, const CF* mu,
+                             const C* lam_next, C* lam, C* gmb, C* Fb, C* phib, C* mub, C* ub)
 {
     const InstDev& I = inst[0];
     const Consts<C>& K0 = consts<C>(I);
+    const Consts<CF>& KF = consts<CF>(I);
     const long long N = (long long)a.nx * a.ny;
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
-    C ph = (C)phi[k];
-    C ux, uy;
-    vel_at(I, tabs, a, x, y, T, ux, uy);
-    const C gx = grad_c<C>(mu, a.nx, a.ny, x, y, 0), gy = grad_c<C>(mu, a.nx, a.ny, x, y, 1);  // grad mu at x
+    // the forward quantities at the node, in CF
+    const CF phf = (CF)phi[k];
+    CF uxf, uyf;
+    vel_at(I, tabs, a, x, y, T, uxf, uyf);
+    const CF gxf = grad_c<CF>(mu, a.nx, a.ny, x, y, 0), gyf = grad_c<CF>(mu, a.nx, a.ny, x, y, 1);  // grad mu
+    const CF rhof = KF.a * phf + KF.b, rf = rcp<CF>(rhof);
+    const CF coeff = phf * phf * rf;                                    // F1 = -coef grad mu
+    const CF dcoeff = phf * (KF.a * phf + CF(2) * KF.b) * (rf * rf);   // d coef / d phi
+    const C ph = (C)phf, ux = (C)uxf, uy = (C)uyf, gx = (C)gxf, gy = (C)gyf, coef = (C)coeff, dcoef = (C)dcoeff;
     C pb[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) {
@@ -163,9 +175,6 @@ __global__ void local_kernel(const InstDev* inst, const double* tabs, AdjArgs a,
     bx *= K0.itau;
     by *= K0.itau;
     const C fbx = C(3) * K0.src * m1x, fby = C(3) * K0.src * m1y;
-    const C rho = K0.a * ph + K0.b, r = rcp<C>(rho);
-    const C coef = ph * ph * r;                                 // F1 = -coef grad mu
-    const C dcoef = ph * (K0.a * ph + C(2) * K0.b) * (r * r);  // d coef / d phi
     gmb[k] = -coef * fbx;
     gmb[N + k] = -coef * fby;
     Fb[k] = fbx;
@@ -192,21 +201,25 @@ __global__ void transpose1_kernel(const InstDev* inst, AdjArgs a, const C* gmb, 
 
 // phi_bar = local + f''(phi) mu_bar - kappa L^T mu_bar + u . G^T D_bar;
 // lambda_q(x) = (1 - 1/tau) lambda_next_q(x + c_q) + phi_bar(x); dL/ds per node
-template <typename C, typename TP, bool ONE>
-__global__ void transpose2_kernel(const InstDev* inst, const double* tabs, AdjArgs a, double T, const TP* phi,
+template <typename C, typename CF, typename TP, bool ONE>
+__global__ void transpose2_kernel(const InstDev* inst, const CF* tabs, AdjArgs a, CF T, const TP* phi,
                                   const C* phib, const C* mub, const C* Db, const C* ub, const C* lam_next, C* lam,
                                   double* ds)
 {
     const InstDev& I = inst[0];
     const Consts<C>& K0 = consts<C>(I);
+    const Consts<CF>& KF = consts<CF>(I);
     const long long N = (long long)a.nx * a.ny;
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
-    C ph = (C)phi[k];
-    C ux, uy;
-    vel_at(I, tabs, a, x, y, T, ux, uy);
-    C pb = phib[k] + d2f(ph, K0.beta, K0.phiA, K0.phiB) * mub[k] - K0.kappa * lapT(mub, a.nx, a.ny, x, y);
+    // the forward quantities at the node, in CF
+    const CF phf = (CF)phi[k];
+    CF uxf, uyf;
+    vel_at(I, tabs, a, x, y, T, uxf, uyf);
+    const C ph = (C)phf, ux = (C)uxf, uy = (C)uyf;
+    const C f2 = (C)d2f(phf, KF.beta, KF.phiA, KF.phiB);
+    C pb = phib[k] + f2 * mub[k] - K0.kappa * lapT(mub, a.nx, a.ny, x, y);
     C bx = ub[k], by = ub[N + k];
     if (a.model == 2) {
         C jbx = gradT(Db, a.nx, a.ny, x, y, 0), jby = gradT(Db, a.nx, a.ny, x, y, 1);
@@ -238,7 +251,7 @@ __global__ void init_local_kernel(const InstDev* inst, const double* tabs, AdjAr
     int y = (int)k / a.nx, x = (int)k - y * a.nx;  // fewer than 2^31 nodes (lb_ch_adjoint_begin checks)
     C ph = (C)phi0[(long long)(I.row0 + y) * pitch0 + GC + x];
     C ux, uy;
-    vel_at(I, tabs, a, x, y, T, ux, uy);
+    vel_at<C>(I, tabs, a, x, y, (C)T, ux, uy);
     C l[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) l[q] = lam[(ONE ? 0 : q * N) + k];

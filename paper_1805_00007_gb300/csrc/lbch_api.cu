@@ -983,25 +983,29 @@ cudaError_t tape_launch(lbch_handle* h, int par, void* dst)
     return cudaGetLastError();
 }
 
+// One adjoint step.  The forward quantities are formed in the tape's type (CF = TP: float for the float
+// path, as its forward step formed them, with the float velocity tables), everything carrying lambda in C.
 template <typename C, typename TP>
 cudaError_t adjoint_step_t(lbch_handle* h, const TP* phi_n, long long n)
 {
+    using CF = TP;
     AdjView v = adj_view(h);
     adj::AdjArgs a = adj_args(h, n);
     const long long N = (long long)a.nx * a.ny;
     const int nb = (int)((N + 255) / 256);
-    const double T = vel_t(h->inst[0].vel, h->inst[0].Tper, n);
+    const CF T = (CF)vel_t(h->inst[0].vel, h->inst[0].Tper, n);
+    const CF* tabs = tables<CF>(h);
     const C* lam_next = static_cast<const C*>(v.lam[h->adj_par]);
     C* lam = static_cast<C*>(v.lam[h->adj_par ^ 1]);
-    adj::fwd_mu_kernel<C, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, a, phi_n, (C*)v.mu);
+    adj::fwd_mu_kernel<CF, TP><<<nb, 256, 0, h->stream>>>(h->d_inst, a, phi_n, (CF*)v.mu);
     const bool one = adj_planes(h) == 1;
-    (one ? adj::local_kernel<C, TP, true> : adj::local_kernel<C, TP, false>)<<<nb, 256, 0, h->stream>>>(
-        h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.mu, lam_next, lam, (C*)v.gmb, (C*)v.Fb, (C*)v.phib, (C*)v.mub,
+    (one ? adj::local_kernel<C, CF, TP, true> : adj::local_kernel<C, CF, TP, false>)<<<nb, 256, 0, h->stream>>>(
+        h->d_inst, tabs, a, T, phi_n, (const CF*)v.mu, lam_next, lam, (C*)v.gmb, (C*)v.Fb, (C*)v.phib, (C*)v.mub,
         (C*)v.ub);
     adj::transpose1_kernel<C><<<nb, 256, 0, h->stream>>>(h->d_inst, a, (const C*)v.gmb, (const C*)v.Fb, (C*)v.mub,
                                                          (C*)v.Db);
-    (one ? adj::transpose2_kernel<C, TP, true> : adj::transpose2_kernel<C, TP, false>)<<<nb, 256, 0, h->stream>>>(
-        h->d_inst, h->d_tabs, a, T, phi_n, (const C*)v.phib, (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam_next,
+    (one ? adj::transpose2_kernel<C, CF, TP, true> : adj::transpose2_kernel<C, CF, TP, false>)<<<nb, 256, 0, h->stream>>>(
+        h->d_inst, tabs, a, T, phi_n, (const C*)v.phib, (const C*)v.mub, (const C*)v.Db, (const C*)v.ub, lam_next,
         lam, v.ds);
     h->adj_par ^= 1;
     return cudaGetLastError();
