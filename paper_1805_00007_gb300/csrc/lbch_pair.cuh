@@ -64,24 +64,6 @@ struct PairShape {
     static constexpr size_t BYTES = OFF_TAB + a128(TAB_BYTES) + 128;  // + alignment slack
 };
 
-// The nodes of a W x H region that the CTA's NT threads take in one phase: f(e, r, c) for node e = r W + c.
-// STRIDE = W: consecutive threads take consecutive nodes.  STRIDE = W + 2, the row width of the region the
-// phase reads its stencil operands from: thread index i stands for row i / STRIDE and column i % STRIDE, and
-// the two columns past W idle.  A warp's operand reads then cover consecutive words of the source region;
-// with the compact order a warp that crosses a row boundary spans STRIDE + 2 words, so that two of its reads
-// fall in one shared-memory bank.  The wider order is taken only where it needs no more passes of the NT
-// threads than the compact one.
-template <int W, int H, int STRIDE, int NT, typename F>
-__device__ __forceinline__ void for_region(F&& f)
-{
-    constexpr int SW = (H * STRIDE + NT - 1) / NT == (H * W + NT - 1) / NT ? STRIDE : W;
-    for (int i = threadIdx.x; i < H * SW; i += NT) {
-        const int r = i / SW, c = i - r * SW;
-        if (SW != W && c >= W) continue;
-        f(r * W + c, r, c);
-    }
-}
-
 // i reduced into [0, n); i lies within a few periods of the domain
 __device__ __forceinline__ int wrap_near(int i, int n)
 {
@@ -96,7 +78,7 @@ template <typename C, typename P, int W, int H, int PW, int NT>
 __device__ __forceinline__ void pair_mu_div(const P* ph, const C* sX1, const C* sX2, const C* sY1, const C* sY2,
                                             int to, const Consts<C>& K0, bool model2, C T, C* s_mu, C* s_D)
 {
-    for_region<W, H, PW, NT>([&](int e, int r, int c) {
+    for_region<W, H, sizeof(C) == 4 ? PW : W, NT>([&](int e, int r, int c) {
         const P* q = ph + (r + 1) * PW + c + 1;
         const C ce = cvt<C>(q[0]);
         const C pE = cvt<C>(q[1]), pW = cvt<C>(q[-1]), pN = cvt<C>(q[PW]), pS = cvt<C>(q[-PW]);
@@ -119,7 +101,7 @@ __device__ __forceinline__ void pair_collide(const P* ph_reg, const C* s_mu, con
                                              const C* sX2, const C* sY1, const C* sY2, int tu, const Consts<C>& K0,
                                              bool model2, C T, C* s_post)
 {
-    for_region<W, H, MW, NT>([&](int e, int r, int c) {
+    for_region<W, H, sizeof(C) == 4 ? MW : W, NT>([&](int e, int r, int c) {
         const int m = (r + 1) * MW + (c + 1);
         C gmx, gmy, gDx = C(0), gDy = C(0);
         grad9(s_mu[m + 1], s_mu[m - 1], s_mu[m + MW], s_mu[m - MW], s_mu[m + MW + 1], s_mu[m + MW - 1],
@@ -275,7 +257,7 @@ __device__ __forceinline__ void pair_steps(const PairSmem<C, P, TX, TY>& S, cons
     pair_collide<C, P, L::W4, L::H4, L::W5, W6, NT, kShift>(S.phi0, S.mu, S.D, S.X1, S.X2, S.Y1, S.Y2, 2, K0, model2, T0,
                                                            S.post);
     __syncthreads();
-    for_region<W3, L::H3, L::W4, NT>([&](int e, int r, int c) {
+    for_region<W3, L::H3, sizeof(C) == 4 ? L::W4 : W3, NT>([&](int e, int r, int c) {
         C v0;
         const C sumq = pair_pull<C, W3, L::N4>(S.post, r, c, v0);
         float lo1;
@@ -291,7 +273,7 @@ __device__ __forceinline__ void pair_steps(const PairSmem<C, P, TX, TY>& S, cons
                                                            S.post);
     __syncthreads();
     const int nx = I.nx, ny = I.ny;
-    for_region<TX, TY, L::W1, NT>([&](int e, int r, int c) {
+    for_region<TX, TY, sizeof(C) == 4 ? L::W1 : TX, NT>([&](int e, int r, int c) {
         const int gx = x0 + c, gy = y0 + r;
         if (gx >= nx || gy >= ny) return;
         C v0;
