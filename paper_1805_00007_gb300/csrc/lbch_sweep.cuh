@@ -713,7 +713,9 @@ __global__ void __launch_bounds__(NW * 32, (sizeof(C) == 8 ? 8 : 12) / NW)
         if constexpr (GEN) {
             // steady state, one row per iteration with the slots rotated by register moves: the body with
             // the populations is large enough that three copies of it (the unrolled rotation below) cost
-            // more in instruction fetch than the moves do (measured: 54 against 49 GLUPS at 4096^2, FP32)
+            // more in instruction fetch than the moves do (measured: 54 against 49 GLUPS at 4096^2, FP32; again
+            // on a build with 7 % fewer instructions per update, 56.8 against 52.8, and 40.0 against 36.0 GLUPS
+            // on the ragged shear ensemble)
 #pragma unroll 1
             for (int j = 6; j < TY + 6; j++) {
                 row_step(Tr(), Tr(), Tr(), j, r0, r1, r2);
